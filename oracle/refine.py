@@ -1,0 +1,256 @@
+"""Forward-error-oriented Ogita-Aishima refinement, step by step (Alg. 1 + Sec. 3-4.1).
+
+ORACLE: test infrastructure only.
+
+One iteration (Algorithm 1 with the Sec. 3 modification, eq. mat_mul):
+  plan   beta from eq. proposed_beta in its Sec. 4.1 form (floor, n*delta, i.e.
+         xi = n), alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1), using the
+         previous eigenvalue estimates (the circularity is broken by lagging them);
+  X1     = fl((tau_j + x_ij) - tau_j), tau_j = 0.75 2^ceil(log2 w_j) 2^beta (eq. tau, x);
+  V      = accurate A X1 from exact 7-bit digit-plane products (line 1, eq. mat_mul);
+  r_i    = 1 - x1_i^T x1_i                                            (line 2);
+  lam_i  = x1_i^T v_i / (1 - r_i)                                     (line 3);
+  W      = X1^T (V - X1 diag(lam))                                    (line 4);
+  E~_ij  = w_ij / (lam_j - lam_i) (i != j), r_i / 2 (i = j)           (line 5);
+  X      <- RN(X1 + X1 E~) by pair arithmetic                         (line 6, Sec. 2.2).
+
+Readings where the paper is silent (each also listed in the design notes):
+* digit planes: 7-bit digits on a fixed grid (see ``ozaki``); X1 is exactly the
+  first s_X = ceil((54 - beta) / 7) planes' worth of bits, so V's products are
+  all exact and only the truncation of A to k_V planes (and of the pair set to
+  r + s <= k_V + 1) is approximate;
+* slice counts (the paper sweeps n_A by hand): k = smallest k with
+  (2^(7k - eL - eR - 6) tau)^2 >= n^3, i.e. 64 n^1.5 2^(eL+eR) 2^(-7k) <= tau,
+  where eL, eR are the operands' largest exponents and tau = delta * g for V and
+  W, delta for the update product;  a fixed k_V may be forced (``slices_A``);
+* beta is clamped to [3, 47] (tau-trick valid, X1 keeps at least one plane);
+* stopping test: ||E~|| cannot fall below ||X^(2)|| (every step re-corrects the
+  truncated tail), so the test uses the observed step d_k = ||X_k - X_{k-1}||_F:
+  est_k = d_k^2 * Lam / (xi_stop * g) with xi_stop = n (the Sec. 4.1 calibration
+  xi = n of the error model eq. assume2); converged when est_k <= delta;
+  'stagnated' when d_k > d_{k-1} / 2 for k >= 2 without convergence;
+* clusters (excluded by the paper): pairs with |lam_j - lam_i| <= omega take
+  e~_ij = r_ij / 2 with r_ij = -x1_i^T x1_j, the Ogita-Aishima rule; omega = 0 by
+  default (only equal estimates), or 'auto': omega = 2 (||W||_F + Lam ||diag R||_2).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import ddarith as dd
+from . import ozaki as oz
+
+U = 2.0 ** -53
+
+
+@dataclasses.dataclass
+class Options:
+    slices_A: int = 0            # 0: automatic k_V; >0: fixed number of A planes
+    xi: float | None = None      # None: xi = n (Sec. 4.1 "n delta"); else eq. proposed_beta's xi
+    beta_rounding: str = "floor"  # Sec. 4.1 floor; "ceil" = eq. proposed_beta
+    theory_alpha: bool = False   # alpha = ceil(53 + log2 n - beta) instead of Sec. 4.1
+    beta_override: int | None = None
+    k_cap: int = 16
+    max_iter: int = 10
+    xi_stop: float | None = None  # None: n
+    cluster: object = 0.0        # threshold omega (float) or "auto"
+
+
+def ceil_log2_sqrt(n: int) -> int:
+    """ceil(log2 sqrt n) for integer n >= 1, exactly."""
+    return ((n - 1).bit_length() + 1) // 2
+
+
+def ceil_log2_int(n: int) -> int:
+    return (n - 1).bit_length()
+
+
+def floor_log2(x: float) -> int:
+    fr, ex = math.frexp(x)
+    return ex - 1
+
+
+def ceil_log2f(x: float) -> int:
+    fr, ex = math.frexp(x)
+    return ex - 1 if fr == 0.5 else ex
+
+
+def min_gap(lam, omega=0.0):
+    """Smallest |lam_j - lam_i| over adjacent sorted estimates exceeding omega.
+
+    Returns (g, Lam); g = Lam if no gap exceeds omega (or n == 1).
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    Lam = float(np.max(np.abs(lam)))
+    s = np.sort(lam)
+    gaps = s[1:] - s[:-1]
+    gaps = gaps[gaps > omega]
+    g = float(np.min(gaps)) if gaps.size else Lam
+    return g, Lam
+
+
+def beta_rule(n, delta, g, Lam, S2, opts: Options) -> int:
+    """Sec. 4.1: beta = floor(log2((1/(0.75u)) sqrt(n delta g / (Lam sum_j 2^(2f_j)))))."""
+    if opts.beta_override is not None:
+        return int(opts.beta_override)
+    xi = float(n) if opts.xi is None else float(opts.xi)
+    if g <= 0.0 or Lam <= 0.0 or S2 <= 0.0:
+        return 3
+    q = math.sqrt((xi * delta * g) / (Lam * S2)) / (0.75 * U)
+    b = floor_log2(q) if opts.beta_rounding == "floor" else ceil_log2f(q)
+    return int(min(max(b, 3), 47))
+
+
+def alpha_rule(n, beta, opts: Options) -> int:
+    if opts.theory_alpha:
+        return 53 - beta + ceil_log2_int(n)
+    return 53 - beta + ceil_log2_sqrt(n)
+
+
+def slices_for(n, eL, eR, tau, k_cap):
+    """Smallest k >= 1 with (2^(7k - eL - eR - 6) * tau)^2 >= n^3, capped."""
+    if eL == oz.EZERO or eR == oz.EZERO:
+        return 0
+    n3 = float(n) ** 3
+    for k in range(1, k_cap + 1):
+        v = math.ldexp(tau, 7 * k - int(eL) - int(eR) - 6)
+        if v * v >= n3:
+            return k
+    return k_cap
+
+
+def sum_pow4(f):
+    """sum_j 2^(2 f_j) over nonzero columns, exactly rounded (math.fsum)."""
+    return math.fsum(math.ldexp(1.0, 2 * int(x)) for x in f if x != oz.EZERO)
+
+
+def plan(A, X, lam_prev, delta, opts: Options, omega_prev=0.0):
+    n = X.shape[0]
+    f = oz.col_exponents(X)
+    g, Lam = min_gap(lam_prev, omega_prev)
+    S2 = sum_pow4(f)
+    beta = beta_rule(n, delta, g, Lam, S2, opts)
+    alpha = alpha_rule(n, beta, opts)
+    sX = -(-(54 - beta) // 7)
+    eA = oz.row_exponents(A)
+    eAmax = int(np.max(eA))
+    fmax = int(np.max(f))
+    if opts.slices_A > 0:
+        kV = int(opts.slices_A)
+    else:
+        kV = slices_for(n, eAmax, fmax, delta * g, opts.k_cap)
+    return dict(n=n, f=f, g=g, Lam=Lam, S2=S2, beta=beta, alpha=alpha, sX=sX,
+                eA=eA, kV=kV)
+
+
+def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exact=False):
+    """One iteration. Returns (X_new, lam, info)."""
+    opts = opts or Options()
+    A = np.asarray(A, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    p = plan(A, X, lam_prev, delta, opts, omega_prev)
+    beta, sX, kV, f, eA = p["beta"], p["sX"], p["kV"], p["f"], p["eA"]
+
+    # X^(1) (eq. tau, eq. x) and V = A X^(1) (line 1, eq. mat_mul)
+    X1, _ = oz.tau_truncate_cols(X, beta, f)
+    V = oz.ozaki_product(A, X1, kV, sX, kV + 1, eL=eA, eR=f, exact=exact)
+    Vh, Vl = V["hi"], V["lo"]
+
+    # line 2: r_i = 1 - x_i^T x_i ; line 3: lam_i = x_i^T v_i / (1 - r_i)
+    ph, pl = dd.two_prod(X1, X1)
+    nh, nl = dd.dd_sum(ph, pl, axis=0)            # x_i^T x_i (double-double)
+    r = dd.dd_add_d(-nh, -nl, 1.0)[0]
+    qh, ql = dd.two_prod(X1, Vh)
+    ql = ql + X1 * Vl
+    dh, dl = dd.dd_sum(qh, ql, axis=0)            # x_i^T v_i
+    lam = dd.dd_div_dd(dh, dl, nh, nl)[0]
+
+    # line 4: Res = V - X1 diag(lam) (double-double, then FP64); W = X1^T Res
+    mh, ml = dd.two_prod(X1, lam[None, :])
+    Res = dd.dd_add(Vh, Vl, -mh, -ml)[0]
+    h = oz.col_exponents(Res)
+    g = p["g"]
+    kW = slices_for(n, int(np.max(f)), int(np.max(h)), delta * g, opts.k_cap)
+    if kW > 0:
+        Wp = oz.ozaki_product(X1.T, Res, min(sX, kW), kW, kW + 1, eL=f, eR=h, exact=exact)
+        W = Wp["hi"] + Wp["lo"]
+    else:
+        Wp = None
+        W = np.zeros((n, n))
+
+    # line 5: E~ with the optional cluster rule
+    if opts.cluster == "auto":
+        offd = W - np.diag(np.diag(W))
+        omega = 2.0 * (math.sqrt(float(np.sum(offd * offd))) + p["Lam"] * float(np.linalg.norm(r)))
+    else:
+        omega = float(opts.cluster)
+    diff = lam[None, :] - lam[:, None]            # lam_j - lam_i
+    clus = np.abs(diff) <= omega
+    np.fill_diagonal(clus, False)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        E = np.where(clus, 0.0, W / np.where(clus, 1.0, diff))
+    if np.any(clus):
+        ii, jj = np.nonzero(clus)
+        for i, j in zip(ii, jj):
+            th, tl = dd.two_prod(X1[:, i], X1[:, j])
+            sh, sl = dd.dd_sum(th, tl, axis=0)
+            E[i, j] = -sh / 2.0                       # r_ij / 2
+    np.fill_diagonal(E, r / 2.0)
+
+    # line 6: X <- accsum(X1, X1 E~): U = X1 E~ (rows of X1, columns of E~)
+    rho = oz.row_exponents(X1)
+    eta = oz.col_exponents(E)
+    kU = slices_for(n, int(np.max(rho)), int(np.max(eta)), delta, opts.k_cap)
+    if kU > 0:
+        Up = oz.ozaki_product(X1, E, kU, kU, kU + 1, eL=rho, eR=eta, exact=exact)
+        ch, cl = dd.pair_add(X1, Up["hi"], Up["lo"])
+        Xn = ch + cl
+    else:
+        Up = None
+        Xn = X1.copy()
+
+    normE = math.sqrt(float(np.sum(E * E)))
+    dX = Xn - X
+    step_norm = math.sqrt(float(np.sum(dX * dX)))
+    g_new, Lam_new = min_gap(lam, omega)
+    xs = float(n) if opts.xi_stop is None else float(opts.xi_stop)
+    est = step_norm * step_norm * Lam_new / (xs * g_new) if g_new > 0 else math.inf
+    info = dict(plan=p, beta=beta, alpha=p["alpha"], sX=sX, kV=kV, kW=kW, kU=kU,
+                products=len(V["pairs"]) + (len(Wp["pairs"]) if Wp else 0) + (len(Up["pairs"]) if Up else 0),
+                normE=normE, step=step_norm, est=est, omega=omega, r=r, W=W, E=E, X1=X1, Vh=Vh, Vl=Vl,
+                Res=Res, h=h, S_V=V["S"], clustered=int(np.sum(clus)) // 2)
+    return Xn, lam, info
+
+
+def refine(A, X, D, delta, opts: Options | None = None, exact=False, history=None):
+    """Iterate until the stopping test passes. Returns (X, lam, info)."""
+    opts = opts or Options()
+    if not (delta > U):
+        raise ValueError("delta must exceed the unit roundoff (Sec. 3.1)")
+    lam = np.asarray(D, dtype=np.float64)
+    prev_step = None
+    omega = 0.0
+    status = "max_iter"
+    total_products = 0
+    it = 0
+    est = math.inf
+    for it in range(1, opts.max_iter + 1):
+        X, lam, info = step(A, X, lam, delta, opts, omega, exact)
+        omega = info["omega"]
+        total_products += info["products"]
+        est = info["est"]
+        if history is not None:
+            history.append(dict(X=X.copy(), lam=lam.copy(), **{k: info[k] for k in
+                                ("beta", "alpha", "sX", "kV", "kW", "kU", "products", "normE", "step", "est")}))
+        if est <= delta:
+            status = "converged"
+            break
+        if prev_step is not None and info["step"] > 0.5 * prev_step:
+            status = "stagnated"
+            break
+        prev_step = info["step"]
+    return X, lam, dict(status=status, iters=it, err_est=est, products=total_products)

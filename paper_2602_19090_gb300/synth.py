@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs for the eigenvector-refinement workloads.
+
+This module builds test matrices and starting guesses only. It holds none of the
+refinement method's arithmetic (no slicing, no products of the method, no
+correction formula), so both the CPU oracle and the CUDA path can take their
+inputs from it without sharing any of the method's code.
+
+Workloads (stand-ins for MATLAB's ``gallery('randsvd', n, -cnd, 3, ...)`` used in
+Sec. 4, whose test matrices are symmetric with a geometric spectrum):
+
+* ``spectrum``: geometric eigenvalues lambda_i = cond^(-(n-1-i)/(n-1)), ascending
+  from 1/cond to 1; variants ``indefinite`` (seeded random signs) and
+  ``clustered`` (pairs lambda_{2m+1} = lambda_{2m}(1 + gap)).
+* ``householder_q``: Q = H_1 H_2 ... H_n with H_k = I - 2 v_k v_k^T / (v_k^T v_k)
+  and v_k ~ N(0, I), applied in blocks (compact WY form) for speed.
+* ``symmetric_matrix``: A = Q diag(lambda) Q^T in FP64, made exactly symmetric by
+  mirroring the upper triangle.
+* ``initial_guess``: X0 = Q + noise of 2-norm about ``rel``, re-orthonormalised
+  by a Householder QR in FP64 (column signs kept), D0 = lambda (1 + rel N(0,1)).
+* ``gemm_operand``: entries N(0,1) * exp(phi N(0,1)) (growing exponent spread).
+
+Seeds follow 2602190900 + 1000 * workload + case.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 2602190900
+
+
+def seed_for(workload: int, case: int = 0) -> int:
+    return SEED_BASE + 1000 * workload + case
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def spectrum(n: int, cond: float, variant: str = "spd", seed: int = 0,
+             cluster_pairs: int = 16, cluster_gap: float = 1e-10) -> np.ndarray:
+    """Ascending geometric spectrum from 1/cond to 1 (randsvd mode 3 shape)."""
+    if n == 1:
+        lam = np.ones(1)
+    else:
+        i = np.arange(n, dtype=np.float64)
+        lam = cond ** (-(n - 1 - i) / (n - 1))
+    if variant == "indefinite":
+        s = rng(seed + 7).integers(0, 2, size=n) * 2 - 1
+        lam = lam * s
+        lam = np.sort(lam)
+    elif variant == "clustered":
+        lam = lam.copy()
+        # spread the pairs over the spectrum: pair m uses indices (2m', 2m'+1)
+        m = min(cluster_pairs, n // 2)
+        starts = np.linspace(0, n - 2, m).astype(np.int64) // 2 * 2
+        for s0 in starts:
+            lam[s0 + 1] = lam[s0] * (1.0 + cluster_gap)
+        lam = np.sort(lam)
+    elif variant != "spd":
+        raise ValueError(f"unknown spectrum variant {variant!r}")
+    return lam
+
+
+def householder_q(n: int, seed: int, block: int = 64) -> np.ndarray:
+    """Q = H_1 H_2 ... H_n from Gaussian Householder vectors (FP64)."""
+    g = rng(seed)
+    V = g.standard_normal((n, n))
+    Q = np.eye(n)
+    for b0 in range(0, n, block):
+        Vb = V[:, b0:b0 + block]
+        nb = Vb.shape[1]
+        tau = 2.0 / np.einsum("ij,ij->j", Vb, Vb)
+        # H_1...H_b = I - Vb T Vb^T with T upper triangular (forward accumulation)
+        T = np.zeros((nb, nb))
+        for k in range(nb):
+            T[k, k] = tau[k]
+            if k:
+                T[:k, k] = -tau[k] * (T[:k, :k] @ (Vb[:, :k].T @ Vb[:, k]))
+        Q = Q - ((Q @ Vb) @ T) @ Vb.T
+    return Q
+
+
+def symmetric_matrix(n: int, cond: float, seed: int, variant: str = "spd", **kw):
+    """(A, Q, lam): exactly symmetric FP64 A close to Q diag(lam) Q^T."""
+    lam = spectrum(n, cond, variant, seed, **kw)
+    Q = householder_q(n, seed)
+    A = (Q * lam) @ Q.T
+    A = np.triu(A) + np.triu(A, 1).T
+    return np.ascontiguousarray(A), Q, lam
+
+
+def initial_guess(Q: np.ndarray, lam: np.ndarray, seed: int, rel: float = 1e-8):
+    """(X0, D0): perturbed and re-orthonormalised starting eigenpairs."""
+    n = Q.shape[0]
+    g = rng(seed + 1)
+    noise = g.standard_normal((n, n)) * (rel / (2.0 * np.sqrt(n)))
+    Y = Q + noise
+    Qr, R = np.linalg.qr(Y)
+    X0 = Qr * np.sign(np.diag(R))
+    D0 = lam * (1.0 + rel * g.standard_normal(n))
+    return np.ascontiguousarray(X0), D0
+
+
+def gemm_operand(m: int, n: int, phi: float, seed: int) -> np.ndarray:
+    g = rng(seed)
+    return g.standard_normal((m, n)) * np.exp(phi * g.standard_normal((m, n)))
+
+
+def workload0():
+    """n=64, cond 1e8 SPD, start perturbed by 1e-8, 8 planes of A, delta 1e-14."""
+    s = seed_for(0)
+    A, Q, lam = symmetric_matrix(64, 1e8, s)
+    X0, D0 = initial_guess(Q, lam, s)
+    return A, X0, D0
+
+
+def refine_workload(n: int, cond: float, variant: str = "spd", case: int = 0, rel: float = 1e-8):
+    """Full-refinement input: (A, X0, D0, lam)."""
+    s = seed_for(2, case)
+    A, Q, lam = symmetric_matrix(n, cond, s, variant)
+    X0, D0 = initial_guess(Q, lam, s, rel)
+    return A, X0, D0, lam
+
+
+def batched_sizes(count: int = 256, lo: int = 32, hi: int = 512, case: int = 0):
+    g = rng(seed_for(3, case))
+    n = g.integers(lo, hi + 1, size=count)
+    logc = g.uniform(2.0, 12.0, size=count)
+    return n, 10.0 ** logc

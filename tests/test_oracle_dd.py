@@ -1,0 +1,64 @@
+"""Pins for the double-double helpers (Sec. 2.2) against exact rational arithmetic."""
+from fractions import Fraction as F
+
+import numpy as np
+
+from oracle import ddarith as dd
+
+
+def _rand(g, n, spread=30):
+    return g.standard_normal(n) * np.exp2(g.integers(-spread, spread, n))
+
+
+def test_two_sum_exact():
+    g = np.random.default_rng(1)
+    a, b = _rand(g, 2000), _rand(g, 2000)
+    x, y = dd.two_sum(a, b)
+    for ai, bi, xi, yi in zip(a, b, x, y):
+        assert F(ai) + F(bi) == F(xi) + F(yi)
+        assert xi == ai + bi
+
+
+def test_two_prod_exact():
+    g = np.random.default_rng(2)
+    a, b = _rand(g, 2000), _rand(g, 2000)
+    p, e = dd.two_prod(a, b)
+    for ai, bi, pi, ei in zip(a, b, p, e):
+        assert F(ai) * F(bi) == F(pi) + F(ei)
+
+
+def test_pair_add_matches_definition():
+    # Sec. 2.2: [c_h, t] = TwoSum(a, b_h), c_l = fl(b_l + t); error only from the final add
+    g = np.random.default_rng(3)
+    a = g.standard_normal(500)
+    bh = g.standard_normal(500)
+    bl = bh * 2.0 ** -60 * g.standard_normal(500)
+    ch, cl = dd.pair_add(a, bh, bl)
+    for i in range(500):
+        exact = F(a[i]) + F(bh[i]) + F(bl[i])
+        err = abs(F(ch[i]) + F(cl[i]) - exact)
+        assert err <= abs(exact) * F(2) ** -100 + F(2) ** -1074
+
+
+def test_dd_matmul_against_fractions():
+    g = np.random.default_rng(4)
+    L = g.standard_normal((5, 7))
+    Ll = L * 2.0 ** -55 * g.standard_normal((5, 7))
+    R = g.standard_normal((7, 4))
+    h, l = dd.dd_matmul(L, Ll, R, None)
+    for i in range(5):
+        for j in range(4):
+            ex = sum(((F(L[i, k]) + F(Ll[i, k])) * F(R[k, j]) for k in range(7)), F(0))
+            mag = sum((abs(F(L[i, k]) * F(R[k, j])) for k in range(7)), F(0))
+            assert abs(F(h[i, j]) + F(l[i, j]) - ex) <= mag * F(2) ** -100
+
+
+def test_dd_div():
+    g = np.random.default_rng(5)
+    a = g.standard_normal(200)
+    b = 1.0 + 1e-3 * g.standard_normal(200)
+    bl = b * 2.0 ** -60
+    q = dd.dd_div_dd(a, np.zeros(200), b, bl)
+    for i in range(200):
+        ex = F(a[i]) / (F(b[i]) + F(bl[i]))
+        assert abs(F(q[0][i]) + F(q[1][i]) - ex) <= abs(ex) * F(2) ** -100

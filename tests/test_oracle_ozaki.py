@@ -1,0 +1,146 @@
+"""Pins for the Ozaki splitting and slice-product oracle (Sec. 2.3)."""
+import math
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+
+from oracle import ozaki as oz
+from paper_2602_19090_gb300 import synth
+
+U = F(1, 2 ** 53)
+
+
+def ufp(x):
+    return F(2) ** math.floor(math.log2(abs(x))) if x != 0 else F(0)
+
+
+def test_ceil_log2_exact():
+    g = np.random.default_rng(11)
+    m = np.abs(g.standard_normal(3000)) * np.exp2(g.integers(-300, 300, 3000))
+    m[:50] = np.exp2(np.arange(-25, 25))          # exact powers of two
+    e = oz.ceil_log2(m)
+    for mi, ei in zip(m, e):
+        assert F(2) ** (int(ei) - 1) < F(mi) <= F(2) ** int(ei)
+    assert oz.ceil_log2(np.array([0.0]))[0] == oz.EZERO
+
+
+@pytest.mark.parametrize("phi", [0.5, 2.0, 4.0])
+def test_slices_round_trip_digits_and_residual_bound(phi):
+    M = synth.gemm_operand(9, 23, phi, 7)
+    M[3, :] = 0.0                                  # zero row: sigma = 0 (eq. sigma)
+    k = 6
+    d, e, res = oz.slice_rows(M, k)
+    assert np.all(np.abs(d) <= 64)
+    assert np.all(d[:, 3, :] == 0)
+    for i in range(M.shape[0]):
+        for j in range(M.shape[1]):
+            acc = F(0)
+            for r in range(1, k + 1):
+                if e[i] != oz.EZERO:
+                    acc += d[r - 1, i, j] * F(2) ** int(e[i] + 1 - 7 * r)
+            assert acc + F(res[i, j]) == F(M[i, j])              # exact split
+            if e[i] != oz.EZERO:
+                assert abs(F(res[i, j])) <= F(2) ** int(e[i] - 7 * k)   # |res_k| <= w_k / 2
+
+
+def test_digit_rule_is_the_sigma_trick():
+    # eq. a: a^(r) = fl((sigma + a_res) - sigma) with ulp(sigma) = w_r gives the same slice
+    M = synth.gemm_operand(16, 40, 2.0, 8)
+    d, e, _ = oz.slice_rows(M, 7)
+    res = M.copy()
+    for r in range(1, 8):
+        w = np.ldexp(1.0, e + 1 - 7 * r)[:, None]
+        sl = oz.sigma_trick_slice(res, e, r)
+        assert np.array_equal(d[r - 1] * w, sl)
+        res = res - sl
+
+
+def test_ties_go_to_even_digit():
+    # e = 0 (max 1.0): w_1 = 2^-6; 2.5 w_1 -> digit 2, 3.5 w_1 -> 4
+    x = np.array([[1.0, 2.5 * 2.0 ** -6, 3.5 * 2.0 ** -6, -2.5 * 2.0 ** -6]])
+    d, e, _ = oz.slice_rows(x, 1)
+    assert e[0] == 0
+    assert list(d[0, 0]) == [64, 2, 4, -2]
+
+
+@pytest.mark.parametrize("beta", [3, 10, 17, 30, 47])
+def test_tau_truncation(beta):
+    X = synth.gemm_operand(30, 12, 1.0, 9)
+    X1, f = oz.tau_truncate_cols(X, beta)
+    for j in range(X.shape[1]):
+        tau = F(3, 4) * F(2) ** int(f[j] + beta)
+        grid = F(2) ** int(f[j] + beta - 53)          # ulp(tau)
+        for i in range(X.shape[0]):
+            x1 = F(X1[i, j])
+            assert (x1 / grid).denominator == 1
+            assert abs(F(X[i, j]) - x1) <= U * ufp(tau)   # eq. minamihata
+            q = F(X[i, j]) / grid                          # round to nearest, ties to even
+            fl = math.floor(q)
+            rnd = fl + (1 if (q - fl > F(1, 2) or (q - fl == F(1, 2) and fl % 2)) else 0)
+            assert x1 == rnd * grid
+
+
+def test_slice_products_brute_force():
+    g = np.random.default_rng(12)
+    dL = g.integers(-64, 65, (3, 4, 6))
+    dR = g.integers(-64, 65, (3, 6, 5))
+    pairs = oz.pair_set(3, 3, 4)
+    S = oz.slice_products(dL, dR, pairs)
+    assert set(S) == {2, 3, 4}
+    for t, St in S.items():
+        for i in range(4):
+            for j in range(5):
+                ref = 0
+                for (r, s) in pairs:
+                    if r + s == t:
+                        ref += sum(int(dL[r - 1, i, k]) * int(dR[s - 1, k, j]) for k in range(6))
+                assert St[i, j] == ref
+
+
+def _exact_product(A, B):
+    m, K = A.shape
+    n = B.shape[1]
+    return [[sum((F(A[i, k]) * F(B[k, j]) for k in range(K)), F(0)) for j in range(n)] for i in range(m)]
+
+
+def test_ozaki_gemm_enough_slices_is_correctly_rounded():
+    A = synth.gemm_operand(6, 9, 0.5, 21)
+    B = synth.gemm_operand(9, 5, 0.5, 22)
+    # exponent spread is small; 12 planes (84 bits) capture both operands exactly
+    _, eA, resA = oz.slice_rows(A, 12)
+    _, eB, resB = oz.slice_cols(B, 12)
+    assert np.all(resA == 0) and np.all(resB == 0)
+    C, out = oz.ozaki_gemm(A, B, 12, "full", exact=True)
+    ex = _exact_product(A, B)
+    for i in range(6):
+        for j in range(5):
+            assert C[i, j] == float(ex[i][j])           # RN of the exact product
+            assert F(out["hi"][i, j]) + F(out["lo"][i, j]) - ex[i][j] <= abs(ex[i][j]) * F(2) ** -104
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 6])
+def test_triangular_truncation_bound(k):
+    A = synth.gemm_operand(7, 11, 2.0, 31)
+    B = synth.gemm_operand(11, 6, 2.0, 32)
+    C, out = oz.ozaki_gemm(A, B, k, "triangular", exact=True)
+    assert len(out["pairs"]) == k * (k + 1) // 2
+    ex = _exact_product(A, B)
+    eA, eB = out["eL"], out["eR"]
+    K = A.shape[1]
+    for i in range(7):
+        for j in range(6):
+            bound = (k + 1) * K * F(2) ** int(eA[i] + eB[j] - 7 * k)
+            assert abs(F(out["hi"][i, j]) + F(out["lo"][i, j]) - ex[i][j]) <= bound
+
+
+def test_recombine_dd_matches_exact():
+    A = synth.gemm_operand(20, 30, 4.0, 41)
+    B = synth.gemm_operand(30, 10, 4.0, 42)
+    _, o1 = oz.ozaki_gemm(A, B, 10, "full", exact=True)
+    _, o2 = oz.ozaki_gemm(A, B, 10, "full", exact=False)
+    for t in o1["S"]:
+        assert np.array_equal(o1["S"][t], o2["S"][t])
+    mag = np.abs(A) @ np.abs(B)
+    diff = np.abs((o1["hi"] - o2["hi"]) + (o1["lo"] - o2["lo"]))
+    assert np.all(diff <= mag * 2.0 ** -100)

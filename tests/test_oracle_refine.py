@@ -1,0 +1,197 @@
+"""Pins for the refinement oracle (Alg. 1, Sec. 3, Sec. 4.1) and the ground truth."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ddarith as dd
+from oracle import ozaki as oz
+from oracle import refine as rf
+from oracle import truth as tr
+from paper_2602_19090_gb300 import synth
+
+U = 2.0 ** -53
+
+
+def test_beta_alpha_worked_example():
+    # Sec. 4.1 rule worked by hand: n = 4096, delta = 1e-14, min gap 2.25e-7, max|lam| = 1,
+    # every column maximum in (2^-4, 2^-3] so sum_j 2^(2 f_j) = 4096 * 2^-6 = 64.
+    # 4096 * 1e-14 * 2.25e-7 / 64 = 1.44e-19; sqrt = 3.795e-10; / (0.75 * 2^-53) = 4.557e6;
+    # log2 = 22.12 -> beta = 22 (floor), 23 (ceil);  alpha = 53 - 22 + ceil(log2 64) = 37
+    # (theory: 53 - 22 + log2 4096 = 43);  X^(1) keeps bits 2^f ... 2^(f+22-53):
+    # 32 bit positions -> ceil(32 / 7) = 5 planes.
+    o = rf.Options()
+    assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, o) == 22
+    assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, rf.Options(beta_rounding="ceil")) == 23
+    assert rf.alpha_rule(4096, 22, o) == 37
+    assert rf.alpha_rule(4096, 22, rf.Options(theory_alpha=True)) == 43
+    X = np.full((4096, 3), 0.07)
+    p = rf.plan(np.eye(3), X[:3], np.array([0.0, 2.25e-7, 1.0]), 1e-14, o)
+    assert p["f"].tolist() == [-3, -3, -3]
+    assert -(-(54 - 22) // 7) == 5
+
+
+def test_ceil_log2_sqrt_exact():
+    for n in range(1, 70000):
+        c = rf.ceil_log2_sqrt(n)
+        assert 4 ** (c - 1) < n <= 4 ** c or (n == 1 and c == 0)
+
+
+def test_slice_rule_definition():
+    for n in (64, 300, 4096):
+        for eL, eR in ((0, -3), (-2, -30), (1, 1)):
+            for tau in (1e-22, 3.4e-23, 1e-14):
+                k = rf.slices_for(n, eL, eR, tau, 40)
+                assert 64 * n ** 1.5 * 2.0 ** (eL + eR - 7 * k) <= tau * (1 + 1e-12)
+                if k > 1:
+                    assert 64 * n ** 1.5 * 2.0 ** (eL + eR - 7 * (k - 1)) > tau * (1 - 1e-12)
+
+
+def test_w_identity():
+    # For i != j, w_ij = s_ij + lam_j r_ij with S = X^T A X, R = I - X^T X (Sec. 2.4).
+    A, X0, D0 = synth.workload0()
+    delta = 1e-14
+    Xn, lam, info = rf.step(A, X0, D0, delta, rf.Options())
+    X1 = info["X1"]
+    Vh, Vl = dd.dd_matmul(A, None, X1, None)
+    Sh, Sl = dd.dd_matmul(X1.T, None, Vh, Vl)
+    Gh, Gl = dd.dd_matmul(X1.T, None, X1, None)
+    ph, pl = dd.two_prod(-Gh, lam[None, :])
+    pl = pl - Gl * lam[None, :]
+    rh, rl = dd.dd_add(Sh, Sl, ph, pl)                 # s_ij - (X^T X)_ij lam_j
+    ref = rh + rl
+    off = ~np.eye(64, dtype=bool)
+    err = np.abs(info["W"] - ref)[off]
+    g = info["plan"]["g"]
+    assert np.sqrt(np.sum(err ** 2)) <= delta * g / 4
+
+
+def test_diagonal_matrix_fixed_point():
+    d = np.array([1.0, -3.0, 0.5, 2.0, 7.0, -0.25])
+    A = np.diag(d)
+    X = np.eye(6)
+    Xn, lam, info = rf.step(A, X, d * (1 + 1e-9), 1e-14, rf.Options())
+    assert np.array_equal(Xn, X)
+    assert np.array_equal(lam, d)
+    assert np.all(info["E"] == 0.0)
+
+
+def test_reduces_to_classic_ogita_aishima():
+    # With X already on the tau grid X^(1) = X, and one step equals the R/S form.
+    A, Q, lam = synth.symmetric_matrix(24, 10.0, 77)
+    X0, D0 = synth.initial_guess(Q, lam, 77, 1e-6)
+    X0 = np.round(X0 * 2.0 ** 28) / 2.0 ** 28
+    opts = rf.Options(beta_override=3)
+    X1, _ = oz.tau_truncate_cols(X0, 3)
+    assert np.array_equal(X1, X0)
+    Xn, lam_o, _ = rf.step(A, X0, D0, 1e-15, opts)
+    Th, Tl, lam_t, _ = tr.eigvecs_dd(A, X0, max_iter=1)
+    assert np.max(np.abs(Xn - (Th + Tl))) <= 4 * U
+    assert np.max(np.abs(lam_o - lam_t)) <= 4 * U * np.max(np.abs(lam_t))
+
+
+def _well_separated(n=16, rel=1e-6, seed=5):
+    A, Q, lam = synth.symmetric_matrix(n, 10.0, seed)
+    X0, D0 = synth.initial_guess(Q, lam, seed, rel)
+    Xh, Xl, lam_t, _ = tr.eigvecs_dd(A, X0)
+    return A, X0, D0, Xh, Xl, lam_t
+
+
+def test_theorem1_bound():
+    A, X0, D0, Xh, Xl, lam_t = _well_separated()
+    n = A.shape[0]
+    Xn, lam, info = rf.step(A, X0, D0, 1e-15, rf.Options())
+    X1 = info["X1"]
+    E = np.linalg.solve(X1, Xh + Xl) - np.eye(n)       # X = X^(1) (I + E), eq. E'
+    eps = np.linalg.norm(E, 2)
+    normA = np.max(np.abs(lam_t))
+    gap = np.min(np.diff(np.sort(lam_t)))
+    assert eps < min(gap / (10 * math.sqrt(n) * normA), 0.01)      # eq. assume1
+    bound = 6.4 * math.sqrt(n) * normA * eps ** 2 / (gap - 14 * normA * eps)
+    assert np.linalg.norm(E - info["E"], 2) <= bound
+
+
+def test_quadratic_convergence():
+    A, X0, D0, Xh, Xl, lam_t = _well_separated(rel=1e-4, seed=6)
+    n = A.shape[0]
+    normA = np.max(np.abs(lam_t))
+    gap = np.min(np.diff(np.sort(lam_t)))
+    hist = []
+    rf.refine(A, X0, D0, 1e-15, rf.Options(max_iter=4), history=hist)
+    fe = [tr.forward_error(Xh, Xl, X0)] + [tr.forward_error(Xh, Xl, h["X"]) for h in hist]
+    assert fe[1] < 1e-6 and fe[2] < 1e-13
+    for a, b in zip(fe[:-1], fe[1:]):
+        assert b <= 6.4 * math.sqrt(n) * normA * a * a / (gap - 14 * normA * a) + 8 * U * math.sqrt(n)
+
+
+def test_workload0_reaches_delta():
+    A, X0, D0 = synth.workload0()
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    X, lam, info = rf.refine(A, X0, D0, 1e-14, rf.Options())
+    assert info["status"] == "converged" and info["iters"] <= 4
+    assert tr.forward_error(Xh, Xl, X) <= 1e-14
+
+
+def test_workload0_fixed_eight_planes_floor():
+    # 8 planes of A (56 bits) cannot resolve gaps of 3.4e-9 to 1e-14: the error stalls
+    # near 2^-56 / gap and the stopping test reports stagnation rather than convergence.
+    A, X0, D0 = synth.workload0()
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    X, lam, info = rf.refine(A, X0, D0, 1e-14, rf.Options(slices_A=8, max_iter=3))
+    fe = tr.forward_error(Xh, Xl, X)
+    assert info["status"] != "converged"
+    assert 1e-10 < fe < 1e-8
+
+
+def test_delta_must_exceed_u():
+    A, X0, D0 = synth.workload0()
+    with pytest.raises(ValueError):
+        rf.refine(A, X0, D0, U, rf.Options())
+
+
+def test_clusters_auto_rule_subspaces():
+    n = 32
+    A, Q, lam = synth.symmetric_matrix(n, 1e2, 5, "clustered", cluster_pairs=2, cluster_gap=1e-10)
+    X0, D0 = synth.initial_guess(Q, lam, 5, 1e-8)
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    X, l, info = rf.refine(A, X0, D0, 1e-12, rf.Options(cluster="auto"))
+    assert info["status"] == "converged"
+    ci = np.nonzero(np.diff(np.sort(lam)) < 1e-9)[0]
+    assert len(ci) == 2
+    mask = np.ones(n, bool)
+    for i in ci:
+        assert tr.subspace_error(Xh, Xl, X, [i, i + 1]) <= 1e-12
+        mask[i] = mask[i + 1] = False
+    assert tr.forward_error(Xh[:, mask], Xl[:, mask], X[:, mask]) <= 1e-12
+
+
+def test_truth_against_mpmath():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    A, Q, lam = synth.symmetric_matrix(10, 1e3, 3)
+    X0, _ = synth.initial_guess(Q, lam, 3, 1e-8)
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    E, V = mpmath.eigsy(mpmath.matrix(A.tolist()))
+    order = np.argsort([float(E[i]) for i in range(10)])
+    Vh = np.array([[float(V[i, j]) for j in order] for i in range(10)])
+    Vl = np.array([[float(V[i, j] - mpmath.mpf(float(V[i, j]))) for j in order] for i in range(10)])
+    s = np.sign(np.sum(Vh * Xh, 0))
+    assert np.max(np.abs((Xh - Vh * s) + (Xl - Vl * s))) <= 1e-28
+
+
+def test_golden_workload0_regression():
+    # tests/golden/workload0_oracle.json is written by tests/golden/make_golden.py (oracle only)
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "workload0_oracle.json")
+    gold = json.load(open(path))
+    A, X0, D0 = synth.workload0()
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    hist = []
+    _, _, info = rf.refine(A, X0, D0, 1e-14, rf.Options(), history=hist)
+    assert info["status"] == gold["auto"]["status"] and info["iters"] == gold["auto"]["iters"]
+    for h, gs in zip(hist, gold["auto"]["steps"]):
+        for key in ("beta", "alpha", "sX", "kV", "kW", "kU", "products"):
+            assert h[key] == gs[key]
+        fe = tr.forward_error(Xh, Xl, h["X"])
+        assert abs(fe - gs["forward_error"]) <= 1e-3 * gs["forward_error"] + 1e-16
