@@ -1,0 +1,196 @@
+/*
+ * frx: forward-error-oriented eigenvector refinement with Ozaki-scheme products
+ * on GB300 (sm_103a).  C ABI.
+ *
+ * Method: Terao & Ozaki, "Forward Error-Oriented Iterative Refinement for
+ * Eigenvectors of a Real Symmetric Matrix": Algorithm 1 (Ogita-Aishima step) with
+ * the Sec. 3 modification (X^ is replaced by its beta-truncated first slice X^(1),
+ * eq. tau / eq. x, and A X^(1) is formed by n_A error-free slice products,
+ * eq. mat_mul) and the Sec. 4.1 choice of alpha and beta.  The error-free slices
+ * of Sec. 2.3 (eq. sigma, eq. a) are taken on a fixed 7-bit digit grid so that
+ * every slice is an integer digit in [-64, 64]: slice r of a row (or column) whose
+ * maximum magnitude v satisfies 2^(e-1) < v <= 2^e has weight 2^(e + 1 - 7r).
+ * Slice products run on the tensor cores with exact integer accumulation and are
+ * recombined in double-double.
+ *
+ * Conventions for every call below:
+ *  - Matrices are FP64, column-major, with a leading dimension ld >= rows
+ *    (element (i, j) at p[i + j * ld]).  All matrix and vector pointers are
+ *    DEVICE pointers unless a parameter says "host".
+ *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default stream).
+ *    Work is enqueued on it; calls that return information to the host
+ *    (frx_refine's info, the status word) synchronise that stream.
+ *  - `work` is caller-owned device scratch of at least the bytes the matching
+ *    *_workspace_bytes call returns, 256-byte aligned.  The library allocates no
+ *    device memory.  Scratch contents are undefined after a call.
+ *  - The caller owns every buffer.  The library keeps no pointer after a call.
+ *  - Return value: an frx_status.  Negative values are hard errors; outputs are
+ *    then unspecified.  No C++ exception crosses this boundary.
+ */
+#ifndef FRX_H
+#define FRX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FRX_API __attribute__((visibility("default")))
+#else
+#define FRX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FRX_OK = 0,              /* converged: error estimate <= delta                       */
+  FRX_MAX_ITER = 1,        /* soft: max_iter reached, info->err_est filled              */
+  FRX_STAGNATED = 2,       /* soft: the step stopped halving before convergence          */
+  FRX_E_ARG = -1,          /* bad size, leading dimension, pointer, option or alignment   */
+  FRX_E_NONFINITE = -2,    /* an input entry is Inf or NaN                                */
+  FRX_E_DELTA = -3,        /* delta <= u = 2^-53 (Sec. 3.1 requires delta > u)            */
+  FRX_E_CUDA = -4,         /* a CUDA runtime call or kernel launch failed                  */
+  FRX_E_WORKSPACE = -5,    /* work is NULL, misaligned or smaller than required            */
+  FRX_E_TIMEOUT = -6,      /* a bounded device-side wait gave up                           */
+  FRX_E_UNSUPPORTED = -7,  /* size outside the supported range                            */
+  FRX_E_RANGE = -8         /* exponent range too wide for the fixed digit grid            */
+} frx_status;
+
+/* Product set of an Ozaki product: all (r, s) with r <= kL, s <= kR. */
+#define FRX_MODE_FULL 0
+/* Triangular set r + s <= k + 1: k(k+1)/2 products (cited after eq. alp_beta). */
+#define FRX_MODE_TRIANGULAR 1
+
+/* Options of frx_refine.  Fill with frx_default_opts, then override. */
+typedef struct {
+  int slices_A;          /* 0: automatic number of A slices k_V; > 0: fixed (e.g. 8)        */
+  double xi;             /* <= 0: xi = n, the Sec. 4.1 "n delta" form; > 0: eq. proposed_beta */
+  int beta_ceil;         /* 0: floor (Sec. 4.1); 1: ceil (eq. proposed_beta)                  */
+  int theory_alpha;      /* 0: alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1);
+                            1: alpha = 53 - beta + ceil(log2 n) (eq. proposed_beta)           */
+  int beta_override;     /* < 0: use the rule; else a fixed beta (clamped to [3, 47])          */
+  int k_cap;             /* largest number of digit planes per operand, 1..16                  */
+  int max_iter;          /* iteration limit (>= 1)                                           */
+  double xi_stop;        /* <= 0: n.  Stop when step^2 * max|lam| / (xi_stop * gap) <= delta  */
+  double cluster_omega;  /* >= 0: |lam_j - lam_i| <= omega is a cluster pair (0: only equal
+                            estimates); < 0: Ogita-Aishima threshold
+                            2 (||W||_F + max|lam| ||diag R||_2) each iteration              */
+} frx_opts;
+
+/* Per-call report of frx_refine (host struct). */
+typedef struct {
+  int status;            /* same as the return value                                      */
+  int iters;             /* iterations performed                                          */
+  int beta, alpha;       /* last iteration's beta (eq. tau) and alpha (Sec. 4.1)           */
+  int s_X;               /* digit planes of X^(1) = ceil((54 - beta) / 7)                 */
+  int k_V, k_W, k_U;     /* slice counts of the three products of the last iteration      */
+  long long products;    /* slice-pair products executed over all iterations              */
+  double err_est;        /* est = step^2 * max|lam| / (xi_stop * gap), last iteration      */
+  double step;           /* ||X_k - X_{k-1}||_F of the last iteration                      */
+  double min_gap;        /* smallest gap of the final eigenvalue estimates (clusters excluded) */
+  double max_lambda;     /* max |lam| of the final estimates                              */
+  double omega;          /* cluster threshold used in the last iteration                  */
+  int clustered_pairs;   /* cluster pairs treated by the r_ij / 2 rule in the last iteration */
+} frx_info;
+
+/* Default options: automatic slices, Sec. 4.1 rule, k_cap 16, max_iter 10. */
+FRX_API void frx_default_opts(frx_opts* opts);
+
+/* Text for a status code (static storage). */
+FRX_API const char* frx_status_string(int status);
+
+/* Scratch bytes frx_refine needs for order n (independent of the options' values
+ * except k_cap).  Returns 0 for n outside [1, FRX_MAX_N]. */
+FRX_API size_t frx_refine_workspace_bytes(int64_t n, const frx_opts* opts);
+
+#define FRX_MAX_N 12288
+
+/*
+ * Refine approximate eigenpairs of the symmetric matrix A (n x n) until the
+ * forward-error estimate reaches delta (Algorithm 1 iterated, Sec. 3 and 4.1).
+ *   A     (in)      n x n, lda >= n.  Must be exactly symmetric; both triangles are read.
+ *   X     (in/out)  n x n, ldx >= n: approximate eigenvectors X^ on entry, refined X^ on
+ *                   exit (the column order and signs are kept).
+ *   D     (in/out)  n: eigenvalue estimates; on entry they set the first iteration's
+ *                   beta and slice counts (the estimates of iteration k-1 are used in
+ *                   iteration k); on exit the estimates lam_i = x_i^T v_i / (1 - r_i)
+ *                   of the last iteration (Alg. 1 line 3).
+ *   delta (in)      target forward error, delta > 2^-53.
+ *   opts  (in,host) options, or NULL for the defaults.
+ *   info  (out,host) may be NULL.
+ * Errors: FRX_E_ARG, FRX_E_DELTA, FRX_E_NONFINITE, FRX_E_WORKSPACE, FRX_E_UNSUPPORTED
+ * (n > FRX_MAX_N), FRX_E_RANGE, FRX_E_CUDA.  Synchronises `stream` several times per
+ * iteration (the plan of each iteration is computed on the host).
+ */
+FRX_API int frx_refine(const double* A, int64_t lda, double* X, int64_t ldx, double* D, int64_t n,
+               double delta, const frx_opts* opts, void* work, size_t work_bytes,
+               frx_info* info, void* stream);
+
+/*
+ * One iteration of Algorithm 1 (Sec. 3 form) with optional copies of its
+ * intermediates, for inspection and testing.  Same arguments as frx_refine;
+ * `D` holds the previous estimates on entry and the new ones on exit; `omega_prev`
+ * is the cluster threshold of the previous iteration (0 on the first).  Each
+ * optional output (NULL to skip) is an n x n column-major FP64 matrix with ld = n:
+ *   X1  the truncated slice X^(1) (eq. tau, eq. x)
+ *   Vh, Vl  V = A X^(1) as a double-double (Alg. 1 line 1, eq. mat_mul)
+ *   Res     V - X^(1) diag(lam), rounded to FP64 (inside line 4)
+ *   W       X^(1)^T Res (line 4)
+ *   E       the correction E~ (line 5)
+ * `r_out` (n, device, optional) receives r_i = 1 - x_i^T x_i (line 2).
+ * info->err_est/step refer to this single step.
+ */
+FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx, double* D, int64_t n,
+                    double delta, const frx_opts* opts, double omega_prev,
+                    void* work, size_t work_bytes, frx_info* info,
+                    double* X1, double* Vh, double* Vl, double* Res, double* W, double* E,
+                    double* r_out, void* stream);
+
+/* Scratch bytes of frx_ozaki_gemm for these sizes and k. */
+FRX_API size_t frx_ozaki_gemm_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices);
+
+/*
+ * C = A B by the Ozaki scheme (Sec. 2.3): A (m x k) is split by rows and B (k x n)
+ * by columns into `slices` digit planes each (eq. sigma/tau, eq. a/x on the fixed
+ * 7-bit grid); the products of the selected plane pairs (FRX_MODE_FULL: all
+ * slices^2; FRX_MODE_TRIANGULAR: r + s <= slices + 1) are exact integer matrices,
+ * recombined exactly per anti-diagonal and rounded: C = RN(C_hi + C_lo).
+ *   C_lo (out, optional) receives the low word of the double-double result
+ *   (ld = ldc).  When the planes hold A and B exactly and mode is FULL, C_hi + C_lo
+ *   equals the exact product to about 2^-104 relative.
+ * slices in [1, 16]; m, n, k in [1, 2^20] with k <= 65536; A, B finite.
+ */
+FRX_API int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_t ldb,
+                   double* C, int64_t ldc, double* C_lo, int64_t m, int64_t n, int64_t k,
+                   int slices, int mode, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Digit planes of the slice products, for bit-exact checks of the integer path.
+ *   frx_exponents: e[i] = ceil(log2 max |row i|) (axis 0) or of column j (axis 1) of an
+ *     rows x cols matrix; -2^30 for an all-zero line.  Returns FRX_E_NONFINITE on Inf/NaN.
+ *     Needs frx_exponents_workspace_bytes(rows) bytes of scratch; synchronises `stream`.
+ *   frx_slice_planes: bfloat16 digit planes (as uint16 bit patterns) of the matrix,
+ *     split by rows (axis 0) or columns (axis 1) with the exponents e; plane r is
+ *     stored at planes + r * plane_stride as `lines x pitch` (line = row for axis 0,
+ *     column for axis 1; pitch >= the other dimension, multiple of 8; the pad is zero).
+ *   frx_plane_products: the exact anti-diagonal sums of the slice products grouped
+ *     into int64 words: out[g * n * m + j * m + i] = sum over t in group g of
+ *     2^(7 (t_last(g) - t)) * sum_{r + s = t, r <= kL, s <= kR, t <= T} (L_r R_s)_ij,
+ *     groups of `frx_group_size(...)` consecutive t starting at t = 2.
+ */
+FRX_API size_t frx_exponents_workspace_bytes(int64_t rows);
+FRX_API int frx_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int axis,
+                  int32_t* e, void* work, size_t work_bytes, void* stream);
+FRX_API int frx_slice_planes(const double* M, int64_t ld, int64_t rows, int64_t cols, int axis,
+                     const int32_t* e, int k, uint16_t* planes, int64_t plane_stride,
+                     int64_t pitch, void* stream);
+FRX_API int frx_group_size(int kL, int kR, int T, int64_t K);
+FRX_API int frx_plane_products(const uint16_t* L, int64_t L_plane_stride, const uint16_t* R,
+                       int64_t R_plane_stride, int64_t pitch, int64_t m, int64_t n, int64_t K,
+                       int kL, int kR, int T, int64_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRX_H */

@@ -1,0 +1,160 @@
+// Exact digit-plane products on the CUDA cores (dp4a), grouped by anti-diagonal.
+// Sec. 2.3: every slice product A^(r) X^(s) is exact; here the slices are 7-bit
+// integer digits, so the products are exact integer matrices (int32 per pair,
+// int64 per anti-diagonal group).  Used for small problems and as the
+// cross-check of the tensor-core path.
+#include "frx_internal.cuh"
+#include "kernels.cuh"
+
+namespace frx {
+
+int pairs_in(int kL, int kR, int T) {
+  int c = 0;
+  for (int r = 1; r <= kL; ++r)
+    for (int s = 1; s <= kR; ++s)
+      if (r + s <= T) ++c;
+  return c;
+}
+
+int plan_plane_gemm(PlaneGemm& g) {
+  g.tmax = g.T < g.kL + g.kR ? g.T : g.kL + g.kR;
+  if (g.kL <= 0 || g.kR <= 0 || g.tmax < 2) {
+    g.groups = 0;
+    g.gs = 1;
+    return FRX_OK;
+  }
+  if (g.K >= (1 << 19)) return FRX_E_UNSUPPORTED;
+  int pmax = 0;
+  for (int t = 2; t <= g.tmax; ++t) {
+    int lo = t - g.kR > 1 ? t - g.kR : 1;
+    int hi = g.kL < t - 1 ? g.kL : t - 1;
+    int c = hi - lo + 1;
+    pmax = c > pmax ? c : pmax;
+  }
+  unsigned long long smax = (unsigned long long)pmax * (unsigned long long)g.K * 4096ull;
+  int bs = 64 - __builtin_clzll(smax);  // smax < 2^bs
+  if (bs > 61) return FRX_E_UNSUPPORTED;
+  g.gs = (61 - bs) / 7 + 1;
+  g.groups = (g.tmax - 1 + g.gs - 1) / g.gs;
+  if (g.groups > 8) return FRX_E_UNSUPPORTED;
+  return FRX_OK;
+}
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32;
+
+__device__ __forceinline__ int bf16_digit(unsigned short b) {
+  return (int)__uint_as_float((unsigned)b << 16);
+}
+
+// 8 bf16 digits -> two int8x4 words
+__device__ __forceinline__ void pack8(uint4 v, int& w0, int& w1) {
+  unsigned short h[8];
+  memcpy(h, &v, 16);
+  int d[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = bf16_digit(h[i]) & 0xff;
+  w0 = d[0] | (d[1] << 8) | (d[2] << 16) | (d[3] << 24);
+  w1 = d[4] | (d[5] << 8) | (d[6] << 16) | (d[7] << 24);
+}
+
+__global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
+  __shared__ __align__(16) int As[BK / 4][BM];
+  __shared__ __align__(16) int Bs[BK / 4][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  const int lrow = tid >> 2, lk = (tid & 3) * 8;
+  const int64_t Kloop = (g.K + BK - 1) / BK * BK;
+  const unsigned short* L = reinterpret_cast<const unsigned short*>(g.L);
+  const unsigned short* R = reinterpret_cast<const unsigned short*>(g.R);
+
+  for (int grp = 0; grp < g.groups; ++grp) {
+    const int t0 = 2 + grp * g.gs;
+    const int t1 = t0 + g.gs - 1 < g.tmax ? t0 + g.gs - 1 : g.tmax;
+    i64 racc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) racc[a][b] = 0;
+    for (int t = t0; t <= t1; ++t) {
+      i64 tacc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tacc[a][b] = 0;
+      const int rlo = t - g.kR > 1 ? t - g.kR : 1;
+      const int rhi = g.kL < t - 1 ? g.kL : t - 1;
+      for (int r = rlo; r <= rhi; ++r) {
+        const unsigned short* Lp = L + (int64_t)(r - 1) * g.Lps;
+        const unsigned short* Rp = R + (int64_t)(t - r - 1) * g.Rps;
+        int acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+        for (int64_t k0 = 0; k0 < Kloop; k0 += BK) {
+          uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+          if (i0 + lrow < g.M && k0 + lk < g.pitch)
+            va = *reinterpret_cast<const uint4*>(Lp + (i0 + lrow) * g.pitch + k0 + lk);
+          if (j0 + lrow < g.N && k0 + lk < g.pitch)
+            vb = *reinterpret_cast<const uint4*>(Rp + (j0 + lrow) * g.pitch + k0 + lk);
+          int a0, a1, b0, b1;
+          pack8(va, a0, a1);
+          pack8(vb, b0, b1);
+          As[lk / 4][lrow] = a0;
+          As[lk / 4 + 1][lrow] = a1;
+          Bs[lk / 4][lrow] = b0;
+          Bs[lk / 4 + 1][lrow] = b1;
+          __syncthreads();
+#pragma unroll
+          for (int qd = 0; qd < BK / 4; ++qd) {
+            int4 av = *reinterpret_cast<const int4*>(&As[qd][ty * 4]);
+            int4 bv = *reinterpret_cast<const int4*>(&Bs[qd][tx * 4]);
+            int ar[4] = {av.x, av.y, av.z, av.w};
+            int br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] = __dp4a(ar[a], br[b], acc[a][b]);
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) tacc[a][b] += acc[a][b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) racc[a][b] = racc[a][b] * 128 + tacc[a][b];
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int64_t j = j0 + tx * 4 + b;
+      if (j >= g.N) continue;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        int64_t i = i0 + ty * 4 + a;
+        if (i < g.M) g.out[grp * g.ogs + j * g.ldo + i] = racc[a][b];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s) {
+  if (g.groups == 0 || g.M == 0 || g.N == 0) return FRX_OK;
+  if (g.pitch % 8) return FRX_E_ARG;
+  dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
+  k_plane_gemm_simt<<<grid, 256, 0, s>>>(g);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) { return launch_plane_gemm_simt(g, s); }
+
+}  // namespace frx

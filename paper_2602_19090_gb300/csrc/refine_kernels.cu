@@ -1,0 +1,282 @@
+// Element-wise and per-column kernels of one refinement iteration (Alg. 1, Sec. 3):
+// recombination of the exact slice-product groups into double-double, r and lambda
+// (lines 2-3), the residual V - X^(1) diag(lambda) (line 4), the correction E~
+// (line 5, with the Ogita-Aishima cluster rule) and the update by pair arithmetic
+// (line 6, Sec. 2.2).
+#include "frx_internal.cuh"
+#include "kernels.cuh"
+#include "refine_kernels.cuh"
+
+namespace frx {
+
+// value of entry (i, j) of an Ozaki product from its int64 groups (least significant first)
+__device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
+  dd acc{0.0, 0.0};
+  if (eLi == EZERO || eRj == EZERO) return acc;
+  for (int g = ga.groups - 1; g >= 0; --g) {
+    i64 R = ga.out[g * ga.ogs + j * ga.ldo + i];
+    if (R == 0) continue;
+    acc = dd_add(acc, i64_to_dd_scaled(R, eLi + eRj + 2 - DIGIT_BITS * ga.tlast[g]));
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_t* __restrict__ eL,
+                                                      const int32_t* __restrict__ eR, int64_t M, int64_t N,
+                                                      double* __restrict__ Ch, int64_t ldh, double* __restrict__ Cl,
+                                                      int64_t ldl) {
+  int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  int64_t j = blockIdx.y;
+  if (i >= M) return;
+  dd v = gather_dd(ga, i, j, eL[i], eR[j]);
+  Ch[i + j * ldh] = v.h;
+  if (Cl) Cl[i + j * ldl] = v.l;
+}
+
+__device__ dd block_sum_dd(dd v, dd* red) {
+  v = warp_sum_dd(v);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : dd{0.0, 0.0};
+    v = warp_sum_dd(v);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  dd r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_sum_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ u64 block_max_u64(u64 v, u64* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    u64 w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      u64 x = __shfl_xor_sync(0xffffffffu, v, o);
+      v = x > v ? x : v;
+    }
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  u64 r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ---- lines 2-4 (inner part): one block per column j --------------------------------
+// smem: n double-doubles (V column)
+__global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
+  extern __shared__ dd vcol[];
+  __shared__ dd redd[32];
+  __shared__ u64 redu[32];
+  const int64_t j = blockIdx.x;
+  const int64_t n = a.n;
+  const int fj = a.f[j];
+  const double* x = a.X1 + j * a.ld1;
+  dd nn{0.0, 0.0}, dv{0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    dd v = gather_dd(a.V, i, j, a.eA[i], fj);
+    vcol[i] = v;
+    if (a.Vh) a.Vh[i + j * n] = v.h;
+    if (a.Vl) a.Vl[i + j * n] = v.l;
+    double xi = x[i];
+    nn = dd_add(nn, two_prod(xi, xi));
+    dd q = two_prod(xi, v.h);
+    q.l = __dadd_rn(q.l, __dmul_rn(xi, v.l));
+    dv = dd_add(dv, q);
+  }
+  nn = block_sum_dd(nn, redd);
+  dv = block_sum_dd(dv, redd);
+  const double lam = dd_div(dv, nn).h;
+  const double r = dd_add_d(dd{-nn.h, -nn.l}, 1.0).h;
+  if (threadIdx.x == 0) {
+    a.lam[j] = lam;
+    a.r[j] = r;
+  }
+  u64 mx = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    dd p = two_prod(x[i], lam);
+    double res = dd_add(vcol[i], dd{-p.h, -p.l}).h;
+    a.Res[i + j * a.ldr] = res;
+    u64 ab = double_to_bits(res) & 0x7fffffffffffffffull;
+    mx = ab > mx ? ab : mx;
+  }
+  mx = block_max_u64(mx, redu);
+  if (threadIdx.x == 0) a.h[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
+}
+
+// ---- ||off-diagonal W||_F^2 (for the automatic cluster threshold) ------------------
+__global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
+  __shared__ double red[32];
+  const int64_t j = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) {
+    if (i == j) continue;
+    double w = gather_dd(a.W, i, j, a.f[i], a.h[j]).h;
+    s += w * w;
+  }
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) atomicAdd(a.norms + 1, s);
+}
+
+// ---- line 5: E~ column j, its exponent, ||E~||_F^2 -----------------------------------
+__global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
+  __shared__ double red[32];
+  __shared__ u64 redu[32];
+  __shared__ dd redd[32];
+  __shared__ int clist[64];
+  __shared__ int ccount;
+  const int64_t j = blockIdx.x;
+  const int64_t n = a.n;
+  const double lj = a.lam[j];
+  const int hj = a.h[j];
+  if (threadIdx.x == 0) ccount = 0;
+  __syncthreads();
+  double s2 = 0.0;
+  u64 mx = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double e;
+    double w = (a.W.groups > 0) ? gather_dd(a.W, i, j, a.f[i], hj).h : 0.0;
+    if (a.Wout) a.Wout[i + j * n] = w;
+    if (i == j) {
+      e = a.r[j] * 0.5;
+    } else {
+      double diff = __dsub_rn(lj, a.lam[i]);
+      if (fabs(diff) <= a.omega) {
+        int slot = atomicAdd(&ccount, 1);
+        if (slot < 64) clist[slot] = (int)i;
+        else atomicOr(a.flags, FLAG_RANGE);
+        e = 0.0;
+      } else {
+        e = __ddiv_rn(w, diff);
+      }
+    }
+    a.E[i + j * a.lde] = e;
+  }
+  __syncthreads();
+  int nc = ccount < 64 ? ccount : 64;
+  const double* xj = a.X1 + j * a.ld1;
+  for (int c = 0; c < nc; ++c) {
+    int i = clist[c];
+    const double* xi = a.X1 + (int64_t)i * a.ld1;
+    dd acc{0.0, 0.0};
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc = dd_add(acc, two_prod(xi[k], xj[k]));
+    acc = block_sum_dd(acc, redd);
+    if (threadIdx.x == 0) a.E[i + j * a.lde] = -acc.h * 0.5;   // r_ij / 2
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && nc) atomicAdd(a.ccount, nc);
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double e = a.E[i + j * a.lde];
+    s2 += e * e;
+    u64 ab = double_to_bits(e) & 0x7fffffffffffffffull;
+    mx = ab > mx ? ab : mx;
+  }
+  s2 = block_sum_d(s2, red);
+  mx = block_max_u64(mx, redu);
+  if (threadIdx.x == 0) {
+    atomicAdd(a.norms + 0, s2);
+    a.eta[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
+  }
+}
+
+// ---- line 6: X <- RN(X1 + X1 E~) (pair arithmetic), ||X_new - X_old||_F^2 ----------------
+__global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
+  __shared__ double red[32];
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  double d2 = 0.0;
+  if (i < a.n) {
+    double x1 = a.X1[i + j * a.ld1];
+    double xn = x1;
+    if (a.U.groups > 0) {
+      dd u = gather_dd(a.U, i, j, a.rho[i], a.eta[j]);
+      dd c = two_sum(x1, u.h);
+      double cl = __dadd_rn(u.l, c.l);
+      xn = __dadd_rn(c.h, cl);
+    }
+    double xo = a.X[i + j * a.ldx];
+    double dx = __dsub_rn(xn, xo);
+    d2 = dx * dx;
+    a.X[i + j * a.ldx] = xn;
+  }
+  d2 = block_sum_d(d2, red);
+  if (threadIdx.x == 0) atomicAdd(a.norms + 2, d2);
+}
+
+// ---------------------------------------------------------------------------
+GroupArgs group_args(const PlaneGemm& g) {
+  GroupArgs ga;
+  ga.out = g.out;
+  ga.ogs = g.ogs;
+  ga.ldo = g.ldo;
+  ga.groups = g.groups;
+  for (int k = 0; k < 8; ++k) ga.tlast[k] = k < g.groups ? group_last_t(g, k) : 0;
+  return ga;
+}
+
+int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR, double* Ch, int64_t ldh,
+                        double* Cl, int64_t ldl, cudaStream_t s) {
+  if (g.M == 0 || g.N == 0) return FRX_OK;
+  dim3 grid((unsigned)((g.M + 255) / 256), (unsigned)g.N);
+  k_groups_to_dd<<<grid, 256, 0, s>>>(group_args(g), eL, eR, g.M, g.N, Ch, ldh, Cl, ldl);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_residual(const ResidualArgs& a, cudaStream_t s) {
+  size_t smem = sizeof(dd) * (size_t)a.n;
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_residual<<<(unsigned)a.n, 256, smem, s>>>(a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s) {
+  k_w_offdiag_norm2<<<(unsigned)a.n, 256, 0, s>>>(a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_correction(const CorrectionArgs& a, cudaStream_t s) {
+  k_correction<<<(unsigned)a.n, 256, 0, s>>>(a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_update(const UpdateArgs& a, cudaStream_t s) {
+  dim3 grid((unsigned)((a.n + 255) / 256), (unsigned)a.n);
+  k_update<<<grid, 256, 0, s>>>(a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+}  // namespace frx

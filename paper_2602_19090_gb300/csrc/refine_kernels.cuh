@@ -1,0 +1,68 @@
+// Argument blocks of the per-iteration kernels.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace frx {
+
+struct GroupArgs {  // int64 anti-diagonal groups of one Ozaki product
+  const i64* out;
+  int64_t ogs, ldo;
+  int groups;
+  int tlast[8];
+};
+
+struct ResidualArgs {
+  int64_t n;
+  GroupArgs V;           // V = A X^(1): left exponents eA (rows of A), right f (columns of X)
+  const int32_t* eA;
+  const int32_t* f;
+  const double* X1;
+  int64_t ld1;
+  double* lam;           // out: lambda_j (Alg. 1 line 3)
+  double* r;             // out: r_j (line 2)
+  double* Res;           // out: V - X1 diag(lambda) rounded to FP64
+  int64_t ldr;
+  int32_t* h;            // out: column exponents of Res
+  double* Vh;            // optional debug copies (ld = n)
+  double* Vl;
+};
+
+struct CorrectionArgs {
+  int64_t n;
+  GroupArgs W;           // W = X1^T Res: left exponents f, right h
+  const int32_t* f;
+  const int32_t* h;
+  const double* lam;
+  const double* r;
+  const double* X1;
+  int64_t ld1;
+  double omega;          // cluster threshold
+  double* E;             // out: E~
+  int64_t lde;
+  int32_t* eta;          // out: column exponents of E~
+  double* norms;         // [0] += ||E~||_F^2, [1] += ||W_offdiag||_F^2, [2] += ||dX||_F^2
+  int* ccount;           // out: cluster pairs found
+  int* flags;
+  double* Wout;          // optional debug copy (ld = n)
+};
+
+struct UpdateArgs {
+  int64_t n;
+  GroupArgs U;           // U = X1 E~: left exponents rho (rows of X1), right eta
+  const int32_t* rho;
+  const int32_t* eta;
+  const double* X1;
+  int64_t ld1;
+  double* X;             // in: X_old, out: X_new
+  int64_t ldx;
+  double* norms;
+};
+
+GroupArgs group_args(const PlaneGemm& g);
+int launch_residual(const ResidualArgs& a, cudaStream_t s);
+int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s);
+int launch_correction(const CorrectionArgs& a, cudaStream_t s);
+int launch_update(const UpdateArgs& a, cudaStream_t s);
+
+}  // namespace frx

@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports every symbol include/frx.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_19090_gb300 import _lib, build_lib
+    if not os.path.exists(_lib.LIB_PATH):
+        build_lib.build()
+    return _lib.load()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "frx.h")).read()
+    return sorted(set(re.findall(r"FRX_API\s+[\w\s\*]*?\b(frx_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for required in ("frx_refine", "frx_ozaki_gemm", "frx_refine_workspace_bytes",
+                     "frx_status_string", "frx_refine_step"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2602_19090_gb300 import _lib
+    for name in declared():
+        assert hasattr(lib, name), name
+    assert sorted(declared()) == _lib.exported_names()
+
+
+def test_host_only_calls(lib):
+    from paper_2602_19090_gb300 import _lib
+    assert lib.frx_status_string(-3) == b"delta must exceed 2^-53"
+    o = _lib.Opts()
+    lib.frx_default_opts(ctypes.byref(o))
+    assert (o.slices_A, o.k_cap, o.max_iter, o.beta_override) == (0, 16, 10, -1)
+    assert lib.frx_refine_workspace_bytes(0, None) == 0
+    assert lib.frx_refine_workspace_bytes(64, None) > 64 * 64 * 8 * 3
+    assert lib.frx_refine_workspace_bytes(12289, None) == 0
+    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 17) == 0
+
+
+def test_argument_errors_before_any_device_work(lib):
+    from paper_2602_19090_gb300 import _lib
+    info = _lib.Info()
+    p = ctypes.c_void_p(256)   # never dereferenced: validation fails first
+    st = lib.frx_refine(p, 4, p, 4, p, 4, 2.0 ** -53, None, p, 1 << 20, ctypes.byref(info), None)
+    assert st == -3 and info.status == -3
+    st = lib.frx_refine(None, 4, p, 4, p, 4, 1e-10, None, p, 1 << 20, None, None)
+    assert st == -1
+    st = lib.frx_refine(p, 3, p, 4, p, 4, 1e-10, None, p, 1 << 20, None, None)
+    assert st == -1
+    st = lib.frx_refine(p, 4, p, 4, p, 4, 1e-10, None, None, 0, None, None)
+    assert st == -5
+    st = lib.frx_ozaki_gemm(p, 4, p, 4, p, 4, None, 4, 4, 4, 0, 0, p, 1 << 20, None)
+    assert st == -1
+
+
+def test_group_size_keeps_sums_exact(lib):
+    # groups of gs anti-diagonals: max|S_t| * 2^(7 (gs - 1)) * 128/127 < 2^62
+    for kL, kR, T, K in ((8, 6, 9, 64), (16, 8, 17, 12288), (16, 16, 32, 65536), (3, 3, 4, 5)):
+        gs = lib.frx_group_size(kL, kR, T, K)
+        pmax = max(sum(1 for r in range(1, kL + 1) if 1 <= t - r <= kR and t <= T)
+                   for t in range(2, min(T, kL + kR) + 1))
+        smax = pmax * K * 4096
+        assert smax * 2 ** (7 * (gs - 1)) * 128 / 127 < 2 ** 62
+        assert smax * 2 ** (7 * gs) * 128 / 127 >= 2 ** 61    # not needlessly small

@@ -1,0 +1,230 @@
+"""Parity of the CUDA path with the CPU oracle (run on a GB300: pytest -m gpu)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ozaki as oz
+from oracle import refine as orf
+from oracle import truth as tr
+from paper_2602_19090_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2602_19090_gb300 import api as a
+    return a
+
+
+def G():
+    from tests import gpu_util
+    return gpu_util
+
+
+@pytest.mark.parametrize("phi", [0.5, 2.0, 4.0])
+def test_exponents_bit_exact(api, phi):
+    g = G()
+    M = synth.gemm_operand(201, 133, phi, 100)
+    M[7, :] = 0.0
+    M[:, 5] = 0.0
+    M[3, 3] = 2.0 ** -1060          # subnormal entry in a row with other entries
+    Mt = g.to_dev(M)
+    e0 = api.exponents(Mt, 0).cpu().numpy()
+    e1 = api.exponents(Mt, 1).cpu().numpy()
+    assert np.array_equal(e0, oz.row_exponents(M))
+    assert np.array_equal(e1, oz.col_exponents(M))
+
+
+def test_exponents_reject_nonfinite(api):
+    g = G()
+    M = np.ones((40, 30))
+    M[4, 9] = np.nan
+    with pytest.raises(api.FrxError) as ex:
+        api.exponents(g.to_dev(M), 1)
+    assert ex.value.status == -2
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("phi", [0.5, 4.0])
+def test_slice_planes_bit_exact(api, axis, phi):
+    g = G()
+    M = synth.gemm_operand(150, 97, phi, 101 + axis)
+    M[11, :] = 0.0
+    Mt = g.to_dev(M)
+    e = api.exponents(Mt, axis)
+    k = 9
+    planes = api.slice_planes(Mt, axis, e, k)
+    d = g.bf16_digits(planes)
+    if axis == 0:
+        ref, _, _ = oz.slice_rows(M, k)                 # (k, rows, cols)
+    else:
+        ref, _, _ = oz.slice_cols(M, k)                 # (k, rows, cols) -> lines = cols
+        ref = np.transpose(ref, (0, 2, 1))
+    lines, other = ref.shape[1], ref.shape[2]
+    assert np.array_equal(d[:, :lines, :other], ref)
+    assert np.all(d[:, :, other:] == 0)
+
+
+@pytest.mark.parametrize("m,n,K,kL,kR,T", [(200, 150, 300, 4, 3, 5), (64, 64, 64, 8, 6, 9),
+                                           (130, 70, 1000, 3, 3, 6), (1, 1, 1, 2, 2, 4)])
+def test_plane_products_bit_exact(api, m, n, K, kL, kR, T):
+    g = G()
+    L = synth.gemm_operand(m, K, 2.0, 200)
+    R = synth.gemm_operand(K, n, 2.0, 201)
+    Lt, Rt = g.to_dev(L), g.to_dev(R)
+    eL = api.exponents(Lt, 0)
+    eR = api.exponents(Rt, 1)
+    Lp = api.slice_planes(Lt, 0, eL, kL)
+    Rp = api.slice_planes(Rt, 1, eR, kR)
+    out, gs = api.plane_products(Lp, Rp, K, kL, kR, T)
+    dL, _, _ = oz.slice_rows(L, kL)
+    dR, _, _ = oz.slice_cols(R, kR)
+    S = oz.slice_products(dL, dR, oz.pair_set(kL, kR, T))
+    ref = g.group_sums(S, kL, kR, T, gs)
+    got = out.cpu().numpy()
+    for gi, Rg in enumerate(ref):
+        assert np.array_equal(got[gi].T.astype(object), Rg)
+
+
+def test_plane_products_worst_case_digits(api):
+    # all digits +64: every partial sum is as large as the exactness bound allows
+    g = G()
+    K, kL, kR = 2048, 4, 4
+    M = np.ones((64, K))
+    Lt = g.to_dev(M)
+    eL = api.exponents(Lt, 0)
+    Lp = api.slice_planes(Lt, 0, eL, kL)
+    d = g.bf16_digits(Lp)
+    assert np.all(d[0, :, :K] == 64)
+    Rp = Lp.clone()
+    out, gs = api.plane_products(Lp, Rp, K, kL, kR, 2 * max(kL, kR))
+    dL = d[:, :, :K]
+    S = oz.slice_products(dL, np.transpose(dL, (0, 2, 1)), oz.pair_set(kL, kR, 8))
+    ref = g.group_sums(S, kL, kR, 8, gs)
+    for gi, Rg in enumerate(ref):
+        assert np.array_equal(out.cpu().numpy()[gi].T.astype(object), Rg)
+
+
+@pytest.mark.parametrize("mode", ["full", "triangular"])
+@pytest.mark.parametrize("phi", [0.5, 2.0, 4.0])
+def test_ozaki_gemm_matches_oracle(api, mode, phi):
+    g = G()
+    m, K, n, k = 150, 190, 70, 6
+    A = synth.gemm_operand(m, K, phi, 300)
+    B = synth.gemm_operand(K, n, phi, 301)
+    Ch, Cl = api.ozaki_gemm(g.to_dev(A), g.to_dev(B), k, mode, return_lo=True)
+    C_ref, o = oz.ozaki_gemm(A, B, k, mode)
+    Ch = Ch.cpu().numpy()
+    Cl = Cl.cpu().numpy()
+    mag = np.abs(A) @ np.abs(B)
+    assert np.all(np.abs((Ch - o["hi"]) + (Cl - o["lo"])) <= mag * 2.0 ** -100)
+    assert np.all(np.abs(Ch - C_ref) <= np.spacing(np.abs(C_ref)))
+    assert np.mean(Ch == C_ref) > 0.999
+
+
+def test_ozaki_gemm_exact_inputs_correctly_rounded(api):
+    g = G()
+    A = synth.gemm_operand(40, 33, 0.5, 310)
+    B = synth.gemm_operand(33, 20, 0.5, 311)
+    C = api.ozaki_gemm(g.to_dev(A), g.to_dev(B), 12, "full").cpu().numpy()
+    C_ref, _ = oz.ozaki_gemm(A, B, 12, "full", exact=True)
+    assert np.array_equal(C, C_ref)
+
+
+def _step_compare(api, A, X0, D0, delta, opts_o, opts_g):
+    g = G()
+    At, Xt, Dt = g.to_dev(A), g.to_dev(X0), g.to_dev(D0)
+    info, mats = api.refine_step(At, Xt, Dt, delta, opts_g)
+    Xn, lam, oi = orf.step(A, X0, D0, delta, opts_o)
+    for key in ("beta", "alpha", "sX", "kV", "kW", "kU"):
+        gk = {"sX": "s_X", "kV": "k_V", "kW": "k_W", "kU": "k_U"}.get(key, key)
+        assert info[gk] == oi[key], key
+    X1 = mats["X1"].cpu().numpy()
+    assert np.array_equal(X1, oi["X1"])
+    Vh, Vl = mats["Vh"].cpu().numpy(), mats["Vl"].cpu().numpy()
+    vmag = np.abs(A) @ np.abs(X1)
+    assert np.all(np.abs((Vh - oi["Vh"]) + (Vl - oi["Vl"])) <= vmag * 2.0 ** -100)
+    assert np.allclose(mats["r"].cpu().numpy(), oi["r"], rtol=0, atol=4 * U * 1e-6)
+    lam_g = Dt.cpu().numpy()
+    assert np.all(np.abs(lam_g - lam) <= 2 * np.spacing(np.abs(lam)))
+    Res = mats["Res"].cpu().numpy()
+    assert np.all(np.abs(Res - oi["Res"]) <= 2 * np.spacing(np.abs(oi["Res"])) + 1e-300)
+    W = mats["W"].cpu().numpy()
+    g_min = oi["plan"]["g"]
+    assert np.sqrt(np.sum((W - oi["W"]) ** 2)) <= delta * g_min * 1e-3
+    E = mats["E"].cpu().numpy()
+    assert np.sqrt(np.sum((E - oi["E"]) ** 2)) <= delta * 1e-3 + 4 * U * np.sqrt(np.sum(oi["E"] ** 2))
+    Xg = Xt.cpu().numpy()
+    assert np.max(np.abs(Xg - Xn)) <= 4 * U * np.max(np.abs(Xn))
+    return info, oi
+
+
+def test_refine_step_parity_workload0(api):
+    A, X0, D0 = synth.workload0()
+    _step_compare(api, A, X0, D0, 1e-14, orf.Options(), api.Options())
+    _step_compare(api, A, X0, D0, 1e-14, orf.Options(slices_A=8), api.Options(slices_A=8))
+
+
+@pytest.mark.parametrize("n,cond,variant", [(300, 1e4, "spd"), (257, 1e6, "indefinite")])
+def test_refine_step_parity_several_tiles(api, n, cond, variant):
+    A, X0, D0, lam = synth.refine_workload(n, cond, variant, case=n)
+    _step_compare(api, A, X0, D0, 1e-12, orf.Options(), api.Options())
+
+
+def test_refine_converges_like_the_oracle(api):
+    g = G()
+    A, X0, D0 = synth.workload0()
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    At, Xt, Dt = g.to_dev(A), g.to_dev(X0), g.to_dev(D0)
+    info = api.refine(At, Xt, Dt, 1e-14)
+    Xo, lo, oi = orf.refine(A, X0, D0, 1e-14, orf.Options())
+    assert info["status"] == 0 and info["iters"] == oi["iters"]
+    assert info["products"] == oi["products"]
+    fe = tr.forward_error(Xh, Xl, Xt.cpu().numpy())
+    assert fe <= 1e-14
+    assert np.max(np.abs(Xt.cpu().numpy() - Xo)) <= 4 * U
+
+
+def test_refine_fixed_slices_stagnates(api):
+    g = G()
+    A, X0, D0 = synth.workload0()
+    At, Xt, Dt = g.to_dev(A), g.to_dev(X0), g.to_dev(D0)
+    info = api.refine(At, Xt, Dt, 1e-14, api.Options(slices_A=8, max_iter=3))
+    assert info["status"] in (1, 2)
+
+
+def test_refine_clustered_auto(api):
+    g = G()
+    n = 32
+    A, Q, lam = synth.symmetric_matrix(n, 1e2, 5, "clustered", cluster_pairs=2, cluster_gap=1e-10)
+    X0, D0 = synth.initial_guess(Q, lam, 5, 1e-8)
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    At, Xt, Dt = g.to_dev(A), g.to_dev(X0), g.to_dev(D0)
+    info = api.refine(At, Xt, Dt, 1e-12, api.Options(cluster_omega=-1.0))
+    assert info["status"] == 0
+    X = Xt.cpu().numpy()
+    ci = np.nonzero(np.diff(np.sort(lam)) < 1e-9)[0]
+    for i in ci:
+        assert tr.subspace_error(Xh, Xl, X, [i, i + 1]) <= 1e-12
+
+
+def test_refine_rejects_bad_input(api):
+    g = G()
+    A, X0, D0 = synth.workload0()
+    At, Xt, Dt = g.to_dev(A), g.to_dev(X0), g.to_dev(D0)
+    with pytest.raises(api.FrxError) as ex:
+        api.refine(At, Xt, Dt, U)
+    assert ex.value.status == -3
+    A2 = A.copy()
+    A2[3, 5] = np.inf
+    with pytest.raises(api.FrxError) as ex:
+        api.refine(g.to_dev(A2), Xt, Dt, 1e-12)
+    assert ex.value.status == -2
+    work = api.workspace(1024)
+    with pytest.raises(api.FrxError) as ex:
+        api.refine(At, Xt, Dt, 1e-12, work=work)
+    assert ex.value.status == -5
