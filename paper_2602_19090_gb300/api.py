@@ -191,7 +191,8 @@ def plane_products(Lp, Rp, K, kL, kR, T, stream=None):
     _, n, pitch2 = Rp.shape
     assert pitch == pitch2
     gs = lib.frx_group_size(kL, kR, T, K)
-    _check(gs, "frx_group_size", soft_ok=False)
+    if gs < 0:
+        raise FrxError(gs, "frx_group_size")
     tmax = min(T, kL + kR)
     groups = (tmax - 1 + gs - 1) // gs
     out = torch.zeros((max(groups, 1), n, m), dtype=torch.int64, device=Lp.device)
