@@ -190,6 +190,30 @@ FRX_API int frx_plane_products(const uint16_t* L, int64_t L_plane_stride, const 
                        int64_t R_plane_stride, int64_t pitch, int64_t m, int64_t n, int64_t K,
                        int kL, int kR, int T, int64_t* out, void* stream);
 
+/*
+ * Launch accounting and kernel timing (native tracing).
+ *   kernel_launches  kernels this library launched since the last reset
+ *   gemm_launches    slice-product GEMM launches among them
+ *   gemm_ms          summed CUDA-event time of those GEMM launches, measured on the
+ *                    stream they were launched on (only while profiling is on)
+ *   gemm_ops         algorithmic operations of those launches: 2 m n K per slice pair
+ *   gemm_bytes       algorithmic bytes: every digit plane read once (2 bytes per
+ *                    digit) plus every int64 group word written once
+ * frx_profile_enable(1) starts timing every GEMM launch with a pair of CUDA events;
+ * frx_profile_read waits for the recorded events, fills `out` (host) and, if `reset`
+ * is nonzero, clears the counters.  Thread-safe; the counters are process-wide.
+ */
+typedef struct {
+  long long kernel_launches;
+  long long gemm_launches;
+  double gemm_ms;
+  double gemm_ops;
+  double gemm_bytes;
+} frx_profile;
+
+FRX_API void frx_profile_enable(int on);
+FRX_API int frx_profile_read(frx_profile* out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,14 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Profile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_longlong), ("gemm_launches", C.c_longlong),
+                ("gemm_ms", C.c_double), ("gemm_ops", C.c_double), ("gemm_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _SIGS = {
     "frx_default_opts": (None, [C.POINTER(Opts)]),
     "frx_status_string": (C.c_char_p, [C.c_int]),
@@ -46,6 +54,8 @@ _SIGS = {
     "frx_group_size": (C.c_int, [C.c_int, C.c_int, C.c_int, c_i64]),
     "frx_plane_products": (C.c_int, [c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64, c_i64, C.c_int,
                                      C.c_int, C.c_int, c_p, c_p]),
+    "frx_profile_enable": (None, [C.c_int]),
+    "frx_profile_read": (C.c_int, [C.POINTER(Profile), C.c_int]),
 }
 
 _lib = None

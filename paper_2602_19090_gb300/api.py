@@ -200,3 +200,15 @@ def plane_products(Lp, Rp, K, kL, kR, T, stream=None):
                                 T, _ptr(out), _stream(stream))
     _check(st, "frx_plane_products", soft_ok=False)
     return out, gs
+
+
+def profile_enable(on: bool = True):
+    """Time every slice-product GEMM launch with CUDA events on its stream."""
+    _lib.load().frx_profile_enable(1 if on else 0)
+
+
+def profile_read(reset: bool = False) -> dict:
+    p = _lib.Profile()
+    st = _lib.load().frx_profile_read(C.byref(p), 1 if reset else 0)
+    _check(st, "frx_profile_read", soft_ok=False)
+    return p.as_dict()

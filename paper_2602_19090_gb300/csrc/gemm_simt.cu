@@ -5,6 +5,7 @@
 // cross-check of the tensor-core path.
 #include "frx_internal.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace frx {
 
@@ -155,6 +156,10 @@ int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s) {
   return FRX_OK;
 }
 
-int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) { return launch_plane_gemm_simt(g, s); }
+int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) {
+  if (g.groups == 0 || g.M == 0 || g.N == 0) return FRX_OK;
+  GemmTimer timer(g, s);
+  return launch_plane_gemm_simt(g, s);
+}
 
 }  // namespace frx

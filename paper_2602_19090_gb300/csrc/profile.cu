@@ -1,0 +1,104 @@
+// Launch accounting and CUDA-event timing of the slice-product GEMMs.
+#include <mutex>
+#include <vector>
+
+#include "frx_internal.cuh"
+#include "kernels.cuh"
+#include "profile.cuh"
+
+namespace frx {
+namespace {
+
+struct Timed {
+  cudaEvent_t a, b;
+};
+
+std::mutex mu;
+bool enabled = false;
+long long launches = 0, gemm_launches = 0;
+double gemm_ms = 0.0, gemm_ops = 0.0, gemm_bytes = 0.0;
+std::vector<Timed> pending;
+std::vector<cudaEvent_t> free_events;
+
+cudaEvent_t get_event() {
+  if (!free_events.empty()) {
+    cudaEvent_t e = free_events.back();
+    free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+}  // namespace
+
+void count_launches(int k) {
+  std::lock_guard<std::mutex> g(mu);
+  launches += k;
+}
+
+GemmTimer::GemmTimer(const PlaneGemm& g, cudaStream_t s) : s_(s) {
+  std::lock_guard<std::mutex> lk(mu);
+  gemm_launches += 1;
+  launches += 1;
+  int pairs = 0;
+  for (int t = 2; t <= g.tmax; ++t) {
+    int lo = t - g.kR > 1 ? t - g.kR : 1;
+    int hi = g.kL < t - 1 ? g.kL : t - 1;
+    if (hi >= lo) pairs += hi - lo + 1;
+  }
+  gemm_ops += 2.0 * (double)g.M * (double)g.N * (double)g.K * pairs;
+  gemm_bytes += 2.0 * (double)g.K * ((double)g.M * g.kL + (double)g.N * g.kR) + 8.0 * g.groups * (double)g.M * g.N;
+  if (enabled) {
+    a_ = get_event();
+    b_ = get_event();
+    cudaEventRecord(a_, s_);
+  }
+}
+
+GemmTimer::~GemmTimer() {
+  if (a_) {
+    cudaEventRecord(b_, s_);
+    std::lock_guard<std::mutex> lk(mu);
+    pending.push_back({a_, b_});
+  }
+}
+
+}  // namespace frx
+
+using namespace frx;
+
+extern "C" {
+
+void frx_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(mu);
+  enabled = on != 0;
+}
+
+int frx_profile_read(frx_profile* out, int reset) {
+  std::lock_guard<std::mutex> g(mu);
+  for (auto& t : pending) {
+    if (cudaEventSynchronize(t.b) != cudaSuccess) return FRX_E_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    gemm_ms += ms;
+    free_events.push_back(t.a);
+    free_events.push_back(t.b);
+  }
+  pending.clear();
+  if (out) {
+    out->kernel_launches = launches;
+    out->gemm_launches = gemm_launches;
+    out->gemm_ms = gemm_ms;
+    out->gemm_ops = gemm_ops;
+    out->gemm_bytes = gemm_bytes;
+  }
+  if (reset) {
+    launches = gemm_launches = 0;
+    gemm_ms = gemm_ops = gemm_bytes = 0.0;
+  }
+  return FRX_OK;
+}
+
+}  // extern "C"

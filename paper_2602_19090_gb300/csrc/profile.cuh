@@ -1,0 +1,21 @@
+// Launch accounting (see frx_profile_* in include/frx.h).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace frx {
+
+void count_launches(int k);
+
+// RAII: counts one GEMM launch and, with profiling on, brackets it with CUDA events
+class GemmTimer {
+ public:
+  GemmTimer(const PlaneGemm& g, cudaStream_t s);
+  ~GemmTimer();
+
+ private:
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+}  // namespace frx

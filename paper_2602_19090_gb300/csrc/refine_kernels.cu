@@ -5,6 +5,7 @@
 // (line 6, Sec. 2.2).
 #include "frx_internal.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 #include "refine_kernels.cuh"
 
 namespace frx {
@@ -248,6 +249,7 @@ int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR
   if (g.M == 0 || g.N == 0) return FRX_OK;
   dim3 grid((unsigned)((g.M + 255) / 256), (unsigned)g.N);
   k_groups_to_dd<<<grid, 256, 0, s>>>(group_args(g), eL, eR, g.M, g.N, Ch, ldh, Cl, ldl);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -256,18 +258,21 @@ int launch_residual(const ResidualArgs& a, cudaStream_t s) {
   size_t smem = sizeof(dd) * (size_t)a.n;
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_residual<<<(unsigned)a.n, 256, smem, s>>>(a);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
 int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s) {
   k_w_offdiag_norm2<<<(unsigned)a.n, 256, 0, s>>>(a);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
 int launch_correction(const CorrectionArgs& a, cudaStream_t s) {
   k_correction<<<(unsigned)a.n, 256, 0, s>>>(a);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -275,6 +280,7 @@ int launch_correction(const CorrectionArgs& a, cudaStream_t s) {
 int launch_update(const UpdateArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((a.n + 255) / 256), (unsigned)a.n);
   k_update<<<grid, 256, 0, s>>>(a);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }

@@ -2,6 +2,7 @@
 // eq. tau with s = 1 for the truncation X^(1) of Sec. 3).
 #include "frx_internal.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace frx {
 
@@ -154,6 +155,7 @@ int launch_col_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols
                          cudaStream_t s) {
   if (cols == 0) return FRX_OK;
   k_col_exponents<<<(unsigned)cols, 256, 0, s>>>(M, ld, rows, cols, e, flags);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -164,7 +166,9 @@ int launch_row_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols
   FRX_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(u64) * rows, s));
   dim3 g((unsigned)((rows + 255) / 256), (unsigned)((cols + 63) / 64));
   k_row_maxbits<<<g, 256, 0, s>>>(M, ld, rows, cols, scratch, flags);
+  count_launches(1);
   k_maxbits_to_exponents<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(scratch, rows, e);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -174,6 +178,7 @@ int launch_slice_cols(const double* M, int64_t ld, int64_t K, int64_t N, const i
   if (N == 0 || nplanes == 0) return FRX_OK;
   dim3 g((unsigned)((pitch + 255) / 256), (unsigned)N);
   k_slice_cols<<<g, 256, 0, s>>>(M, ld, K, N, e, nplanes, planes, ps, pitch);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -183,6 +188,7 @@ int launch_slice_rows(const double* M, int64_t ld, int64_t rows, int64_t K, cons
   if (rows == 0 || nplanes == 0) return FRX_OK;
   dim3 g((unsigned)((pitch + 31) / 32), (unsigned)((rows + 31) / 32));
   k_slice_rows<<<g, 256, 0, s>>>(M, ld, rows, K, e, nplanes, planes, ps, pitch);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -192,6 +198,7 @@ int launch_truncate_slice_x(const double* X, int64_t ldx, int64_t n, const int32
                             cudaStream_t s) {
   dim3 g((unsigned)((pitch + 255) / 256), (unsigned)n);
   k_truncate_slice_x<<<g, 256, 0, s>>>(X, ldx, n, f, beta, nplanes, X1, ld1, planes, ps, pitch);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
