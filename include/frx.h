@@ -166,6 +166,27 @@ FRX_API int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_
                    int slices, int mode, void* work, size_t work_bytes, void* stream);
 
 /*
+ * frx_ozaki_gemm without caller scratch, for callers that cannot allocate device
+ * memory (for example a plugin inside a framework that has reserved the whole device
+ * memory for its own allocator, or code that is given a stream but no allocator).
+ * The paper has no counterpart: this is a library convenience around frx_ozaki_gemm.
+ * Same arguments and results as frx_ozaki_gemm, minus `work`/`work_bytes`.
+ *   Limits: m, n, k <= 512 and slices <= 8; larger sizes return FRX_E_UNSUPPORTED
+ *   before any device work.
+ *   Scratch: a fixed 24 MiB + 64 KiB array of device memory inside this library; every
+ *   device that loads the library holds it until the process exits.  The call
+ *   allocates nothing.  The first call on a device (with that device current) looks
+ *   up the array's device address once; make that first call before any stream
+ *   capture begins.  Call with the device that owns `stream` current.
+ *   Sharing: every call uses the same array and leaves its contents behind (each call
+ *   clears what it needs).  Calls whose GPU work overlaps (different streams or host
+ *   threads without ordering) race on the array: order them, e.g. on one stream.
+ */
+FRX_API int frx_ozaki_gemm_static(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                  double* C, int64_t ldc, double* C_lo, int64_t m, int64_t n,
+                                  int64_t k, int slices, int mode, void* stream);
+
+/*
  * Digit planes of the slice products, for bit-exact checks of the integer path.
  *   frx_exponents: e[i] = ceil(log2 max |row i|) (axis 0) or of column j (axis 1) of an
  *     rows x cols matrix; -2^30 for an all-zero line.  Returns FRX_E_NONFINITE on Inf/NaN.

@@ -54,6 +54,8 @@ _SIGS = {
     "frx_group_size": (C.c_int, [C.c_int, C.c_int, C.c_int, c_i64]),
     "frx_plane_products": (C.c_int, [c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64, c_i64, C.c_int,
                                      C.c_int, C.c_int, c_p, c_p]),
+    "frx_ozaki_gemm_static": (C.c_int, [c_p, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64,
+                                        c_i64, C.c_int, C.c_int, c_p]),
     "frx_profile_enable": (None, [C.c_int]),
     "frx_profile_read": (C.c_int, [C.POINTER(Profile), C.c_int]),
 }
