@@ -235,6 +235,7 @@ PlaneGemm make_gemm(const __nv_bfloat16* L, int64_t Lps, const __nv_bfloat16* R,
   g.out = out;
   g.ogs = M * N;
   g.ldo = M;
+  g.flags = nullptr;
   g.tmax = g.gs = g.groups = 0;
   return g;
 }
@@ -281,6 +282,7 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
 
   // S5/S6: V = A X^(1) (Alg. 1 line 1 with eq. mat_mul), pairs r + s <= k_V + 1
   PlaneGemm gv = make_gemm(ws.Ap, ws.ps, ws.Xp, ws.ps, ws.pitch, n, n, n, kV, sX, kV + 1, ws.groups);
+  gv.flags = ws.flags;
   FRX_TRY(plan_plane_gemm(gv));
   if (gv.groups > 4) return FRX_E_UNSUPPORTED;
   FRX_TRY(launch_plane_gemm(gv, s));
@@ -309,6 +311,7 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   int kW = slices_for(n, fmax, hmax, delta * g, o.k_cap);
   PlaneGemm gw = make_gemm(ws.Xp, ws.ps, ws.Rp, ws.ps, ws.pitch, n, n, n, std::min(sX, kW), kW, kW + 1,
                            ws.groups);
+  gw.flags = ws.flags;
   if (kW > 0) {
     FRX_TRY(launch_slice_cols(ws.Res, n, n, n, ws.h, kW, ws.Rp, ws.ps, ws.pitch, s));
     FRX_TRY(plan_plane_gemm(gw));
@@ -362,6 +365,7 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   FRX_TRY(to_host(rho_h, ws.rho, n, s));
   int kU = slices_for(n, vmax(rho_h), vmax(eta_h), delta, o.k_cap);
   PlaneGemm gu = make_gemm(ws.X1rp, ws.ps, ws.Rp, ws.ps, ws.pitch, n, n, n, kU, kU, kU + 1, ws.groups);
+  gu.flags = ws.flags;
   if (kU > 0) {
     FRX_TRY(launch_slice_rows(ws.X1, n, n, n, ws.rho, kU, ws.X1rp, ws.ps, ws.pitch, s));
     FRX_TRY(launch_slice_cols(ws.E, n, n, n, ws.eta, kU, ws.Rp, ws.ps, ws.pitch, s));
@@ -560,6 +564,7 @@ int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_t ldb, d
   FRX_TRY(launch_slice_cols(B, ldb, k, n, ws.eB, slices, ws.Bp, n * ws.pitch, ws.pitch, s));
   int T = mode == FRX_MODE_FULL ? 2 * slices : slices + 1;
   PlaneGemm g = make_gemm(ws.Ap, m * ws.pitch, ws.Bp, n * ws.pitch, ws.pitch, m, n, k, slices, slices, T, ws.groups);
+  g.flags = ws.flags;
   FRX_TRY(plan_plane_gemm(g));
   FRX_TRY(launch_plane_gemm(g, s));
   FRX_TRY(launch_groups_to_dd(g, ws.eA, ws.eB, C, ldc, C_lo, ldc, s));

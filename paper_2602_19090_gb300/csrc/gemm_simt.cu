@@ -3,6 +3,8 @@
 // integer digits, so the products are exact integer matrices (int32 per pair,
 // int64 per anti-diagonal group).  Used for small problems and as the
 // cross-check of the tensor-core path.
+#include <stdlib.h>
+
 #include "frx_internal.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
@@ -156,9 +158,14 @@ int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s) {
   return FRX_OK;
 }
 
+// Tensor-core kernel when the operands allow it; FRX_GEMM=simt selects the CUDA-core
+// kernel (used to cross-check the two implementations bit for bit).
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) {
   if (g.groups == 0 || g.M == 0 || g.N == 0) return FRX_OK;
+  const char* env = getenv("FRX_GEMM");
+  bool simt = env && env[0] == 's';
   GemmTimer timer(g, s);
+  if (!simt && plane_gemm_tc_supported(g)) return launch_plane_gemm_tc(g, g.flags, s);
   return launch_plane_gemm_simt(g, s);
 }
 

@@ -1,0 +1,441 @@
+// Exact digit-plane products on the 5th-generation tensor cores (sm_103a).
+//
+// Sec. 2.3 multiplies error-free slices so that every slice product is exact.  The
+// slices here are integer digits in [-64, 64] stored as bfloat16, multiplied by
+// tcgen05.mma (.kind::f16, bf16 x bf16 -> f32 in TMEM).  Every product is an integer
+// of magnitude <= 2^12, so an FP32 accumulator holds exact integers as long as the
+// accumulated count stays <= 2^11 terms per lane (|sum| <= 2^23); the accumulator is
+// therefore drained into int64 every CHUNK_KB k-blocks (and at the end of every
+// anti-diagonal t) and the int64 sums are combined in Horner form per group:
+//   R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
+//
+// CTA = one 128 x 128 output tile.  Warp roles:
+//   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
+//   warp 1       TMEM allocator and single-thread MMA issuer
+//   warps 2..9   epilogue: tcgen05.ld of the FP32 accumulator, exact int64 sums
+// Pipeline: STAGES smem stages (A 16 KB + B 16 KB), two TMEM accumulators of 128
+// columns each.  Every mbarrier wait is bounded by the global timer; on expiry the
+// CTA raises FLAG_TIMEOUT, drains what it issued and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "frx_internal.cuh"
+#include "kernels.cuh"
+#include "profile.cuh"
+
+namespace frx {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;   // BK bf16 = 128 bytes = one swizzle row
+constexpr int STAGES = 6;
+constexpr int CHUNK_KB = 32;                 // 32 * 64 = 2048 products per accumulation
+constexpr int NUM_EPI_WARPS = 8;
+constexpr int NUM_THREADS = 32 * (2 + NUM_EPI_WARPS);
+constexpr uint32_t STAGE_A_BYTES = BM * BK * 2;
+constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+
+struct Smem {
+  // tiles first (1024-byte aligned by the dynamic smem base adjustment)
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false on timeout or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* flags) {
+  uint32_t addr = smem_u32(bar);
+  if (mbar_try(addr, parity)) return true;
+  unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(addr, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort) return false;
+      if (gtimer() - t0 > WAIT_LIMIT_NS) {
+        *abort = 1;
+        if (flags) atomicOr(flags, FLAG_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart (SBO), version 1
+__device__ __forceinline__ uint64_t smem_desc(const void* tile) {
+  uint64_t addr = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3fff;
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = BN
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+  int64_t M, N;
+  int nkb;       // k-blocks of 64
+  int kL, kR, tmax, gs, groups;
+  i64* out;
+  int64_t ogs, ldo;
+  int* flags;
+};
+
+__device__ __forceinline__ int pair_lo(int t, int kR) { return t - kR > 1 ? t - kR : 1; }
+__device__ __forceinline__ int pair_hi(int t, int kL) { return kL < t - 1 ? kL : t - 1; }
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
+  unsigned char* tiles = base;
+  Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&sm->full[s], 1);
+      mbar_init(&sm->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm->acc_full[b], 1);
+      mbar_init(&sm->acc_empty[b], NUM_EPI_WARPS);
+    }
+    mbar_init(&sm->drain, 1);
+    sm->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm->tmem_base;
+  volatile int* abort = &sm->abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&mapL) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&mapR) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      long long issued = 0;
+      bool ok = true;
+      for (int grp = 0; grp < a.groups && ok; ++grp) {
+        int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
+        for (int t = t0; t <= t1 && ok; ++t) {
+          for (int r = pair_lo(t, a.kR); r <= pair_hi(t, a.kL) && ok; ++r) {
+            int s = t - r;
+            for (int kb = 0; kb < a.nkb; ++kb) {
+              if (!mbar_wait(&sm->empty[stage], phase ^ 1, abort, a.flags)) {
+                ok = false;
+                break;
+              }
+              unsigned char* st = tiles + stage * STAGE_BYTES;
+              mbar_expect_tx(&sm->full[stage], STAGE_BYTES);
+              tma_load_3d(st, &mapL, kb * BK, i0, r - 1, &sm->full[stage]);
+              tma_load_3d(st + STAGE_A_BYTES, &mapR, kb * BK, j0, s - 1, &sm->full[stage]);
+              ++issued;
+              if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies this thread issued land before the CTA exits (bounded)
+        unsigned long long t0 = gtimer();
+        long long back = issued < STAGES ? issued : STAGES;
+        int st2 = stage;
+        uint32_t ph2 = phase;
+        for (long long q = 0; q < back; ++q) {
+          if (--st2 < 0) {
+            st2 = STAGES - 1;
+            ph2 ^= 1;
+          }
+          while (!mbar_try(smem_u32(&sm->full[st2]), ph2) && gtimer() - t0 < 10000000ull) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t acc_phase[2] = {0, 0};
+      bool ok = true;
+      bool any = false;
+      for (int grp = 0; grp < a.groups && ok; ++grp) {
+        int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
+        for (int t = t0; t <= t1 && ok; ++t) {
+          int rlo = pair_lo(t, a.kR), rhi = pair_hi(t, a.kL);
+          int total = (rhi - rlo + 1) * a.nkb;
+          int cnt = 0, done = 0;
+          for (int r = rlo; r <= rhi && ok; ++r) {
+            for (int kb = 0; kb < a.nkb; ++kb) {
+              if (cnt == 0) {
+                if (!mbar_wait(&sm->acc_empty[buf], acc_phase[buf] ^ 1, abort, a.flags)) {
+                  ok = false;
+                  break;
+                }
+                fence_after();
+              }
+              if (!mbar_wait(&sm->full[stage], phase, abort, a.flags)) {
+                ok = false;
+                break;
+              }
+              fence_after();
+              unsigned char* st = tiles + stage * STAGE_BYTES;
+              uint64_t da = smem_desc(st), db = smem_desc(st + STAGE_A_BYTES);
+              uint32_t d = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), (cnt > 0 || kk > 0) ? 1u : 0u);
+              mma_commit(&sm->empty[stage]);
+              any = true;
+              if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+              ++cnt;
+              ++done;
+              if (cnt == CHUNK_KB || done == total) {
+                mma_commit(&sm->acc_full[buf]);
+                acc_phase[buf] ^= 1;
+                buf ^= 1;
+                cnt = 0;
+              }
+            }
+          }
+        }
+      }
+      if (!ok && any) {
+        // wait (bounded) for the MMAs already issued before the CTA frees TMEM
+        mma_commit(&sm->drain);
+        unsigned long long t0 = gtimer();
+        while (!mbar_try(smem_u32(&sm->drain), 0) && gtimer() - t0 < 10000000ull) {
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int ew = warp - 2;                 // 0..7
+    const int quad = warp & 3;               // TMEM lanes 32*quad .. +31 (warp % 4 rule)
+    const int col0 = (ew >> 2) * 64;         // columns [col0, col0 + 64)
+    const int64_t row = (int64_t)i0 + quad * 32 + lane;
+    i64 R[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) R[c] = 0;
+    int buf = 0;
+    uint32_t acc_phase[2] = {0, 0};
+    bool ok = true;
+    for (int grp = 0; grp < a.groups && ok; ++grp) {
+      int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
+      for (int t = t0; t <= t1 && ok; ++t) {
+        int total = (pair_hi(t, a.kL) - pair_lo(t, a.kR) + 1) * a.nkb;
+        int chunks = (total + CHUNK_KB - 1) / CHUNK_KB;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) R[c] <<= 7;
+        for (int ch = 0; ch < chunks; ++ch) {
+          if (!mbar_wait(&sm->acc_full[buf], acc_phase[buf], abort, a.flags)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + col0);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t v[32];
+            tmem_ld32(taddr + h * 32, v);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) R[h * 32 + c] += (i64)__float2int_rn(__uint_as_float(v[c]));
+          }
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+          acc_phase[buf] ^= 1;
+          buf ^= 1;
+        }
+      }
+      if (!ok) break;
+      if (row < a.M) {
+        i64* o = a.out + grp * a.ogs + row;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          int64_t j = (int64_t)j0 + col0 + c;
+          if (j < a.N) o[j * a.ldo] = R[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 64; ++c) R[c] = 0;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int64_t K, int64_t rows, int planes, int64_t pitch,
+              int64_t plane_stride, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * 2, (cuuint64_t)plane_stride * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t smem_bytes() { return (size_t)STAGES * STAGE_BYTES + sizeof(Smem) + 1024; }
+
+}  // namespace
+
+bool plane_gemm_tc_supported(const PlaneGemm& g) {
+  if (g.groups <= 0 || g.M < 1 || g.N < 1 || g.K < 1) return false;
+  if (g.pitch % 8 || g.Lps % 8 || g.Rps % 8) return false;
+  if (((uintptr_t)g.L & 15) || ((uintptr_t)g.R & 15)) return false;
+  if (g.M > (1 << 24) || g.N > (1 << 24)) return false;
+  return get_encode() != nullptr;
+}
+
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
+  CUtensorMap mL, mR;
+  if (!make_map(&mL, g.L, g.K, g.M, g.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
+  if (!make_map(&mR, g.R, g.K, g.N, g.kR, g.pitch, g.Rps, BN)) return FRX_E_CUDA;
+  TcArgs a;
+  a.M = g.M;
+  a.N = g.N;
+  a.nkb = (int)((g.K + BK - 1) / BK);
+  a.kL = g.kL;
+  a.kR = g.kR;
+  a.tmax = g.tmax;
+  a.gs = g.gs;
+  a.groups = g.groups;
+  a.out = g.out;
+  a.ogs = g.ogs;
+  a.ldo = g.ldo;
+  a.flags = flags;
+  size_t smem = smem_bytes();
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&]() {
+    attr_err = cudaFuncSetAttribute(k_plane_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  FRX_CUDA_TRY(attr_err);
+  dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
+  k_plane_gemm_tc<<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+}  // namespace frx

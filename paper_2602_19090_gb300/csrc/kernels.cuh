@@ -36,6 +36,7 @@ struct PlaneGemm {
   int tmax, gs, groups;
   i64* out;
   int64_t ogs, ldo;
+  int* flags;   // device status word (timeouts), may be null
 };
 
 // host: fill tmax / gs / groups; returns FRX_E_UNSUPPORTED if exactness cannot be guaranteed
@@ -49,7 +50,7 @@ inline int group_last_t(const PlaneGemm& g, int grp) {
 // gemm_simt.cu / gemm_tc.cu
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s);
 int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s);
-int launch_plane_gemm_tc(const PlaneGemm& g, cudaStream_t s);
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s);
 bool plane_gemm_tc_supported(const PlaneGemm& g);
 
 // refine_kernels.cu

@@ -1,0 +1,69 @@
+"""The tcgen05 slice-product kernel against the CUDA-core kernel, bit for bit (GB300)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2602_19090_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_19090_gb300 import api as a
+    return a
+
+
+def _both(api, Lp, Rp, K, kL, kR, T):
+    import torch
+    old = os.environ.get("FRX_GEMM")
+    try:
+        os.environ["FRX_GEMM"] = "simt"
+        ref, gs = api.plane_products(Lp, Rp, K, kL, kR, T)
+        os.environ["FRX_GEMM"] = "tc"
+        got, gs2 = api.plane_products(Lp, Rp, K, kL, kR, T)
+        torch.cuda.synchronize()
+    finally:
+        if old is None:
+            os.environ.pop("FRX_GEMM", None)
+        else:
+            os.environ["FRX_GEMM"] = old
+    assert gs == gs2
+    return ref.cpu().numpy(), got.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,K,kL,kR,T", [
+    (128, 128, 64, 1, 1, 2),          # one tile, one k-block, one product
+    (128, 128, 128, 2, 2, 4),
+    (200, 150, 300, 4, 3, 5),         # ragged tiles and K
+    (256, 384, 2048, 3, 3, 4),        # exactly one chunk per pair
+    (130, 260, 5000, 5, 4, 6),        # chunks split inside pairs, several groups
+    (1, 1, 1, 2, 2, 4),
+])
+def test_tc_matches_simt(api, m, n, K, kL, kR, T):
+    from tests import gpu_util as g
+    L = synth.gemm_operand(m, K, 2.0, 500 + m)
+    R = synth.gemm_operand(K, n, 2.0, 600 + n)
+    Lt, Rt = g.to_dev(L), g.to_dev(R)
+    Lp = api.slice_planes(Lt, 0, api.exponents(Lt, 0), kL)
+    Rp = api.slice_planes(Rt, 1, api.exponents(Rt, 1), kR)
+    ref, got = _both(api, Lp, Rp, K, kL, kR, T)
+    assert np.array_equal(ref, got)
+
+
+def test_tc_worst_case_digits(api):
+    # every digit +64 (all-ones matrix): FP32 chunk sums reach 2048 * 4096 = 2^23 exactly
+    from tests import gpu_util as g
+    K = 4096 + 64
+    Lt = g.to_dev(np.ones((256, K)))
+    Lp = api.slice_planes(Lt, 0, api.exponents(Lt, 0), 3)
+    ref, got = _both(api, Lp, Lp.clone(), K, 3, 3, 6)
+    assert np.array_equal(ref, got)
+    # only plane 1 is nonzero (digit 64), so group 0 holds S_2 shifted to its last t
+    gs = api.group_size(3, 3, 6, K)
+    t_last = min(2 + gs - 1, 6)
+    assert ref[0, 0, 0] == 64 * 64 * K * 2 ** (7 * (t_last - 2))
