@@ -260,6 +260,8 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   std::vector<int32_t> f_h;
   FRX_TRY(to_host(f_h, ws.f, n, s));
   FRX_TRY(check_flags(ws.flags, s));
+  for (int32_t e : f_h)
+    if (e == EZERO) return FRX_E_ARG;  // a zero column is not an eigenvector approximation
 
   // S2: plan (Sec. 4.1), using the previous eigenvalue estimates
   double Lam;
@@ -300,6 +302,7 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   ra.Res = ws.Res;
   ra.ldr = n;
   ra.h = ws.h;
+  ra.beta = beta;
   ra.Vh = dbg ? dbg->Vh : nullptr;
   ra.Vl = dbg ? dbg->Vl : nullptr;
   FRX_TRY(launch_residual(ra, s));

@@ -10,8 +10,12 @@
 
 namespace frx {
 
-// value of entry (i, j) of an Ozaki product from its int64 groups (least significant first)
-__device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// value of entry (i, j) of an Ozaki product from its int64 groups (least significant first),
+// as a double-double; general path (any number of groups)
+__device__ __forceinline__ dd gather_dd_general(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
   dd acc{0.0, 0.0};
   if (eLi == EZERO || eRj == EZERO) return acc;
   for (int g = ga.groups - 1; g >= 0; --g) {
@@ -20,6 +24,83 @@ __device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t 
     acc = dd_add(acc, i64_to_dd_scaled(R, eLi + eRj + 2 - DIGIT_BITS * ga.tlast[g]));
   }
   return acc;
+}
+
+__device__ __forceinline__ int clz128(u128 a) {
+  u64 hi = (u64)(a >> 64), lo = (u64)a;
+  return hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+}
+
+// round-to-nearest-even of a 128-bit integer to a double
+__device__ __forceinline__ double i128_to_double_rn(i128 N) {
+  if (N == 0) return 0.0;
+  bool neg = N < 0;
+  u128 a = neg ? (u128)(-N) : (u128)N;
+  double r;
+  if ((a >> 63) == 0) {
+    r = __ull2double_rn((u64)a);
+  } else {
+    int sh = (127 - clz128(a)) - 62;                 // keep 63 bits; the rest is a sticky bit
+    u64 v = (u64)(a >> sh);
+    if ((a & (((u128)1 << sh) - 1)) != 0) v |= 1ull;
+    r = __dmul_rn(__ull2double_rn(v), pow2(sh));
+  }
+  return neg ? -r : r;
+}
+
+// integer value of an integer-valued double
+__device__ __forceinline__ i128 double_to_i128(double h) {
+  u64 b = (u64)__double_as_longlong(h);
+  int bexp = (int)((b >> 52) & 0x7ff);
+  if (bexp == 0) return 0;
+  int e = bexp - 1075;
+  u64 m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  u128 v = e >= 0 ? ((u128)m << e) : (u128)(m >> (-e));
+  return (b >> 63) ? -(i128)v : (i128)v;
+}
+
+// sum_g R_g 2^(7 (tlast[G-1] - tlast[g])), exact (caller checks ga.exact128)
+__device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, int64_t j) {
+  i128 N = 0;
+  for (int g = 0; g < ga.groups; ++g) {
+    if (g) N <<= DIGIT_BITS * (ga.tlast[g] - ga.tlast[g - 1]);
+    N += (i128)ga.out[g * ga.ogs + j * ga.ldo + i];
+  }
+  return N;
+}
+
+__device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
+  if (!ga.exact128) return gather_dd_general(ga, i, j, eLi, eRj);
+  if (eLi == EZERO || eRj == EZERO || ga.groups == 0) return dd{0.0, 0.0};
+  i128 N = combine_groups(ga, i, j);
+  double h = i128_to_double_rn(N);
+  double l = i128_to_double_rn(N - double_to_i128(h));
+  int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tlast[ga.groups - 1];
+  if (ex >= -1022 + 130 && ex <= 1023 - 130) {
+    double sc = pow2(ex);
+    return {__dmul_rn(h, sc), __dmul_rn(l, sc)};
+  }
+  return {ldexp(h, ex), ldexp(l, ex)};
+}
+
+// RN of the entry as a single double
+__device__ __forceinline__ double gather_d(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
+  if (!ga.exact128) return gather_dd_general(ga, i, j, eLi, eRj).h;
+  if (eLi == EZERO || eRj == EZERO || ga.groups == 0) return 0.0;
+  double h = i128_to_double_rn(combine_groups(ga, i, j));
+  int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tlast[ga.groups - 1];
+  if (ex >= -1022 + 130 && ex <= 1023 - 130) return __dmul_rn(h, pow2(ex));
+  return ldexp(h, ex);
+}
+
+__device__ __forceinline__ i128 warp_sum_i128(i128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    u64 lo = (u64)v, hi = (u64)((u128)v >> 64);
+    u64 lo2 = __shfl_xor_sync(0xffffffffu, lo, o), hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    v += (i128)(((u128)hi2 << 64) | (u128)lo2);
+  }
+  return v;
 }
 
 __global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_t* __restrict__ eL,
@@ -92,29 +173,74 @@ __device__ u64 block_max_u64(u64 v, u64* red) {
 }
 
 // ---- lines 2-4 (inner part): one block per column j --------------------------------
-// smem: n double-doubles (V column)
+// smem: n double-doubles (V column).  x^T x is exact in integers (X1 lies on the grid
+// 2^(f_j + beta - 53)); x^T v is accumulated with TwoProduct/TwoSum (Dot2 form).
 __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
   extern __shared__ dd vcol[];
   __shared__ dd redd[32];
   __shared__ u64 redu[32];
+  __shared__ i128 redi[32];
   const int64_t j = blockIdx.x;
   const int64_t n = a.n;
   const int fj = a.f[j];
+  const int gj = fj + a.beta - 53;
   const double* x = a.X1 + j * a.ld1;
-  dd nn{0.0, 0.0}, dv{0.0, 0.0};
+  i128 nn_int = 0;
+  double s = 0.0, err = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     dd v = gather_dd(a.V, i, j, a.eA[i], fj);
     vcol[i] = v;
     if (a.Vh) a.Vh[i + j * n] = v.h;
     if (a.Vl) a.Vl[i + j * n] = v.l;
     double xi = x[i];
-    nn = dd_add(nn, two_prod(xi, xi));
-    dd q = two_prod(xi, v.h);
-    q.l = __dadd_rn(q.l, __dmul_rn(xi, v.l));
-    dv = dd_add(dv, q);
+    if (xi != 0.0) {
+      i64 P;
+      int q;
+      decompose(xi, P, q);
+      i64 m = q >= gj ? (P << (q - gj)) : (P >> (gj - q));
+      nn_int += (i128)m * (i128)m;
+    }
+    dd p = two_prod(xi, v.h);
+    dd t = two_sum(s, p.h);
+    s = t.h;
+    err = __dadd_rn(err, __dadd_rn(t.l, __dadd_rn(p.l, __dmul_rn(xi, v.l))));
   }
-  nn = block_sum_dd(nn, redd);
-  dv = block_sum_dd(dv, redd);
+  // block reductions
+  nn_int = warp_sum_i128(nn_int);
+  {
+    dd w{s, err};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double s2 = __shfl_xor_sync(0xffffffffu, w.h, o), e2 = __shfl_xor_sync(0xffffffffu, w.l, o);
+      dd t = two_sum(w.h, s2);
+      w = {t.h, __dadd_rn(__dadd_rn(w.l, e2), t.l)};
+    }
+    int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      redi[wi] = nn_int;
+      redd[wi] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int nw = blockDim.x >> 5;
+      i128 tot = 0;
+      dd acc{0.0, 0.0};
+      for (int k = 0; k < nw; ++k) {
+        tot += redi[k];
+        dd t = two_sum(acc.h, redd[k].h);
+        acc = {t.h, __dadd_rn(__dadd_rn(acc.l, redd[k].l), t.l)};
+      }
+      redi[0] = tot;
+      redd[0] = fast_two_sum(acc.h, acc.l);
+    }
+    __syncthreads();
+  }
+  const i128 nt = redi[0];
+  const dd dv = redd[0];
+  double nh = i128_to_double_rn(nt);
+  double nl = i128_to_double_rn(nt - double_to_i128(nh));
+  const double sc = pow2(2 * gj);
+  const dd nn{__dmul_rn(nh, sc), __dmul_rn(nl, sc)};
   const double lam = dd_div(dv, nn).h;
   const double r = dd_add_d(dd{-nn.h, -nn.l}, 1.0).h;
   if (threadIdx.x == 0) {
@@ -123,8 +249,10 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
   }
   u64 mx = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    dd v = vcol[i];
     dd p = two_prod(x[i], lam);
-    double res = dd_add(vcol[i], dd{-p.h, -p.l}).h;
+    dd t = two_sum(v.h, -p.h);
+    double res = __dadd_rn(t.h, __dadd_rn(t.l, __dsub_rn(v.l, p.l)));
     a.Res[i + j * a.ldr] = res;
     u64 ab = double_to_bits(res) & 0x7fffffffffffffffull;
     mx = ab > mx ? ab : mx;
@@ -140,7 +268,7 @@ __global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) {
     if (i == j) continue;
-    double w = gather_dd(a.W, i, j, a.f[i], a.h[j]).h;
+    double w = gather_d(a.W, i, j, a.f[i], a.h[j]);
     s += w * w;
   }
   s = block_sum_d(s, red);
@@ -164,7 +292,7 @@ __global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
   u64 mx = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     double e;
-    double w = (a.W.groups > 0) ? gather_dd(a.W, i, j, a.f[i], hj).h : 0.0;
+    double w = (a.W.groups > 0) ? gather_d(a.W, i, j, a.f[i], hj) : 0.0;
     if (a.Wout) a.Wout[i + j * n] = w;
     if (i == j) {
       e = a.r[j] * 0.5;
@@ -241,6 +369,7 @@ GroupArgs group_args(const PlaneGemm& g) {
   ga.ldo = g.ldo;
   ga.groups = g.groups;
   for (int k = 0; k < 8; ++k) ga.tlast[k] = k < g.groups ? group_last_t(g, k) : 0;
+  ga.exact128 = g.groups > 0 && DIGIT_BITS * (ga.tlast[g.groups - 1] - ga.tlast[0]) <= 63;
   return ga;
 }
 

@@ -10,6 +10,7 @@ struct GroupArgs {  // int64 anti-diagonal groups of one Ozaki product
   int64_t ogs, ldo;
   int groups;
   int tlast[8];
+  int exact128;  // all groups combine exactly in 128 bits: 7 (tlast[G-1] - tlast[0]) <= 63
 };
 
 struct ResidualArgs {
@@ -24,6 +25,7 @@ struct ResidualArgs {
   double* Res;           // out: V - X1 diag(lambda) rounded to FP64
   int64_t ldr;
   int32_t* h;            // out: column exponents of Res
+  int beta;              // X1 lies on the grid 2^(f_j + beta - 53)
   double* Vh;            // optional debug copies (ld = n)
   double* Vl;
 };
