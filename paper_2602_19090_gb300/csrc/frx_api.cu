@@ -68,7 +68,7 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   w.Xp = c.take<__nv_bfloat16>((size_t)8 * w.ps);
   w.Rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
   w.X1rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
-  w.groups = c.take<i64>((size_t)4 * n * n);
+  w.groups = c.take<i64>((size_t)8 * n * n);   // 64 bytes per entry: 8 int64 groups or 16 int32 planes
   w.bytes = c.off + 256;
   return w;
 }
@@ -236,6 +236,8 @@ PlaneGemm make_gemm(const __nv_bfloat16* L, int64_t Lps, const __nv_bfloat16* R,
   g.ogs = M * N;
   g.ldo = M;
   g.flags = nullptr;
+  g.word32 = 0;
+  g.out_bytes_per_elem = 64;
   g.tmax = g.gs = g.groups = 0;
   return g;
 }
@@ -286,7 +288,6 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   PlaneGemm gv = make_gemm(ws.Ap, ws.ps, ws.Xp, ws.ps, ws.pitch, n, n, n, kV, sX, kV + 1, ws.groups);
   gv.flags = ws.flags;
   FRX_TRY(plan_plane_gemm(gv));
-  if (gv.groups > 4) return FRX_E_UNSUPPORTED;
   FRX_TRY(launch_plane_gemm(gv, s));
 
   // S7/S8: r, lambda, Res (lines 2-4)
@@ -318,7 +319,6 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   if (kW > 0) {
     FRX_TRY(launch_slice_cols(ws.Res, n, n, n, ws.h, kW, ws.Rp, ws.ps, ws.pitch, s));
     FRX_TRY(plan_plane_gemm(gw));
-    if (gw.groups > 4) return FRX_E_UNSUPPORTED;
     FRX_TRY(launch_plane_gemm(gw, s));
   } else {
     gw.groups = 0;
@@ -373,7 +373,6 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
     FRX_TRY(launch_slice_rows(ws.X1, n, n, n, ws.rho, kU, ws.X1rp, ws.ps, ws.pitch, s));
     FRX_TRY(launch_slice_cols(ws.E, n, n, n, ws.eta, kU, ws.Rp, ws.ps, ws.pitch, s));
     FRX_TRY(plan_plane_gemm(gu));
-    if (gu.groups > 4) return FRX_E_UNSUPPORTED;
     FRX_TRY(launch_plane_gemm(gu, s));
   } else {
     gu.groups = 0;
@@ -608,6 +607,7 @@ int frx_slice_planes(const double* M, int64_t ld, int64_t rows, int64_t cols, in
 
 int frx_group_size(int kL, int kR, int T, int64_t K) {
   PlaneGemm g = make_gemm(nullptr, 0, nullptr, 0, 8, 1, 1, K, kL, kR, T, nullptr);
+  g.out_bytes_per_elem = 0;  // int64 groups only (any count): the documented format
   int st = plan_plane_gemm(g);
   return st < 0 ? st : g.gs;
 }
@@ -619,6 +619,7 @@ int frx_plane_products(const uint16_t* L, int64_t L_plane_stride, const uint16_t
   PlaneGemm g = make_gemm(reinterpret_cast<const __nv_bfloat16*>(L), L_plane_stride,
                           reinterpret_cast<const __nv_bfloat16*>(R), R_plane_stride, pitch, m, n, K, kL, kR, T,
                           reinterpret_cast<i64*>(out));
+  g.out_bytes_per_elem = 0;
   FRX_TRY(plan_plane_gemm(g));
   return launch_plane_gemm(g, (cudaStream_t)stream);
 }

@@ -37,9 +37,18 @@ int plan_plane_gemm(PlaneGemm& g) {
   unsigned long long smax = (unsigned long long)pmax * (unsigned long long)g.K * 4096ull;
   int bs = 64 - __builtin_clzll(smax);  // smax < 2^bs
   if (bs > 61) return FRX_E_UNSUPPORTED;
+  g.word32 = 0;
+  if (g.out_bytes_per_elem > 0 && smax < (1ull << 31) && (g.tmax - 1) * 4 <= g.out_bytes_per_elem) {
+    // one exact int32 plane per anti-diagonal (the layout of the 128 x 256 tensor-core tiles)
+    g.word32 = 1;
+    g.gs = 1;
+    g.groups = g.tmax - 1;
+    return FRX_OK;
+  }
   g.gs = (61 - bs) / 7 + 1;
   g.groups = (g.tmax - 1 + g.gs - 1) / g.gs;
-  if (g.groups > 8) return FRX_E_UNSUPPORTED;
+  // out_bytes_per_elem == 0: int64 groups in a buffer the caller sized from frx_group_size
+  if (g.out_bytes_per_elem > 0 && g.groups * 8 > g.out_bytes_per_elem) return FRX_E_UNSUPPORTED;
   return FRX_OK;
 }
 
@@ -141,7 +150,11 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         int64_t i = i0 + ty * 4 + a;
-        if (i < g.M) g.out[grp * g.ogs + j * g.ldo + i] = racc[a][b];
+        if (i >= g.M) continue;
+        if (g.word32)
+          g.out32()[grp * g.ogs + j * g.ldo + i] = (int32_t)racc[a][b];
+        else
+          g.out[grp * g.ogs + j * g.ldo + i] = racc[a][b];
       }
     }
   }

@@ -9,17 +9,21 @@
 // anti-diagonal t) and the int64 sums are combined in Horner form per group:
 //   R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
 //
-// CTA = one 128 x 128 output tile.  Warp roles:
+// CTA = one 128 x BN output tile (BN = 256 with int32 per-t planes, else 128 with
+// int64 groups).  Warp roles:
 //   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
 //   warp 1       TMEM allocator and single-thread MMA issuer
 //   warps 2..9   epilogue: tcgen05.ld of the FP32 accumulator, exact int64 sums
-// Pipeline: STAGES smem stages (A 16 KB + B 16 KB), two TMEM accumulators of 128
+// Pipeline: 4-6 smem stages (A 16 KB + B BN * 128 bytes), two TMEM accumulators of BN
 // columns each.  Every mbarrier wait is bounded by the global timer; on expiry the
 // CTA raises FLAG_TIMEOUT, drains what it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <stdlib.h>
+
 #include <mutex>
+#include <type_traits>
 
 #include "frx_internal.cuh"
 #include "kernels.cuh"
@@ -28,21 +32,18 @@
 namespace frx {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;   // BK bf16 = 128 bytes = one swizzle row
-constexpr int STAGES = 6;
+constexpr int BM = 128, BK = 64;   // BK bf16 = 128 bytes = one swizzle row
+constexpr int MAX_STAGES = 6;
 constexpr int CHUNK_KB = 32;                 // 32 * 64 = 2048 products per accumulation
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = 32 * (2 + NUM_EPI_WARPS);
 constexpr uint32_t STAGE_A_BYTES = BM * BK * 2;
-constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
-constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
 struct Smem {
   // tiles first (1024-byte aligned by the dynamic smem base adjustment)
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
   uint64_t drain;
@@ -122,15 +123,17 @@ __device__ __forceinline__ uint64_t smem_desc(const void* tile) {
   return d;
 }
 
-// kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = BN
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = bn
+__host__ __device__ constexpr uint32_t idesc_for(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -158,7 +161,7 @@ struct TcArgs {
   int64_t M, N;
   int nkb;       // k-blocks of 64
   int kL, kR, tmax, gs, groups;
-  i64* out;
+  void* out;     // int64 groups, or int32 per-t planes when W32
   int64_t ogs, ldo;
   int* flags;
 };
@@ -166,15 +169,25 @@ struct TcArgs {
 __device__ __forceinline__ int pair_lo(int t, int kR) { return t - kR > 1 ? t - kR : 1; }
 __device__ __forceinline__ int pair_hi(int t, int kL) { return kL < t - 1 ? kL : t - 1; }
 
+// BN_ = 128: int64 Horner groups of gs anti-diagonals, 64 columns per epilogue thread.
+// BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
+template <int BN_, bool W32>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR, TcArgs a) {
+  constexpr int BN = BN_;
+  constexpr int STAGES = BN == 256 ? 4 : 6;
+  constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
+  constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t IDESC = idesc_for(BN);
+  constexpr int NCOL = BN / 2;   // columns per epilogue thread
+  typedef typename std::conditional<W32, int, i64>::type Acc;
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
   unsigned char* tiles = base;
   Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&sm->full[s], 1);
@@ -207,7 +220,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       long long issued = 0;
-      bool ok = true;
+      bool ok = !*abort;
       for (int grp = 0; grp < a.groups && ok; ++grp) {
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
@@ -231,7 +244,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
       }
-      if (!ok) {
+      if (ok) {
+        // every consumer (local MMA and, in a cluster, the peers') has released the stages
+        // this CTA's copies filled: no arrival can target this CTA's barriers after it exits
+        for (int q = 0; q < STAGES; ++q) {
+          if (!mbar_wait(&sm->empty[stage], phase ^ 1, abort, a.flags)) break;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      } else {
         // let the copies this thread issued land before the CTA exits (bounded)
         unsigned long long t0 = gtimer();
         long long back = issued < STAGES ? issued : STAGES;
@@ -281,7 +304,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               uint32_t d = tmem + (uint32_t)(buf * BN);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), (cnt > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), IDESC, (cnt > 0 || kk > 0) ? 1u : 0u);
               mma_commit(&sm->empty[stage]);
               any = true;
               if (++stage == STAGES) {
@@ -312,11 +335,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // ---------------- epilogue ----------------
     const int ew = warp - 2;                 // 0..7
     const int quad = warp & 3;               // TMEM lanes 32*quad .. +31 (warp % 4 rule)
-    const int col0 = (ew >> 2) * 64;         // columns [col0, col0 + 64)
+    const int col0 = (ew >> 2) * NCOL;       // columns [col0, col0 + NCOL)
     const int64_t row = (int64_t)i0 + quad * 32 + lane;
-    i64 R[64];
+    Acc R[NCOL];
 #pragma unroll
-    for (int c = 0; c < 64; ++c) R[c] = 0;
+    for (int c = 0; c < NCOL; ++c) R[c] = 0;
     int buf = 0;
     uint32_t acc_phase[2] = {0, 0};
     bool ok = true;
@@ -325,8 +348,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       for (int t = t0; t <= t1 && ok; ++t) {
         int total = (pair_hi(t, a.kL) - pair_lo(t, a.kR) + 1) * a.nkb;
         int chunks = (total + CHUNK_KB - 1) / CHUNK_KB;
+        if constexpr (!W32) {
 #pragma unroll
-        for (int c = 0; c < 64; ++c) R[c] <<= 7;
+          for (int c = 0; c < NCOL; ++c) R[c] <<= 7;
+        }
         for (int ch = 0; ch < chunks; ++ch) {
           if (!mbar_wait(&sm->acc_full[buf], acc_phase[buf], abort, a.flags)) {
             ok = false;
@@ -335,11 +360,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           fence_after();
           uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + col0);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < NCOL / 32; ++h) {
             uint32_t v[32];
             tmem_ld32(taddr + h * 32, v);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) R[h * 32 + c] += (i64)__float2int_rn(__uint_as_float(v[c]));
+            for (int c = 0; c < 32; ++c) R[h * 32 + c] += (Acc)__float2int_rn(__uint_as_float(v[c]));
           }
           fence_before();
           __syncwarp();
@@ -350,15 +375,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       if (!ok) break;
       if (row < a.M) {
-        i64* o = a.out + grp * a.ogs + row;
+        Acc* o = reinterpret_cast<Acc*>(a.out) + grp * a.ogs + row;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
+        for (int c = 0; c < NCOL; ++c) {
           int64_t j = (int64_t)j0 + col0 + c;
           if (j < a.N) o[j * a.ldo] = R[c];
         }
       }
 #pragma unroll
-      for (int c = 0; c < 64; ++c) R[c] = 0;
+      for (int c = 0; c < NCOL; ++c) R[c] = 0;
     }
   }
   fence_before();
@@ -396,7 +421,10 @@ bool make_map(CUtensorMap* m, const void* base, int64_t K, int64_t rows, int pla
   return r == CUDA_SUCCESS;
 }
 
-size_t smem_bytes() { return (size_t)STAGES * STAGE_BYTES + sizeof(Smem) + 1024; }
+size_t smem_bytes(int bn) {
+  int stages = bn == 256 ? 4 : 6;
+  return (size_t)stages * (STAGE_A_BYTES + (size_t)bn * BK * 2) + sizeof(Smem) + 1024;
+}
 
 }  // namespace
 
@@ -408,10 +436,25 @@ bool plane_gemm_tc_supported(const PlaneGemm& g) {
   return get_encode() != nullptr;
 }
 
-int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
+template <int BN, bool W32>
+int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   CUtensorMap mL, mR;
   if (!make_map(&mL, g.L, g.K, g.M, g.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
   if (!make_map(&mR, g.R, g.K, g.N, g.kR, g.pitch, g.Rps, BN)) return FRX_E_CUDA;
+  size_t smem = smem_bytes(BN);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&]() {
+    attr_err = cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  FRX_CUDA_TRY(attr_err);
+  dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
+  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
@@ -421,21 +464,12 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
   a.tmax = g.tmax;
   a.gs = g.gs;
   a.groups = g.groups;
-  a.out = g.out;
+  a.out = (void*)g.out;
   a.ogs = g.ogs;
   a.ldo = g.ldo;
   a.flags = flags;
-  size_t smem = smem_bytes();
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&]() {
-    attr_err = cudaFuncSetAttribute(k_plane_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  FRX_CUDA_TRY(attr_err);
-  dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
-  k_plane_gemm_tc<<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
-  FRX_CUDA_TRY(cudaGetLastError());
-  return FRX_OK;
+  if (g.word32) return launch_variant<256, true>(g, a, s);
+  return launch_variant<128, false>(g, a, s);
 }
 
 }  // namespace frx

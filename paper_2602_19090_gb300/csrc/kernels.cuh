@@ -34,9 +34,14 @@ struct PlaneGemm {
   int64_t M, N, K;
   int kL, kR, T;
   int tmax, gs, groups;
-  i64* out;
+  i64* out;     // int64 groups (word32 == 0) ...
   int64_t ogs, ldo;
   int* flags;   // device status word (timeouts), may be null
+  // int32 per-anti-diagonal planes: plane t - 2 at (int32_t*)out + (t - 2) * ogs (gs = 1).
+  // Chosen by plan_plane_gemm when every S_t fits int32 and `out_bytes_per_elem` holds them.
+  int word32;
+  int out_bytes_per_elem;
+  __host__ __device__ int32_t* out32() const { return reinterpret_cast<int32_t*>(out); }
 };
 
 // host: fill tmax / gs / groups; returns FRX_E_UNSUPPORTED if exactness cannot be guaranteed
@@ -54,10 +59,6 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s);
 bool plane_gemm_tc_supported(const PlaneGemm& g);
 
 // refine_kernels.cu
-struct GroupScales {
-  int groups;
-  int tlast[8];
-};
 int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR, double* Ch, int64_t ldh,
                         double* Cl, int64_t ldl, cudaStream_t s);
 

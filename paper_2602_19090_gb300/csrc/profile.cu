@@ -49,7 +49,7 @@ GemmTimer::GemmTimer(const PlaneGemm& g, cudaStream_t s) : s_(s) {
     if (hi >= lo) pairs += hi - lo + 1;
   }
   gemm_ops += 2.0 * (double)g.M * (double)g.N * (double)g.K * pairs;
-  gemm_bytes += 2.0 * (double)g.K * ((double)g.M * g.kL + (double)g.N * g.kR) + 8.0 * g.groups * (double)g.M * g.N;
+  gemm_bytes += 2.0 * (double)g.K * ((double)g.M * g.kL + (double)g.N * g.kR) + (g.word32 ? 4.0 : 8.0) * g.groups * (double)g.M * g.N;
   if (enabled) {
     a_ = get_event();
     b_ = get_event();

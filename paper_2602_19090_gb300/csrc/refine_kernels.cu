@@ -15,13 +15,23 @@ typedef unsigned __int128 u128;
 
 // value of entry (i, j) of an Ozaki product from its int64 groups (least significant first),
 // as a double-double; general path (any number of groups)
+__device__ __forceinline__ int tlast_of(const GroupArgs& ga, int g) {
+  int t1 = 2 + (g + 1) * ga.gs - 1;
+  return t1 < ga.tmax ? t1 : ga.tmax;
+}
+
+__device__ __forceinline__ i64 group_word(const GroupArgs& ga, int g, int64_t i, int64_t j) {
+  int64_t idx = g * ga.ogs + j * ga.ldo + i;
+  return ga.word32 ? (i64) reinterpret_cast<const int32_t*>(ga.out)[idx] : reinterpret_cast<const i64*>(ga.out)[idx];
+}
+
 __device__ __forceinline__ dd gather_dd_general(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
   dd acc{0.0, 0.0};
   if (eLi == EZERO || eRj == EZERO) return acc;
   for (int g = ga.groups - 1; g >= 0; --g) {
-    i64 R = ga.out[g * ga.ogs + j * ga.ldo + i];
+    i64 R = group_word(ga, g, i, j);
     if (R == 0) continue;
-    acc = dd_add(acc, i64_to_dd_scaled(R, eLi + eRj + 2 - DIGIT_BITS * ga.tlast[g]));
+    acc = dd_add(acc, i64_to_dd_scaled(R, eLi + eRj + 2 - DIGIT_BITS * tlast_of(ga, g)));
   }
   return acc;
 }
@@ -63,8 +73,8 @@ __device__ __forceinline__ i128 double_to_i128(double h) {
 __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, int64_t j) {
   i128 N = 0;
   for (int g = 0; g < ga.groups; ++g) {
-    if (g) N <<= DIGIT_BITS * (ga.tlast[g] - ga.tlast[g - 1]);
-    N += (i128)ga.out[g * ga.ogs + j * ga.ldo + i];
+    if (g) N <<= DIGIT_BITS * (tlast_of(ga, g) - tlast_of(ga, g - 1));
+    N += (i128)group_word(ga, g, i, j);
   }
   return N;
 }
@@ -75,7 +85,7 @@ __device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t 
   i128 N = combine_groups(ga, i, j);
   double h = i128_to_double_rn(N);
   double l = i128_to_double_rn(N - double_to_i128(h));
-  int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tlast[ga.groups - 1];
+  int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tmax;
   if (ex >= -1022 + 130 && ex <= 1023 - 130) {
     double sc = pow2(ex);
     return {__dmul_rn(h, sc), __dmul_rn(l, sc)};
@@ -88,7 +98,7 @@ __device__ __forceinline__ double gather_d(const GroupArgs& ga, int64_t i, int64
   if (!ga.exact128) return gather_dd_general(ga, i, j, eLi, eRj).h;
   if (eLi == EZERO || eRj == EZERO || ga.groups == 0) return 0.0;
   double h = i128_to_double_rn(combine_groups(ga, i, j));
-  int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tlast[ga.groups - 1];
+  int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tmax;
   if (ex >= -1022 + 130 && ex <= 1023 - 130) return __dmul_rn(h, pow2(ex));
   return ldexp(h, ex);
 }
@@ -368,8 +378,13 @@ GroupArgs group_args(const PlaneGemm& g) {
   ga.ogs = g.ogs;
   ga.ldo = g.ldo;
   ga.groups = g.groups;
-  for (int k = 0; k < 8; ++k) ga.tlast[k] = k < g.groups ? group_last_t(g, k) : 0;
-  ga.exact128 = g.groups > 0 && DIGIT_BITS * (ga.tlast[g.groups - 1] - ga.tlast[0]) <= 63;
+  ga.gs = g.gs;
+  ga.tmax = g.tmax;
+  ga.word32 = g.word32;
+  // |R_g| < 2^31 (int32 planes) or 2^62 (int64 groups); the combination spans
+  // 7 (tmax - t_last(0)) more bits and must stay below 2^127
+  int span = g.groups > 0 ? DIGIT_BITS * (g.tmax - group_last_t(g, 0)) : 0;
+  ga.exact128 = g.groups > 0 && (g.word32 ? 31 : 62) + span + 1 <= 127;
   return ga;
 }
 

@@ -5,12 +5,12 @@
 
 namespace frx {
 
-struct GroupArgs {  // int64 anti-diagonal groups of one Ozaki product
-  const i64* out;
+struct GroupArgs {  // exact anti-diagonal sums of one Ozaki product (int64 groups or int32 planes)
+  const void* out;
   int64_t ogs, ldo;
-  int groups;
-  int tlast[8];
-  int exact128;  // all groups combine exactly in 128 bits: 7 (tlast[G-1] - tlast[0]) <= 63
+  int groups, gs, tmax;
+  int word32;
+  int exact128;  // all groups combine exactly in 128 bits
 };
 
 struct ResidualArgs {

@@ -67,3 +67,26 @@ def test_tc_worst_case_digits(api):
     gs = api.group_size(3, 3, 6, K)
     t_last = min(2 + gs - 1, 6)
     assert ref[0, 0, 0] == 64 * 64 * K * 2 ** (7 * (t_last - 2))
+
+
+@pytest.mark.parametrize("m,k,n,slices,mode", [(300, 513, 260, 6, "full"), (1024, 2048, 512, 8, "triangular"),
+                                               (129, 4100, 257, 5, "full")])
+def test_ozaki_gemm_tensor_core_equals_cuda_core(api, m, k, n, slices, mode):
+    # exercises the 128 x 256 tiles with one int32 plane per anti-diagonal
+    import torch
+    from tests import gpu_util as g
+    A = g.to_dev(synth.gemm_operand(m, k, 2.0, 700 + m))
+    B = g.to_dev(synth.gemm_operand(k, n, 2.0, 800 + n))
+    old = os.environ.get("FRX_GEMM")
+    try:
+        os.environ["FRX_GEMM"] = "simt"
+        ch0, cl0 = api.ozaki_gemm(A, B, slices, mode, return_lo=True)
+        os.environ["FRX_GEMM"] = "tc"
+        ch1, cl1 = api.ozaki_gemm(A, B, slices, mode, return_lo=True)
+        torch.cuda.synchronize()
+    finally:
+        if old is None:
+            os.environ.pop("FRX_GEMM", None)
+        else:
+            os.environ["FRX_GEMM"] = old
+    assert torch.equal(ch0, ch1) and torch.equal(cl0, cl1)
