@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--delta", type=float, default=1e-14)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sample-rows", type=int, default=8)
+    p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     return p.parse_args()
 
 
@@ -238,6 +239,29 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(Xo_h.numel() * 8 + Do_h.numel() * 8)},
         "clocks": clk,
     }
+    if not args.no_fp64:
+        # comparator: the same refinement with native FP64 products (cuBLAS DGEMM), timed once
+        from paper_2602_19090_gb300 import fp64_refine
+        Xr = X0t.clone()
+        torch.cuda.synchronize()
+        (torch.ones(64, 64, dtype=torch.float64, device=dev) @ torch.ones(64, 64, dtype=torch.float64, device=dev))
+        torch.cuda.synchronize()
+        s3 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        s3.record()
+        Xb, lamb, ib = fp64_refine.refine(At, Xr, D0t, delta)
+        e3.record()
+        torch.cuda.synchronize()
+        b1_ms = allmax(ws, s3.elapsed_time(e3))
+        X.copy_(X0t)
+        D.copy_(D0t)
+        api.refine(At, X, D, delta, opts, work=work)
+        diff = (Xb - X).abs().max().item()
+        line["fp64_refine"] = {"seconds": b1_ms / 1e3, "status": ib["status"], "iters": ib["iters"],
+                               "dgemms": ib["products"], "n_A": ib["nA"], "err_est": ib["err_est"],
+                               "speedup_ours_vs_fp64": b1_ms / ms,
+                               "max_abs_diff_X_vs_ours": diff,
+                               "note": "paper's FP64 slicing (Sec. 4.1 alpha, beta) with cuBLAS DGEMM on the same GPU"}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], args.sample_rows)
     if rank == 0:

@@ -228,3 +228,14 @@ def test_refine_rejects_bad_input(api):
     with pytest.raises(api.FrxError) as ex:
         api.refine(At, Xt, Dt, 1e-12, work=work)
     assert ex.value.status == -5
+
+
+def test_fp64_comparator_reaches_delta():
+    import torch
+    from paper_2602_19090_gb300 import fp64_refine
+    g = G()
+    A, X0, D0 = synth.workload0()
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    X, lam, info = fp64_refine.refine(g.to_dev(A), g.to_dev(X0), g.to_dev(D0), 1e-14)
+    assert info["status"] == "converged"
+    assert tr.forward_error(Xh, Xl, X.cpu().numpy()) <= 1e-14
