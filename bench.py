@@ -214,7 +214,9 @@ def run_ours(args):
     e2e_ms = allmax(ws, s2.elapsed_time(e2)) / args.steps
 
     pk, src = peaks()
-    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    # the GEMM launches run in bursts of a few ms inside a ~30 ms step, far from the
+    # seconds-long power-capped loop of the sustained figure: use the burst peak
+    peak = pk.get("bf16_tflops")
     achieved = prof["gemm_ops"] / (prof["gemm_ms"] * 1e-3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -232,7 +234,7 @@ def run_ours(args):
         "roofline": {"bound": "tensor", "kernel": "slice-product GEMM (digit planes)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
-                     "peak_source": f"{src} bf16_tflops_sustained",
+                     "peak_source": f"{src} bf16_tflops (burst; sustained {pk.get('bf16_tflops_sustained')})",
                      "gemm_share_of_step": prof["gemm_ms"] / (ms * args.steps) if ms else None},
         "gpu_launches": prof["kernel_launches"],
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(A_h.numel() * 8 + X0_h.numel() * 8 + D0_h.numel() * 8),

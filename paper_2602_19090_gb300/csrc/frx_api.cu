@@ -389,6 +389,8 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   ua.U = group_args(gu);
   ua.rho = ws.rho;
   ua.eta = ws.eta;
+  ua.f = ws.f;
+  ua.beta = beta;
   ua.X1 = ws.X1;
   ua.ld1 = n;
   ua.X = X;

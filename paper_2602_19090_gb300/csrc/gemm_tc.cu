@@ -9,8 +9,9 @@
 // anti-diagonal t) and the int64 sums are combined in Horner form per group:
 //   R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
 //
-// CTA = one 128 x BN output tile (BN = 256 with int32 per-t planes, else 128 with
-// int64 groups).  Warp roles:
+// Persistent: one CTA per SM walks the units (output tile of 128 x BN, group of
+// anti-diagonals) in a static round-robin, groups ordered by decreasing work.  BN = 256
+// with int32 per-t planes, else 128 with int64 groups.  Warp roles:
 //   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
 //   warp 1       TMEM allocator and single-thread MMA issuer
 //   warps 2..9   epilogue: tcgen05.ld of the FP32 accumulator, exact int64 sums
@@ -22,6 +23,7 @@
 
 #include <stdlib.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -164,6 +166,11 @@ struct TcArgs {
   void* out;     // int64 groups, or int32 per-t planes when W32
   int64_t ogs, ldo;
   int* flags;
+  // persistent schedule: unit u = (group gorder[u / tiles], tile u % tiles), tiles = ntm * ntn,
+  // groups ordered by decreasing work so a static round-robin over CTAs stays balanced
+  int ntm, ntn;
+  int units;
+  int gorder[32];
 };
 
 __device__ __forceinline__ int pair_lo(int t, int kR) { return t - kR > 1 ? t - kR : 1; }
@@ -184,10 +191,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   typedef typename std::conditional<W32, int, i64>::type Acc;
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
-  unsigned char* tiles = base;
+  unsigned char* tiles_smem = base;
   Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&sm->full[s], 1);
@@ -221,7 +227,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       long long issued = 0;
       bool ok = !*abort;
-      for (int grp = 0; grp < a.groups && ok; ++grp) {
+      const int tiles = a.ntm * a.ntn;
+      for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+        const int grp = a.gorder[u / tiles], tile = u % tiles;
+        const int i0 = (tile / a.ntn) * BM, j0 = (tile % a.ntn) * BN;
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           for (int r = pair_lo(t, a.kR); r <= pair_hi(t, a.kL) && ok; ++r) {
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 ok = false;
                 break;
               }
-              unsigned char* st = tiles + stage * STAGE_BYTES;
+              unsigned char* st = tiles_smem + stage * STAGE_BYTES;
               mbar_expect_tx(&sm->full[stage], STAGE_BYTES);
               tma_load_3d(st, &mapL, kb * BK, i0, r - 1, &sm->full[stage]);
               tma_load_3d(st + STAGE_A_BYTES, &mapR, kb * BK, j0, s - 1, &sm->full[stage]);
@@ -279,7 +288,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t acc_phase[2] = {0, 0};
       bool ok = true;
       bool any = false;
-      for (int grp = 0; grp < a.groups && ok; ++grp) {
+      const int tiles = a.ntm * a.ntn;
+      for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+        const int grp = a.gorder[u / tiles];
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           int rlo = pair_lo(t, a.kR), rhi = pair_hi(t, a.kL);
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 break;
               }
               fence_after();
-              unsigned char* st = tiles + stage * STAGE_BYTES;
+              unsigned char* st = tiles_smem + stage * STAGE_BYTES;
               uint64_t da = smem_desc(st), db = smem_desc(st + STAGE_A_BYTES);
               uint32_t d = tmem + (uint32_t)(buf * BN);
 #pragma unroll
@@ -336,14 +347,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int ew = warp - 2;                 // 0..7
     const int quad = warp & 3;               // TMEM lanes 32*quad .. +31 (warp % 4 rule)
     const int col0 = (ew >> 2) * NCOL;       // columns [col0, col0 + NCOL)
-    const int64_t row = (int64_t)i0 + quad * 32 + lane;
     Acc R[NCOL];
 #pragma unroll
     for (int c = 0; c < NCOL; ++c) R[c] = 0;
     int buf = 0;
     uint32_t acc_phase[2] = {0, 0};
     bool ok = true;
-    for (int grp = 0; grp < a.groups && ok; ++grp) {
+    const int tiles = a.ntm * a.ntn;
+    for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+      const int grp = a.gorder[u / tiles], tile = u % tiles;
+      const int i0 = (tile / a.ntn) * BM, j0 = (tile % a.ntn) * BN;
+      const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
       for (int t = t0; t <= t1 && ok; ++t) {
         int total = (pair_hi(t, a.kL) - pair_lo(t, a.kR) + 1) * a.nkb;
@@ -448,8 +462,30 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
     attr_err = cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   FRX_CUDA_TRY(attr_err);
-  dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
-  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  TcArgs b = a;
+  b.ntm = (int)((g.M + BM - 1) / BM);
+  b.ntn = (int)((g.N + BN - 1) / BN);
+  b.units = b.ntm * b.ntn * g.groups;
+  // groups by decreasing work (pairs summed over their anti-diagonals), ties by group index
+  int work[32];
+  for (int q = 0; q < g.groups; ++q) {
+    int t0 = 2 + q * g.gs, t1 = t0 + g.gs - 1 < g.tmax ? t0 + g.gs - 1 : g.tmax, w = 0;
+    for (int t = t0; t <= t1; ++t) {
+      int lo = t - g.kR > 1 ? t - g.kR : 1, hi = g.kL < t - 1 ? g.kL : t - 1;
+      w += hi - lo + 1;
+    }
+    work[q] = w;
+    b.gorder[q] = q;
+  }
+  std::stable_sort(b.gorder, b.gorder + g.groups, [&](int x, int y) { return work[x] > work[y]; });
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    FRX_CUDA_TRY(cudaGetDevice(&dev));
+    FRX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  unsigned grid = (unsigned)(b.units < sms ? b.units : sms);
+  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, b);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }

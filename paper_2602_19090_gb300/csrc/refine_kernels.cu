@@ -103,6 +103,27 @@ __device__ __forceinline__ double gather_d(const GroupArgs& ga, int64_t i, int64
   return ldexp(h, ex);
 }
 
+__device__ __forceinline__ int bitlen128(i128 v) {
+  u128 a = v < 0 ? (u128)(-v) : (u128)v;
+  return a == 0 ? 0 : 128 - clz128(a);
+}
+
+// RN(S * 2^ex) for an exact 128-bit S
+__device__ __forceinline__ double i128_scaled_rn(i128 S, int ex) {
+  double h = i128_to_double_rn(S);
+  if (ex >= -1022 + 130 && ex <= 1023 - 130) return __dmul_rn(h, pow2(ex));
+  return ldexp(h, ex);
+}
+
+// integer m with x = m * 2^G (x on the grid 2^G, |m| < 2^62)
+__device__ __forceinline__ i64 grid_mantissa(double x, int G) {
+  if (x == 0.0) return 0;
+  i64 P;
+  int q;
+  decompose(x, P, q);
+  return q >= G ? (P << (q - G)) : (P >> (G - q));
+}
+
 __device__ __forceinline__ i128 warp_sum_i128(i128 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -195,21 +216,34 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
   const int fj = a.f[j];
   const int gj = fj + a.beta - 53;
   const double* x = a.X1 + j * a.ld1;
+  const bool exact = a.V.exact128 != 0;
+  i128* ncol = reinterpret_cast<i128*>(vcol);   // exact V entries when exact128
   i128 nn_int = 0;
   double s = 0.0, err = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    dd v = gather_dd(a.V, i, j, a.eA[i], fj);
-    vcol[i] = v;
+    dd v;
+    int ei = a.eA[i];
+    if (exact) {
+      i128 N = (ei == EZERO || a.V.groups == 0) ? (i128)0 : combine_groups(a.V, i, j);
+      ncol[i] = N;
+      int ex = ei + fj + 2 - DIGIT_BITS * a.V.tmax;
+      double h = i128_to_double_rn(N);
+      double l = i128_to_double_rn(N - double_to_i128(h));
+      if (ex >= -1022 + 130 && ex <= 1023 - 130) {
+        double sc = pow2(ex);
+        v = {__dmul_rn(h, sc), __dmul_rn(l, sc)};
+      } else {
+        v = {ldexp(h, ex), ldexp(l, ex)};
+      }
+    } else {
+      v = gather_dd(a.V, i, j, ei, fj);
+      vcol[i] = v;
+    }
     if (a.Vh) a.Vh[i + j * n] = v.h;
     if (a.Vl) a.Vl[i + j * n] = v.l;
     double xi = x[i];
-    if (xi != 0.0) {
-      i64 P;
-      int q;
-      decompose(xi, P, q);
-      i64 m = q >= gj ? (P << (q - gj)) : (P >> (gj - q));
-      nn_int += (i128)m * (i128)m;
-    }
+    i64 m = grid_mantissa(xi, gj);
+    nn_int += (i128)m * (i128)m;
     dd p = two_prod(xi, v.h);
     dd t = two_sum(s, p.h);
     s = t.h;
@@ -257,12 +291,40 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     a.lam[j] = lam;
     a.r[j] = r;
   }
+  i64 L = 0;
+  int qL = 0;
+  if (lam != 0.0) decompose(lam, L, qL);
   u64 mx = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    dd v = vcol[i];
-    dd p = two_prod(x[i], lam);
-    dd t = two_sum(v.h, -p.h);
-    double res = __dadd_rn(t.h, __dadd_rn(t.l, __dsub_rn(v.l, p.l)));
+    double xi = x[i];
+    double res;
+    bool done = false;
+    if (exact) {
+      // Res = N 2^c - (m L) 2^(gj + qL), exact in 128 bits after alignment
+      int ei = a.eA[i];
+      i128 N = ncol[i];
+      i128 ML = (i128)grid_mantissa(xi, gj) * (i128)L;
+      int c = ei + fj + 2 - DIGIT_BITS * a.V.tmax;
+      int d = (gj + qL) - c;
+      if (ei == EZERO) {
+        N = 0;
+        d = 0;
+        c = gj + qL;
+      }
+      if (d >= 0 && bitlen128(ML) + d <= 125 && bitlen128(N) <= 125) {
+        res = i128_scaled_rn(N - (ML << d), c);
+        done = true;
+      } else if (d < 0 && bitlen128(N) - d <= 125 && bitlen128(ML) <= 125) {
+        res = i128_scaled_rn((N << (-d)) - ML, gj + qL);
+        done = true;
+      }
+    }
+    if (!done) {
+      dd v = exact ? gather_dd_general(a.V, i, j, a.eA[i], fj) : vcol[i];
+      dd p = two_prod(xi, lam);
+      dd t = two_sum(v.h, -p.h);
+      res = __dadd_rn(t.h, __dadd_rn(t.l, __dsub_rn(v.l, p.l)));
+    }
     a.Res[i + j * a.ldr] = res;
     u64 ab = double_to_bits(res) & 0x7fffffffffffffffull;
     mx = ab > mx ? ab : mx;
@@ -357,10 +419,29 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
     double x1 = a.X1[i + j * a.ld1];
     double xn = x1;
     if (a.U.groups > 0) {
-      dd u = gather_dd(a.U, i, j, a.rho[i], a.eta[j]);
-      dd c = two_sum(x1, u.h);
-      double cl = __dadd_rn(u.l, c.l);
-      xn = __dadd_rn(c.h, cl);
+      bool done = false;
+      int ri = a.rho[i], ej = a.eta[j];
+      if (a.U.exact128 && ri != EZERO && ej != EZERO) {
+        // RN(x1 + U) with x1 = m 2^G and U = N 2^c, combined exactly in 128 bits
+        i128 N = combine_groups(a.U, i, j);
+        int G = a.f[j] + a.beta - 53;
+        int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
+        i128 m = (i128)grid_mantissa(x1, G);
+        int d = G - c;
+        if (d >= 0 && bitlen128(m) + d <= 124 && bitlen128(N) <= 124) {
+          xn = i128_scaled_rn((m << d) + N, c);
+          done = true;
+        } else if (d < 0 && bitlen128(N) - d <= 124) {
+          xn = i128_scaled_rn(m + (N << (-d)), G);
+          done = true;
+        }
+      }
+      if (!done) {
+        dd u = gather_dd(a.U, i, j, ri, ej);
+        dd c2 = two_sum(x1, u.h);
+        double cl = __dadd_rn(u.l, c2.l);
+        xn = __dadd_rn(c2.h, cl);
+      }
     }
     double xo = a.X[i + j * a.ldx];
     double dx = __dsub_rn(xn, xo);

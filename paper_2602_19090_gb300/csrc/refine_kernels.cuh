@@ -54,6 +54,8 @@ struct UpdateArgs {
   GroupArgs U;           // U = X1 E~: left exponents rho (rows of X1), right eta
   const int32_t* rho;
   const int32_t* eta;
+  const int32_t* f;      // X1 lies on the grid 2^(f_j + beta - 53)
+  int beta;
   const double* X1;
   int64_t ld1;
   double* X;             // in: X_old, out: X_new
