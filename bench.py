@@ -121,6 +121,23 @@ def allmax(ws, x):
     return float(t.item())
 
 
+def gemm_traffic():
+    """Per-launch DRAM bytes of the GEMM from the committed ncu summary, if the kernel is unchanged."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_2602_19090_gb300", "csrc", "gemm_tc.cu")
+    md = os.path.join(ROOT, "profiles", "plane_gemm_tc256_n4096_traffic.md")
+    if not (os.path.exists(src) and os.path.exists(md)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    txt = open(md).read()
+    m1 = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
+    m2 = re.search(r"kernel_source_sha256_16: (\w+)", txt)
+    if m1 and m2 and m2.group(1) == sha:
+        return int(m1.group(1))
+    return None
+
+
 def cpu_oracle_sample(A, X0, D0, delta, total_products, rows):
     """Times the CPU oracle on a bounded sample and extrapolates to one full refinement.
 
@@ -233,7 +250,7 @@ def run_ours(args):
         "refinements_per_s": ws * 1e3 / ms,
         "roofline": {"bound": "tensor", "kernel": "slice-product GEMM (digit planes)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None, "traffic": gemm_traffic(),
                      "peak_source": f"{src} bf16_tflops (burst; sustained {pk.get('bf16_tflops_sustained')})",
                      "gemm_share_of_step": prof["gemm_ms"] / (ms * args.steps) if ms else None},
         "gpu_launches": prof["kernel_launches"],
