@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sample-rows", type=int, default=8)
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
+    p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
     return p.parse_args()
 
 
@@ -281,6 +282,43 @@ def run_ours(args):
                                "speedup_ours_vs_fp64": b1_ms / ms,
                                "max_abs_diff_X_vs_ours": diff,
                                "note": "paper's FP64 slicing (Sec. 4.1 alpha, beta) with cuBLAS DGEMM on the same GPU"}
+    if not args.no_gemm:
+        # Ozaki GEMM alone (operands N(0,1) * exp(2 N(0,1)), 8 slices per operand): TFLOPS-eq = 2 n^3 / t
+        from paper_2602_19090_gb300 import synth as _syn
+        Ag = torch.from_numpy(_syn.gemm_operand(n, n, 2.0, 1001)).to(dev)
+        Bg = torch.from_numpy(_syn.gemm_operand(n, n, 2.0, 1002)).to(dev)
+        Agc, _, _ = api.colmajor(Ag)
+        Bgc, _, _ = api.colmajor(Bg)
+        ref = (Agc @ Bgc)
+        torch.cuda.synchronize()
+        s5 = torch.cuda.Event(enable_timing=True)
+        e5 = torch.cuda.Event(enable_timing=True)
+        s5.record()
+        ref = Agc @ Bgc
+        e5.record()
+        torch.cuda.synchronize()
+        dgemm_ms = s5.elapsed_time(e5)
+        mag = Agc.abs() @ Bgc.abs()
+        gl = {}
+        for mode in ("triangular", "full"):
+            gw = api.workspace(api._lib.load().frx_ozaki_gemm_workspace_bytes(n, n, n, 8), dev)
+            C = api.ozaki_gemm(Agc, Bgc, 8, mode, work=gw)
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(3):
+                s4 = torch.cuda.Event(enable_timing=True)
+                e4 = torch.cuda.Event(enable_timing=True)
+                s4.record()
+                C = api.ozaki_gemm(Agc, Bgc, 8, mode, work=gw)
+                e4.record()
+                torch.cuda.synchronize()
+                best = min(best, s4.elapsed_time(e4))
+            gl[mode] = {"ms": best, "tflops_eq": 2 * n ** 3 / best / 1e9, "products": 36 if mode == "triangular" else 64,
+                        "max_err_vs_dgemm_rel_absAabsB": float(((C - ref).abs() / mag).max())}
+            del gw
+        line["ozaki_gemm"] = {"n": n, "phi": 2.0, "slices": 8, "dgemm_ms": dgemm_ms,
+                              "dgemm_tflops": 2 * n ** 3 / dgemm_ms / 1e9, **gl}
+        del Ag, Bg, Agc, Bgc, ref, mag
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], args.sample_rows)
     if rank == 0:

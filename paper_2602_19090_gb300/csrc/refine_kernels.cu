@@ -71,6 +71,21 @@ __device__ __forceinline__ i128 double_to_i128(double h) {
 
 // sum_g R_g 2^(7 (tlast[G-1] - tlast[g])), exact (caller checks ga.exact128)
 __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, int64_t j) {
+  if (ga.word32) {
+    // one int32 plane per anti-diagonal: Horner with the constant shift 7 in int64 chunks of
+    // four planes (|chunk| < 2^(31 + 21)), chunks merged in 128 bits
+    const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
+    i128 N = 0;
+    int g = 0;
+    while (g < ga.groups) {
+      int len = ga.groups - g < 4 ? ga.groups - g : 4;
+      i64 c = 0;
+      for (int q = 0; q < len; ++q) c = (c << 7) + (i64)p[(g + q) * ga.ogs];
+      N = g ? (N << (7 * len)) + (i128)c : (i128)c;
+      g += len;
+    }
+    return N;
+  }
   i128 N = 0;
   for (int g = 0; g < ga.groups; ++g) {
     if (g) N <<= DIGIT_BITS * (tlast_of(ga, g) - tlast_of(ga, g - 1));
@@ -79,8 +94,36 @@ __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, i
   return N;
 }
 
+// int32 planes in chunks of at most 13 (|chunk| < 2^(31 + 84)): each chunk is exact in 128
+// bits and converted to a double-double; chunks are added most significant first
+__device__ __forceinline__ dd gather_dd_w32_chunked(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
+  dd acc{0.0, 0.0};
+  if (eLi == EZERO || eRj == EZERO) return acc;
+  const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
+  int g = 0;
+  while (g < ga.groups) {
+    int len = ga.groups - g < 13 ? ga.groups - g : 13;
+    i128 N = 0;
+    for (int q = 0; q < len; q += 4) {
+      int l4 = len - q < 4 ? len - q : 4;
+      i64 c = 0;
+      for (int u = 0; u < l4; ++u) c = (c << 7) + (i64)p[(g + q + u) * ga.ogs];
+      N = q ? (N << (7 * l4)) + (i128)c : (i128)c;
+    }
+    int ex = eLi + eRj + 2 - DIGIT_BITS * (g + len + 1);   // plane g has t = g + 2
+    double h = i128_to_double_rn(N);
+    double l = i128_to_double_rn(N - double_to_i128(h));
+    dd part = (ex >= -1022 + 130 && ex <= 1023 - 130) ? dd{__dmul_rn(h, pow2(ex)), __dmul_rn(l, pow2(ex))}
+                                                       : dd{ldexp(h, ex), ldexp(l, ex)};
+    acc = g ? dd_add(acc, part) : part;
+    g += len;
+  }
+  return acc;
+}
+
 __device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
-  if (!ga.exact128) return gather_dd_general(ga, i, j, eLi, eRj);
+  if (!ga.exact128)
+    return ga.word32 ? gather_dd_w32_chunked(ga, i, j, eLi, eRj) : gather_dd_general(ga, i, j, eLi, eRj);
   if (eLi == EZERO || eRj == EZERO || ga.groups == 0) return dd{0.0, 0.0};
   i128 N = combine_groups(ga, i, j);
   double h = i128_to_double_rn(N);
@@ -95,7 +138,8 @@ __device__ __forceinline__ dd gather_dd(const GroupArgs& ga, int64_t i, int64_t 
 
 // RN of the entry as a single double
 __device__ __forceinline__ double gather_d(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
-  if (!ga.exact128) return gather_dd_general(ga, i, j, eLi, eRj).h;
+  if (!ga.exact128)
+    return (ga.word32 ? gather_dd_w32_chunked(ga, i, j, eLi, eRj) : gather_dd_general(ga, i, j, eLi, eRj)).h;
   if (eLi == EZERO || eRj == EZERO || ga.groups == 0) return 0.0;
   double h = i128_to_double_rn(combine_groups(ga, i, j));
   int ex = eLi + eRj + 2 - DIGIT_BITS * ga.tmax;
