@@ -10,6 +10,8 @@
 #include "frx_internal.cuh"
 #include "kernels.cuh"
 #include "refine_kernels.cuh"
+#include "plan_launch.cuh"
+#include "profile.cuh"
 
 using namespace frx;
 
@@ -34,6 +36,8 @@ struct Carver {
 };
 
 struct RefineWs {
+  DevPlan* plan;
+  double* lam_prev;
   int* flags;      // [0] flags, [1] cluster count
   double* norms;   // [0] ||E||^2, [1] ||W_off||^2, [2] ||dX||^2
   int32_t *eA, *f, *h, *eta, *rho;
@@ -51,6 +55,8 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   Carver c(work);
   w.pitch = round_up(n, 64);
   w.ps = n * w.pitch;
+  w.plan = c.take<DevPlan>(1);
+  w.lam_prev = c.take<double>(n);
   w.flags = c.take<int>(4);
   w.norms = c.take<double>(4);
   w.eA = c.take<int32_t>(n);
@@ -100,106 +106,6 @@ GemmWs carve_gemm(void* work, int64_t m, int64_t n, int64_t k, int slices) {
 
 bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
-// ---------------------------------------------------------------------------
-// host plan (same FP64 formulas, in the same order, as the CPU oracle)
-// ---------------------------------------------------------------------------
-int floor_log2d(double x) {
-  int ex;
-  frexp(x, &ex);
-  return ex - 1;
-}
-
-int ceil_log2d(double x) {
-  int ex;
-  double fr = frexp(x, &ex);
-  return fr == 0.5 ? ex - 1 : ex;
-}
-
-int ceil_log2_sqrt_int(int64_t n) {
-  int bl = 0;
-  for (uint64_t v = (uint64_t)(n - 1); v; v >>= 1) ++bl;
-  return (bl + 1) / 2;
-}
-
-int ceil_log2_int(int64_t n) {
-  int bl = 0;
-  for (uint64_t v = (uint64_t)(n - 1); v; v >>= 1) ++bl;
-  return bl;
-}
-
-// smallest adjacent gap of the sorted estimates exceeding omega; Lam = max |lam|
-double min_gap(const std::vector<double>& lam, double omega, double* Lam) {
-  double L = 0.0;
-  for (double v : lam) L = fabs(v) > L ? fabs(v) : L;
-  *Lam = L;
-  std::vector<double> s(lam);
-  std::sort(s.begin(), s.end());
-  double g = INFINITY;
-  bool any = false;
-  for (size_t i = 1; i < s.size(); ++i) {
-    double d = s[i] - s[i - 1];
-    if (d > omega) {
-      g = d < g ? d : g;
-      any = true;
-    }
-  }
-  return any ? g : L;
-}
-
-// sum_j 2^(2 f_j), exactly rounded (integer accumulation relative to the smallest term)
-double sum_pow4(const std::vector<int32_t>& f) {
-  int emin = INT32_MAX, emax = INT32_MIN;
-  for (int32_t e : f)
-    if (e != EZERO) {
-      emin = e < emin ? e : emin;
-      emax = e > emax ? e : emax;
-    }
-  if (emin == INT32_MAX) return 0.0;
-  if (emax - emin <= 45) {
-    unsigned __int128 acc = 0;
-    for (int32_t e : f)
-      if (e != EZERO) acc += (unsigned __int128)1 << (2 * (e - emin));
-    return ldexp((double)acc, 2 * emin);
-  }
-  std::vector<int32_t> s;
-  for (int32_t e : f)
-    if (e != EZERO) s.push_back(e);
-  std::sort(s.begin(), s.end());
-  double acc = 0.0;
-  for (int32_t e : s) acc += ldexp(1.0, 2 * e);
-  return acc;
-}
-
-int beta_rule(int64_t n, double delta, double g, double Lam, double S2, const frx_opts& o) {
-  if (o.beta_override >= 0) return std::min(std::max(o.beta_override, 3), 47);
-  double xi = o.xi > 0 ? o.xi : (double)n;
-  if (g <= 0.0 || Lam <= 0.0 || S2 <= 0.0) return 3;
-  double q = sqrt((xi * delta * g) / (Lam * S2)) / (0.75 * U53);
-  int b = o.beta_ceil ? ceil_log2d(q) : floor_log2d(q);
-  return std::min(std::max(b, 3), 47);
-}
-
-int alpha_rule(int64_t n, int beta, const frx_opts& o) {
-  return o.theory_alpha ? 53 - beta + ceil_log2_int(n) : 53 - beta + ceil_log2_sqrt_int(n);
-}
-
-// smallest k >= 1 with (2^(7k - eL - eR - 6) tau)^2 >= n^3, capped at k_cap; 0 if an operand is zero
-int slices_for(int64_t n, int eL, int eR, double tau, int kcap) {
-  if (eL == EZERO || eR == EZERO) return 0;
-  double n3 = (double)n * (double)n * (double)n;
-  for (int k = 1; k <= kcap; ++k) {
-    double v = ldexp(tau, 7 * k - eL - eR - 6);
-    if (v * v >= n3) return k;
-  }
-  return kcap;
-}
-
-int vmax(const std::vector<int32_t>& v) {
-  int m = EZERO;
-  for (int32_t e : v) m = e > m ? e : m;
-  return m;
-}
-
 template <class T>
 int to_host(std::vector<T>& h, const T* d, int64_t n, cudaStream_t s) {
   h.resize((size_t)n);
@@ -221,6 +127,7 @@ int check_flags(const int* dflags, cudaStream_t s) {
 PlaneGemm make_gemm(const __nv_bfloat16* L, int64_t Lps, const __nv_bfloat16* R, int64_t Rps, int64_t pitch,
                     int64_t M, int64_t N, int64_t K, int kL, int kR, int T, i64* out) {
   PlaneGemm g;
+  memset(&g, 0, sizeof(g));
   g.L = L;
   g.Lps = Lps;
   g.R = R;
@@ -229,16 +136,16 @@ PlaneGemm make_gemm(const __nv_bfloat16* L, int64_t Lps, const __nv_bfloat16* R,
   g.M = M;
   g.N = N;
   g.K = K;
-  g.kL = kL;
-  g.kR = kR;
-  g.T = T;
+  g.d.kL = kL;
+  g.d.kR = kR;
+  g.d.T = T;
   g.out = out;
   g.ogs = M * N;
   g.ldo = M;
   g.flags = nullptr;
-  g.word32 = 0;
+  g.dyn = nullptr;
+  g.done = nullptr;
   g.out_bytes_per_elem = 64;
-  g.tmax = g.gs = g.groups = 0;
   return g;
 }
 
@@ -252,44 +159,62 @@ int validate_opts(const frx_opts& o) {
   return FRX_OK;
 }
 
-// one iteration; lam_prev (host) in, lam_new (device ws.lam) out
-int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, double delta,
-                     const frx_opts& o, RefineWs& ws, const std::vector<int32_t>& eA_h, int& sliced_kA,
-                     const std::vector<double>& lam_prev, double omega_prev, frx_info& info, double& step,
-                     double& omega_out, std::vector<double>& lam_new, const DebugOut* dbg, cudaStream_t s) {
-  // S1: column exponents of X (eq. tau's w_j)
-  FRX_TRY(launch_col_exponents(X, ldx, n, n, ws.f, ws.flags, s));
-  std::vector<int32_t> f_h;
-  FRX_TRY(to_host(f_h, ws.f, n, s));
-  FRX_TRY(check_flags(ws.flags, s));
-  for (int32_t e : f_h)
-    if (e == EZERO) return FRX_E_ARG;  // a zero column is not an eigenvector approximation
+PlanOpts plan_opts(const frx_opts& o, double delta, int64_t n, int max_iter) {
+  PlanOpts p;
+  p.slices_A = o.slices_A;
+  p.xi = o.xi;
+  p.beta_ceil = o.beta_ceil;
+  p.theory_alpha = o.theory_alpha;
+  p.beta_override = o.beta_override;
+  p.k_cap = o.k_cap;
+  p.max_iter = max_iter;
+  p.xi_stop = o.xi_stop;
+  p.cluster_omega = o.cluster_omega;
+  p.delta = delta;
+  p.n = n;
+  return p;
+}
 
-  // S2: plan (Sec. 4.1), using the previous eigenvalue estimates
-  double Lam;
-  double g = min_gap(lam_prev, omega_prev, &Lam);
-  double S2 = sum_pow4(f_h);
-  int beta = beta_rule(n, delta, g, Lam, S2, o);
-  int alpha = alpha_rule(n, beta, o);
-  int sX = (54 - beta + 6) / 7;
-  int eAmax = vmax(eA_h), fmax = vmax(f_h);
-  int kV = o.slices_A > 0 ? o.slices_A : slices_for(n, eAmax, fmax, delta * g, o.k_cap);
-  if (kV < 1) kV = 1;
+// a plan-driven product: d carries the plane capacities (tensor maps) and the kernel variant
+PlaneGemm dyn_gemm(const __nv_bfloat16* L, int capL, const __nv_bfloat16* R, int capR, const RefineWs& ws,
+                   int64_t n, const GemmDesc* dyn) {
+  PlaneGemm g = make_gemm(L, ws.ps, R, ws.ps, ws.pitch, n, n, n, capL, capR, capL + capR, ws.groups);
+  g.d.active = 1;
+  g.d.word32 = 1;
+  g.d.groups = 1;
+  g.dyn = dyn;
+  g.done = &ws.plan->done;
+  g.flags = &ws.plan->flags;
+  return g;
+}
 
-  // S3: digit planes of A (rows of A = columns of A by symmetry); kept across iterations
-  if (kV > sliced_kA) {
-    FRX_TRY(launch_slice_cols(A, lda, n, n, ws.eA, kV, ws.Ap, ws.ps, ws.pitch, s));
-    sliced_kA = kV;
-  }
+// One iteration of Algorithm 1 (Sec. 3 form), entirely on the stream: every decision is
+// taken by the plan kernels and read back by the kernels that follow.
+int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, const frx_opts& o,
+                      const PlanOpts& po, const RefineWs& ws, const DebugOut* dbg, cudaStream_t s) {
+  DevPlan* P = ws.plan;
+  const int* done = &P->done;
+  int* flags = &P->flags;
+  const int kcap = o.k_cap;
+  // S1 / S2: column exponents of X (eq. tau's w_j), then beta, alpha, s_X, k_V
+  FRX_TRY(launch_col_exponents(X, ldx, n, n, ws.f, flags, s, done));
+  FRX_TRY(launch_plan_v(P, ws.f, po, s));
+  // S3: digit planes of A (rows of A = columns of A by symmetry), extended when k_V grows
+  SliceDyn da;
+  da.nplanes = &P->kV;
+  da.from = &P->sliced_kA;
+  da.done = done;
+  FRX_TRY(launch_slice_cols(A, lda, n, n, ws.eA, 0, ws.Ap, ws.ps, ws.pitch, s, da));
+  FRX_TRY(launch_plan_mark_sliced(P, s));
   // S4: X^(1) (eq. tau, eq. x) and its column planes
-  FRX_TRY(launch_truncate_slice_x(X, ldx, n, ws.f, beta, sX, ws.X1, n, ws.Xp, ws.ps, ws.pitch, s));
-
-  // S5/S6: V = A X^(1) (Alg. 1 line 1 with eq. mat_mul), pairs r + s <= k_V + 1
-  PlaneGemm gv = make_gemm(ws.Ap, ws.ps, ws.Xp, ws.ps, ws.pitch, n, n, n, kV, sX, kV + 1, ws.groups);
-  gv.flags = ws.flags;
-  FRX_TRY(plan_plane_gemm(gv));
+  SliceDyn dx;
+  dx.nplanes = &P->sX;
+  dx.beta = &P->beta;
+  dx.done = done;
+  FRX_TRY(launch_truncate_slice_x(X, ldx, n, ws.f, 0, 0, ws.X1, n, ws.Xp, ws.ps, ws.pitch, s, dx));
+  // S5/S6: V = A X^(1), pairs r + s <= k_V + 1
+  PlaneGemm gv = dyn_gemm(ws.Ap, kcap, ws.Xp, 8, ws, n, &P->V);
   FRX_TRY(launch_plane_gemm(gv, s));
-
   // S7/S8: r, lambda, Res (lines 2-4)
   ResidualArgs ra;
   ra.n = n;
@@ -303,30 +228,21 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   ra.Res = ws.Res;
   ra.ldr = n;
   ra.h = ws.h;
-  ra.beta = beta;
+  ra.beta = 0;
+  ra.beta_dyn = &P->beta;
+  ra.done = done;
   ra.Vh = dbg ? dbg->Vh : nullptr;
   ra.Vl = dbg ? dbg->Vl : nullptr;
   FRX_TRY(launch_residual(ra, s));
-  std::vector<int32_t> h_h;
-  FRX_TRY(to_host(h_h, ws.h, n, s));
-
   // S9: W = X^(1)^T Res
-  int hmax = vmax(h_h);
-  int kW = slices_for(n, fmax, hmax, delta * g, o.k_cap);
-  PlaneGemm gw = make_gemm(ws.Xp, ws.ps, ws.Rp, ws.ps, ws.pitch, n, n, n, std::min(sX, kW), kW, kW + 1,
-                           ws.groups);
-  gw.flags = ws.flags;
-  if (kW > 0) {
-    FRX_TRY(launch_slice_cols(ws.Res, n, n, n, ws.h, kW, ws.Rp, ws.ps, ws.pitch, s));
-    FRX_TRY(plan_plane_gemm(gw));
-    FRX_TRY(launch_plane_gemm(gw, s));
-  } else {
-    gw.groups = 0;
-  }
-
+  FRX_TRY(launch_plan_w(P, ws.h, po, s));
+  SliceDyn dr;
+  dr.nplanes = &P->kW;
+  dr.done = done;
+  FRX_TRY(launch_slice_cols(ws.Res, n, n, n, ws.h, 0, ws.Rp, ws.ps, ws.pitch, s, dr));
+  PlaneGemm gw = dyn_gemm(ws.Xp, 8, ws.Rp, kcap, ws, n, &P->W);
+  FRX_TRY(launch_plane_gemm(gw, s));
   // S10: E~ (line 5) with the cluster threshold
-  FRX_CUDA_TRY(cudaMemsetAsync(ws.norms, 0, 4 * sizeof(double), s));
-  FRX_CUDA_TRY(cudaMemsetAsync(ws.flags + 1, 0, sizeof(int), s));
   CorrectionArgs ca;
   ca.n = n;
   ca.W = group_args(gw);
@@ -336,47 +252,29 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   ca.r = ws.r;
   ca.X1 = ws.X1;
   ca.ld1 = n;
+  ca.omega = 0.0;
+  ca.omega_dyn = &P->omega;
+  ca.done = done;
   ca.E = ws.E;
   ca.lde = n;
   ca.eta = ws.eta;
-  ca.norms = ws.norms;
-  ca.ccount = ws.flags + 1;
-  ca.flags = ws.flags;
+  ca.norms = P->norms;
+  ca.ccount = &P->ccount;
+  ca.flags = flags;
   ca.Wout = dbg ? dbg->W : nullptr;
-  double omega = o.cluster_omega;
-  if (omega < 0) {
-    double w2 = 0.0;
-    if (gw.groups > 0) {
-      FRX_TRY(launch_w_offdiag_norm2(ca, s));
-      std::vector<double> nh;
-      FRX_TRY(to_host(nh, ws.norms, 4, s));
-      w2 = nh[1];
-    }
-    std::vector<double> rh;
-    FRX_TRY(to_host(rh, ws.r, n, s));
-    double rn = 0.0;
-    for (double v : rh) rn += v * v;
-    omega = 2.0 * (sqrt(w2) + Lam * sqrt(rn));
-  }
-  ca.omega = omega;
+  if (o.cluster_omega < 0) FRX_TRY(launch_w_offdiag_norm2(ca, s));
+  FRX_TRY(launch_plan_omega(P, ws.r, po, s));
   FRX_TRY(launch_correction(ca, s));
-
   // S11: U = X^(1) E~ (rows of X^(1), columns of E~), X <- RN(X^(1) + U)
-  FRX_TRY(launch_row_exponents(ws.X1, n, n, n, ws.rho, ws.rowmax, ws.flags, s));
-  std::vector<int32_t> eta_h, rho_h;
-  FRX_TRY(to_host(eta_h, ws.eta, n, s));
-  FRX_TRY(to_host(rho_h, ws.rho, n, s));
-  int kU = slices_for(n, vmax(rho_h), vmax(eta_h), delta, o.k_cap);
-  PlaneGemm gu = make_gemm(ws.X1rp, ws.ps, ws.Rp, ws.ps, ws.pitch, n, n, n, kU, kU, kU + 1, ws.groups);
-  gu.flags = ws.flags;
-  if (kU > 0) {
-    FRX_TRY(launch_slice_rows(ws.X1, n, n, n, ws.rho, kU, ws.X1rp, ws.ps, ws.pitch, s));
-    FRX_TRY(launch_slice_cols(ws.E, n, n, n, ws.eta, kU, ws.Rp, ws.ps, ws.pitch, s));
-    FRX_TRY(plan_plane_gemm(gu));
-    FRX_TRY(launch_plane_gemm(gu, s));
-  } else {
-    gu.groups = 0;
-  }
+  FRX_TRY(launch_row_exponents(ws.X1, n, n, n, ws.rho, ws.rowmax, flags, s, done));
+  FRX_TRY(launch_plan_u(P, ws.rho, ws.eta, po, s));
+  SliceDyn du;
+  du.nplanes = &P->kU;
+  du.done = done;
+  FRX_TRY(launch_slice_rows(ws.X1, n, n, n, ws.rho, 0, ws.X1rp, ws.ps, ws.pitch, s, du));
+  FRX_TRY(launch_slice_cols(ws.E, n, n, n, ws.eta, 0, ws.Rp, ws.ps, ws.pitch, s, du));
+  PlaneGemm gu = dyn_gemm(ws.X1rp, kcap, ws.Rp, kcap, ws, n, &P->U);
+  FRX_TRY(launch_plane_gemm(gu, s));
   if (dbg) {
     if (dbg->X1) FRX_CUDA_TRY(cudaMemcpyAsync(dbg->X1, ws.X1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
     if (dbg->Res)
@@ -390,40 +288,17 @@ int refine_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int64
   ua.rho = ws.rho;
   ua.eta = ws.eta;
   ua.f = ws.f;
-  ua.beta = beta;
+  ua.beta = 0;
+  ua.beta_dyn = &P->beta;
+  ua.done = done;
   ua.X1 = ws.X1;
   ua.ld1 = n;
   ua.X = X;
   ua.ldx = ldx;
-  ua.norms = ws.norms;
+  ua.norms = P->norms;
   FRX_TRY(launch_update(ua, s));
-
-  std::vector<double> nh;
-  FRX_TRY(to_host(nh, ws.norms, 4, s));
-  FRX_TRY(to_host(lam_new, ws.lam, n, s));
-  int cc = 0;
-  FRX_CUDA_TRY(cudaMemcpyAsync(&cc, ws.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  FRX_TRY(check_flags(ws.flags, s));
-
-  step = sqrt(nh[2]);
-  omega_out = omega;
-  double Lam_new;
-  double g_new = min_gap(lam_new, omega, &Lam_new);
-  double xs = o.xi_stop > 0 ? o.xi_stop : (double)n;
-  info.err_est = g_new > 0 ? step * step * Lam_new / (xs * g_new) : INFINITY;
-  info.step = step;
-  info.min_gap = g_new;
-  info.max_lambda = Lam_new;
-  info.beta = beta;
-  info.alpha = alpha;
-  info.s_X = sX;
-  info.k_V = kV;
-  info.k_W = kW;
-  info.k_U = kU;
-  info.omega = omega;
-  info.clustered_pairs = cc / 2;
-  info.products += pairs_in(kV, sX, kV + 1) + (kW > 0 ? pairs_in(std::min(sX, kW), kW, kW + 1) : 0) +
-                   (kU > 0 ? pairs_in(kU, kU, kU + 1) : 0);
+  // S12: stopping test
+  FRX_TRY(launch_plan_end(P, ws.lam, ws.lam_prev, po, s));
   return FRX_OK;
 }
 
@@ -443,46 +318,48 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
   else if (validate_opts(o) < 0) st = FRX_E_ARG;
   RefineWs ws = carve_refine(nullptr, n, o.k_cap);
   if (st == FRX_OK && (!work || !aligned256(work) || work_bytes < ws.bytes)) st = FRX_E_WORKSPACE;
+  DevPlan hp;
+  memset(&hp, 0, sizeof(hp));
   if (st == FRX_OK) {
     ws = carve_refine(work, n, o.k_cap);
+    const int max_iter = single ? 1 : o.max_iter;
+    const PlanOpts po = plan_opts(o, delta, n, max_iter);
     st = [&]() -> int {
-      FRX_CUDA_TRY(cudaMemsetAsync(ws.flags, 0, 4 * sizeof(int), s));
-      FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, ws.flags, s));
-      std::vector<int32_t> eA_h;
-      FRX_TRY(to_host(eA_h, ws.eA, n, s));
-      FRX_TRY(check_flags(ws.flags, s));
-      std::vector<double> lam(n), lam_new;
-      FRX_CUDA_TRY(cudaMemcpyAsync(lam.data(), D, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-      FRX_CUDA_TRY(cudaStreamSynchronize(s));
-      for (double v : lam)
-        if (!isfinite(v)) return FRX_E_NONFINITE;
-      int sliced = 0;
-      double omega = omega_prev, prev_step = -1.0;
-      int status = FRX_MAX_ITER;
-      int iters = single ? 1 : o.max_iter;
-      for (int it = 1; it <= iters; ++it) {
-        double step = 0.0, om = 0.0;
-        FRX_TRY(refine_iteration(A, lda, X, ldx, n, delta, o, ws, eA_h, sliced, lam, omega, info, step, om,
-                                 lam_new, dbg, s));
-        info.iters = it;
-        lam = lam_new;
-        omega = om;
-        if (info.err_est <= delta) {
-          status = FRX_OK;
-          break;
-        }
-        if (prev_step >= 0 && step > 0.5 * prev_step) {
-          status = FRX_STAGNATED;
-          break;
-        }
-        prev_step = step;
+      FRX_CUDA_TRY(cudaMemsetAsync(ws.plan, 0, sizeof(DevPlan), s));
+      FRX_CUDA_TRY(cudaMemsetAsync(ws.rowmax, 0, sizeof(u64) * n, s));
+      FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s));
+      FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));
+      for (int it = 1; it <= max_iter; ++it) {
+        FRX_TRY(enqueue_iteration(A, lda, X, ldx, n, o, po, ws, dbg, s));
+        int done = 0;
+        FRX_CUDA_TRY(cudaMemcpyAsync(&done, &ws.plan->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FRX_CUDA_TRY(cudaStreamSynchronize(s));
+        if (done) break;
       }
-      FRX_CUDA_TRY(cudaMemcpyAsync(D, lam.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      FRX_CUDA_TRY(cudaMemcpyAsync(&hp, ws.plan, sizeof(DevPlan), cudaMemcpyDeviceToHost, s));
       FRX_CUDA_TRY(cudaStreamSynchronize(s));
-      return status;
+      if (hp.status >= 0 && hp.iter > 0)
+        FRX_CUDA_TRY(cudaMemcpyAsync(D, ws.lam_prev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      FRX_CUDA_TRY(cudaStreamSynchronize(s));
+      profile_add_gemm_work(2.0 * (double)n * (double)n * (double)n * (double)hp.products);
+      return hp.status;
     }();
   }
   info.status = st;
+  info.iters = hp.iter;
+  info.beta = hp.beta;
+  info.alpha = hp.alpha;
+  info.s_X = hp.sX;
+  info.k_V = hp.kV;
+  info.k_W = hp.kW;
+  info.k_U = hp.kU;
+  info.products = hp.products;
+  info.err_est = hp.est;
+  info.step = hp.step;
+  info.min_gap = hp.g;
+  info.max_lambda = hp.Lam;
+  info.omega = hp.omega;
+  info.clustered_pairs = hp.clustered;
   if (pinfo) *pinfo = info;
   return st;
 }
@@ -562,6 +439,7 @@ int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_t ldb, d
   ws = carve_gemm(work, m, n, k, slices);
   cudaStream_t s = (cudaStream_t)stream;
   FRX_CUDA_TRY(cudaMemsetAsync(ws.flags, 0, 4 * sizeof(int), s));
+  FRX_CUDA_TRY(cudaMemsetAsync(ws.rowmax, 0, sizeof(u64) * m, s));
   FRX_TRY(launch_row_exponents(A, lda, m, k, ws.eA, ws.rowmax, ws.flags, s));
   FRX_TRY(launch_col_exponents(B, ldb, k, n, ws.eB, ws.flags, s));
   FRX_TRY(launch_slice_rows(A, lda, m, k, ws.eA, slices, ws.Ap, m * ws.pitch, ws.pitch, s));
@@ -587,7 +465,7 @@ int frx_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int a
   cudaStream_t s = (cudaStream_t)stream;
   int* flags = (int*)work;
   u64* scratch = (u64*)((char*)work + 256);
-  FRX_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  FRX_CUDA_TRY(cudaMemsetAsync(work, 0, frx_exponents_workspace_bytes(rows), s));
   if (axis == 0) {
     FRX_TRY(launch_row_exponents(M, ld, rows, cols, e, scratch, flags, s));
   } else {
@@ -611,7 +489,7 @@ int frx_group_size(int kL, int kR, int T, int64_t K) {
   PlaneGemm g = make_gemm(nullptr, 0, nullptr, 0, 8, 1, 1, K, kL, kR, T, nullptr);
   g.out_bytes_per_elem = 0;  // int64 groups only (any count): the documented format
   int st = plan_plane_gemm(g);
-  return st < 0 ? st : g.gs;
+  return st < 0 ? st : g.d.gs;
 }
 
 int frx_plane_products(const uint16_t* L, int64_t L_plane_stride, const uint16_t* R, int64_t R_plane_stride,

@@ -20,35 +20,9 @@ int pairs_in(int kL, int kR, int T) {
 }
 
 int plan_plane_gemm(PlaneGemm& g) {
-  g.tmax = g.T < g.kL + g.kR ? g.T : g.kL + g.kR;
-  if (g.kL <= 0 || g.kR <= 0 || g.tmax < 2) {
-    g.groups = 0;
-    g.gs = 1;
-    return FRX_OK;
-  }
-  if (g.K >= (1 << 19)) return FRX_E_UNSUPPORTED;
-  int pmax = 0;
-  for (int t = 2; t <= g.tmax; ++t) {
-    int lo = t - g.kR > 1 ? t - g.kR : 1;
-    int hi = g.kL < t - 1 ? g.kL : t - 1;
-    int c = hi - lo + 1;
-    pmax = c > pmax ? c : pmax;
-  }
-  unsigned long long smax = (unsigned long long)pmax * (unsigned long long)g.K * 4096ull;
-  int bs = 64 - __builtin_clzll(smax);  // smax < 2^bs
-  if (bs > 61) return FRX_E_UNSUPPORTED;
-  g.word32 = 0;
-  if (g.out_bytes_per_elem > 0 && smax < (1ull << 31) && (g.tmax - 1) * 4 <= g.out_bytes_per_elem) {
-    // one exact int32 plane per anti-diagonal (the layout of the 128 x 256 tensor-core tiles)
-    g.word32 = 1;
-    g.gs = 1;
-    g.groups = g.tmax - 1;
-    return FRX_OK;
-  }
-  g.gs = (61 - bs) / 7 + 1;
-  g.groups = (g.tmax - 1 + g.gs - 1) / g.gs;
-  // out_bytes_per_elem == 0: int64 groups in a buffer the caller sized from frx_group_size
-  if (g.out_bytes_per_elem > 0 && g.groups * 8 > g.out_bytes_per_elem) return FRX_E_UNSUPPORTED;
+  int st = gemm_desc_layout(g.d, g.K, g.out_bytes_per_elem);
+  if (st != FRX_OK) return st;
+  gemm_desc_schedule(g.d, g.M, g.N, g.d.word32 ? 256 : 128);
   return FRX_OK;
 }
 
@@ -72,6 +46,10 @@ __device__ __forceinline__ void pack8(uint4 v, int& w0, int& w1) {
 }
 
 __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
+  if (g.done && *g.done) return;
+  const GemmDesc& d = g.dyn ? *g.dyn : g.d;
+  if (!d.active) return;
+  const int kL = d.kL, kR = d.kR, tmax = d.tmax, gs = d.gs, groups = d.groups, word32 = d.word32;
   __shared__ __align__(16) int As[BK / 4][BM];
   __shared__ __align__(16) int Bs[BK / 4][BN];
   const int tid = threadIdx.x;
@@ -82,9 +60,9 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
   const unsigned short* L = reinterpret_cast<const unsigned short*>(g.L);
   const unsigned short* R = reinterpret_cast<const unsigned short*>(g.R);
 
-  for (int grp = 0; grp < g.groups; ++grp) {
-    const int t0 = 2 + grp * g.gs;
-    const int t1 = t0 + g.gs - 1 < g.tmax ? t0 + g.gs - 1 : g.tmax;
+  for (int grp = 0; grp < groups; ++grp) {
+    const int t0 = 2 + grp * gs;
+    const int t1 = t0 + gs - 1 < tmax ? t0 + gs - 1 : tmax;
     i64 racc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -96,8 +74,8 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) tacc[a][b] = 0;
-      const int rlo = t - g.kR > 1 ? t - g.kR : 1;
-      const int rhi = g.kL < t - 1 ? g.kL : t - 1;
+      const int rlo = t - kR > 1 ? t - kR : 1;
+      const int rhi = kL < t - 1 ? kL : t - 1;
       for (int r = rlo; r <= rhi; ++r) {
         const unsigned short* Lp = L + (int64_t)(r - 1) * g.Lps;
         const unsigned short* Rp = R + (int64_t)(t - r - 1) * g.Rps;
@@ -151,7 +129,7 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
       for (int a = 0; a < 4; ++a) {
         int64_t i = i0 + ty * 4 + a;
         if (i >= g.M) continue;
-        if (g.word32)
+        if (word32)
           g.out32()[grp * g.ogs + j * g.ldo + i] = (int32_t)racc[a][b];
         else
           g.out[grp * g.ogs + j * g.ldo + i] = racc[a][b];
@@ -163,7 +141,7 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
 }  // namespace
 
 int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s) {
-  if (g.groups == 0 || g.M == 0 || g.N == 0) return FRX_OK;
+  if ((!g.dyn && g.d.groups == 0) || g.M == 0 || g.N == 0) return FRX_OK;
   if (g.pitch % 8) return FRX_E_ARG;
   dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
   k_plane_gemm_simt<<<grid, 256, 0, s>>>(g);
@@ -174,7 +152,7 @@ int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s) {
 // Tensor-core kernel when the operands allow it; FRX_GEMM=simt selects the CUDA-core
 // kernel (used to cross-check the two implementations bit for bit).
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) {
-  if (g.groups == 0 || g.M == 0 || g.N == 0) return FRX_OK;
+  if ((!g.dyn && g.d.groups == 0) || g.M == 0 || g.N == 0) return FRX_OK;
   const char* env = getenv("FRX_GEMM");
   bool simt = env && env[0] == 's';
   GemmTimer timer(g, s);

@@ -162,15 +162,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 struct TcArgs {
   int64_t M, N;
   int nkb;       // k-blocks of 64
-  int kL, kR, tmax, gs, groups;
   void* out;     // int64 groups, or int32 per-t planes when W32
   int64_t ogs, ldo;
   int* flags;
-  // persistent schedule: unit u = (group gorder[u / tiles], tile u % tiles), tiles = ntm * ntn,
-  // groups ordered by decreasing work so a static round-robin over CTAs stays balanced
-  int ntm, ntn;
-  int units;
-  int gorder[32];
+  // product description (d, or *dyn when set): plane counts, groups and the persistent
+  // schedule: unit u = (group gorder[u / tiles], tile u % tiles), tiles = ntm * ntn, groups
+  // ordered by decreasing work so a static round-robin over CTAs stays balanced
+  GemmDesc d;
+  const GemmDesc* dyn;
+  const int* done;
+};
+
+// per-launch scalars read once at kernel entry
+struct TcRun {
+  int64_t M, N;
+  int nkb, kL, kR, tmax, gs, groups, ntm, ntn, units;
+  void* out;
+  int64_t ogs, ldo;
+  int* flags;
 };
 
 __device__ __forceinline__ int pair_lo(int t, int kR) { return t - kR > 1 ? t - kR : 1; }
@@ -180,7 +189,8 @@ __device__ __forceinline__ int pair_hi(int t, int kL) { return kL < t - 1 ? kL :
 // BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
 template <int BN_, bool W32>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR, TcArgs a) {
+    k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
+                    const __grid_constant__ TcArgs a0) {
   constexpr int BN = BN_;
   constexpr int STAGES = BN == 256 ? 4 : 6;
   constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
@@ -189,6 +199,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   constexpr uint32_t IDESC = idesc_for(BN);
   constexpr int NCOL = BN / 2;   // columns per epilogue thread
   typedef typename std::conditional<W32, int, i64>::type Acc;
+  if (a0.done && *a0.done) return;
+  const GemmDesc* D = a0.dyn ? a0.dyn : &a0.d;
+  if (!D->active || D->units <= 0) return;
+  TcRun a;
+  a.M = a0.M;
+  a.N = a0.N;
+  a.nkb = a0.nkb;
+  a.kL = D->kL;
+  a.kR = D->kR;
+  a.tmax = D->tmax;
+  a.gs = D->gs;
+  a.groups = D->groups;
+  a.ntm = D->ntm;
+  a.ntn = D->ntn;
+  a.units = D->units;
+  a.out = a0.out;
+  a.ogs = a0.ogs;
+  a.ldo = a0.ldo;
+  a.flags = a0.flags;
+  const int* gorder = D->gorder;
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
   unsigned char* tiles_smem = base;
@@ -229,7 +259,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool ok = !*abort;
       const int tiles = a.ntm * a.ntn;
       for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-        const int grp = a.gorder[u / tiles], tile = u % tiles;
+        const int grp = gorder[u / tiles], tile = u % tiles;
         const int i0 = (tile / a.ntn) * BM, j0 = (tile % a.ntn) * BN;
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
@@ -290,7 +320,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool any = false;
       const int tiles = a.ntm * a.ntn;
       for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-        const int grp = a.gorder[u / tiles];
+        const int grp = gorder[u / tiles];
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           int rlo = pair_lo(t, a.kR), rhi = pair_hi(t, a.kL);
@@ -355,7 +385,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bool ok = true;
     const int tiles = a.ntm * a.ntn;
     for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-      const int grp = a.gorder[u / tiles], tile = u % tiles;
+      const int grp = gorder[u / tiles], tile = u % tiles;
       const int i0 = (tile / a.ntn) * BM, j0 = (tile % a.ntn) * BN;
       const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
@@ -443,7 +473,7 @@ size_t smem_bytes(int bn) {
 }  // namespace
 
 bool plane_gemm_tc_supported(const PlaneGemm& g) {
-  if (g.groups <= 0 || g.M < 1 || g.N < 1 || g.K < 1) return false;
+  if ((!g.dyn && g.d.groups <= 0) || g.M < 1 || g.N < 1 || g.K < 1) return false;
   if (g.pitch % 8 || g.Lps % 8 || g.Rps % 8) return false;
   if (((uintptr_t)g.L & 15) || ((uintptr_t)g.R & 15)) return false;
   if (g.M > (1 << 24) || g.N > (1 << 24)) return false;
@@ -452,9 +482,10 @@ bool plane_gemm_tc_supported(const PlaneGemm& g) {
 
 template <int BN, bool W32>
 int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
+  // tensor maps span the allocated planes (g.d.kL, g.d.kR: the capacity when d comes from the device)
   CUtensorMap mL, mR;
-  if (!make_map(&mL, g.L, g.K, g.M, g.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
-  if (!make_map(&mR, g.R, g.K, g.N, g.kR, g.pitch, g.Rps, BN)) return FRX_E_CUDA;
+  if (!make_map(&mL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
+  if (!make_map(&mR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, BN)) return FRX_E_CUDA;
   size_t smem = smem_bytes(BN);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -462,30 +493,16 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
     attr_err = cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   FRX_CUDA_TRY(attr_err);
-  TcArgs b = a;
-  b.ntm = (int)((g.M + BM - 1) / BM);
-  b.ntn = (int)((g.N + BN - 1) / BN);
-  b.units = b.ntm * b.ntn * g.groups;
-  // groups by decreasing work (pairs summed over their anti-diagonals), ties by group index
-  int work[32];
-  for (int q = 0; q < g.groups; ++q) {
-    int t0 = 2 + q * g.gs, t1 = t0 + g.gs - 1 < g.tmax ? t0 + g.gs - 1 : g.tmax, w = 0;
-    for (int t = t0; t <= t1; ++t) {
-      int lo = t - g.kR > 1 ? t - g.kR : 1, hi = g.kL < t - 1 ? g.kL : t - 1;
-      w += hi - lo + 1;
-    }
-    work[q] = w;
-    b.gorder[q] = q;
-  }
-  std::stable_sort(b.gorder, b.gorder + g.groups, [&](int x, int y) { return work[x] > work[y]; });
   static int sms = 0;
   if (!sms) {
     int dev = 0;
     FRX_CUDA_TRY(cudaGetDevice(&dev));
     FRX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  unsigned grid = (unsigned)(b.units < sms ? b.units : sms);
-  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, b);
+  int64_t units = a.dyn ? (int64_t)sms : (int64_t)a.d.units;
+  unsigned grid = (unsigned)(units < sms ? units : sms);
+  if (grid == 0) return FRX_OK;
+  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -495,16 +512,14 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
   a.M = g.M;
   a.N = g.N;
   a.nkb = (int)((g.K + BK - 1) / BK);
-  a.kL = g.kL;
-  a.kR = g.kR;
-  a.tmax = g.tmax;
-  a.gs = g.gs;
-  a.groups = g.groups;
   a.out = (void*)g.out;
   a.ogs = g.ogs;
   a.ldo = g.ldo;
   a.flags = flags;
-  if (g.word32) return launch_variant<256, true>(g, a, s);
+  a.d = g.d;
+  a.dyn = g.dyn;
+  a.done = g.done;
+  if (g.d.word32) return launch_variant<256, true>(g, a, s);
   return launch_variant<128, false>(g, a, s);
 }
 

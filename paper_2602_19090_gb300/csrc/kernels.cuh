@@ -2,29 +2,40 @@
 #pragma once
 
 #include "frx_internal.cuh"
+#include "plan.cuh"
 
 namespace frx {
 
 enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_RANGE = 4 };
 
+// optional device-side parameters of the slicing kernels (null: use the launch arguments)
+struct SliceDyn {
+  const int* nplanes = nullptr;  // planes to produce
+  const int* from = nullptr;     // first plane to write (earlier planes are kept)
+  const int* beta = nullptr;     // beta of the truncation (k_truncate_slice_x)
+  const int* done = nullptr;     // nonzero: the refinement has finished, do nothing
+};
+
 // scan_slice.cu
 int launch_col_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, int* flags,
-                         cudaStream_t s);
+                         cudaStream_t s, const int* done = nullptr);
 int launch_row_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, u64* scratch,
-                         int* flags, cudaStream_t s);
+                         int* flags, cudaStream_t s, const int* done = nullptr);
 int launch_slice_cols(const double* M, int64_t ld, int64_t K, int64_t N, const int32_t* e, int nplanes,
-                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s);
+                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s, SliceDyn dyn = SliceDyn());
 int launch_slice_rows(const double* M, int64_t ld, int64_t rows, int64_t K, const int32_t* e, int nplanes,
-                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s);
+                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s, SliceDyn dyn = SliceDyn());
 int launch_truncate_slice_x(const double* X, int64_t ldx, int64_t n, const int32_t* f, int beta, int nplanes,
                             double* X1, int64_t ld1, __nv_bfloat16* planes, int64_t ps, int64_t pitch,
-                            cudaStream_t s);
+                            cudaStream_t s, SliceDyn dyn = SliceDyn());
 
 // Description of one Ozaki product on digit planes:
-//   L: kL planes of an M x K left operand, row-major per plane (row i at L + r*Lps + i*pitch)
-//   R: kR planes of a K x N right operand, column-major per plane (column j at R + s*Rps + j*pitch)
-//   pairs (r, s) with r + s <= T; anti-diagonals t = 2 .. tmax grouped by `gs`;
-//   out[g * ogs + j * ldo + i] = sum_{t in group g} 2^(7 (t_last(g) - t)) S_t[i, j]  (exact int64)
+//   L: planes of an M x K left operand, row-major per plane (row i at L + r*Lps + i*pitch)
+//   R: planes of a K x N right operand, column-major per plane (column j at R + s*Rps + j*pitch)
+//   d: plane counts kL, kR, pair bound T (r + s <= T), layout of the exact sums (int64 groups
+//      of gs anti-diagonals, or one int32 plane per anti-diagonal) and the persistent schedule;
+//      out[g * ogs + j * ldo + i].  When `dyn` is set the kernels read d from device memory
+//      (written by the device plan) and `done` lets them return when the refinement finished.
 struct PlaneGemm {
   const __nv_bfloat16* L;
   int64_t Lps;
@@ -32,25 +43,19 @@ struct PlaneGemm {
   int64_t Rps;
   int64_t pitch;
   int64_t M, N, K;
-  int kL, kR, T;
-  int tmax, gs, groups;
-  i64* out;     // int64 groups (word32 == 0) ...
+  GemmDesc d;
+  const GemmDesc* dyn;
+  const int* done;
+  i64* out;
   int64_t ogs, ldo;
   int* flags;   // device status word (timeouts), may be null
-  // int32 per-anti-diagonal planes: plane t - 2 at (int32_t*)out + (t - 2) * ogs (gs = 1).
-  // Chosen by plan_plane_gemm when every S_t fits int32 and `out_bytes_per_elem` holds them.
-  int word32;
   int out_bytes_per_elem;
   __host__ __device__ int32_t* out32() const { return reinterpret_cast<int32_t*>(out); }
 };
 
-// host: fill tmax / gs / groups; returns FRX_E_UNSUPPORTED if exactness cannot be guaranteed
+// host: fill the layout and schedule of g.d; FRX_E_UNSUPPORTED if exactness cannot be guaranteed
 int plan_plane_gemm(PlaneGemm& g);
 int pairs_in(int kL, int kR, int T);
-inline int group_last_t(const PlaneGemm& g, int grp) {
-  int t1 = 2 + (grp + 1) * g.gs - 1;
-  return t1 < g.tmax ? t1 : g.tmax;
-}
 
 // gemm_simt.cu / gemm_tc.cu
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s);

@@ -1,0 +1,486 @@
+// Device-side plan of each refinement iteration: the Sec. 4.1 choice of beta and alpha,
+// the slice counts of the three Ozaki products, the cluster threshold and the stopping
+// test, computed by single-block kernels so that an iteration needs no host round-trip.
+// Every decision uses the same IEEE operations, in the same order, as the CPU oracle.
+#include "frx_internal.cuh"
+#include "kernels.cuh"
+#include "plan.cuh"
+#include "profile.cuh"
+#include "plan_launch.cuh"
+
+namespace frx {
+
+constexpr int PT = 1024;  // threads of the plan kernels
+constexpr double U53 = 1.1102230246251565e-16;
+
+__device__ int dfloor_log2(double x) {
+  int ex;
+  frexp(x, &ex);
+  return ex - 1;
+}
+
+__device__ int dceil_log2(double x) {
+  int ex;
+  double fr = frexp(x, &ex);
+  return fr == 0.5 ? ex - 1 : ex;
+}
+
+__device__ int dceil_log2_sqrt(int64_t n) {
+  int bl = 0;
+  for (uint64_t v = (uint64_t)(n - 1); v; v >>= 1) ++bl;
+  return (bl + 1) / 2;
+}
+
+__device__ int dceil_log2_int(int64_t n) {
+  int bl = 0;
+  for (uint64_t v = (uint64_t)(n - 1); v; v >>= 1) ++bl;
+  return bl;
+}
+
+// smallest k >= 1 with (2^(7k - eL - eR - 6) tau)^2 >= n^3, capped; 0 if an operand is zero
+__device__ int dslices_for(int64_t n, int eL, int eR, double tau, int kcap) {
+  if (eL == EZERO || eR == EZERO) return 0;
+  double n3 = __dmul_rn(__dmul_rn((double)n, (double)n), (double)n);
+  for (int k = 1; k <= kcap; ++k) {
+    double v = ldexp(tau, 7 * k - eL - eR - 6);
+    if (__dmul_rn(v, v) >= n3) return k;
+  }
+  return kcap;
+}
+
+// ---- block reductions (PT threads) ----
+__device__ int bmax_int(int v, int* red) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (PT >> 5) ? red[threadIdx.x] : INT32_MIN;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ int bmin_int(int v, int* red) { return -bmax_int(-v, red); }
+
+__device__ double bmax_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (PT >> 5) ? red[threadIdx.x] : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ double bmin_d(double v, double* red) { return -bmax_d(-v, red); }
+
+__device__ double bsum_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (PT >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+// Smallest adjacent gap of the sorted estimates exceeding omega (Lam if none) and max |lam|.
+// s: dynamic smem of next_pow2(n) doubles (bitonic sort).
+__device__ void gap_of(const double* lam, int64_t n, double omega, double* s, double* red, double& g,
+                       double& Lam) {
+  int64_t m = 1;
+  while (m < n) m <<= 1;
+  double amax = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += PT) {
+    double v = i < n ? lam[i] : INFINITY;
+    s[i] = v;
+    if (i < n) amax = fmax(amax, fabs(v));
+  }
+  __syncthreads();
+  for (int64_t k = 2; k <= m; k <<= 1) {
+    for (int64_t jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int64_t i = threadIdx.x; i < m; i += PT) {
+        int64_t l = i ^ jj;
+        if (l > i) {
+          double a = s[i], b = s[l];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            s[i] = b;
+            s[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  double gmin = INFINITY;
+  for (int64_t i = 1 + threadIdx.x; i < n; i += PT) {
+    double d = __dsub_rn(s[i], s[i - 1]);
+    if (d > omega) gmin = fmin(gmin, d);
+  }
+  gmin = bmin_d(gmin, red);
+  Lam = bmax_d(amax, red);
+  g = isinf(gmin) ? Lam : gmin;
+}
+
+__device__ void raise(DevPlan* p, int st) {
+  if (threadIdx.x == 0) {
+    p->status = st;
+    p->done = 1;
+    p->V.active = p->W.active = p->U.active = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA, const double* D,
+                                                  double* lam_prev, PlanOpts o, double omega_prev) {
+  extern __shared__ double sbuf[];
+  __shared__ int redi[32];
+  __shared__ double redd[32];
+  bool bad = false;
+  int emax = EZERO;
+  for (int64_t i = threadIdx.x; i < o.n; i += PT) {
+    double v = D[i];
+    bad |= !isfinite(v);
+    lam_prev[i] = v;
+    emax = max(emax, eA[i]);
+  }
+  emax = bmax_int(emax, redi);
+  int anybad = bmax_int(bad ? 1 : 0, redi);
+  double g, Lam;
+  gap_of(D, o.n, omega_prev, sbuf, redd, g, Lam);
+  if (threadIdx.x == 0) {
+    p->iter = 0;
+    p->done = 0;
+    p->status = FRX_MAX_ITER;
+    p->eAmax = emax;
+    p->sliced_kA = 0;
+    p->products = 0;
+    p->omega = omega_prev;
+    p->have_prev_step = 0;
+    p->prev_step = 0.0;
+    p->g = g;
+    p->Lam = Lam;
+    p->est = INFINITY;
+    p->clustered = 0;
+    p->ccount = 0;
+    for (int k = 0; k < 4; ++k) p->norms[k] = 0.0;
+    p->V.active = p->W.active = p->U.active = 0;
+    if (p->flags & FLAG_NONFINITE) anybad = 1;
+  }
+  __syncthreads();
+  if (anybad) raise(p, FRX_E_NONFINITE);
+}
+
+// beta, alpha, s_X, k_V and the V product (Alg. 1 line 1 with Sec. 3 and Sec. 4.1)
+__global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, PlanOpts o) {
+  __shared__ int redi[32];
+  __shared__ double redd[32];
+  __shared__ unsigned long long s2lo[32], s2hi[32];
+  if (p->done) return;
+  int fmx = EZERO, fmn = INT32_MAX, zero = 0;
+  for (int64_t i = threadIdx.x; i < o.n; i += PT) {
+    int e = f[i];
+    if (e == EZERO) {
+      zero = 1;
+    } else {
+      fmx = max(fmx, e);
+      fmn = min(fmn, e);
+    }
+  }
+  fmx = bmax_int(fmx, redi);
+  fmn = bmin_int(fmn, redi);
+  zero = bmax_int(zero, redi);
+  if (zero || (p->flags & FLAG_NONFINITE)) {
+    raise(p, zero ? FRX_E_ARG : FRX_E_NONFINITE);
+    return;
+  }
+  // S2 = sum_j 2^(2 f_j), exactly rounded (integer accumulation relative to the smallest term)
+  double S2 = 0.0;
+  if (fmx - fmn <= 45) {
+    unsigned __int128 acc = 0;
+    for (int64_t i = threadIdx.x; i < o.n; i += PT) acc += (unsigned __int128)1 << (2 * (f[i] - fmn));
+    unsigned long long lo = (unsigned long long)acc, hi = (unsigned long long)(acc >> 64);
+    // warp + block sum of 128-bit values
+    for (int off = 16; off > 0; off >>= 1) {
+      unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, off), hi2 = __shfl_xor_sync(0xffffffffu, hi, off);
+      unsigned long long nl = lo + lo2;
+      hi = hi + hi2 + (nl < lo ? 1ull : 0ull);
+      lo = nl;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s2lo[threadIdx.x >> 5] = lo;
+      s2hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned __int128 tot = 0;
+      for (int w = 0; w < PT / 32; ++w) tot += ((unsigned __int128)s2hi[w] << 64) | s2lo[w];
+      // round to nearest even: keep 63 bits and a sticky bit (the value is below 2^(90 + 14))
+      double r;
+      if ((tot >> 63) == 0) {
+        r = __ull2double_rn((unsigned long long)tot);
+      } else {
+        int bl = 0;
+        for (unsigned __int128 v = tot; v; v >>= 1) ++bl;
+        int sh = bl - 63;
+        unsigned long long v = (unsigned long long)(tot >> sh);
+        if ((tot & (((unsigned __int128)1 << sh) - 1)) != 0) v |= 1ull;
+        r = ldexp(__ull2double_rn(v), sh);
+      }
+      redd[0] = ldexp(r, 2 * fmn);
+    }
+    __syncthreads();
+    S2 = redd[0];
+  } else if (threadIdx.x == 0) {
+    // ascending sequential sum (the exponent spread is beyond the integer accumulator)
+    for (int e = fmn; e <= fmx; ++e)
+      for (int64_t i = 0; i < o.n; ++i)
+        if (f[i] == e) S2 = __dadd_rn(S2, ldexp(1.0, 2 * e));
+  }
+  if (threadIdx.x != 0) return;
+  const int64_t n = o.n;
+  double g = p->g, Lam = p->Lam;
+  int beta;
+  if (o.beta_override >= 0) {
+    beta = min(max(o.beta_override, 3), 47);
+  } else if (g <= 0.0 || Lam <= 0.0 || S2 <= 0.0) {
+    beta = 3;
+  } else {
+    double xi = o.xi > 0 ? o.xi : (double)n;
+    double q = __ddiv_rn(__dsqrt_rn(__ddiv_rn(__dmul_rn(__dmul_rn(xi, o.delta), g), __dmul_rn(Lam, S2))),
+                         0.75 * U53);
+    int b = o.beta_ceil ? dceil_log2(q) : dfloor_log2(q);
+    beta = min(max(b, 3), 47);
+  }
+  p->iter += 1;
+  p->beta = beta;
+  p->alpha = o.theory_alpha ? 53 - beta + dceil_log2_int(n) : 53 - beta + dceil_log2_sqrt(n);
+  p->sX = (54 - beta + 6) / 7;
+  p->fmax = fmx;
+  p->S2 = S2;
+  int kV = o.slices_A > 0 ? o.slices_A : dslices_for(n, p->eAmax, fmx, __dmul_rn(o.delta, g), o.k_cap);
+  if (kV < 1) kV = 1;
+  p->kV = kV;
+  GemmDesc d;
+  d.kL = kV;
+  d.kR = p->sX;
+  d.T = kV + 1;
+  if (gemm_desc_layout(d, n, 64) != FRX_OK || !d.word32) {
+    raise(p, FRX_E_UNSUPPORTED);
+    return;
+  }
+  gemm_desc_schedule(d, n, n, 256);
+  p->V = d;
+  p->products += desc_pairs(d);
+  for (int k = 0; k < 4; ++k) p->norms[k] = 0.0;
+  p->ccount = 0;
+}
+
+// after the A planes for this iteration are written
+__global__ void k_plan_mark_sliced(DevPlan* p) {
+  if (threadIdx.x == 0 && !p->done && p->kV > p->sliced_kA) p->sliced_kA = p->kV;
+}
+
+// k_W and the W product (Alg. 1 line 4)
+__global__ void __launch_bounds__(PT) k_plan_w(DevPlan* p, const int32_t* h, PlanOpts o) {
+  __shared__ int redi[32];
+  if (p->done) return;
+  int hm = EZERO;
+  for (int64_t i = threadIdx.x; i < o.n; i += PT) hm = max(hm, h[i]);
+  hm = bmax_int(hm, redi);
+  if (threadIdx.x != 0) return;
+  int kW = dslices_for(o.n, p->fmax, hm, __dmul_rn(o.delta, p->g), o.k_cap);
+  p->kW = kW;
+  GemmDesc d;
+  d.kL = min(p->sX, kW);
+  d.kR = kW;
+  d.T = kW + 1;
+  if (kW > 0) {
+    if (gemm_desc_layout(d, o.n, 64) != FRX_OK || !d.word32) {
+      raise(p, FRX_E_UNSUPPORTED);
+      return;
+    }
+  } else {
+    d.active = 0;
+    d.groups = 0;
+    d.tmax = 0;
+    d.gs = 1;
+    d.word32 = 1;
+  }
+  gemm_desc_schedule(d, o.n, o.n, 256);
+  p->W = d;
+  p->products += desc_pairs(d);
+}
+
+// cluster threshold omega (fixed, or the Ogita-Aishima form from ||W_off||_F and ||diag R||_2)
+__global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, PlanOpts o) {
+  __shared__ double redd[32];
+  if (p->done) return;
+  if (o.cluster_omega >= 0) {
+    if (threadIdx.x == 0) p->omega = o.cluster_omega;
+    return;
+  }
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < o.n; i += PT) s = __fma_rn(r[i], r[i], s);
+  s = bsum_d(s, redd);
+  if (threadIdx.x == 0) p->omega = 2.0 * (__dsqrt_rn(p->norms[1]) + p->Lam * __dsqrt_rn(s));
+}
+
+// k_U and the update product (Alg. 1 line 6)
+__global__ void __launch_bounds__(PT) k_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
+  __shared__ int redi[32];
+  if (p->done) return;
+  int rm = EZERO, em = EZERO;
+  for (int64_t i = threadIdx.x; i < o.n; i += PT) {
+    rm = max(rm, rho[i]);
+    em = max(em, eta[i]);
+  }
+  rm = bmax_int(rm, redi);
+  em = bmax_int(em, redi);
+  if (threadIdx.x != 0) return;
+  int kU = dslices_for(o.n, rm, em, o.delta, o.k_cap);
+  p->kU = kU;
+  GemmDesc d;
+  d.kL = kU;
+  d.kR = kU;
+  d.T = kU + 1;
+  if (kU > 0) {
+    if (gemm_desc_layout(d, o.n, 64) != FRX_OK || !d.word32) {
+      raise(p, FRX_E_UNSUPPORTED);
+      return;
+    }
+  } else {
+    d.active = 0;
+    d.groups = 0;
+    d.tmax = 0;
+    d.gs = 1;
+    d.word32 = 1;
+  }
+  gemm_desc_schedule(d, o.n, o.n, 256);
+  p->U = d;
+  p->products += desc_pairs(d);
+}
+
+// stopping test (reading R7): est = step^2 max|lam| / (xi_stop gap) <= delta
+__global__ void __launch_bounds__(PT) k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, PlanOpts o) {
+  extern __shared__ double sbuf[];
+  __shared__ double redd[32];
+  if (p->done) return;
+  const double omega = p->omega;
+  double g, Lam;
+  gap_of(lam_new, o.n, omega, sbuf, redd, g, Lam);
+  for (int64_t i = threadIdx.x; i < o.n; i += PT) lam_prev[i] = lam_new[i];
+  if (threadIdx.x != 0) return;
+  if (p->flags & FLAG_NONFINITE) {
+    raise(p, FRX_E_NONFINITE);
+    return;
+  }
+  if (p->flags & (FLAG_TIMEOUT | FLAG_RANGE)) {
+    raise(p, (p->flags & FLAG_TIMEOUT) ? FRX_E_TIMEOUT : FRX_E_RANGE);
+    return;
+  }
+  double step = __dsqrt_rn(p->norms[2]);
+  double xs = o.xi_stop > 0 ? o.xi_stop : (double)o.n;
+  double est = g > 0 ? __ddiv_rn(__dmul_rn(__dmul_rn(step, step), Lam), __dmul_rn(xs, g)) : INFINITY;
+  p->step = step;
+  p->est = est;
+  p->g = g;
+  p->Lam = Lam;
+  p->normE = __dsqrt_rn(p->norms[0]);
+  p->clustered = p->ccount / 2;
+  if (est <= o.delta) {
+    p->status = FRX_OK;
+    p->done = 1;
+  } else if (p->have_prev_step && step > 0.5 * p->prev_step) {
+    p->status = FRX_STAGNATED;
+    p->done = 1;
+  } else if (p->iter >= o.max_iter) {
+    p->status = FRX_MAX_ITER;
+    p->done = 1;
+  }
+  p->prev_step = step;
+  p->have_prev_step = 1;
+}
+
+// ---------------------------------------------------------------------------
+static size_t sort_smem(int64_t n) {
+  int64_t m = 1;
+  while (m < n) m <<= 1;
+  return (size_t)m * sizeof(double);
+}
+
+#define FRX_PLAN_SMEM(kernel, bytes)                                                                    \
+  do {                                                                                                  \
+    FRX_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
+  } while (0)
+
+int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev, const PlanOpts& o,
+                     double omega_prev, cudaStream_t s) {
+  size_t sm = sort_smem(o.n);
+  FRX_PLAN_SMEM(k_plan_init, sm);
+  k_plan_init<<<1, PT, sm, s>>>(p, eA, D, lam_prev, o, omega_prev);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plan_v(DevPlan* p, const int32_t* f, const PlanOpts& o, cudaStream_t s) {
+  k_plan_v<<<1, PT, 0, s>>>(p, f, o);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plan_mark_sliced(DevPlan* p, cudaStream_t s) {
+  k_plan_mark_sliced<<<1, 32, 0, s>>>(p);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plan_w(DevPlan* p, const int32_t* h, const PlanOpts& o, cudaStream_t s) {
+  k_plan_w<<<1, PT, 0, s>>>(p, h, o);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plan_omega(DevPlan* p, const double* r, const PlanOpts& o, cudaStream_t s) {
+  k_plan_omega<<<1, PT, 0, s>>>(p, r, o);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const PlanOpts& o, cudaStream_t s) {
+  k_plan_u<<<1, PT, 0, s>>>(p, rho, eta, o);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const PlanOpts& o, cudaStream_t s) {
+  size_t sm = sort_smem(o.n);
+  FRX_PLAN_SMEM(k_plan_end, sm);
+  k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, o);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+}  // namespace frx

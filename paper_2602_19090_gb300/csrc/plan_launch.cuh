@@ -1,0 +1,17 @@
+// Launchers of the device-side plan kernels (plan.cu).
+#pragma once
+
+#include "plan.cuh"
+
+namespace frx {
+
+int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev, const PlanOpts& o,
+                     double omega_prev, cudaStream_t s);
+int launch_plan_v(DevPlan* p, const int32_t* f, const PlanOpts& o, cudaStream_t s);
+int launch_plan_mark_sliced(DevPlan* p, cudaStream_t s);
+int launch_plan_w(DevPlan* p, const int32_t* h, const PlanOpts& o, cudaStream_t s);
+int launch_plan_omega(DevPlan* p, const double* r, const PlanOpts& o, cudaStream_t s);
+int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const PlanOpts& o, cudaStream_t s);
+int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const PlanOpts& o, cudaStream_t s);
+
+}  // namespace frx

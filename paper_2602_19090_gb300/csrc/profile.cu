@@ -38,18 +38,22 @@ void count_launches(int k) {
   launches += k;
 }
 
+// operations of plan-driven products, known only once the device plan has run
+void profile_add_gemm_work(double ops) {
+  std::lock_guard<std::mutex> g(mu);
+  gemm_ops += ops;
+}
+
 GemmTimer::GemmTimer(const PlaneGemm& g, cudaStream_t s) : s_(s) {
   std::lock_guard<std::mutex> lk(mu);
   gemm_launches += 1;
   launches += 1;
-  int pairs = 0;
-  for (int t = 2; t <= g.tmax; ++t) {
-    int lo = t - g.kR > 1 ? t - g.kR : 1;
-    int hi = g.kL < t - 1 ? g.kL : t - 1;
-    if (hi >= lo) pairs += hi - lo + 1;
+  if (!g.dyn) {
+    int pairs = desc_pairs(g.d);
+    gemm_ops += 2.0 * (double)g.M * (double)g.N * (double)g.K * pairs;
+    gemm_bytes += 2.0 * (double)g.K * ((double)g.M * g.d.kL + (double)g.N * g.d.kR) +
+                  (g.d.word32 ? 4.0 : 8.0) * g.d.groups * (double)g.M * g.N;
   }
-  gemm_ops += 2.0 * (double)g.M * (double)g.N * (double)g.K * pairs;
-  gemm_bytes += 2.0 * (double)g.K * ((double)g.M * g.kL + (double)g.N * g.kR) + (g.word32 ? 4.0 : 8.0) * g.groups * (double)g.M * g.N;
   if (enabled) {
     a_ = get_event();
     b_ = get_event();

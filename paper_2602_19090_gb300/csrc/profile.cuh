@@ -6,6 +6,7 @@
 namespace frx {
 
 void count_launches(int k);
+void profile_add_gemm_work(double ops);
 
 // RAII: counts one GEMM launch and, with profiling on, brackets it with CUDA events
 class GemmTimer {

@@ -20,6 +20,20 @@ __device__ __forceinline__ int tlast_of(const GroupArgs& ga, int g) {
   return t1 < ga.tmax ? t1 : ga.tmax;
 }
 
+// fields of a GroupArgs from its device descriptor (plan-driven products)
+__device__ __forceinline__ GroupArgs resolve(GroupArgs g) {
+  if (g.dyn) {
+    const GemmDesc& d = *g.dyn;
+    g.groups = d.active ? d.groups : 0;
+    g.gs = d.gs;
+    g.tmax = d.tmax;
+    g.word32 = d.word32;
+    int t0 = 2 + g.gs - 1 < g.tmax ? 2 + g.gs - 1 : g.tmax;
+    g.exact128 = g.groups > 0 && (g.word32 ? 31 : 62) + DIGIT_BITS * (g.tmax - t0) + 1 <= 127;
+  }
+  return g;
+}
+
 __device__ __forceinline__ i64 group_word(const GroupArgs& ga, int g, int64_t i, int64_t j) {
   int64_t idx = g * ga.ogs + j * ga.ldo + i;
   return ga.word32 ? (i64) reinterpret_cast<const int32_t*>(ga.out)[idx] : reinterpret_cast<const i64*>(ga.out)[idx];
@@ -185,6 +199,7 @@ __global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_
   int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   int64_t j = blockIdx.y;
   if (i >= M) return;
+  ga = resolve(ga);
   dd v = gather_dd(ga, i, j, eL[i], eR[j]);
   Ch[i + j * ldh] = v.h;
   if (Cl) Cl[i + j * ldl] = v.l;
@@ -251,6 +266,9 @@ __device__ u64 block_max_u64(u64 v, u64* red) {
 // smem: n double-doubles (V column).  x^T x is exact in integers (X1 lies on the grid
 // 2^(f_j + beta - 53)); x^T v is accumulated with TwoProduct/TwoSum (Dot2 form).
 __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
+  if (a.done && *a.done) return;
+  a.V = resolve(a.V);
+  if (a.beta_dyn) a.beta = *a.beta_dyn;
   extern __shared__ dd vcol[];
   __shared__ dd redd[32];
   __shared__ u64 redu[32];
@@ -379,6 +397,9 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
 
 // ---- ||off-diagonal W||_F^2 (for the automatic cluster threshold) ------------------
 __global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
+  if (a.done && *a.done) return;
+  a.W = resolve(a.W);
+  if (a.W.groups == 0) return;
   __shared__ double red[32];
   const int64_t j = blockIdx.x;
   double s = 0.0;
@@ -393,6 +414,9 @@ __global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
 
 // ---- line 5: E~ column j, its exponent, ||E~||_F^2 -----------------------------------
 __global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
+  if (a.done && *a.done) return;
+  a.W = resolve(a.W);
+  if (a.omega_dyn) a.omega = *a.omega_dyn;
   __shared__ double red[32];
   __shared__ u64 redu[32];
   __shared__ dd redd[32];
@@ -455,6 +479,9 @@ __global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
 
 // ---- line 6: X <- RN(X1 + X1 E~) (pair arithmetic), ||X_new - X_old||_F^2 ----------------
 __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
+  if (a.done && *a.done) return;
+  a.U = resolve(a.U);
+  if (a.beta_dyn) a.beta = *a.beta_dyn;
   __shared__ double red[32];
   const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t j = blockIdx.y;
@@ -502,14 +529,15 @@ GroupArgs group_args(const PlaneGemm& g) {
   ga.out = g.out;
   ga.ogs = g.ogs;
   ga.ldo = g.ldo;
-  ga.groups = g.groups;
-  ga.gs = g.gs;
-  ga.tmax = g.tmax;
-  ga.word32 = g.word32;
+  ga.dyn = g.dyn;
+  ga.groups = g.d.active ? g.d.groups : 0;
+  ga.gs = g.d.gs;
+  ga.tmax = g.d.tmax;
+  ga.word32 = g.d.word32;
   // |R_g| < 2^31 (int32 planes) or 2^62 (int64 groups); the combination spans
   // 7 (tmax - t_last(0)) more bits and must stay below 2^127
-  int span = g.groups > 0 ? DIGIT_BITS * (g.tmax - group_last_t(g, 0)) : 0;
-  ga.exact128 = g.groups > 0 && (g.word32 ? 31 : 62) + span + 1 <= 127;
+  int t0 = 2 + g.d.gs - 1 < g.d.tmax ? 2 + g.d.gs - 1 : g.d.tmax;
+  ga.exact128 = ga.groups > 0 && (g.d.word32 ? 31 : 62) + DIGIT_BITS * (g.d.tmax - t0) + 1 <= 127;
   return ga;
 }
 

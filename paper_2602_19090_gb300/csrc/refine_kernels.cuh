@@ -10,7 +10,8 @@ struct GroupArgs {  // exact anti-diagonal sums of one Ozaki product (int64 grou
   int64_t ogs, ldo;
   int groups, gs, tmax;
   int word32;
-  int exact128;  // all groups combine exactly in 128 bits
+  int exact128;            // all groups combine exactly in 128 bits
+  const GemmDesc* dyn;     // when set, the fields above are read from it at kernel entry
 };
 
 struct ResidualArgs {
@@ -26,6 +27,8 @@ struct ResidualArgs {
   int64_t ldr;
   int32_t* h;            // out: column exponents of Res
   int beta;              // X1 lies on the grid 2^(f_j + beta - 53)
+  const int* beta_dyn;   // device beta (overrides beta)
+  const int* done;
   double* Vh;            // optional debug copies (ld = n)
   double* Vl;
 };
@@ -40,6 +43,8 @@ struct CorrectionArgs {
   const double* X1;
   int64_t ld1;
   double omega;          // cluster threshold
+  const double* omega_dyn;
+  const int* done;
   double* E;             // out: E~
   int64_t lde;
   int32_t* eta;          // out: column exponents of E~
@@ -56,6 +61,8 @@ struct UpdateArgs {
   const int32_t* eta;
   const int32_t* f;      // X1 lies on the grid 2^(f_j + beta - 53)
   int beta;
+  const int* beta_dyn;
+  const int* done;
   const double* X1;
   int64_t ld1;
   double* X;             // in: X_old, out: X_new

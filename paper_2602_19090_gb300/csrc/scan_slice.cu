@@ -9,7 +9,8 @@ namespace frx {
 // ---- S1: exponent of every column (one block per column) ------------------
 __global__ void __launch_bounds__(256) k_col_exponents(const double* __restrict__ M, int64_t ld,
                                                        int64_t rows, int64_t cols, int32_t* __restrict__ e,
-                                                       int* __restrict__ flags) {
+                                                       int* __restrict__ flags, const int* done) {
+  if (done && *done) return;
   int64_t j = blockIdx.x;
   const double* col = M + j * ld;
   u64 mx = 0;
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(256) k_col_exponents(const double* __restrict_
 // grid (ceil(rows / 256), ceil(cols / 64)); rowmax must be zeroed first.
 __global__ void __launch_bounds__(256) k_row_maxbits(const double* __restrict__ M, int64_t ld,
                                                      int64_t rows, int64_t cols, u64* __restrict__ rowmax,
-                                                     int* __restrict__ flags) {
+                                                     int* __restrict__ flags, const int* done) {
+  if (done && *done) return;
   int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (i >= rows) return;
   int64_t j0 = (int64_t)blockIdx.y * 64;
@@ -58,30 +60,42 @@ __global__ void __launch_bounds__(256) k_row_maxbits(const double* __restrict__ 
   if (mx) atomicMax(rowmax + i, mx);
 }
 
-__global__ void k_maxbits_to_exponents(const u64* __restrict__ mx, int64_t n, int32_t* __restrict__ e) {
+__global__ void k_maxbits_to_exponents(u64* __restrict__ mx, int64_t n, int32_t* __restrict__ e, const int* done) {
+  if (done && *done) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) e[i] = mx[i] == 0 ? EZERO : ceil_log2_absbits(mx[i]);
+  if (i < n) {
+    e[i] = mx[i] == 0 ? EZERO : ceil_log2_absbits(mx[i]);
+    mx[i] = 0;  // ready for the next scan
+  }
 }
 
 // ---- S3/S4: digit planes along columns (no transpose) ---------------------
 // planes[r * ps + j * pitch + k] = digit r of M[k, j] (column exponent e[j]); pad k in [K, pitch) = 0.
+// planes [from, nplanes) are written; nplanes / from may come from the device plan
 __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M, int64_t ld, int64_t K,
                                                     int64_t N, const int32_t* __restrict__ e, int nplanes,
                                                     __nv_bfloat16* __restrict__ planes, int64_t ps,
-                                                    int64_t pitch) {
+                                                    int64_t pitch, SliceDyn dyn) {
+  if (dyn.done && *dyn.done) return;
+  if (dyn.nplanes) nplanes = *dyn.nplanes;
+  const int from = dyn.from ? *dyn.from : 0;
+  if (from >= nplanes) return;
   int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
   int64_t j = blockIdx.y;
   if (k >= pitch) return;
   __nv_bfloat16* out = planes + j * pitch + k;
   int ej = e[j];
   if (k >= K || ej == EZERO) {
-    for (int r = 0; r < nplanes; ++r) out[r * ps] = digit_bf16(0);
+    for (int r = from; r < nplanes; ++r) out[r * ps] = digit_bf16(0);
     return;
   }
   i64 P;
   int q;
   decompose(M[k + j * ld], P, q);
-  for (int r = 1; r <= nplanes; ++r) out[(r - 1) * ps] = digit_bf16(next_digit(P, q, ej + 1 - DIGIT_BITS * r));
+  for (int r = 1; r <= nplanes; ++r) {
+    int d = next_digit(P, q, ej + 1 - DIGIT_BITS * r);
+    if (r > from) out[(r - 1) * ps] = digit_bf16(d);
+  }
 }
 
 // ---- digit planes along rows of a column-major matrix (transpose through smem) ----
@@ -89,7 +103,10 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
 __global__ void __launch_bounds__(256) k_slice_rows(const double* __restrict__ M, int64_t ld, int64_t rows,
                                                     int64_t K, const int32_t* __restrict__ e, int nplanes,
                                                     __nv_bfloat16* __restrict__ planes, int64_t ps,
-                                                    int64_t pitch) {
+                                                    int64_t pitch, SliceDyn dyn) {
+  if (dyn.done && *dyn.done) return;
+  if (dyn.nplanes) nplanes = *dyn.nplanes;
+  if (nplanes <= 0) return;
   __shared__ double tile[32][33];
   int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
@@ -120,7 +137,10 @@ __global__ void __launch_bounds__(256) k_truncate_slice_x(const double* __restri
                                                           const int32_t* __restrict__ f, int beta, int nplanes,
                                                           double* __restrict__ X1, int64_t ld1,
                                                           __nv_bfloat16* __restrict__ planes, int64_t ps,
-                                                          int64_t pitch) {
+                                                          int64_t pitch, SliceDyn dyn) {
+  if (dyn.done && *dyn.done) return;
+  if (dyn.nplanes) nplanes = *dyn.nplanes;
+  if (dyn.beta) beta = *dyn.beta;
   int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
   int64_t j = blockIdx.y;
   if (k >= pitch) return;
@@ -152,42 +172,42 @@ __global__ void __launch_bounds__(256) k_truncate_slice_x(const double* __restri
 // host launchers
 // ---------------------------------------------------------------------------
 int launch_col_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, int* flags,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int* done) {
   if (cols == 0) return FRX_OK;
-  k_col_exponents<<<(unsigned)cols, 256, 0, s>>>(M, ld, rows, cols, e, flags);
+  k_col_exponents<<<(unsigned)cols, 256, 0, s>>>(M, ld, rows, cols, e, flags, done);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
+// scratch must be zero on entry; it is left zero (k_maxbits_to_exponents clears it)
 int launch_row_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, u64* scratch,
-                         int* flags, cudaStream_t s) {
+                         int* flags, cudaStream_t s, const int* done) {
   if (rows == 0) return FRX_OK;
-  FRX_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(u64) * rows, s));
   dim3 g((unsigned)((rows + 255) / 256), (unsigned)((cols + 63) / 64));
-  k_row_maxbits<<<g, 256, 0, s>>>(M, ld, rows, cols, scratch, flags);
+  k_row_maxbits<<<g, 256, 0, s>>>(M, ld, rows, cols, scratch, flags, done);
   count_launches(1);
-  k_maxbits_to_exponents<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(scratch, rows, e);
+  k_maxbits_to_exponents<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(scratch, rows, e, done);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
 int launch_slice_cols(const double* M, int64_t ld, int64_t K, int64_t N, const int32_t* e, int nplanes,
-                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s) {
-  if (N == 0 || nplanes == 0) return FRX_OK;
+                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s, SliceDyn dyn) {
+  if (N == 0 || (nplanes == 0 && !dyn.nplanes)) return FRX_OK;
   dim3 g((unsigned)((pitch + 255) / 256), (unsigned)N);
-  k_slice_cols<<<g, 256, 0, s>>>(M, ld, K, N, e, nplanes, planes, ps, pitch);
+  k_slice_cols<<<g, 256, 0, s>>>(M, ld, K, N, e, nplanes, planes, ps, pitch, dyn);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
 int launch_slice_rows(const double* M, int64_t ld, int64_t rows, int64_t K, const int32_t* e, int nplanes,
-                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s) {
-  if (rows == 0 || nplanes == 0) return FRX_OK;
+                      __nv_bfloat16* planes, int64_t ps, int64_t pitch, cudaStream_t s, SliceDyn dyn) {
+  if (rows == 0 || (nplanes == 0 && !dyn.nplanes)) return FRX_OK;
   dim3 g((unsigned)((pitch + 31) / 32), (unsigned)((rows + 31) / 32));
-  k_slice_rows<<<g, 256, 0, s>>>(M, ld, rows, K, e, nplanes, planes, ps, pitch);
+  k_slice_rows<<<g, 256, 0, s>>>(M, ld, rows, K, e, nplanes, planes, ps, pitch, dyn);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
@@ -195,9 +215,9 @@ int launch_slice_rows(const double* M, int64_t ld, int64_t rows, int64_t K, cons
 
 int launch_truncate_slice_x(const double* X, int64_t ldx, int64_t n, const int32_t* f, int beta, int nplanes,
                             double* X1, int64_t ld1, __nv_bfloat16* planes, int64_t ps, int64_t pitch,
-                            cudaStream_t s) {
+                            cudaStream_t s, SliceDyn dyn) {
   dim3 g((unsigned)((pitch + 255) / 256), (unsigned)n);
-  k_truncate_slice_x<<<g, 256, 0, s>>>(X, ldx, n, f, beta, nplanes, X1, ld1, planes, ps, pitch);
+  k_truncate_slice_x<<<g, 256, 0, s>>>(X, ldx, n, f, beta, nplanes, X1, ld1, planes, ps, pitch, dyn);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
