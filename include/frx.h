@@ -147,6 +147,24 @@ FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx
                     double* X1, double* Vh, double* Vl, double* Res, double* W, double* E,
                     double* r_out, void* stream);
 
+/*
+ * Batched refinement of `count` independent symmetric problems of possibly different
+ * orders (each as in frx_refine, with the same delta and options).  A, X, D, lda, ldx and
+ * n are HOST arrays of length `count` holding device pointers and sizes.  One iteration of
+ * the whole batch is captured once into a CUDA graph (one independent branch per problem)
+ * and replayed until every problem has converged, stagnated or reached max_iter; each
+ * problem's plan lives on the device, so the host reads only an array of finish flags per
+ * iteration.  `infos` (host, `count` entries) may be NULL.
+ * Returns FRX_OK if every problem converged, else the largest soft status (1, 2), or the
+ * first hard error (< 0; the per-problem statuses are then in infos when it is not NULL).
+ * The call must not be made while `stream` is being captured.
+ */
+FRX_API size_t frx_refine_batched_workspace_bytes(const int64_t* n, int count, const frx_opts* opts);
+FRX_API int frx_refine_batched(const double* const* A, const int64_t* lda, double* const* X,
+                               const int64_t* ldx, double* const* D, const int64_t* n, int count,
+                               double delta, const frx_opts* opts, void* work, size_t work_bytes,
+                               frx_info* infos, void* stream);
+
 /* Scratch bytes of frx_ozaki_gemm for these sizes and k. */
 FRX_API size_t frx_ozaki_gemm_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices);
 

@@ -44,6 +44,10 @@ _SIGS = {
     "frx_refine_step": (C.c_int, [c_p, c_i64, c_p, c_i64, c_p, c_i64, C.c_double, C.POINTER(Opts),
                                   C.c_double, c_p, C.c_size_t, C.POINTER(Info),
                                   c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "frx_refine_batched_workspace_bytes": (C.c_size_t, [C.POINTER(c_i64), C.c_int, C.POINTER(Opts)]),
+    "frx_refine_batched": (C.c_int, [C.POINTER(c_p), C.POINTER(c_i64), C.POINTER(c_p), C.POINTER(c_i64),
+                                     C.POINTER(c_p), C.POINTER(c_i64), C.c_int, C.c_double, C.POINTER(Opts),
+                                     c_p, C.c_size_t, C.POINTER(Info), c_p]),
     "frx_ozaki_gemm_workspace_bytes": (C.c_size_t, [c_i64, c_i64, c_i64, C.c_int]),
     "frx_ozaki_gemm": (C.c_int, [c_p, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64,
                                  C.c_int, C.c_int, c_p, C.c_size_t, c_p]),

@@ -106,6 +106,40 @@ def refine(A, X, D, delta, opts: Options | None = None, work=None, stream=None):
     return d
 
 
+def refine_batched(As, Xs, Ds, delta, opts: Options | None = None, work=None, stream=None):
+    """Batched in-place refinement of independent problems; returns a list of info dicts."""
+    lib = _lib.load()
+    count = len(As)
+    o = (opts or Options()).to_c()
+    cols = [colmajor(A) for A in As]
+    xcols = [colmajor(X) for X in Xs]
+    for t in list(As) + list(Xs) + list(Ds):
+        _f64_cuda(t, "batched operand")
+    P = C.c_void_p * count
+    I64 = C.c_int64 * count
+    n = I64(*[A.shape[0] for A in As])
+    Ap = P(*[c[0].data_ptr() for c in cols])
+    lda = I64(*[c[1] for c in cols])
+    Xp = P(*[c[0].data_ptr() for c in xcols])
+    ldx = I64(*[c[1] for c in xcols])
+    Dp = P(*[D.data_ptr() for D in Ds])
+    if work is None:
+        work = workspace(lib.frx_refine_batched_workspace_bytes(n, count, C.byref(o)), As[0].device)
+    infos = (_lib.Info * count)()
+    st = lib.frx_refine_batched(Ap, lda, Xp, ldx, Dp, n, count, float(delta), C.byref(o), _ptr(work),
+                                work.numel(), infos, _stream(stream))
+    _check(st, "frx_refine_batched")
+    for (Xc, _, copied), X in zip(xcols, Xs):
+        if copied:
+            X.copy_(Xc)
+    out = []
+    for i in range(count):
+        d = infos[i].as_dict()
+        d["status_name"] = STATUS.get(d["status"], str(d["status"]))
+        out.append(d)
+    return out
+
+
 def refine_step(A, X, D, delta, opts: Options | None = None, omega_prev: float = 0.0,
                 intermediates: bool = True, work=None, stream=None):
     """One iteration; returns (info, dict of intermediates as row-major tensors)."""

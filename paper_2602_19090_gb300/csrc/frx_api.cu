@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
+#include <mutex>
 #include <vector>
 
 #include "frx_internal.cuh"
@@ -302,6 +304,17 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   return FRX_OK;
 }
 
+// dynamic shared memory limits of the refinement kernels, set once before any launch or capture
+int ensure_attributes() {
+  static std::once_flag once;
+  static int st = FRX_OK;
+  std::call_once(once, []() {
+    st = set_refine_kernel_attributes();
+    if (st == FRX_OK) st = set_plan_kernel_attributes();
+  });
+  return st;
+}
+
 int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* D, int64_t n, double delta,
                   const frx_opts* popts, double omega_prev, void* work, size_t work_bytes, frx_info* pinfo,
                   const DebugOut* dbg, bool single, void* stream) {
@@ -325,6 +338,7 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
     const int max_iter = single ? 1 : o.max_iter;
     const PlanOpts po = plan_opts(o, delta, n, max_iter);
     st = [&]() -> int {
+      FRX_TRY(ensure_attributes());
       FRX_CUDA_TRY(cudaMemsetAsync(ws.plan, 0, sizeof(DevPlan), s));
       FRX_CUDA_TRY(cudaMemsetAsync(ws.rowmax, 0, sizeof(u64) * n, s));
       FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s));
@@ -361,6 +375,197 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
   info.omega = hp.omega;
   info.clustered_pairs = hp.clustered;
   if (pinfo) *pinfo = info;
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// batched refinement: one CUDA graph per phase with an independent branch per problem
+// ---------------------------------------------------------------------------
+struct ForkPool {
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t origin = nullptr;       // captures run here (the caller's stream may be the legacy one)
+  cudaEvent_t enter = nullptr, leave = nullptr;
+};
+
+int fork_pool(int k, ForkPool** out) {
+  static std::mutex mu;
+  static ForkPool pools[64];
+  int dev = 0;
+  FRX_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return FRX_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  ForkPool& p = pools[dev];
+  if (!p.fork) {
+    FRX_CUDA_TRY(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
+    FRX_CUDA_TRY(cudaEventCreateWithFlags(&p.enter, cudaEventDisableTiming));
+    FRX_CUDA_TRY(cudaEventCreateWithFlags(&p.leave, cudaEventDisableTiming));
+    FRX_CUDA_TRY(cudaStreamCreateWithFlags(&p.origin, cudaStreamNonBlocking));
+  }
+  while ((int)p.side.size() < k) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    FRX_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    FRX_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    p.side.push_back(st);
+    p.join.push_back(ev);
+  }
+  *out = &p;
+  return FRX_OK;
+}
+
+// capture body(b, stream) for b < count on `k` side streams forked from s, then tail(s)
+int capture_fanout(cudaStream_t s, ForkPool* pool, int k, int count, const std::function<int(int, cudaStream_t)>& body,
+                   const std::function<int(cudaStream_t)>& tail, cudaGraphExec_t* exec) {
+  cudaGraph_t graph = nullptr;
+  FRX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int st = [&]() -> int {
+    FRX_CUDA_TRY(cudaEventRecord(pool->fork, s));
+    for (int q = 0; q < k; ++q) FRX_CUDA_TRY(cudaStreamWaitEvent(pool->side[q], pool->fork, 0));
+    for (int b = 0; b < count; ++b) FRX_TRY(body(b, pool->side[b % k]));
+    for (int q = 0; q < k; ++q) {
+      FRX_CUDA_TRY(cudaEventRecord(pool->join[q], pool->side[q]));
+      FRX_CUDA_TRY(cudaStreamWaitEvent(s, pool->join[q], 0));
+    }
+    if (tail) FRX_TRY(tail(s));
+    return FRX_OK;
+  }();
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st != FRX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return FRX_E_CUDA;
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? FRX_OK : FRX_E_CUDA;
+}
+
+struct BatchLayout {
+  std::vector<size_t> off;
+  size_t plans_off, done_off, gather_off, bytes;
+};
+
+BatchLayout batch_layout(const int64_t* n, int count, int kcap) {
+  BatchLayout L;
+  size_t off = 0;
+  for (int b = 0; b < count; ++b) {
+    L.off.push_back(off);
+    off += round_up((int64_t)carve_refine(nullptr, n[b], kcap).bytes, 256);
+  }
+  L.plans_off = off;
+  off += round_up(sizeof(DevPlan*) * (size_t)count, 256);
+  L.done_off = off;
+  off += round_up(sizeof(int) * (size_t)count, 256);
+  L.gather_off = off;
+  off += round_up(sizeof(DevPlan) * (size_t)count, 256);
+  L.bytes = off + 256;
+  return L;
+}
+
+int refine_batched_impl(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                        double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, void* work,
+                        size_t work_bytes, frx_info* infos, cudaStream_t caller) {
+  BatchLayout L = batch_layout(n, count, o.k_cap);
+  if (!work || !aligned256(work) || work_bytes < L.bytes) return FRX_E_WORKSPACE;
+  FRX_TRY(ensure_attributes());
+  char* base = (char*)work;
+  std::vector<RefineWs> ws(count);
+  std::vector<DevPlan*> hplans(count);
+  std::vector<PlanOpts> po(count);
+  for (int b = 0; b < count; ++b) {
+    ws[b] = carve_refine(base + L.off[b], n[b], o.k_cap);
+    hplans[b] = ws[b].plan;
+    po[b] = plan_opts(o, delta, n[b], o.max_iter);
+  }
+  DevPlan** dplans = (DevPlan**)(base + L.plans_off);
+  int* ddone = (int*)(base + L.done_off);
+  DevPlan* gathered = (DevPlan*)(base + L.gather_off);
+  ForkPool* pool = nullptr;
+  FRX_TRY(fork_pool(count < 64 ? count : 64, &pool));
+  cudaStream_t s = pool->origin;
+  FRX_CUDA_TRY(cudaEventRecord(pool->enter, caller));
+  FRX_CUDA_TRY(cudaStreamWaitEvent(s, pool->enter, 0));
+  FRX_CUDA_TRY(cudaMemcpyAsync(dplans, hplans.data(), sizeof(DevPlan*) * count, cudaMemcpyHostToDevice, s));
+  const int k = count < 64 ? count : 64;
+  cudaGraphExec_t g_setup = nullptr, g_iter = nullptr, g_end = nullptr;
+  int st = [&]() -> int {
+    FRX_TRY(capture_fanout(
+        s, pool, k, count,
+        [&](int b, cudaStream_t q) -> int {
+          FRX_CUDA_TRY(cudaMemsetAsync(ws[b].plan, 0, sizeof(DevPlan), q));
+          FRX_CUDA_TRY(cudaMemsetAsync(ws[b].rowmax, 0, sizeof(u64) * n[b], q));
+          FRX_TRY(launch_col_exponents(A[b], lda[b], n[b], n[b], ws[b].eA, &ws[b].plan->flags, q));
+          return launch_plan_init(ws[b].plan, ws[b].eA, D[b], ws[b].lam_prev, po[b], 0.0, q);
+        },
+        nullptr, &g_setup));
+    FRX_TRY(capture_fanout(
+        s, pool, k, count,
+        [&](int b, cudaStream_t q) -> int {
+          return enqueue_iteration(A[b], lda[b], X[b], ldx[b], n[b], o, po[b], ws[b], nullptr, q);
+        },
+        [&](cudaStream_t q) -> int { return launch_collect_done(dplans, count, ddone, q); }, &g_iter));
+    FRX_TRY(capture_fanout(
+        s, pool, k, count,
+        [&](int b, cudaStream_t q) -> int {
+          FRX_CUDA_TRY(
+              cudaMemcpyAsync(D[b], ws[b].lam_prev, sizeof(double) * n[b], cudaMemcpyDeviceToDevice, q));
+          return FRX_OK;
+        },
+        [&](cudaStream_t q) -> int { return launch_gather_plans(dplans, count, gathered, q); }, &g_end));
+    FRX_CUDA_TRY(cudaGraphLaunch(g_setup, s));
+    std::vector<int> done(count);
+    for (int it = 1; it <= o.max_iter; ++it) {
+      FRX_CUDA_TRY(cudaGraphLaunch(g_iter, s));
+      FRX_CUDA_TRY(cudaMemcpyAsync(done.data(), ddone, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+      FRX_CUDA_TRY(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int b = 0; b < count; ++b) all &= done[b] != 0;
+      if (all) break;
+    }
+    FRX_CUDA_TRY(cudaGraphLaunch(g_end, s));
+    std::vector<DevPlan> hp(count);
+    FRX_CUDA_TRY(cudaMemcpyAsync(hp.data(), gathered, sizeof(DevPlan) * count, cudaMemcpyDeviceToHost, s));
+    FRX_CUDA_TRY(cudaStreamSynchronize(s));
+    int worst = FRX_OK;
+    double ops = 0.0;
+    for (int b = 0; b < count; ++b) {
+      const DevPlan& P = hp[b];
+      ops += 2.0 * (double)n[b] * (double)n[b] * (double)n[b] * (double)P.products;
+      if (infos) {
+        frx_info& I = infos[b];
+        memset(&I, 0, sizeof(I));
+        I.status = P.status;
+        I.iters = P.iter;
+        I.beta = P.beta;
+        I.alpha = P.alpha;
+        I.s_X = P.sX;
+        I.k_V = P.kV;
+        I.k_W = P.kW;
+        I.k_U = P.kU;
+        I.products = P.products;
+        I.err_est = P.est;
+        I.step = P.step;
+        I.min_gap = P.g;
+        I.max_lambda = P.Lam;
+        I.omega = P.omega;
+        I.clustered_pairs = P.clustered;
+      }
+      if (P.status < 0) {
+        if (worst >= 0) worst = P.status;
+      } else if (worst >= 0 && P.status > worst) {
+        worst = P.status;
+      }
+    }
+    profile_add_gemm_work(ops);
+    return worst;
+  }();
+  if (g_setup) cudaGraphExecDestroy(g_setup);
+  if (g_iter) cudaGraphExecDestroy(g_iter);
+  if (g_end) cudaGraphExecDestroy(g_end);
+  if (cudaEventRecord(pool->leave, s) != cudaSuccess || cudaStreamWaitEvent(caller, pool->leave, 0) != cudaSuccess)
+    return FRX_E_CUDA;
   return st;
 }
 
@@ -421,6 +626,35 @@ int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx, double
   int st = refine_common(A, lda, X, ldx, D, n, delta, opts, omega_prev, work, work_bytes, info, &d, true, stream);
   // a single step reports soft statuses as-is; FRX_MAX_ITER only means "not yet converged"
   return st;
+}
+
+size_t frx_refine_batched_workspace_bytes(const int64_t* n, int count, const frx_opts* opts) {
+  if (!n || count < 1) return 0;
+  int kcap = opts ? opts->k_cap : 16;
+  if (kcap < 1 || kcap > MAX_PLANES) return 0;
+  for (int b = 0; b < count; ++b)
+    if (n[b] < 1 || n[b] > FRX_MAX_N) return 0;
+  return batch_layout(n, count, kcap).bytes;
+}
+
+int frx_refine_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                       double* const* D, const int64_t* n, int count, double delta, const frx_opts* opts, void* work,
+                       size_t work_bytes, frx_info* infos, void* stream) {
+  frx_opts o;
+  frx_default_opts(&o);
+  if (opts) o = *opts;
+  if (!A || !lda || !X || !ldx || !D || !n || count < 1) return FRX_E_ARG;
+  if (!(delta > U53)) return FRX_E_DELTA;
+  if (validate_opts(o) < 0) return FRX_E_ARG;
+  for (int b = 0; b < count; ++b) {
+    if (!A[b] || !X[b] || !D[b] || n[b] < 1 || lda[b] < n[b] || ldx[b] < n[b]) return FRX_E_ARG;
+    if (n[b] > FRX_MAX_N) return FRX_E_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FRX_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return FRX_E_ARG;
+  return refine_batched_impl(A, lda, X, ldx, D, n, count, delta, o, work, work_bytes, infos, s);
 }
 
 size_t frx_ozaki_gemm_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices) {

@@ -424,15 +424,16 @@ static size_t sort_smem(int64_t n) {
   return (size_t)m * sizeof(double);
 }
 
-#define FRX_PLAN_SMEM(kernel, bytes)                                                                    \
-  do {                                                                                                  \
-    FRX_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
-  } while (0)
+int set_plan_kernel_attributes() {
+  int bytes = (int)sort_smem(FRX_MAX_N);
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plan_init, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plan_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return FRX_OK;
+}
 
 int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev, const PlanOpts& o,
                      double omega_prev, cudaStream_t s) {
   size_t sm = sort_smem(o.n);
-  FRX_PLAN_SMEM(k_plan_init, sm);
   k_plan_init<<<1, PT, sm, s>>>(p, eA, D, lam_prev, o, omega_prev);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -476,8 +477,34 @@ int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const Plan
 
 int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const PlanOpts& o, cudaStream_t s) {
   size_t sm = sort_smem(o.n);
-  FRX_PLAN_SMEM(k_plan_end, sm);
   k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, o);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+__global__ void k_collect_done(DevPlan* const* plans, int count, int* done) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < count) done[b] = plans[b]->done;
+}
+
+__global__ void k_gather_plans(DevPlan* const* plans, int count, DevPlan* out) {
+  int b = blockIdx.x;
+  if (b >= count) return;
+  const int* src = reinterpret_cast<const int*>(plans[b]);
+  int* dst = reinterpret_cast<int*>(out + b);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevPlan) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+}
+
+int launch_collect_done(DevPlan* const* plans, int count, int* done, cudaStream_t s) {
+  k_collect_done<<<(count + 255) / 256, 256, 0, s>>>(plans, count, done);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+int launch_gather_plans(DevPlan* const* plans, int count, DevPlan* out, cudaStream_t s) {
+  k_gather_plans<<<count, 128, 0, s>>>(plans, count, out);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;

@@ -13,5 +13,8 @@ int launch_plan_w(DevPlan* p, const int32_t* h, const PlanOpts& o, cudaStream_t 
 int launch_plan_omega(DevPlan* p, const double* r, const PlanOpts& o, cudaStream_t s);
 int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const PlanOpts& o, cudaStream_t s);
 int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const PlanOpts& o, cudaStream_t s);
+int set_plan_kernel_attributes();
+int launch_collect_done(DevPlan* const* plans, int count, int* done, cudaStream_t s);
+int launch_gather_plans(DevPlan* const* plans, int count, DevPlan* out, cudaStream_t s);
 
 }  // namespace frx

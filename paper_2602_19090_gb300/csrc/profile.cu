@@ -54,7 +54,9 @@ GemmTimer::GemmTimer(const PlaneGemm& g, cudaStream_t s) : s_(s) {
     gemm_bytes += 2.0 * (double)g.K * ((double)g.M * g.d.kL + (double)g.N * g.d.kR) +
                   (g.d.word32 ? 4.0 : 8.0) * g.d.groups * (double)g.M * g.N;
   }
-  if (enabled) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s_, &cs);
+  if (enabled && cs == cudaStreamCaptureStatusNone) {
     a_ = get_event();
     b_ = get_event();
     cudaEventRecord(a_, s_);

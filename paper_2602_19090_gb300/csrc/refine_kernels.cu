@@ -551,9 +551,14 @@ int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR
   return FRX_OK;
 }
 
+int set_refine_kernel_attributes() {
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(dd) * (size_t)FRX_MAX_N)));
+  return FRX_OK;
+}
+
 int launch_residual(const ResidualArgs& a, cudaStream_t s) {
   size_t smem = sizeof(dd) * (size_t)a.n;
-  FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_residual<<<(unsigned)a.n, 256, smem, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());

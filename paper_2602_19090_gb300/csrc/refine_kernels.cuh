@@ -71,6 +71,7 @@ struct UpdateArgs {
 };
 
 GroupArgs group_args(const PlaneGemm& g);
+int set_refine_kernel_attributes();
 int launch_residual(const ResidualArgs& a, cudaStream_t s);
 int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s);
 int launch_correction(const CorrectionArgs& a, cudaStream_t s);

@@ -127,3 +127,43 @@ def batched_sizes(count: int = 256, lo: int = 32, hi: int = 512, case: int = 0):
     n = g.integers(lo, hi + 1, size=count)
     logc = g.uniform(2.0, 12.0, size=count)
     return n, 10.0 ** logc
+
+
+def hadamard_workload(n: int, cond: float, seed: int, rel: float = 1e-8):
+    """Exact-truth workload for n = 4^k: A = Q diag(lam) Q^T with Q = H_n / sqrt(n) (Sylvester
+    Hadamard, exactly orthogonal in FP64) and dyadic eigenvalues lam_k = m_k 2^-40, so every
+    entry of A is an exact FP64 number (integer Walsh-Hadamard sums below 2^53).
+    Returns (A, X0, D0, Q, lam) with Q's columns ordered like lam (ascending)."""
+    k = int(round(np.log2(n) / 2))
+    if 4 ** k != n:
+        raise ValueError("n must be a power of 4")
+    lam = spectrum(n, cond)
+    m = np.maximum(np.rint(lam * 2.0 ** 40), 1).astype(np.int64)
+    lam = m.astype(np.float64) * 2.0 ** -40
+    # W = H diag(m) H by two integer fast Walsh-Hadamard transforms (rows, then columns)
+    W = np.diag(m).astype(np.int64)
+
+    def fwht_rows(M):
+        M = M.copy()
+        h = 1
+        while h < n:
+            M = M.reshape(M.shape[0], -1, 2 * h)
+            a = M[:, :, :h].copy()
+            b = M[:, :, h:].copy()
+            M[:, :, :h] = a + b
+            M[:, :, h:] = a - b
+            M = M.reshape(M.shape[0], n)
+            h *= 2
+        return M
+
+    W = fwht_rows(W)          # diag(m) H  (H symmetric)
+    W = fwht_rows(W.T).T      # H diag(m) H
+    A = W.astype(np.float64) * (2.0 ** -40 / n)
+    Hm = fwht_rows(np.eye(n, dtype=np.int64))
+    Q = Hm.astype(np.float64) / np.sqrt(float(n))
+    g = rng(seed + 1)
+    Y = Q + g.standard_normal((n, n)) * (rel / (2.0 * np.sqrt(n)))
+    Qr, R = np.linalg.qr(Y)
+    X0 = np.ascontiguousarray(Qr * np.sign(np.diag(R)))
+    D0 = lam * (1.0 + rel * g.standard_normal(n))
+    return np.ascontiguousarray(A), X0, D0, Q, lam

@@ -239,3 +239,36 @@ def test_fp64_comparator_reaches_delta():
     X, lam, info = fp64_refine.refine(g.to_dev(A), g.to_dev(X0), g.to_dev(D0), 1e-14)
     assert info["status"] == "converged"
     assert tr.forward_error(Xh, Xl, X.cpu().numpy()) <= 1e-14
+
+
+def test_refine_batched_matches_single(api):
+    # the graph-captured batch runs the same kernels and device plans as frx_refine
+    g = G()
+    probs = [synth.refine_workload(nn, c, v, case=nn) for nn, c, v in
+             ((40, 1e3, "spd"), (64, 1e6, "spd"), (130, 1e4, "indefinite"), (257, 1e2, "spd"), (65, 1e8, "spd"))]
+    As = [g.to_dev(p[0]) for p in probs]
+    Xb = [g.to_dev(p[1]) for p in probs]
+    Db = [g.to_dev(p[2]) for p in probs]
+    infos = api.refine_batched(As, Xb, Db, 1e-13)
+    for p, A, Xg, Dg, info in zip(probs, As, Xb, Db, infos):
+        Xs, Ds = g.to_dev(p[1]), g.to_dev(p[2])
+        ref = api.refine(A, Xs, Ds, 1e-13)
+        assert info["iters"] == ref["iters"] and info["status"] == ref["status"]
+        assert info["products"] == ref["products"]
+        assert np.array_equal(Xg.cpu().numpy(), Xs.cpu().numpy())
+        assert np.array_equal(Dg.cpu().numpy(), Ds.cpu().numpy())
+
+
+@pytest.mark.parametrize("xi,factor", [(0.0, 2.0), (1.0, 1.0)])
+def test_refine_batched_forward_error(api, xi, factor):
+    # Sec. 4.1 (xi = n) aims at an error of about delta (O(delta), the paper's figures);
+    # the eq. proposed_beta form with xi = 1 keeps it below delta
+    g = G()
+    probs = [synth.refine_workload(nn, 1e3, "spd", case=7 + nn) for nn in (33, 96, 200)]
+    Xs = [g.to_dev(p[1]) for p in probs]
+    infos = api.refine_batched([g.to_dev(p[0]) for p in probs], Xs, [g.to_dev(p[2]) for p in probs], 1e-13,
+                               api.Options(xi=xi))
+    for p, X, info in zip(probs, Xs, infos):
+        Xh, Xl, _, _ = tr.eigvecs_dd(p[0], p[1])
+        assert info["status"] == 0
+        assert tr.forward_error(Xh, Xl, X.cpu().numpy()) <= factor * 1e-13
