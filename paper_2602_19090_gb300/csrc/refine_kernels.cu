@@ -85,19 +85,30 @@ __device__ __forceinline__ i128 double_to_i128(double h) {
 
 // sum_g R_g 2^(7 (tlast[G-1] - tlast[g])), exact (caller checks ga.exact128)
 __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, int64_t j) {
-  if (ga.word32) {
-    // one int32 plane per anti-diagonal: Horner with the constant shift 7 in int64 chunks of
-    // four planes (|chunk| < 2^(31 + 21)), chunks merged in 128 bits
+  if (ga.word32 && ga.groups <= 16) {
+    // one int32 plane per anti-diagonal: all loads issued first, then Horner with the
+    // constant shift 7 in int64 chunks of four planes (|chunk| < 2^(31 + 21)), merged in 128 bits
     const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
+    int32_t v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = q < ga.groups ? __ldg(p + q * ga.ogs) : 0;
     i128 N = 0;
-    int g = 0;
-    while (g < ga.groups) {
+#pragma unroll
+    for (int g = 0; g < 16; g += 4) {
+      if (g >= ga.groups) break;
       int len = ga.groups - g < 4 ? ga.groups - g : 4;
       i64 c = 0;
-      for (int q = 0; q < len; ++q) c = (c << 7) + (i64)p[(g + q) * ga.ogs];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < len) c = (c << 7) + (i64)v[g + q];
       N = g ? (N << (7 * len)) + (i128)c : (i128)c;
-      g += len;
     }
+    return N;
+  }
+  if (ga.word32) {
+    const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
+    i128 N = 0;
+    for (int g = 0; g < ga.groups; ++g) N = (N << 7) + (i128)p[g * ga.ogs];
     return N;
   }
   i128 N = 0;
@@ -478,33 +489,76 @@ __global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
 }
 
 // ---- line 6: X <- RN(X1 + X1 E~) (pair arithmetic), ||X_new - X_old||_F^2 ----------------
-__global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
+// RN(x1 + N 2^c) for int64 N with |N 2^c| well below |x1|: x1 = P 2^q (53-bit P) and the
+// sum is rounded on x1's grid with round-half-even on the combined integer.  Returns false
+// when the result leaves x1's binade (then the caller takes the general path).
+__device__ __forceinline__ bool add_small_rn(double x1, i64 N, int c, double& out) {
+  if (x1 == 0.0) return false;
+  i64 P;
+  int q;
+  decompose(x1, P, q);
+  if (P > -(1ll << 52) && P < (1ll << 52)) return false;   // subnormal x1
+  int sh = q - c;   // N 2^c = (N / 2^sh) ulps of x1
+  i64 T;
+  if (sh <= 0) {
+    return false;     // U is not below x1's grid: general path
+  } else if (sh >= 63) {
+    // |N| < 2^63 <= 2^sh: |N / 2^sh| < 1; below half an ulp whenever |N| < 2^(sh - 1)
+    if (sh == 63 && (N >= (1ll << 62) || N <= -(1ll << 62))) return false;
+    T = P;
+  } else {
+    i64 fl = N >> sh;
+    i64 rem = N - (fl << sh);
+    i64 half = 1ll << (sh - 1);
+    T = P + fl;
+    if (rem > half || (rem == half && (T & 1))) T += 1;
+  }
+  if (T >= (1ll << 53) || T <= -(1ll << 53) || (T > -(1ll << 52) && T < (1ll << 52))) return false;
+  out = __dmul_rn(__ll2double_rn(T), pow2(q));
+  return true;
+}
+
+// one block per column: X(:, j) <- RN(X1(:, j) + U(:, j)); one atomic per column for ||dX||_F^2
+__global__ void __launch_bounds__(1024) k_update(UpdateArgs a) {
   if (a.done && *a.done) return;
   a.U = resolve(a.U);
   if (a.beta_dyn) a.beta = *a.beta_dyn;
   __shared__ double red[32];
-  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  const int64_t j = blockIdx.y;
+  const int64_t j = blockIdx.x;
+  const int ej = a.eta[j];
   double d2 = 0.0;
-  if (i < a.n) {
+  for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) {
     double x1 = a.X1[i + j * a.ld1];
     double xn = x1;
     if (a.U.groups > 0) {
       bool done = false;
-      int ri = a.rho[i], ej = a.eta[j];
-      if (a.U.exact128 && ri != EZERO && ej != EZERO) {
-        // RN(x1 + U) with x1 = m 2^G and U = N 2^c, combined exactly in 128 bits
-        i128 N = combine_groups(a.U, i, j);
-        int G = a.f[j] + a.beta - 53;
+      int ri = a.rho[i];
+      if (ri != EZERO && ej != EZERO) {
         int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
-        i128 m = (i128)grid_mantissa(x1, G);
-        int d = G - c;
-        if (d >= 0 && bitlen128(m) + d <= 124 && bitlen128(N) <= 124) {
-          xn = i128_scaled_rn((m << d) + N, c);
-          done = true;
-        } else if (d < 0 && bitlen128(N) - d <= 124) {
-          xn = i128_scaled_rn(m + (N << (-d)), G);
-          done = true;
+        if (a.U.word32 && a.U.groups <= 5) {
+          // the anti-diagonal planes combine exactly in int64 (31 + 28 bits)
+          const int32_t* p = reinterpret_cast<const int32_t*>(a.U.out) + j * a.U.ldo + i;
+          int32_t v[5];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) v[q] = q < a.U.groups ? __ldg(p + q * a.U.ogs) : 0;
+          i64 N = 0;
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+            if (q < a.U.groups) N = (N << 7) + (i64)v[q];
+          done = add_small_rn(x1, N, c, xn);
+        }
+        if (!done && a.U.exact128) {
+          i128 N = combine_groups(a.U, i, j);
+          const int G = a.f[j] + a.beta - 53;
+          i128 m = (i128)grid_mantissa(x1, G);
+          int d = G - c;
+          if (d >= 0 && bitlen128(m) + d <= 124 && bitlen128(N) <= 124) {
+            xn = i128_scaled_rn((m << d) + N, c);
+            done = true;
+          } else if (d < 0 && bitlen128(N) - d <= 124) {
+            xn = i128_scaled_rn(m + (N << (-d)), G);
+            done = true;
+          }
         }
       }
       if (!done) {
@@ -516,7 +570,7 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
     }
     double xo = a.X[i + j * a.ldx];
     double dx = __dsub_rn(xn, xo);
-    d2 = dx * dx;
+    d2 = __fma_rn(dx, dx, d2);
     a.X[i + j * a.ldx] = xn;
   }
   d2 = block_sum_d(d2, red);
@@ -580,8 +634,7 @@ int launch_correction(const CorrectionArgs& a, cudaStream_t s) {
 }
 
 int launch_update(const UpdateArgs& a, cudaStream_t s) {
-  dim3 grid((unsigned)((a.n + 255) / 256), (unsigned)a.n);
-  k_update<<<grid, 256, 0, s>>>(a);
+  k_update<<<(unsigned)a.n, 1024, 0, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
