@@ -43,8 +43,9 @@ def parse():
     p.add_argument("--sample-rows", type=int, default=8)
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
-    p.add_argument("--workload", choices=["refine", "batched"], default="refine",
-                   help="refine: one n=4096 refinement per step; batched: 256 matrices, n in [32, 512]")
+    p.add_argument("--workload", choices=["refine", "batched", "configs"], default="refine",
+                   help="refine: one n=4096 refinement per step; batched: 256 matrices, n in [32, 512]; "
+                        "configs: the n=2048 variants and the n=8192 forward-error sweep")
     p.add_argument("--count", type=int, default=256)
     return p.parse_args()
 
@@ -115,31 +116,25 @@ def barrier(ws):
         dist.barrier()
 
 
-def allmax(ws, x):
+def allmax(ws, x, device="cuda"):
+    """Maximum of a per-rank scalar (the job's time is the slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def gemm_traffic():
-    """Per-launch DRAM bytes of the GEMM from the committed ncu summary, if the kernel is unchanged."""
-    import hashlib
-    import re
-    src = os.path.join(ROOT, "paper_2602_19090_gb300", "csrc", "gemm_tc.cu")
-    md = os.path.join(ROOT, "profiles", "plane_gemm_tc256_n4096_traffic.md")
-    if not (os.path.exists(src) and os.path.exists(md)):
-        return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    txt = open(md).read()
-    m1 = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
-    m2 = re.search(r"kernel_source_sha256_16: (\w+)", txt)
-    if m1 and m2 and m2.group(1) == sha:
-        return int(m1.group(1))
-    return None
+def replica_case(rank):
+    """Each rank refines its own matrix (weak scaling, no data-path collective)."""
+    return rank
+
+
+def job_throughput(ws, units_per_rank, ms_max):
+    """Whole-job rate: units all ranks processed / the slowest rank's time."""
+    return ws * units_per_rank * 1e3 / ms_max
 
 
 def cpu_oracle_sample(A, X0, D0, delta, total_products, rows):
@@ -174,7 +169,7 @@ def run_ours(args):
     ws, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     n, delta = args.n, args.delta
-    A, X0, D0, lam = synth.refine_workload(n, args.cond, "spd", case=rank)
+    A, X0, D0, lam = synth.refine_workload(n, args.cond, "spd", case=replica_case(rank))
     At = torch.from_numpy(A).to(dev)
     X0t, _, _ = api.colmajor(torch.from_numpy(X0).to(dev))
     D0t = torch.from_numpy(D0).to(dev)
@@ -251,7 +246,7 @@ def run_ours(args):
         "refine": {"status": info["status_name"], "iters": info["iters"], "err_est": info["err_est"],
                    "step": info["step"], "products": info["products"], "k_V": info["k_V"],
                    "s_X": info["s_X"], "beta": info["beta"]},
-        "refinements_per_s": ws * 1e3 / ms,
+        "refinements_per_s": job_throughput(ws, 1, ms),
         "roofline": {"bound": "tensor", "kernel": "slice-product GEMM (digit planes)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": gemm_traffic(),
@@ -398,7 +393,8 @@ def run_batched(args):
     torch.cuda.synchronize()
     fp64_ms = s2.elapsed_time(e2)
     line = {
-        "metric": "matrices/s refined to the forward-error target (batched)", "value": ws * args.count * 1e3 / ms,
+        "metric": "matrices/s refined to the forward-error target (batched)",
+        "value": job_throughput(ws, args.count, ms),
         "unit": "matrices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 digit planes, int64 exact sums, f64/dd elsewhere", "data": "synthetic",
@@ -412,6 +408,86 @@ def run_batched(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _timed_refine(api, A, X0, D0, delta, opts, work, reps=1):
+    import torch
+    best, info, X, D = 1e30, None, None, None
+    for _ in range(reps):
+        X = X0.clone()
+        D = D0.clone()
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        info = api.refine(A, X, D, delta, opts, work=work)
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e))
+    return best, info, X
+
+
+def run_configs(args):
+    """Config-2 variants at n = 2048 and the config-4 sweep at n = 8192 (one JSON line)."""
+    import torch
+
+    from paper_2602_19090_gb300 import api, fp64_refine, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    out = {"metric": "configs", "variants_n2048": [], "sweep_n8192": []}
+    n = 2048
+    work = api.workspace(api.refine_workspace_bytes(n), dev)
+    for cond, variant in ((1e4, "spd"), (1e10, "spd"), (1e14, "spd"), (1e4, "indefinite"), (1e4, "clustered")):
+        A, X0, D0, lam = synth.refine_workload(n, cond, variant, case=int(cond) % 97 + len(variant))
+        At = torch.from_numpy(A).to(dev)
+        X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
+        D0t = torch.from_numpy(D0).to(dev)
+        opts = api.Options(cluster_omega=-1.0 if variant == "clustered" else 0.0)
+        for delta in (1e-10, 1e-14):
+            ms, info, X = _timed_refine(api, At, X0t, D0t, delta, opts, work, reps=2)
+            rec = {"cond": cond, "variant": variant, "delta": delta, "ms": ms, "status": info["status_name"],
+                   "iters": info["iters"], "products": info["products"], "k_V": info["k_V"], "s_X": info["s_X"],
+                   "err_est": info["err_est"], "clustered_pairs": info["clustered_pairs"]}
+            if variant == "spd" or delta == 1e-14:
+                torch.cuda.synchronize()
+                s = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                s.record()
+                Xb, _, ib = fp64_refine.refine(At, X0t.clone(), D0t.clone(), delta)
+                e.record()
+                torch.cuda.synchronize()
+                rec.update(fp64_ms=s.elapsed_time(e), fp64_status=ib["status"], fp64_iters=ib["iters"],
+                           max_abs_diff_vs_fp64=float((Xb - X).abs().max()))
+            out["variants_n2048"].append(rec)
+        del At, X0t, D0t
+    del work
+    n = 8192
+    A, X0, D0, lam = synth.refine_workload(n, 1e12, "spd", case=4)
+    At = torch.from_numpy(A).to(dev)
+    X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
+    D0t = torch.from_numpy(D0).to(dev)
+    del A, X0
+    work = api.workspace(api.refine_workspace_bytes(n), dev)
+    for k in range(8, 16):
+        delta = 10.0 ** (-k)
+        ms, info, X = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work)
+        rec = {"delta": delta, "ms": ms, "status": info["status_name"], "iters": info["iters"],
+               "products": info["products"], "k_V": info["k_V"], "s_X": info["s_X"], "beta": info["beta"],
+               "err_est": info["err_est"], "step": info["step"]}
+        if k in (8, 12):
+            torch.cuda.synchronize()
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            Xb, _, ib = fp64_refine.refine(At, X0t.clone(), D0t.clone(), delta)
+            e.record()
+            torch.cuda.synchronize()
+            rec.update(fp64_ms=s.elapsed_time(e), fp64_status=ib["status"], fp64_iters=ib["iters"],
+                       max_abs_diff_vs_fp64=float((Xb - X).abs().max()))
+        out["sweep_n8192"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -453,6 +529,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "configs":
+        run_configs(args)
     else:
         run_ours(args)
 
