@@ -30,6 +30,30 @@ METRIC = ("seconds to reach forward error ≤1e-14 at n=4096 vs native-FP64 refi
           "Ozaki GEMM TFLOPS-eq")
 
 
+def gemm_traffic():
+    """DRAM bytes per launch of the tensor-core product kernel from the committed ncu summary,
+    or None when the kernel source has changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "plane_gemm_tc256_n4096_traffic.md")
+    src = os.path.join(ROOT, "paper_2602_19090_gb300", "csrc", "gemm_tc.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        for key in ("traffic_bytes_per_launch:", "kernel_source_sha256_16:"):
+            if key in line:
+                vals[key] = line.split(key, 1)[1].strip().split()[0]
+    if vals.get("kernel_source_sha256_16:") != sha:
+        return None
+    try:
+        return int(vals["traffic_bytes_per_launch:"])
+    except (KeyError, ValueError):
+        return None
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)

@@ -123,6 +123,58 @@ __host__ __device__ inline int next_digit(i64& P, int q, int wexp) {
 
 __device__ inline __nv_bfloat16 digit_bf16(int d) { return __float2bfloat16_rn((float)d); }
 
+// P 2^q as a double for |P| < 2^53, assembled from its fields with integer instructions
+// when the result is normal (ldexp otherwise)
+__device__ __forceinline__ double exact_double(i64 P, int q) {
+  if (P == 0) return 0.0;
+  const u64 a = P < 0 ? (u64)0 - (u64)P : (u64)P;
+  const int L = 64 - __clzll((long long)a);
+  const int E = L - 1 + q;
+  if (L <= 53 && E >= -1022 && E <= 1023)
+    return __longlong_as_double((long long)((P < 0 ? (1ull << 63) : 0ull) | ((u64)(E + 1023) << 52) |
+                                            ((a << (53 - L)) & ((1ull << 52) - 1))));
+  return ldexp((double)P, q);
+}
+
+// Digits of x = P 2^q on the fixed grid of exponent e, plane by plane without the
+// sequential remainder.  After r round-half-even digits the partial sum is the
+// round-half-even multiple Q_r 2^(s_r) of P, s_r = e + 1 - 7r - q (a tie leaves Q_r even
+// because Q_r = 128 Q_(r-1) + d_r and d_r is chosen even), so d_r = Q_r - 128 Q_(r-1);
+// |d_r| <= 64 makes it a function of Q_r mod 256 and Q_(r-1) mod 2.  Signs are symmetric:
+// the digits of -x are the negated digits of x.
+struct DigitSource {
+  u64 a;     // |P|
+  int q;     // x = +-a 2^q
+  int tz;    // trailing zero bits of a
+  bool neg;
+};
+
+__device__ __forceinline__ DigitSource digit_source(i64 P, int q) {
+  DigitSource s;
+  s.neg = P < 0;
+  s.a = s.neg ? (u64)0 - (u64)P : (u64)P;
+  s.q = q;
+  s.tz = s.a ? __ffsll((long long)s.a) - 1 : 64;
+  return s;
+}
+
+// Q_r mod 256 for the plane of weight 2^(wexp) (s = wexp - q)
+__device__ __forceinline__ unsigned digit_q8(const DigitSource& s, int wexp) {
+  const int sh = wexp - s.q;
+  if (sh <= 0) return sh <= -8 ? 0u : (unsigned)(s.a << (-sh)) & 0xffu;
+  const unsigned t8 = sh >= 64 ? 0u : (unsigned)(s.a >> sh) & 0xffu;
+  const unsigned rb = sh > 64 ? 0u : (unsigned)(s.a >> (sh - 1)) & 1u;
+  const unsigned sticky = s.tz < sh - 1 ? 1u : 0u;
+  return (t8 + (rb & (sticky | (t8 & 1u)))) & 0xffu;
+}
+
+// digit for plane weight 2^(wexp) given Q mod 256 of this plane and Q mod 2 of the previous one
+__device__ __forceinline__ int digit_from_q(const DigitSource& s, unsigned q8, unsigned prev_par) {
+  int d = (int)((q8 - (prev_par << 7)) & 0xffu);
+  d = d >= 128 ? d - 256 : d;
+  return s.neg ? -d : d;
+}
+
 // ---------------------------------------------------------------------------
 // Double-double arithmetic (FMA-based TwoProduct; explicit roundings)
 // ---------------------------------------------------------------------------

@@ -4,14 +4,12 @@
 // (line 5, with the Ogita-Aishima cluster rule) and the update by pair arithmetic
 // (line 6, Sec. 2.2).
 #include "frx_internal.cuh"
+#include "intround.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
 #include "refine_kernels.cuh"
 
 namespace frx {
-
-typedef __int128 i128;
-typedef unsigned __int128 u128;
 
 // value of entry (i, j) of an Ozaki product from its int64 groups (least significant first),
 // as a double-double; general path (any number of groups)
@@ -273,14 +271,71 @@ __device__ u64 block_max_u64(u64 v, u64* red) {
   return r;
 }
 
+// Rows handled per thread and loop trip in the element-wise kernels (every load of those
+// rows is issued before the first use) and the minimum resident blocks per SM requested
+// from the register allocator; tuning constants, measured on GB300.
+#ifndef FRX_RPT_RESIDUAL
+#define FRX_RPT_RESIDUAL 1
+#endif
+#ifndef FRX_RPT_CORRECTION
+#define FRX_RPT_CORRECTION 1
+#endif
+#ifndef FRX_RPT_UPDATE
+#define FRX_RPT_UPDATE 1
+#endif
+#ifndef FRX_MINB_RESIDUAL
+#define FRX_MINB_RESIDUAL 3
+#endif
+#ifndef FRX_MINB_CORRECTION
+#define FRX_MINB_CORRECTION 3
+#endif
+#ifndef FRX_MINB_UPDATE
+#define FRX_MINB_UPDATE 3
+#endif
+constexpr int RPT = 2;   // launch sizing: threads cover n / RPT rows (at most ELEM_THREADS)
+constexpr int ELEM_THREADS = 256;
+
+__host__ __device__ inline int elem_threads(int64_t n) {
+  int64_t t = (n + RPT - 1) / RPT;
+  t = (t + 31) / 32 * 32;
+  return (int)(t < 32 ? 32 : (t > ELEM_THREADS ? ELEM_THREADS : t));
+}
+
+// the int32 anti-diagonal planes of entry (i, j) (at most MP; zero beyond groups)
+template <int MP>
+__device__ __forceinline__ void load_planes(const GroupArgs& g, int64_t i, int64_t j, bool valid, int32_t (&v)[MP]) {
+  const int32_t* p = reinterpret_cast<const int32_t*>(g.out) + j * g.ldo + i;
+#pragma unroll
+  for (int q = 0; q < MP; ++q) v[q] = (valid && q < g.groups) ? __ldg(p + q * g.ogs) : 0;
+}
+
+// sum_q v_q 2^(7 (groups - 1 - q)) exactly (|result| < 2^127 when the product's
+// exact128 flag holds): Horner in int64 chunks of four planes, merged in 128 bits
+template <int MP>
+__device__ __forceinline__ i128 horner(const int32_t (&v)[MP], int groups) {
+  i128 N = 0;
+#pragma unroll
+  for (int g = 0; g < MP; g += 4) {
+    if (g < groups) {
+      const int len = groups - g < 4 ? groups - g : 4;
+      i64 c = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < len && g + q < MP) c = (c << 7) + (i64)v[g + q];
+      N = g ? (N << (7 * len)) + (i128)c : (i128)c;
+    }
+  }
+  return N;
+}
+
+constexpr int MP_RESIDUAL = 16;   // planes kept in registers by the fast paths
+constexpr int MP_UPDATE = 12;
+
 // ---- lines 2-4 (inner part): one block per column j --------------------------------
 // smem: n double-doubles (V column).  x^T x is exact in integers (X1 lies on the grid
 // 2^(f_j + beta - 53)); x^T v is accumulated with TwoProduct/TwoSum (Dot2 form).
-__global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
-  if (a.done && *a.done) return;
-  a.V = resolve(a.V);
-  if (a.beta_dyn) a.beta = *a.beta_dyn;
-  extern __shared__ dd vcol[];
+__device__ __noinline__ void residual_general(ResidualArgs a) {
+  extern __shared__ __align__(16) dd vcol[];
   __shared__ dd redd[32];
   __shared__ u64 redu[32];
   __shared__ i128 redi[32];
@@ -406,6 +461,179 @@ __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
   if (threadIdx.x == 0) a.h[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
 }
 
+// Integer fast path of lines 2-4 for int32 planes (at most 16) that combine exactly in 128
+// bits.  Pass 1 forms each V entry N_i 2^(c_i) (kept in shared memory), x^T x exactly and a
+// bound 2^T on the terms of x^T v; pass 2 accumulates x^T v on the fixed grid 2^(T + log2 n
+// - 126) (every term truncated once: relative error below 2^(2 log2 n - 126) of the largest
+// term); pass 3 rounds Res = V - x lambda once from its exact integer value.
+__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(ResidualArgs a) {
+  if (a.done && *a.done) return;
+  a.V = resolve(a.V);
+  if (a.beta_dyn) a.beta = *a.beta_dyn;
+  if (!(a.V.word32 && a.V.exact128 && a.V.groups <= MP_RESIDUAL)) {
+    residual_general(a);
+    return;
+  }
+  extern __shared__ __align__(16) dd vcol[];
+  i128* ncol = reinterpret_cast<i128*>(vcol);
+  __shared__ u64 redu[32];
+  __shared__ i128 redi[32];
+  __shared__ int redt[32];
+  const int64_t j = blockIdx.x;
+  const int64_t n = a.n;
+  const int fj = a.f[j];
+  const int gj = fj + a.beta - 53;
+  const int cbase = fj + 2 - DIGIT_BITS * a.V.tmax;   // c_i = eA_i + cbase
+  const double* x = a.X1 + j * a.ld1;
+  const int nb = a.V.groups;
+  u128 nn = 0;
+  int tb = -(1 << 30);
+  // pass 1
+  for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)FRX_RPT_RESIDUAL * blockDim.x) {
+    double xv[FRX_RPT_RESIDUAL];
+    int ei[FRX_RPT_RESIDUAL];
+    int32_t v[FRX_RPT_RESIDUAL][MP_RESIDUAL];
+#pragma unroll
+    for (int k = 0; k < FRX_RPT_RESIDUAL; ++k) {
+      const int64_t i = i0 + (int64_t)k * blockDim.x;
+      const bool ok = i < n;
+      xv[k] = ok ? x[i] : 0.0;
+      ei[k] = ok ? a.eA[i] : EZERO;
+      load_planes<MP_RESIDUAL>(a.V, i, j, ok && ei[k] != EZERO, v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < FRX_RPT_RESIDUAL; ++k) {
+      const int64_t i = i0 + (int64_t)k * blockDim.x;
+      if (i >= n) continue;
+      const i128 N = ei[k] == EZERO ? (i128)0 : horner<MP_RESIDUAL>(v[k], nb);
+      ncol[i] = N;
+      if (a.Vh || a.Vl) {   // debug copies of V as double-doubles
+        const double h = i128_to_double_rn(N), l = i128_to_double_rn(N - double_to_i128(h));
+        const int ex = ei[k] + cbase;
+        const dd vd = (ex >= -1022 + 130 && ex <= 1023 - 130) ? dd{__dmul_rn(h, pow2(ex)), __dmul_rn(l, pow2(ex))}
+                                                              : dd{ldexp(h, ex), ldexp(l, ex)};
+        if (a.Vh) a.Vh[i + j * n] = vd.h;
+        if (a.Vl) a.Vl[i + j * n] = vd.l;
+      }
+      const i64 m = grid_mantissa(xv[k], gj);
+      const u64 am = m < 0 ? (u64)0 - (u64)m : (u64)m;
+      nn += (u128)am * am;
+      if (N != 0 && m != 0) {
+        const int t = bitlen_u64(am) + bitlen_u128(abs_i128(N)) + ei[k] + cbase;
+        tb = t > tb ? t : tb;
+      }
+    }
+  }
+  // block reductions: x^T x (exact) and the term bound
+  {
+    u64 lo = (u64)nn, hi = (u64)(nn >> 64);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const u64 lo2 = __shfl_xor_sync(0xffffffffu, lo, o), hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      const u128 sum = (((u128)hi << 64) | lo) + (((u128)hi2 << 64) | lo2);
+      lo = (u64)sum;
+      hi = (u64)(sum >> 64);
+      const int t2 = __shfl_xor_sync(0xffffffffu, tb, o);
+      tb = t2 > tb ? t2 : tb;
+    }
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      redi[wi] = (i128)(((u128)hi << 64) | lo);
+      redt[wi] = tb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u128 tot = 0;
+      int tm = -(1 << 30);
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        tot += (u128)redi[k];
+        tm = redt[k] > tm ? redt[k] : tm;
+      }
+      redi[0] = (i128)tot;
+      redt[0] = tm;
+    }
+    __syncthreads();
+  }
+  const u128 nn_tot = (u128)redi[0];
+  const int T = redt[0];
+  __syncthreads();
+  // pass 2: x^T v on the grid 2^(lsb + gj)
+  int lg = 0;
+  while (((int64_t)1 << lg) < n) ++lg;
+  const int lsb = T + lg - 126;
+  i128 acc = 0;
+  if (T > -(1 << 29)) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const i128 N = ncol[i];
+      if (N == 0) continue;
+      const i64 m = grid_mantissa(x[i], gj);
+      if (m == 0) continue;
+      acc += mul_shift(m, N, lsb - (a.eA[i] + cbase));
+    }
+  }
+  acc = warp_sum_i128(acc);
+  {
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) redi[wi] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      i128 tot = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += redi[k];
+      redi[0] = tot;
+      // lambda_j = x^T v / x^T x and r_j = 1 - x^T x (double-double, once per column)
+      const i128 nt = (i128)nn_tot;
+      const double nh = i128_to_double_rn(nt);
+      const double nl = i128_to_double_rn(nt - double_to_i128(nh));
+      const double sc = pow2(2 * gj);
+      const dd nnd{__dmul_rn(nh, sc), __dmul_rn(nl, sc)};
+      const double dh = i128_to_double_rn(tot);
+      const double dl = i128_to_double_rn(tot - double_to_i128(dh));
+      const int ex = lsb + gj;
+      const dd dv = (ex >= -1022 + 130 && ex <= 1023 - 130) ? dd{__dmul_rn(dh, pow2(ex)), __dmul_rn(dl, pow2(ex))}
+                                                            : dd{ldexp(dh, ex), ldexp(dl, ex)};
+      const double lam = T > -(1 << 29) ? dd_div(dv, nnd).h : 0.0;
+      a.lam[j] = lam;
+      a.r[j] = dd_add_d(dd{-nnd.h, -nnd.l}, 1.0).h;
+      redu[0] = (u64)__double_as_longlong(lam);
+    }
+    __syncthreads();
+  }
+  const double lam = __longlong_as_double((long long)redu[0]);
+  __syncthreads();
+  // pass 3: Res = N 2^c - (m L) 2^(gj + qL), rounded once
+  i64 L = 0;
+  int qL = 0;
+  if (lam != 0.0) decompose(lam, L, qL);
+  u64 mx = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double xi = x[i];
+    const int ei = a.eA[i];
+    const i128 N = ncol[i];
+    const i128 ML = (i128)grid_mantissa(xi, gj) * (i128)L;
+    const int c = ei == EZERO ? gj + qL : ei + cbase;
+    const int d = (gj + qL) - c;
+    double res;
+    bool done = false;
+    if (d >= 0) {
+      if (bitlen_u128(abs_i128(ML)) + d <= 125 && bitlen_u128(abs_i128(N)) <= 125)
+        done = rn_scaled(N - (ML << d), c, res);
+    } else if (bitlen_u128(abs_i128(N)) - d <= 125 && bitlen_u128(abs_i128(ML)) <= 125) {
+      done = rn_scaled((N << (-d)) - ML, gj + qL, res);
+    }
+    if (!done) {
+      const dd v = gather_dd_general(a.V, i, j, ei, fj);
+      const dd p = two_prod(xi, lam);
+      const dd t = two_sum(v.h, -p.h);
+      res = __dadd_rn(t.h, __dadd_rn(t.l, __dsub_rn(v.l, p.l)));
+    }
+    a.Res[i + j * a.ldr] = res;
+    const u64 ab = double_to_bits(res) & 0x7fffffffffffffffull;
+    mx = ab > mx ? ab : mx;
+  }
+  mx = block_max_u64(mx, redu);
+  if (threadIdx.x == 0) a.h[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
+}
+
 // ---- ||off-diagonal W||_F^2 (for the automatic cluster threshold) ------------------
 __global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
   if (a.done && *a.done) return;
@@ -424,7 +652,17 @@ __global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
 }
 
 // ---- line 5: E~ column j, its exponent, ||E~||_F^2 -----------------------------------
-__global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
+// e_ij = w_ij / (lambda_j - lambda_i) (one IEEE division), e_jj = r_j / 2, and the
+// Ogita-Aishima rule e_ij = r_ij / 2 inside clusters (|lambda_j - lambda_i| <= omega, with
+// r_ij = -x_i^T x_j in double-double).  w_ij is the exact W entry rounded once on the
+// integer pipes; ||E~||_F^2 (an estimate only) is accumulated in single precision.
+constexpr int MP_CORRECTION = 12;
+
+__device__ __noinline__ double gather_d_general(GroupArgs g, int64_t i, int64_t j, int eLi, int eRj) {
+  return gather_d(g, i, j, eLi, eRj);
+}
+
+__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_CORRECTION) k_correction(CorrectionArgs a) {
   if (a.done && *a.done) return;
   a.W = resolve(a.W);
   if (a.omega_dyn) a.omega = *a.omega_dyn;
@@ -437,50 +675,79 @@ __global__ void __launch_bounds__(256) k_correction(CorrectionArgs a) {
   const int64_t n = a.n;
   const double lj = a.lam[j];
   const int hj = a.h[j];
+  const bool have_w = a.W.groups > 0 && hj != EZERO;
+  const bool fast = a.W.word32 && a.W.exact128 && a.W.groups <= MP_CORRECTION;
+  const int cbase = hj + 2 - DIGIT_BITS * a.W.tmax;   // c_i = f_i + cbase
   if (threadIdx.x == 0) ccount = 0;
   __syncthreads();
-  double s2 = 0.0;
+  float s2f = 0.f;
+  double s2d = 0.0;
   u64 mx = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double e;
-    double w = (a.W.groups > 0) ? gather_d(a.W, i, j, a.f[i], hj) : 0.0;
-    if (a.Wout) a.Wout[i + j * n] = w;
-    if (i == j) {
-      e = a.r[j] * 0.5;
-    } else {
-      double diff = __dsub_rn(lj, a.lam[i]);
-      if (fabs(diff) <= a.omega) {
-        int slot = atomicAdd(&ccount, 1);
-        if (slot < 64) clist[slot] = (int)i;
-        else atomicOr(a.flags, FLAG_RANGE);
-        e = 0.0;
-      } else {
-        e = __ddiv_rn(w, diff);
-      }
+  for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)FRX_RPT_CORRECTION * blockDim.x) {
+    double li[FRX_RPT_CORRECTION];
+    int fi[FRX_RPT_CORRECTION];
+    int32_t v[FRX_RPT_CORRECTION][MP_CORRECTION];
+#pragma unroll
+    for (int k = 0; k < FRX_RPT_CORRECTION; ++k) {
+      const int64_t i = i0 + (int64_t)k * blockDim.x;
+      const bool ok = i < n;
+      li[k] = ok ? a.lam[i] : 0.0;
+      fi[k] = ok ? a.f[i] : EZERO;
+      load_planes<MP_CORRECTION>(a.W, i, j, ok && have_w && fast && fi[k] != EZERO, v[k]);
     }
-    a.E[i + j * a.lde] = e;
+#pragma unroll
+    for (int k = 0; k < FRX_RPT_CORRECTION; ++k) {
+      const int64_t i = i0 + (int64_t)k * blockDim.x;
+      if (i >= n) continue;
+      double w = 0.0;
+      if (have_w && fi[k] != EZERO) {
+        bool ok = false;
+        if (fast) ok = rn_scaled(horner<MP_CORRECTION>(v[k], a.W.groups), fi[k] + cbase, w);
+        if (!ok) w = gather_d_general(a.W, i, j, fi[k], hj);
+      }
+      if (a.Wout) a.Wout[i + j * n] = w;
+      double e;
+      if (i == j) {
+        e = a.r[j] * 0.5;
+      } else {
+        const double diff = __dsub_rn(lj, li[k]);
+        if (fabs(diff) <= a.omega) {
+          const int slot = atomicAdd(&ccount, 1);
+          if (slot < 64) clist[slot] = (int)i;
+          else atomicOr(a.flags, FLAG_RANGE);
+          e = 0.0;
+        } else {
+          e = __ddiv_rn(w, diff);
+        }
+      }
+      a.E[i + j * a.lde] = e;
+      float f;
+      if (f32_of_double(e, 32, f)) s2f = __fmaf_rn(f, f, s2f);
+      else s2d = __fma_rn(e, e, s2d);
+      const u64 ab = double_to_bits(e) & 0x7fffffffffffffffull;
+      mx = ab > mx ? ab : mx;
+    }
   }
   __syncthreads();
-  int nc = ccount < 64 ? ccount : 64;
+  const int nc = ccount < 64 ? ccount : 64;
   const double* xj = a.X1 + j * a.ld1;
   for (int c = 0; c < nc; ++c) {
-    int i = clist[c];
+    const int i = clist[c];
     const double* xi = a.X1 + (int64_t)i * a.ld1;
     dd acc{0.0, 0.0};
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc = dd_add(acc, two_prod(xi[k], xj[k]));
     acc = block_sum_dd(acc, redd);
-    if (threadIdx.x == 0) a.E[i + j * a.lde] = -acc.h * 0.5;   // r_ij / 2
+    if (threadIdx.x == 0) {
+      const double e = -acc.h * 0.5;   // r_ij / 2
+      a.E[i + j * a.lde] = e;
+      s2d = __fma_rn(e, e, s2d);
+      const u64 ab = double_to_bits(e) & 0x7fffffffffffffffull;
+      mx = ab > mx ? ab : mx;
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0 && nc) atomicAdd(a.ccount, nc);
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double e = a.E[i + j * a.lde];
-    s2 += e * e;
-    u64 ab = double_to_bits(e) & 0x7fffffffffffffffull;
-    mx = ab > mx ? ab : mx;
-  }
-  s2 = block_sum_d(s2, red);
+  const double s2 = block_sum_d(__fma_rn((double)s2f, 0x1p-64, s2d), red);
   mx = block_max_u64(mx, redu);
   if (threadIdx.x == 0) {
     atomicAdd(a.norms + 0, s2);
@@ -518,62 +785,116 @@ __device__ __forceinline__ bool add_small_rn(double x1, i64 N, int c, double& ou
   return true;
 }
 
-// one block per column: X(:, j) <- RN(X1(:, j) + U(:, j)); one atomic per column for ||dX||_F^2
-__global__ void __launch_bounds__(1024) k_update(UpdateArgs a) {
+// general per-element path of the update (int64 groups, > 16 planes, wide exponent gaps,
+// subnormal results): RN(x1 + U) through int64/int128 sums, else double-double
+__device__ __noinline__ double update_general(const UpdateArgs& a, double x1, int64_t i, int64_t j, int ri, int ej) {
+  int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
+  double xn;
+  if (a.U.word32 && a.U.groups <= 5) {
+    // the anti-diagonal planes combine exactly in int64 (31 + 28 bits)
+    const int32_t* p = reinterpret_cast<const int32_t*>(a.U.out) + j * a.U.ldo + i;
+    i64 N = 0;
+    for (int q = 0; q < a.U.groups; ++q) N = (N << 7) + (i64)p[q * a.U.ogs];
+    if (add_small_rn(x1, N, c, xn)) return xn;
+  }
+  if (a.U.exact128) {
+    i128 N = combine_groups(a.U, i, j);
+    const int G = a.f[j] + a.beta - 53;
+    i128 m = (i128)grid_mantissa(x1, G);
+    int d = G - c;
+    if (d >= 0 && bitlen128(m) + d <= 124 && bitlen128(N) <= 124) return i128_scaled_rn((m << d) + N, c);
+    if (d < 0 && bitlen128(N) - d <= 124) return i128_scaled_rn(m + (N << (-d)), G);
+  }
+  dd u = gather_dd(a.U, i, j, ri, ej);
+  dd c2 = two_sum(x1, u.h);
+  double cl = __dadd_rn(u.l, c2.l);
+  return __dadd_rn(c2.h, cl);
+}
+
+// RN(x1 + N 2^c) exactly in 128-bit integers; false when the aligned sum would not fit
+// or the result leaves the normal range
+__device__ __forceinline__ bool add_exact_rn(double x1, i128 N, int c, double& out) {
+  if (x1 == 0.0) return rn_scaled(N, c, out);
+  i64 P;
+  int q;
+  decompose(x1, P, q);
+  const int bn = N == 0 ? 0 : bitlen_u128(abs_i128(N));
+  const int d = q - c;
+  if (d >= 0) {
+    if (d > 72 || bn > 125) return false;
+    return rn_scaled(((i128)P << d) + N, c, out);
+  }
+  if (bn - d > 125) return false;
+  return rn_scaled((i128)P + (N << (-d)), q, out);
+}
+
+// (xn - xo)^2 into a single-precision partial (scaled by 2^64) when the two exponents are
+// close, else into an FP64 partial; only the norm estimate of the stopping test reads it
+__device__ __forceinline__ void accumulate_dx2(double xn, double xo, float& d2f, double& d2d) {
+  i64 Pn, Po;
+  int qn, qo;
+  decompose(xn, Pn, qn);
+  decompose(xo, Po, qo);
+  const int dq = qn - qo;
+  if (dq >= -9 && dq <= 9) {
+    const i64 D = dq >= 0 ? (Pn << dq) - Po : Pn - (Po << (-dq));
+    float f;
+    if (f32_scaled(D, (dq >= 0 ? qo : qn) + 32, f)) {
+      d2f = __fmaf_rn(f, f, d2f);
+      return;
+    }
+  }
+  const double dx = __dsub_rn(xn, xo);
+  d2d = __fma_rn(dx, dx, d2d);
+}
+
+// X(:, j) <- RN(X1(:, j) + U(:, j)) (Alg. 1 line 6, one rounding); ||X_new - X_old||_F^2
+// partial per column.  One block per column; exact sums and their rounding run on the
+// integer pipes.
+__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_UPDATE) k_update(UpdateArgs a) {
   if (a.done && *a.done) return;
   a.U = resolve(a.U);
   if (a.beta_dyn) a.beta = *a.beta_dyn;
   __shared__ double red[32];
   const int64_t j = blockIdx.x;
   const int ej = a.eta[j];
-  double d2 = 0.0;
-  for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) {
-    double x1 = a.X1[i + j * a.ld1];
-    double xn = x1;
-    if (a.U.groups > 0) {
-      bool done = false;
-      int ri = a.rho[i];
-      if (ri != EZERO && ej != EZERO) {
-        int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
-        if (a.U.word32 && a.U.groups <= 5) {
-          // the anti-diagonal planes combine exactly in int64 (31 + 28 bits)
-          const int32_t* p = reinterpret_cast<const int32_t*>(a.U.out) + j * a.U.ldo + i;
-          int32_t v[5];
+  const bool none = a.U.groups == 0 || ej == EZERO;
+  const bool fast = a.U.word32 && a.U.exact128 && a.U.groups <= MP_UPDATE;
+  const double* x1c = a.X1 + j * a.ld1;
+  double* xc = a.X + j * a.ldx;
+  float d2f = 0.f;
+  double d2d = 0.0;
+  for (int64_t i0 = threadIdx.x; i0 < a.n; i0 += (int64_t)FRX_RPT_UPDATE * blockDim.x) {
+    double x1[FRX_RPT_UPDATE], xo[FRX_RPT_UPDATE];
+    int ri[FRX_RPT_UPDATE];
+    int32_t v[FRX_RPT_UPDATE][MP_UPDATE];
 #pragma unroll
-          for (int q = 0; q < 5; ++q) v[q] = q < a.U.groups ? __ldg(p + q * a.U.ogs) : 0;
-          i64 N = 0;
-#pragma unroll
-          for (int q = 0; q < 5; ++q)
-            if (q < a.U.groups) N = (N << 7) + (i64)v[q];
-          done = add_small_rn(x1, N, c, xn);
-        }
-        if (!done && a.U.exact128) {
-          i128 N = combine_groups(a.U, i, j);
-          const int G = a.f[j] + a.beta - 53;
-          i128 m = (i128)grid_mantissa(x1, G);
-          int d = G - c;
-          if (d >= 0 && bitlen128(m) + d <= 124 && bitlen128(N) <= 124) {
-            xn = i128_scaled_rn((m << d) + N, c);
-            done = true;
-          } else if (d < 0 && bitlen128(N) - d <= 124) {
-            xn = i128_scaled_rn(m + (N << (-d)), G);
-            done = true;
-          }
-        }
-      }
-      if (!done) {
-        dd u = gather_dd(a.U, i, j, ri, ej);
-        dd c2 = two_sum(x1, u.h);
-        double cl = __dadd_rn(u.l, c2.l);
-        xn = __dadd_rn(c2.h, cl);
-      }
+    for (int k = 0; k < FRX_RPT_UPDATE; ++k) {
+      const int64_t i = i0 + (int64_t)k * blockDim.x;
+      const bool ok = i < a.n;
+      x1[k] = ok ? x1c[i] : 0.0;
+      xo[k] = ok ? xc[i] : 0.0;
+      ri[k] = ok ? a.rho[i] : EZERO;
+      load_planes<MP_UPDATE>(a.U, i, j, ok && fast && !none, v[k]);
     }
-    double xo = a.X[i + j * a.ldx];
-    double dx = __dsub_rn(xn, xo);
-    d2 = __fma_rn(dx, dx, d2);
-    a.X[i + j * a.ldx] = xn;
+#pragma unroll
+    for (int k = 0; k < FRX_RPT_UPDATE; ++k) {
+      const int64_t i = i0 + (int64_t)k * blockDim.x;
+      if (i >= a.n) continue;
+      double xn = x1[k];
+      if (!none && ri[k] != EZERO) {
+        bool done = false;
+        if (fast) {
+          const int c = ri[k] + ej + 2 - DIGIT_BITS * a.U.tmax;
+          done = add_exact_rn(x1[k], horner<MP_UPDATE>(v[k], a.U.groups), c, xn);
+        }
+        if (!done) xn = update_general(a, x1[k], i, j, ri[k], ej);
+      }
+      xc[i] = xn;
+      accumulate_dx2(xn, xo[k], d2f, d2d);
+    }
   }
-  d2 = block_sum_d(d2, red);
+  const double d2 = block_sum_d(__fma_rn((double)d2f, 0x1p-64, d2d), red);
   if (threadIdx.x == 0) atomicAdd(a.norms + 2, d2);
 }
 
@@ -613,7 +934,7 @@ int set_refine_kernel_attributes() {
 
 int launch_residual(const ResidualArgs& a, cudaStream_t s) {
   size_t smem = sizeof(dd) * (size_t)a.n;
-  k_residual<<<(unsigned)a.n, 256, smem, s>>>(a);
+  k_residual<<<(unsigned)a.n, elem_threads(a.n), smem, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
@@ -627,14 +948,14 @@ int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s) {
 }
 
 int launch_correction(const CorrectionArgs& a, cudaStream_t s) {
-  k_correction<<<(unsigned)a.n, 256, 0, s>>>(a);
+  k_correction<<<(unsigned)a.n, elem_threads(a.n), 0, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
 int launch_update(const UpdateArgs& a, cudaStream_t s) {
-  k_update<<<(unsigned)a.n, 1024, 0, s>>>(a);
+  k_update<<<(unsigned)a.n, elem_threads(a.n), 0, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;

@@ -92,9 +92,12 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
   i64 P;
   int q;
   decompose(M[k + j * ld], P, q);
-  for (int r = 1; r <= nplanes; ++r) {
-    int d = next_digit(P, q, ej + 1 - DIGIT_BITS * r);
-    if (r > from) out[(r - 1) * ps] = digit_bf16(d);
+  const DigitSource src = digit_source(P, q);
+  unsigned par = from > 0 ? digit_q8(src, ej + 1 - DIGIT_BITS * from) & 1u : 0u;
+  for (int r = from + 1; r <= nplanes; ++r) {
+    const unsigned q8 = digit_q8(src, ej + 1 - DIGIT_BITS * r);
+    out[(r - 1) * ps] = digit_bf16(digit_from_q(src, q8, par));
+    par = q8 & 1u;
   }
 }
 
@@ -127,7 +130,13 @@ __global__ void __launch_bounds__(256) k_slice_rows(const double* __restrict__ M
     i64 P;
     int q;
     decompose(tile[tx][yy], P, q);
-    for (int r = 1; r <= nplanes; ++r) out[(r - 1) * ps] = digit_bf16(next_digit(P, q, ei + 1 - DIGIT_BITS * r));
+    const DigitSource src = digit_source(P, q);
+    unsigned par = 0;
+    for (int r = 1; r <= nplanes; ++r) {
+      const unsigned q8 = digit_q8(src, ei + 1 - DIGIT_BITS * r);
+      out[(r - 1) * ps] = digit_bf16(digit_from_q(src, q8, par));
+      par = q8 & 1u;
+    }
   }
 }
 
@@ -164,8 +173,14 @@ __global__ void __launch_bounds__(256) k_truncate_slice_x(const double* __restri
       q = gexp;
     }
   }
-  X1[k + j * ld1] = P == 0 ? 0.0 : ldexp((double)P, q);
-  for (int r = 1; r <= nplanes; ++r) out[(r - 1) * ps] = digit_bf16(next_digit(P, q, fj + 1 - DIGIT_BITS * r));
+  X1[k + j * ld1] = exact_double(P, q);
+  const DigitSource src = digit_source(P, q);
+  unsigned par = 0;
+  for (int r = 1; r <= nplanes; ++r) {
+    const unsigned q8 = digit_q8(src, fj + 1 - DIGIT_BITS * r);
+    out[(r - 1) * ps] = digit_bf16(digit_from_q(src, q8, par));
+    par = q8 & 1u;
+  }
 }
 
 // ---------------------------------------------------------------------------
