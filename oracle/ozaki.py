@@ -115,10 +115,24 @@ def pair_set(kL, kR, T):
 
 
 def slice_products(dL, dR, pairs):
-    """S_t = sum over pairs with r + s = t of dL_r @ dR_s, exact int64 matrices."""
+    """S_t = sum over pairs with r + s = t of dL_r @ dR_s, exact int64 matrices.
+
+    Every entry of dL_r @ dR_s is a sum of K integer terms of magnitude <= 64 * 64 = 2^12,
+    so all its partial sums are integers of magnitude <= K * 2^12.  While that bound is
+    below 2^53 an FP64 matrix product is exact whatever its summation order, and the
+    library routine evaluates it; otherwise the products are taken in int64.
+    """
     S = {}
+    K = dL.shape[-1]
+    exact_f64 = K * 4096 < 2 ** 53
+    if exact_f64:
+        fL = dL.astype(np.float64)
+        fR = dR.astype(np.float64)
     for (r, s) in pairs:
-        P = dL[r - 1] @ dR[s - 1]
+        if exact_f64:
+            P = (fL[r - 1] @ fR[s - 1]).astype(np.int64)
+        else:
+            P = dL[r - 1] @ dR[s - 1]
         t = r + s
         S[t] = S[t] + P if t in S else P
     return S

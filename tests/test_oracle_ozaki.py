@@ -81,6 +81,28 @@ def test_tau_truncation(beta):
             assert x1 == rnd * grid
 
 
+def test_slice_products_fp64_route_is_exact_at_the_extremes():
+    # all digits +-64 with K = 2048: partial sums reach K * 2^12 = 2^23; and a random sign
+    # pattern checked against Python integers term by term on a few entries
+    K = 2048
+    dL = np.full((2, 3, K), 64, dtype=np.int64)
+    dR = np.full((2, K, 4), 64, dtype=np.int64)
+    dR[1] = -64
+    S = oz.slice_products(dL, dR, oz.pair_set(2, 2, 4))
+    assert int(S[2][0, 0]) == K * 4096
+    assert int(S[3][0, 0]) == 0          # (1,2) gives -K 2^12, (2,1) gives +K 2^12
+    assert int(S[4][0, 0]) == -K * 4096
+    g = np.random.default_rng(13)
+    dL = g.integers(-64, 65, (2, 3, 5000))
+    dR = g.integers(-64, 65, (2, 5000, 3))
+    S = oz.slice_products(dL, dR, oz.pair_set(2, 2, 4))
+    for i in range(3):
+        for j in range(3):
+            ref = sum(int(a) * int(b) for a, b in zip(dL[0, i], dR[1, :, j])) + \
+                  sum(int(a) * int(b) for a, b in zip(dL[1, i], dR[0, :, j]))
+            assert int(S[3][i, j]) == ref
+
+
 def test_slice_products_brute_force():
     g = np.random.default_rng(12)
     dL = g.integers(-64, 65, (3, 4, 6))
