@@ -436,7 +436,7 @@ def run_batched(args):
 
 def _timed_refine(api, A, X0, D0, delta, opts, work, reps=1):
     import torch
-    best, info, X, D = 1e30, None, None, None
+    best, info, X = 1e30, None, None
     for _ in range(reps):
         X = X0.clone()
         D = D0.clone()
@@ -451,65 +451,144 @@ def _timed_refine(api, A, X0, D0, delta, opts, work, reps=1):
     return best, info, X
 
 
-def run_configs(args):
-    """Config-2 variants at n = 2048 and the config-4 sweep at n = 8192 (one JSON line)."""
+def _timed_fp64(At, X0t, D0t, delta):
     import torch
 
-    from paper_2602_19090_gb300 import api, fp64_refine, synth
+    from paper_2602_19090_gb300 import fp64_refine
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    Xb, _, ib = fp64_refine.refine(At, X0t.clone(), D0t.clone(), delta)
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e), ib, Xb
+
+
+def _forward_error(X, Qh, Ql):
+    """||X - Q||_2 with columns sign-aligned (Q = Qh + Ql known exactly); also the Frobenius
+    norm and the largest column norm, which bracket it.  The 2-norm is a 40-step power
+    iteration on the difference scaled to unit Frobenius norm, in single precision."""
+    import torch
+    sg = torch.sign((Qh * X).sum(0))
+    sg[sg == 0] = 1
+    D = (X * sg - Qh) - Ql
+    fro = float(torch.linalg.norm(D))
+    col = float(torch.linalg.norm(D, dim=0).max())
+    if fro == 0.0:
+        return {"two": 0.0, "fro": 0.0, "maxcol": 0.0}
+    Ds = (D / fro).float()
+    g = torch.Generator(device=D.device).manual_seed(7)
+    v = torch.randn(D.shape[1], device=D.device, generator=g)
+    v /= torch.linalg.norm(v)
+    lam2 = 0.0
+    for _ in range(40):
+        w = Ds.T @ (Ds @ v)
+        lam2 = float(torch.linalg.norm(w))
+        v = w / lam2
+    return {"two": math.sqrt(lam2) * fro, "fro": fro, "maxcol": col}
+
+
+def run_configs(args):
+    """Refinement configurations beside the headline one (one JSON line):
+    the n=2048 variants of the randsvd-like workload with native-FP64 times, the n=8192
+    cond-1e12 target sweep, and exact-truth workloads (Hadamard eigenvectors) with the
+    forward error of both paths measured against the known eigenvectors."""
+    import torch
+
+    from paper_2602_19090_gb300 import api, synth
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    out = {"metric": "configs", "variants_n2048": [], "sweep_n8192": []}
+    out = {"metric": "configs", "variants_n2048": [], "sweep_n8192": [], "exact_truth_n4096": [],
+           "exact_truth_sweep_n8192": []}
+
+    def dev_inputs(A, X0, D0):
+        return (torch.from_numpy(A).to(dev), api.colmajor(torch.from_numpy(X0).to(dev))[0],
+                torch.from_numpy(D0).to(dev))
+
+    # warm the native-FP64 path (library handles, kernels) on a small problem
+    A, X0, D0, _ = synth.refine_workload(256, 1e4, "spd", case=99)
+    _timed_fp64(*dev_inputs(A, X0, D0), 1e-12)
+
     n = 2048
     work = api.workspace(api.refine_workspace_bytes(n), dev)
     for cond, variant in ((1e4, "spd"), (1e10, "spd"), (1e14, "spd"), (1e4, "indefinite"), (1e4, "clustered")):
         A, X0, D0, lam = synth.refine_workload(n, cond, variant, case=int(cond) % 97 + len(variant))
-        At = torch.from_numpy(A).to(dev)
-        X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
-        D0t = torch.from_numpy(D0).to(dev)
+        At, X0t, D0t = dev_inputs(A, X0, D0)
         opts = api.Options(cluster_omega=-1.0 if variant == "clustered" else 0.0)
         for delta in (1e-10, 1e-14):
             ms, info, X = _timed_refine(api, At, X0t, D0t, delta, opts, work, reps=2)
             rec = {"cond": cond, "variant": variant, "delta": delta, "ms": ms, "status": info["status_name"],
                    "iters": info["iters"], "products": info["products"], "k_V": info["k_V"], "s_X": info["s_X"],
                    "err_est": info["err_est"], "clustered_pairs": info["clustered_pairs"]}
-            if variant == "spd" or delta == 1e-14:
-                torch.cuda.synchronize()
-                s = torch.cuda.Event(enable_timing=True)
-                e = torch.cuda.Event(enable_timing=True)
-                s.record()
-                Xb, _, ib = fp64_refine.refine(At, X0t.clone(), D0t.clone(), delta)
-                e.record()
-                torch.cuda.synchronize()
-                rec.update(fp64_ms=s.elapsed_time(e), fp64_status=ib["status"], fp64_iters=ib["iters"],
-                           max_abs_diff_vs_fp64=float((Xb - X).abs().max()))
+            fms, ib, Xb = _timed_fp64(At, X0t, D0t, delta)
+            rec.update(fp64_ms=fms, fp64_status=ib["status"], fp64_iters=ib["iters"],
+                       max_abs_diff_vs_fp64=float((Xb - X).abs().max()))
             out["variants_n2048"].append(rec)
+            print(json.dumps(rec), file=sys.stderr, flush=True)
         del At, X0t, D0t
     del work
+
+    # exact truth, n = 4096 (the geometric spectra are kept exactly for cond 1e4 and 1e10)
+    n = 4096
+    work = api.workspace(api.refine_workspace_bytes(n), dev)
+    for cond, variant in ((1e4, "spd"), (1e10, "spd"), (1e4, "indefinite"), (1e10, "indefinite")):
+        A, X0, D0, lam, Qh, Ql, hinfo = synth.hadamard_workload(n, cond, synth.seed_for(2, 500), variant=variant)
+        At, X0t, D0t = dev_inputs(A, X0, D0)
+        Qht, Qlt = torch.from_numpy(Qh).to(dev), torch.from_numpy(Ql).to(dev)
+        for delta in (1e-10, 1e-14):
+            ms, info, X = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work, reps=2)
+            fe = _forward_error(X, Qht, Qlt)
+            fms, ib, Xb = _timed_fp64(At, X0t, D0t, delta)
+            fe_b = _forward_error(Xb, Qht, Qlt)
+            rec = {"cond": cond, "variant": variant, "delta": delta, "min_gap": hinfo["min_gap"], "ms": ms,
+                   "status": info["status_name"], "iters": info["iters"], "products": info["products"],
+                   "k_V": info["k_V"], "s_X": info["s_X"], "err_est": info["err_est"], "forward_error": fe,
+                   "fp64_ms": fms, "fp64_status": ib["status"], "fp64_iters": ib["iters"], "fp64_forward_error": fe_b}
+            out["exact_truth_n4096"].append(rec)
+            print(json.dumps(rec), file=sys.stderr, flush=True)
+        del At, X0t, D0t, Qht, Qlt
+    del work
+
+    # n = 8192, cond 1e12: the randsvd-like workload (no reference eigenvectors: the estimate
+    # and the distance to the native-FP64 result are reported) ...
     n = 8192
     A, X0, D0, lam = synth.refine_workload(n, 1e12, "spd", case=4)
-    At = torch.from_numpy(A).to(dev)
-    X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
-    D0t = torch.from_numpy(D0).to(dev)
+    At, X0t, D0t = dev_inputs(A, X0, D0)
     del A, X0
     work = api.workspace(api.refine_workspace_bytes(n), dev)
     for k in range(8, 16):
         delta = 10.0 ** (-k)
         ms, info, X = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work)
         rec = {"delta": delta, "ms": ms, "status": info["status_name"], "iters": info["iters"],
-               "products": info["products"], "k_V": info["k_V"], "s_X": info["s_X"], "beta": info["beta"],
-               "err_est": info["err_est"], "step": info["step"]}
+               "products": info["products"], "k_V": info["k_V"], "k_W": info["k_W"], "k_U": info["k_U"],
+               "s_X": info["s_X"], "beta": info["beta"], "err_est": info["err_est"], "step": info["step"]}
         if k in (8, 12):
-            torch.cuda.synchronize()
-            s = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            s.record()
-            Xb, _, ib = fp64_refine.refine(At, X0t.clone(), D0t.clone(), delta)
-            e.record()
-            torch.cuda.synchronize()
-            rec.update(fp64_ms=s.elapsed_time(e), fp64_status=ib["status"], fp64_iters=ib["iters"],
+            fms, ib, Xb = _timed_fp64(At, X0t, D0t, delta)
+            rec.update(fp64_ms=fms, fp64_status=ib["status"], fp64_iters=ib["iters"],
                        max_abs_diff_vs_fp64=float((Xb - X).abs().max()))
         out["sweep_n8192"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    del At, X0t, D0t
+    # ... and its exact-truth analog (Hadamard eigenvectors, geometric magnitudes with the
+    # smallest ones raised to distinct integers), where both forward errors are measured
+    A, X0, D0, lam, Qh, Ql, hinfo = synth.hadamard_workload(n, 1e12, synth.seed_for(4, 500))
+    At, X0t, D0t = dev_inputs(A, X0, D0)
+    Qht, Qlt = torch.from_numpy(Qh).to(dev), torch.from_numpy(Ql).to(dev)
+    del A, X0, Qh, Ql
+    for k in range(8, 16):
+        delta = 10.0 ** (-k)
+        ms, info, X = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work)
+        rec = {"delta": delta, "min_gap": hinfo["min_gap"], "ms": ms, "status": info["status_name"],
+               "iters": info["iters"], "products": info["products"], "k_V": info["k_V"], "k_W": info["k_W"],
+               "k_U": info["k_U"], "s_X": info["s_X"], "beta": info["beta"], "err_est": info["err_est"],
+               "forward_error": _forward_error(X, Qht, Qlt)}
+        if k in (8, 12):
+            fms, ib, Xb = _timed_fp64(At, X0t, D0t, delta)
+            rec.update(fp64_ms=fms, fp64_status=ib["status"], fp64_iters=ib["iters"],
+                       fp64_forward_error=_forward_error(Xb, Qht, Qlt))
+        out["exact_truth_sweep_n8192"].append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
     print(json.dumps(out), flush=True)
 

@@ -233,6 +233,7 @@ def refine(A, X, D, delta, opts: Options | None = None, exact=False, history=Non
         raise ValueError("delta must exceed the unit roundoff (Sec. 3.1)")
     lam = np.asarray(D, dtype=np.float64)
     prev_step = None
+    noncontract = 0
     omega = 0.0
     status = "max_iter"
     total_products = 0
@@ -246,10 +247,14 @@ def refine(A, X, D, delta, opts: Options | None = None, exact=False, history=Non
         if history is not None:
             history.append(dict(X=X.copy(), lam=lam.copy(), **{k: info[k] for k in
                                 ("beta", "alpha", "sX", "kV", "kW", "kU", "products", "normE", "step", "est")}))
+        # stagnation (reading of the missing stopping rule): two consecutive steps that
+        # fail to halve; a single one occurs when the start lies outside Theorem 1's basin
+        # and the next step repairs the first
+        noncontract = noncontract + 1 if (prev_step is not None and info["step"] > 0.5 * prev_step) else 0
         if est <= delta:
             status = "converged"
             break
-        if prev_step is not None and info["step"] > 0.5 * prev_step:
+        if noncontract >= 2:
             status = "stagnated"
             break
         prev_step = info["step"]

@@ -98,29 +98,44 @@ __device__ double bsum_d(double v, double* red) {
   return v;
 }
 
+// Order-preserving integer keys of doubles (non-NaN): the bitonic sort compares integers,
+// since one SM's FP64 pipe would take ~0.1 ms for the ~78 compare stages at n = 4096.
+__device__ __forceinline__ u64 order_key(double v) {
+  const u64 b = double_to_bits(v);
+  return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+
+__device__ __forceinline__ double key_value(u64 k) {
+  return bits_to_double((k >> 63) ? (k & ~(1ull << 63)) : ~k);
+}
+
 // Smallest adjacent gap of the sorted estimates exceeding omega (Lam if none) and max |lam|.
-// s: dynamic smem of next_pow2(n) doubles (bitonic sort).
+// s: dynamic smem of next_pow2(n) doubles (bitonic sort of their integer keys).
 __device__ void gap_of(const double* lam, int64_t n, double omega, double* s, double* red, double& g,
                        double& Lam) {
+  u64* key = reinterpret_cast<u64*>(s);
   int64_t m = 1;
   while (m < n) m <<= 1;
-  double amax = 0.0;
+  u64 amax = 0;
   for (int64_t i = threadIdx.x; i < m; i += PT) {
-    double v = i < n ? lam[i] : INFINITY;
-    s[i] = v;
-    if (i < n) amax = fmax(amax, fabs(v));
+    const double v = i < n ? lam[i] : INFINITY;
+    key[i] = order_key(v);
+    if (i < n) {
+      const u64 ab = double_to_bits(v) & 0x7fffffffffffffffull;
+      amax = ab > amax ? ab : amax;
+    }
   }
   __syncthreads();
   for (int64_t k = 2; k <= m; k <<= 1) {
     for (int64_t jj = k >> 1; jj > 0; jj >>= 1) {
       for (int64_t i = threadIdx.x; i < m; i += PT) {
-        int64_t l = i ^ jj;
+        const int64_t l = i ^ jj;
         if (l > i) {
-          double a = s[i], b = s[l];
-          bool up = (i & k) == 0;
+          const u64 a = key[i], b = key[l];
+          const bool up = (i & k) == 0;
           if ((a > b) == up) {
-            s[i] = b;
-            s[l] = a;
+            key[i] = b;
+            key[l] = a;
           }
         }
       }
@@ -129,11 +144,11 @@ __device__ void gap_of(const double* lam, int64_t n, double omega, double* s, do
   }
   double gmin = INFINITY;
   for (int64_t i = 1 + threadIdx.x; i < n; i += PT) {
-    double d = __dsub_rn(s[i], s[i - 1]);
+    const double d = __dsub_rn(key_value(key[i]), key_value(key[i - 1]));
     if (d > omega) gmin = fmin(gmin, d);
   }
   gmin = bmin_d(gmin, red);
-  Lam = bmax_d(amax, red);
+  Lam = bmax_d(bits_to_double(amax), red);
   g = isinf(gmin) ? Lam : gmin;
 }
 
@@ -172,6 +187,7 @@ __global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA,
     p->products = 0;
     p->omega = omega_prev;
     p->have_prev_step = 0;
+    p->noncontract = 0;
     p->prev_step = 0.0;
     p->g = g;
     p->Lam = Lam;
@@ -403,10 +419,13 @@ __global__ void __launch_bounds__(PT) k_plan_end(DevPlan* p, const double* lam_n
   p->Lam = Lam;
   p->normE = __dsqrt_rn(p->norms[0]);
   p->clustered = p->ccount / 2;
+  // stagnation: two consecutive steps that failed to halve (a single one is expected when
+  // the start lies outside Theorem 1's basin and the next step repairs the first)
+  p->noncontract = (p->have_prev_step && step > 0.5 * p->prev_step) ? p->noncontract + 1 : 0;
   if (est <= o.delta) {
     p->status = FRX_OK;
     p->done = 1;
-  } else if (p->have_prev_step && step > 0.5 * p->prev_step) {
+  } else if (p->noncontract >= 2) {
     p->status = FRX_STAGNATED;
     p->done = 1;
   } else if (p->iter >= o.max_iter) {

@@ -102,6 +102,7 @@ struct DevPlan {
   int iter, done, status;
   int beta, alpha, sX, kV, kW, kU, sliced_kA, eAmax, fmax;
   int clustered, have_prev_step;
+  int noncontract;  // consecutive iterations whose step exceeded half the previous one
   long long products;
   double g, Lam, S2, omega, step, prev_step, est, normE;
   double norms[4];  // [0] ||E~||_F^2, [1] ||W_off||_F^2, [2] ||dX||_F^2

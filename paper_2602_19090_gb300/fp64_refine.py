@@ -153,15 +153,17 @@ def refine(A, X, D, delta, max_iter=10):
     """Returns (X, lam, info); A, X, D float64 CUDA tensors (X, D are not modified)."""
     lam = D.clone()
     prev = None
+    noncontract = 0
     status, it, total, est = "max_iter", 0, 0, math.inf
     for it in range(1, max_iter + 1):
         X, lam, info = step(A, X, lam, delta)
         total += info["products"]
         est = info["est"]
+        noncontract = noncontract + 1 if (prev is not None and info["step"] > 0.5 * prev) else 0
         if est <= delta:
             status = "converged"
             break
-        if prev is not None and info["step"] > 0.5 * prev:
+        if noncontract >= 2:
             status = "stagnated"
             break
         prev = info["step"]

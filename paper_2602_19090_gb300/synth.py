@@ -129,41 +129,84 @@ def batched_sizes(count: int = 256, lo: int = 32, hi: int = 512, case: int = 0):
     return n, 10.0 ** logc
 
 
-def hadamard_workload(n: int, cond: float, seed: int, rel: float = 1e-8):
-    """Exact-truth workload for n = 4^k: A = Q diag(lam) Q^T with Q = H_n / sqrt(n) (Sylvester
-    Hadamard, exactly orthogonal in FP64) and dyadic eigenvalues lam_k = m_k 2^-40, so every
-    entry of A is an exact FP64 number (integer Walsh-Hadamard sums below 2^53).
-    Returns (A, X0, D0, Q, lam) with Q's columns ordered like lam (ascending)."""
-    k = int(round(np.log2(n) / 2))
-    if 4 ** k != n:
-        raise ValueError("n must be a power of 4")
-    lam = spectrum(n, cond)
-    m = np.maximum(np.rint(lam * 2.0 ** 40), 1).astype(np.int64)
-    lam = m.astype(np.float64) * 2.0 ** -40
-    # W = H diag(m) H by two integer fast Walsh-Hadamard transforms (rows, then columns)
-    W = np.diag(m).astype(np.int64)
+def _fwht_rows(M):
+    """Unnormalised Sylvester-Hadamard transform of every row (exact for integer input)."""
+    n = M.shape[1]
+    M = M.copy()
+    h = 1
+    while h < n:
+        M = M.reshape(M.shape[0], -1, 2 * h)
+        a = M[:, :, :h].copy()
+        b = M[:, :, h:].copy()
+        M[:, :, :h] = a + b
+        M[:, :, h:] = a - b
+        M = M.reshape(M.shape[0], n)
+        h *= 2
+    return M
 
-    def fwht_rows(M):
-        M = M.copy()
-        h = 1
-        while h < n:
-            M = M.reshape(M.shape[0], -1, 2 * h)
-            a = M[:, :, :h].copy()
-            b = M[:, :, h:].copy()
-            M[:, :, :h] = a + b
-            M[:, :, h:] = a - b
-            M = M.reshape(M.shape[0], n)
-            h *= 2
-        return M
 
-    W = fwht_rows(W)          # diag(m) H  (H symmetric)
-    W = fwht_rows(W.T).T      # H diag(m) H
-    A = W.astype(np.float64) * (2.0 ** -40 / n)
-    Hm = fwht_rows(np.eye(n, dtype=np.int64))
-    Q = Hm.astype(np.float64) / np.sqrt(float(n))
+def _inv_sqrt_dd(n: int):
+    """1/sqrt(n) for n = 2^p as a double-double (exact when p is even)."""
+    import decimal
+    p = n.bit_length() - 1
+    with decimal.localcontext() as ctx:
+        ctx.prec = 60
+        v = decimal.Decimal(1) / decimal.Decimal(n).sqrt()
+        hi = float(v)
+        lo = float(v - decimal.Decimal(hi))
+    if p % 2 == 0:
+        assert lo == 0.0
+    return hi, lo
+
+
+def hadamard_workload(n: int, cond: float, seed: int, rel: float = 1e-8, variant: str = "spd"):
+    """Exact-truth workload for n = 2^p.
+
+    A = H diag(s_k m_k) H 2^-S / n with H the Sylvester Hadamard matrix, m_k distinct positive
+    integers and s_k = +1 ("spd") or seeded random signs ("indefinite").  Every entry of A is
+    an exact FP64 number (|sum_k +-m_k| < 2^53, power-of-two scaling), so the eigenvectors of
+    the stored A are exactly the columns of H / sqrt(n).  The magnitudes follow the geometric
+    spectrum of ``spectrum(n, cond)``: m_k = round(2^S geom_k) with S as large as the 2^53
+    bound allows, raised where needed to keep the m_k distinct (for cond * n large the
+    smallest eigenvalues become consecutive integers, widening the smallest gaps).
+    Returns (A, X0, D0, lam, Qh, Ql, info): lam ascending, Q = Qh + Ql = H / sqrt(n) with
+    columns ordered like lam (Ql = 0 when p is even); X0, D0 as in ``initial_guess``.
+    """
+    p = n.bit_length() - 1
+    if n < 2 or (1 << p) != n:
+        raise ValueError("n must be a power of 2")
+    geom = spectrum(n, cond)
+    S = int(np.floor(np.log2(2.0 ** 52 / float(np.sum(geom)))))
+    m = np.maximum(np.rint(geom * 2.0 ** S), 1).astype(np.int64)
+    k = np.arange(n, dtype=np.int64)
+    m = np.maximum.accumulate(m - k) + k                     # strictly increasing
+    assert int(np.sum(m)) < (1 << 53)
+    if variant == "indefinite":
+        sgn = rng(seed + 7).integers(0, 2, size=n).astype(np.int64) * 2 - 1
+    elif variant == "spd":
+        sgn = np.ones(n, dtype=np.int64)
+    else:
+        raise ValueError(f"unknown variant {variant!r}")
+    sm = sgn * m
+    W = _fwht_rows(np.diag(sm))                              # diag(sm) H
+    W = _fwht_rows(np.ascontiguousarray(W.T)).T              # H diag(sm) H
+    A = np.ascontiguousarray(W.astype(np.float64) * (2.0 ** -S / n))
+    del W
+    lam_all = sm.astype(np.float64) * 2.0 ** -S
+    order = np.argsort(lam_all, kind="stable")
+    lam = lam_all[order]
+    Hm = _fwht_rows(np.eye(n, dtype=np.int8).astype(np.int64)[:, :])   # H (symmetric)
+    Hc = Hm[:, order].astype(np.float64)
+    del Hm
+    ih, il = _inv_sqrt_dd(n)
+    Qh = np.ascontiguousarray(Hc * ih)
+    Ql = np.ascontiguousarray(Hc * il)
     g = rng(seed + 1)
-    Y = Q + g.standard_normal((n, n)) * (rel / (2.0 * np.sqrt(n)))
+    Y = Qh + g.standard_normal((n, n)) * (rel / (2.0 * np.sqrt(n)))
     Qr, R = np.linalg.qr(Y)
     X0 = np.ascontiguousarray(Qr * np.sign(np.diag(R)))
     D0 = lam * (1.0 + rel * g.standard_normal(n))
-    return np.ascontiguousarray(A), X0, D0, Q, lam
+    gaps = np.diff(lam)
+    info = dict(scale_exp=-S, min_gap=float(gaps.min()), max_abs=float(np.abs(lam).max()),
+                cond=float(np.abs(lam).max() / np.abs(lam).min()))
+    return A, X0, D0, lam, Qh, Ql, info

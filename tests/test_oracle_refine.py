@@ -195,3 +195,22 @@ def test_golden_workload0_regression():
             assert h[key] == gs[key]
         fe = tr.forward_error(Xh, Xl, h["X"])
         assert abs(fe - gs["forward_error"]) <= 1e-3 * gs["forward_error"] + 1e-16
+
+
+def test_start_outside_the_basin_still_converges():
+    # Exact-truth workload (Hadamard eigenvectors), n = 512, cond 1e12: gaps of 5.7e-14 put the
+    # 1e-8 start far outside Theorem 1's basin.  The first correction raises the error (the
+    # near-degenerate pairs mix), the second repairs it; one non-contracting step is not
+    # stagnation, and the iteration reaches delta against the known eigenvectors.
+    A, X0, D0, lam, Qh, Ql, info = synth.hadamard_workload(512, 1e12, synth.seed_for(4, 500))
+    hist = []
+    X, lam_out, res = rf.refine(A, X0, D0, 1e-14, rf.Options(), history=hist)
+
+    def fe(Y):
+        s = np.sign(np.sum(Qh * Y, 0))
+        return np.linalg.norm((Y * s - Qh) - Ql, 2)
+
+    assert fe(hist[0]["X"]) > 100 * fe(X0)          # the first step makes things worse
+    assert hist[1]["step"] > 0.5 * hist[0]["step"]  # ... and the second step is as large
+    assert res["status"] == "converged"
+    assert fe(X) <= 1e-14
