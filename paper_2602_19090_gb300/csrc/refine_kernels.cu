@@ -201,6 +201,85 @@ __device__ __forceinline__ i128 warp_sum_i128(i128 v) {
   return v;
 }
 
+// Rows handled per thread and loop trip in the element-wise kernels (every load of those
+// rows is issued before the first use) and the minimum resident blocks per SM requested
+// from the register allocator; tuning constants, measured on GB300.
+#ifndef FRX_RPT_RESIDUAL
+#define FRX_RPT_RESIDUAL 1
+#endif
+#ifndef FRX_RPT_CORRECTION
+#define FRX_RPT_CORRECTION 1
+#endif
+#ifndef FRX_RPT_UPDATE
+#define FRX_RPT_UPDATE 1
+#endif
+#ifndef FRX_MINB_RESIDUAL
+#define FRX_MINB_RESIDUAL 3
+#endif
+#ifndef FRX_MINB_CORRECTION
+#define FRX_MINB_CORRECTION 3
+#endif
+#ifndef FRX_MINB_UPDATE
+#define FRX_MINB_UPDATE 3
+#endif
+constexpr int RPT = 2;   // launch sizing: threads cover n / RPT rows (at most ELEM_THREADS)
+constexpr int ELEM_THREADS = 256;
+
+__host__ __device__ inline int elem_threads(int64_t n) {
+  int64_t t = (n + RPT - 1) / RPT;
+  t = (t + 31) / 32 * 32;
+  return (int)(t < 32 ? 32 : (t > ELEM_THREADS ? ELEM_THREADS : t));
+}
+
+// the int32 anti-diagonal planes of entry (i, j) (at most MP; zero beyond groups)
+template <int MP>
+__device__ __forceinline__ void load_planes(const GroupArgs& g, int64_t i, int64_t j, bool valid, int32_t (&v)[MP]) {
+  const int32_t* p = reinterpret_cast<const int32_t*>(g.out) + j * g.ldo + i;
+#pragma unroll
+  for (int q = 0; q < MP; ++q) v[q] = (valid && q < g.groups) ? __ldg(p + q * g.ogs) : 0;
+}
+
+// sum_q v_q 2^(7 (groups - 1 - q)) exactly (|result| < 2^127 when the product's
+// exact128 flag holds): Horner in int64 chunks of four planes, merged in 128 bits
+template <int MP>
+__device__ __forceinline__ i128 horner(const int32_t (&v)[MP], int groups) {
+  i128 N = 0;
+#pragma unroll
+  for (int g = 0; g < MP; g += 4) {
+    if (g < groups) {
+      const int len = groups - g < 4 ? groups - g : 4;
+      i64 c = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < len && g + q < MP) c = (c << 7) + (i64)v[g + q];
+      N = g ? (N << (7 * len)) + (i128)c : (i128)c;
+    }
+  }
+  return N;
+}
+
+constexpr int MP_RESIDUAL = 16;   // planes kept in registers by the fast paths
+constexpr int MP_UPDATE = 12;
+
+// N 2^ex as a double-double (h = RN(N 2^ex), l = RN of the rest) on the integer pipes;
+// false when a part would be subnormal or overflow
+__device__ __forceinline__ bool dd_from_i128(i128 N, int ex, dd& out) {
+  double h;
+  if (!rn_scaled(N, ex, h)) return false;
+  if (h == 0.0) {
+    out = dd{0.0, 0.0};
+    return true;
+  }
+  i64 P;
+  int q;
+  decompose(h, P, q);
+  const i128 R = q >= ex ? N - ((i128)P << (q - ex)) : (i128)0;
+  double l;
+  if (!rn_scaled(R, ex, l)) return false;
+  out = dd{h, l};
+  return true;
+}
+
 __global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_t* __restrict__ eL,
                                                       const int32_t* __restrict__ eR, int64_t M, int64_t N,
                                                       double* __restrict__ Ch, int64_t ldh, double* __restrict__ Cl,
@@ -209,7 +288,15 @@ __global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_
   int64_t j = blockIdx.y;
   if (i >= M) return;
   ga = resolve(ga);
-  dd v = gather_dd(ga, i, j, eL[i], eR[j]);
+  const int ei = eL[i], ej = eR[j];
+  dd v{0.0, 0.0};
+  bool done = ei == EZERO || ej == EZERO || ga.groups == 0;
+  if (!done && ga.word32 && ga.exact128 && ga.groups <= 16) {
+    int32_t pl[16];
+    load_planes<16>(ga, i, j, true, pl);
+    done = dd_from_i128(horner<16>(pl, ga.groups), ei + ej + 2 - DIGIT_BITS * ga.tmax, v);
+  }
+  if (!done) v = gather_dd(ga, i, j, ei, ej);
   Ch[i + j * ldh] = v.h;
   if (Cl) Cl[i + j * ldl] = v.l;
 }
@@ -270,66 +357,6 @@ __device__ u64 block_max_u64(u64 v, u64* red) {
   __syncthreads();
   return r;
 }
-
-// Rows handled per thread and loop trip in the element-wise kernels (every load of those
-// rows is issued before the first use) and the minimum resident blocks per SM requested
-// from the register allocator; tuning constants, measured on GB300.
-#ifndef FRX_RPT_RESIDUAL
-#define FRX_RPT_RESIDUAL 1
-#endif
-#ifndef FRX_RPT_CORRECTION
-#define FRX_RPT_CORRECTION 1
-#endif
-#ifndef FRX_RPT_UPDATE
-#define FRX_RPT_UPDATE 1
-#endif
-#ifndef FRX_MINB_RESIDUAL
-#define FRX_MINB_RESIDUAL 3
-#endif
-#ifndef FRX_MINB_CORRECTION
-#define FRX_MINB_CORRECTION 3
-#endif
-#ifndef FRX_MINB_UPDATE
-#define FRX_MINB_UPDATE 3
-#endif
-constexpr int RPT = 2;   // launch sizing: threads cover n / RPT rows (at most ELEM_THREADS)
-constexpr int ELEM_THREADS = 256;
-
-__host__ __device__ inline int elem_threads(int64_t n) {
-  int64_t t = (n + RPT - 1) / RPT;
-  t = (t + 31) / 32 * 32;
-  return (int)(t < 32 ? 32 : (t > ELEM_THREADS ? ELEM_THREADS : t));
-}
-
-// the int32 anti-diagonal planes of entry (i, j) (at most MP; zero beyond groups)
-template <int MP>
-__device__ __forceinline__ void load_planes(const GroupArgs& g, int64_t i, int64_t j, bool valid, int32_t (&v)[MP]) {
-  const int32_t* p = reinterpret_cast<const int32_t*>(g.out) + j * g.ldo + i;
-#pragma unroll
-  for (int q = 0; q < MP; ++q) v[q] = (valid && q < g.groups) ? __ldg(p + q * g.ogs) : 0;
-}
-
-// sum_q v_q 2^(7 (groups - 1 - q)) exactly (|result| < 2^127 when the product's
-// exact128 flag holds): Horner in int64 chunks of four planes, merged in 128 bits
-template <int MP>
-__device__ __forceinline__ i128 horner(const int32_t (&v)[MP], int groups) {
-  i128 N = 0;
-#pragma unroll
-  for (int g = 0; g < MP; g += 4) {
-    if (g < groups) {
-      const int len = groups - g < 4 ? groups - g : 4;
-      i64 c = 0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (q < len && g + q < MP) c = (c << 7) + (i64)v[g + q];
-      N = g ? (N << (7 * len)) + (i128)c : (i128)c;
-    }
-  }
-  return N;
-}
-
-constexpr int MP_RESIDUAL = 16;   // planes kept in registers by the fast paths
-constexpr int MP_UPDATE = 12;
 
 // ---- lines 2-4 (inner part): one block per column j --------------------------------
 // smem: n double-doubles (V column).  x^T x is exact in integers (X1 lies on the grid
