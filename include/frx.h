@@ -70,7 +70,7 @@ typedef struct {
   int theory_alpha;      /* 0: alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1);
                             1: alpha = 53 - beta + ceil(log2 n) (eq. proposed_beta)           */
   int beta_override;     /* < 0: use the rule; else a fixed beta (clamped to [3, 47])          */
-  int k_cap;             /* largest number of digit planes per operand, 1..16                  */
+  int k_cap;             /* largest number of digit planes per operand, 1..18                  */
   int max_iter;          /* iteration limit (>= 1)                                           */
   double xi_stop;        /* <= 0: n.  Stop when step^2 * max|lam| / (xi_stop * gap) <= delta  */
   double cluster_omega;  /* >= 0: |lam_j - lam_i| <= omega is a cluster pair (0: only equal
@@ -177,7 +177,7 @@ FRX_API size_t frx_ozaki_gemm_workspace_bytes(int64_t m, int64_t n, int64_t k, i
  *   C_lo (out, optional) receives the low word of the double-double result
  *   (ld = ldc).  When the planes hold A and B exactly and mode is FULL, C_hi + C_lo
  *   equals the exact product to about 2^-104 relative.
- * slices in [1, 16]; m, n, k in [1, 2^20] with k <= 65536; A, B finite.
+ * slices in [1, 18]; m, n, k in [1, 2^20] with k <= 65536; A, B finite.
  */
 FRX_API int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_t ldb,
                    double* C, int64_t ldc, double* C_lo, int64_t m, int64_t n, int64_t k,

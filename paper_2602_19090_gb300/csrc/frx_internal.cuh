@@ -11,7 +11,7 @@ namespace frx {
 
 constexpr int EZERO = -(1 << 30);   // exponent of an all-zero row or column
 constexpr int DIGIT_BITS = 7;       // 7-bit digits: |d| <= 64
-constexpr int MAX_PLANES = 16;
+constexpr int MAX_PLANES = 18;   // digit planes per operand (7 bits each: 126 bits)
 
 typedef unsigned long long u64;
 typedef long long i64;
@@ -136,43 +136,64 @@ __device__ __forceinline__ double exact_double(i64 P, int q) {
   return ldexp((double)P, q);
 }
 
-// Digits of x = P 2^q on the fixed grid of exponent e, plane by plane without the
-// sequential remainder.  After r round-half-even digits the partial sum is the
-// round-half-even multiple Q_r 2^(s_r) of P, s_r = e + 1 - 7r - q (a tie leaves Q_r even
-// because Q_r = 128 Q_(r-1) + d_r and d_r is chosen even), so d_r = Q_r - 128 Q_(r-1);
-// |d_r| <= 64 makes it a function of Q_r mod 256 and Q_(r-1) mod 2.  Signs are symmetric:
-// the digits of -x are the negated digits of x.
-struct DigitSource {
-  u64 a;     // |P|
-  int q;     // x = +-a 2^q
-  int tz;    // trailing zero bits of a
-  bool neg;
-};
-
-__device__ __forceinline__ DigitSource digit_source(i64 P, int q) {
-  DigitSource s;
-  s.neg = P < 0;
-  s.a = s.neg ? (u64)0 - (u64)P : (u64)P;
-  s.q = q;
-  s.tz = s.a ? __ffsll((long long)s.a) - 1 : 64;
-  return s;
-}
-
-// Q_r mod 256 for the plane of weight 2^(wexp) (s = wexp - q)
-__device__ __forceinline__ unsigned digit_q8(const DigitSource& s, int wexp) {
-  const int sh = wexp - s.q;
-  if (sh <= 0) return sh <= -8 ? 0u : (unsigned)(s.a << (-sh)) & 0xffu;
-  const unsigned t8 = sh >= 64 ? 0u : (unsigned)(s.a >> sh) & 0xffu;
-  const unsigned rb = sh > 64 ? 0u : (unsigned)(s.a >> (sh - 1)) & 1u;
-  const unsigned sticky = s.tz < sh - 1 ? 1u : 0u;
-  return (t8 + (rb & (sticky | (t8 & 1u)))) & 0xffu;
-}
-
-// digit for plane weight 2^(wexp) given Q mod 256 of this plane and Q mod 2 of the previous one
-__device__ __forceinline__ int digit_from_q(const DigitSource& s, unsigned q8, unsigned prev_par) {
-  int d = (int)((q8 - (prev_par << 7)) & 0xffu);
-  d = d >= 128 ? d - 256 : d;
-  return s.neg ? -d : d;
+// Digits of x = P 2^q on the fixed grid of exponent e, computed plane by plane instead of
+// through the sequential remainder.  After r round-half-even digits the partial sum is the
+// round-half-even multiple Q_r 2^(s_r) of P, s_r = e + 1 - 7r - q (a tie leaves Q_r even,
+// since Q_r = 128 Q_(r-1) + d_r with d_r chosen even), so d_r = Q_r - 128 Q_(r-1); as
+// |d_r| <= 64 it depends only on Q_r mod 256 and Q_(r-1) mod 2 (Q_0 = 0 because |x| < 2^e).
+// The digits of -x are those of x negated.
+//
+// The value is placed once on the grid one bit below the last plane's LSB:
+// A = |P| 2^(q - g), g = e - 7K (bits shifted out only set a sticky flag; A < 2^(7K)).
+// Plane r = K - j then has its LSB at bit p = 1 + 7j of A, a constant in the unrolled loop,
+// and its sticky bit is "trailing zeros of A < p - 1".  L lanes (values) share e and K;
+// emit(r, d) receives plane r's digits of all lanes, from r = 1 down to r = K.
+template <int L, class Emit>
+__device__ __forceinline__ void for_each_digit(const i64 (&P)[L], const int (&q)[L], int e, int K, Emit emit) {
+  unsigned __int128 A[L];
+  bool neg[L], sticky0[L];
+  int tz[L];
+  unsigned par[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    neg[l] = P[l] < 0;
+    const u64 a = neg[l] ? (u64)0 - (u64)P[l] : (u64)P[l];
+    A[l] = 0;
+    sticky0[l] = false;
+    if (a != 0) {
+      const int sh = q[l] - (e - DIGIT_BITS * K);
+      if (sh >= 0) {
+        A[l] = sh <= 74 ? (unsigned __int128)a << sh : (unsigned __int128)0;
+      } else if (sh > -64) {
+        A[l] = a >> (-sh);
+        sticky0[l] = (a & ((1ull << (-sh)) - 1)) != 0;
+      } else {
+        sticky0[l] = true;
+      }
+    }
+    const u64 lo = (u64)A[l], hi = (u64)(A[l] >> 64);
+    tz[l] = lo ? __ffsll((long long)lo) - 1 : (hi ? 63 + __ffsll((long long)hi) : 128);
+    par[l] = 0;
+  }
+#pragma unroll
+  for (int j = MAX_PLANES - 1; j >= 0; --j) {
+    if (j < K) {
+      const int p = 1 + DIGIT_BITS * j;
+      int d[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        const unsigned t8 = (unsigned)(A[l] >> p) & 0xffu;
+        const unsigned rb = (unsigned)(A[l] >> (p - 1)) & 1u;
+        const unsigned st = (sticky0[l] || tz[l] < p - 1) ? 1u : 0u;
+        const unsigned q8 = (t8 + (rb & (st | (t8 & 1u)))) & 0xffu;
+        int v = (int)((q8 - (par[l] << 7)) & 0xffu);
+        v = v >= 128 ? v - 256 : v;
+        d[l] = neg[l] ? -v : v;
+        par[l] = q8 & 1u;
+      }
+      emit(K - j, d);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -6,6 +6,8 @@
 
 namespace frx {
 
+constexpr int MAX_GROUPS = 40;   // anti-diagonal groups of one product (2 * MAX_PLANES - 1 fit)
+
 // One Ozaki product: plane counts, pair bound, layout of the exact sums and the
 // persistent schedule (units = ntm * ntn * groups, groups ordered by decreasing work).
 struct GemmDesc {
@@ -13,7 +15,7 @@ struct GemmDesc {
   int kL, kR, T;
   int tmax, gs, groups, word32;
   int ntm, ntn, units;
-  int gorder[32];
+  int gorder[MAX_GROUPS];
 };
 
 // host/device: fill tmax, gs, groups, word32 (same rule as plan_plane_gemm); returns FRX_OK or
@@ -40,7 +42,8 @@ __host__ __device__ inline int gemm_desc_layout(GemmDesc& d, int64_t K, int out_
   int bs = 0;
   for (unsigned long long v = smax; v; v >>= 1) ++bs;  // smax < 2^bs
   if (bs > 61) return FRX_E_UNSUPPORTED;
-  if (out_bytes_per_elem > 0 && smax < (1ull << 31) && (d.tmax - 1) * 4 <= out_bytes_per_elem) {
+  if (out_bytes_per_elem > 0 && smax < (1ull << 31) && (d.tmax - 1) * 4 <= out_bytes_per_elem &&
+      d.tmax - 1 <= MAX_GROUPS) {
     d.word32 = 1;
     d.gs = 1;
     d.groups = d.tmax - 1;
@@ -48,7 +51,7 @@ __host__ __device__ inline int gemm_desc_layout(GemmDesc& d, int64_t K, int out_
   }
   d.gs = (61 - bs) / 7 + 1;
   d.groups = (d.tmax - 1 + d.gs - 1) / d.gs;
-  if (d.groups > 31) return FRX_E_UNSUPPORTED;
+  if (d.groups > MAX_GROUPS) return FRX_E_UNSUPPORTED;
   if (out_bytes_per_elem > 0 && d.groups * 8 > out_bytes_per_elem) return FRX_E_UNSUPPORTED;
   return FRX_OK;
 }
@@ -58,8 +61,8 @@ __host__ __device__ inline void gemm_desc_schedule(GemmDesc& d, int64_t M, int64
   d.ntm = (int)((M + 127) / 128);
   d.ntn = (int)((N + bn - 1) / bn);
   d.units = d.active ? d.ntm * d.ntn * d.groups : 0;
-  int work[32];
-  for (int q = 0; q < d.groups && q < 32; ++q) {
+  int work[MAX_GROUPS];
+  for (int q = 0; q < d.groups && q < MAX_GROUPS; ++q) {
     int t0 = 2 + q * d.gs, t1 = t0 + d.gs - 1 < d.tmax ? t0 + d.gs - 1 : d.tmax, w = 0;
     for (int t = t0; t <= t1; ++t) {
       int lo = t - d.kR > 1 ? t - d.kR : 1, hi = d.kL < t - 1 ? d.kL : t - 1;
@@ -69,7 +72,7 @@ __host__ __device__ inline void gemm_desc_schedule(GemmDesc& d, int64_t M, int64
     d.gorder[q] = q;
   }
   // stable insertion sort by decreasing work
-  for (int a = 1; a < d.groups && a < 32; ++a) {
+  for (int a = 1; a < d.groups && a < MAX_GROUPS; ++a) {
     int x = d.gorder[a], b = a - 1;
     while (b >= 0 && work[d.gorder[b]] < work[x]) {
       d.gorder[b + 1] = d.gorder[b];

@@ -284,8 +284,8 @@ __global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_
                                                       const int32_t* __restrict__ eR, int64_t M, int64_t N,
                                                       double* __restrict__ Ch, int64_t ldh, double* __restrict__ Cl,
                                                       int64_t ldl) {
-  int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  int64_t j = blockIdx.y;
+  int64_t i = (int64_t)blockIdx.y * 256 + threadIdx.x;
+  int64_t j = blockIdx.x;   // columns on x: N may exceed 65535
   if (i >= M) return;
   ga = resolve(ga);
   const int ei = eL[i], ej = eR[j];
@@ -946,7 +946,7 @@ GroupArgs group_args(const PlaneGemm& g) {
 int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR, double* Ch, int64_t ldh,
                         double* Cl, int64_t ldl, cudaStream_t s) {
   if (g.M == 0 || g.N == 0) return FRX_OK;
-  dim3 grid((unsigned)((g.M + 255) / 256), (unsigned)g.N);
+  dim3 grid((unsigned)g.N, (unsigned)((g.M + 255) / 256));
   k_groups_to_dd<<<grid, 256, 0, s>>>(group_args(g), eL, eR, g.M, g.N, Ch, ldh, Cl, ldl);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());

@@ -44,7 +44,8 @@ def test_host_only_calls(lib):
     assert lib.frx_refine_workspace_bytes(0, None) == 0
     assert lib.frx_refine_workspace_bytes(64, None) > 64 * 64 * 8 * 3
     assert lib.frx_refine_workspace_bytes(12289, None) == 0
-    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 17) == 0
+    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 19) == 0
+    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 18) > 0
 
 
 def test_argument_errors_before_any_device_work(lib):

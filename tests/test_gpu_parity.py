@@ -272,3 +272,18 @@ def test_refine_batched_forward_error(api, xi, factor):
         Xh, Xl, _, _ = tr.eigvecs_dd(p[0], p[1])
         assert info["status"] == 0
         assert tr.forward_error(Xh, Xl, X.cpu().numpy()) <= factor * 1e-13
+
+
+def test_ozaki_gemm_more_than_65535_columns(api):
+    # column counts beyond the 65535 limit of a grid's y dimension (slicing and recombination
+    # put columns on x); small m and k keep the oracle quick
+    g = G()
+    m, K, n, k = 8, 40, 70000, 5
+    A = synth.gemm_operand(m, K, 1.0, 320)
+    B = synth.gemm_operand(K, n, 1.0, 321)
+    Ch, Cl = api.ozaki_gemm(g.to_dev(A), g.to_dev(B), k, "triangular", return_lo=True)
+    C_ref, o = oz.ozaki_gemm(A, B, k, "triangular")
+    Ch, Cl = Ch.cpu().numpy(), Cl.cpu().numpy()
+    mag = np.abs(A) @ np.abs(B)
+    assert np.all(np.abs((Ch - o["hi"]) + (Cl - o["lo"])) <= mag * 2.0 ** -100)
+    assert np.all(np.abs(Ch - C_ref) <= np.spacing(np.abs(C_ref)))
