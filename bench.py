@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--sample-rows", type=int, default=8)
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
-    p.add_argument("--workload", choices=["refine", "batched", "configs"], default="refine",
+    p.add_argument("--workload", choices=["refine", "batched", "configs", "previous"], default="refine",
                    help="refine: one n=4096 refinement per step; batched: 256 matrices, n in [32, 512]; "
                         "configs: the n=2048 variants and the n=8192 forward-error sweep")
     p.add_argument("--count", type=int, default=256)
@@ -593,6 +593,67 @@ def run_configs(args):
     print(json.dumps(out), flush=True)
 
 
+def run_previous(args):
+    """The proposed truncation of X (Sec. 3, beta rule) against the "previous study" form in
+    which X is sliced at full FP64 width (8 digit planes), at the settings of the paper's
+    convergence figures (cond 1e10, n = 1024/4096/8192, delta = 1e-8/1e-10/1e-12): products,
+    iterations and time of both, and their ratio (the paper's 4/3 - 2x claim counts products)."""
+    import torch
+
+    from paper_2602_19090_gb300 import api, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    out = {"metric": "previous_study", "randsvd_cond1e10": [], "exact_truth_n4096_cond1e10": []}
+
+    def dev_inputs(A, X0, D0):
+        return (torch.from_numpy(A).to(dev), api.colmajor(torch.from_numpy(X0).to(dev))[0],
+                torch.from_numpy(D0).to(dev))
+
+    for n in (1024, 4096, 8192):
+        A, X0, D0, lam = synth.refine_workload(n, 1e10, "spd", case=600 + n % 97)
+        At, X0t, D0t = dev_inputs(A, X0, D0)
+        del A, X0
+        work = api.workspace(api.refine_workspace_bytes(n), dev)
+        for delta in (1e-8, 1e-10, 1e-12):
+            ms_p, ip, Xp = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work, reps=2)
+            ms_q, iq, Xq = _timed_refine(api, At, X0t, D0t, delta, api.Options(x_planes=8), work, reps=2)
+            ms_x, ix, Xx = _timed_refine(api, At, X0t, D0t, delta, api.Options(xi=1.0), work, reps=2)
+            rec = {"n": n, "delta": delta,
+                   "proposed_xi1": {"ms": ms_x, "status": ix["status_name"], "iters": ix["iters"],
+                                    "products": ix["products"], "s_X": ix["s_X"], "err_est": ix["err_est"]},
+                   "proposed": {"ms": ms_p, "status": ip["status_name"], "iters": ip["iters"],
+                                "products": ip["products"], "s_X": ip["s_X"], "k_V": ip["k_V"], "err_est": ip["err_est"]},
+                   "previous_8_planes": {"ms": ms_q, "status": iq["status_name"], "iters": iq["iters"],
+                                         "products": iq["products"], "s_X": iq["s_X"], "k_V": iq["k_V"],
+                                         "err_est": iq["err_est"]},
+                   "product_ratio": iq["products"] / max(ip["products"], 1), "time_ratio": ms_q / ms_p,
+                   "max_abs_diff": float((Xp - Xq).abs().max())}
+            out["randsvd_cond1e10"].append(rec)
+            print(json.dumps(rec), file=sys.stderr, flush=True)
+        del At, X0t, D0t, work
+    n = 4096
+    A, X0, D0, lam, Qh, Ql, hinfo = synth.hadamard_workload(n, 1e10, synth.seed_for(2, 500))
+    At, X0t, D0t = dev_inputs(A, X0, D0)
+    Qht, Qlt = torch.from_numpy(Qh).to(dev), torch.from_numpy(Ql).to(dev)
+    work = api.workspace(api.refine_workspace_bytes(n), dev)
+    for delta in (1e-8, 1e-10, 1e-12):
+        ms_p, ip, Xp = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work, reps=2)
+        ms_q, iq, Xq = _timed_refine(api, At, X0t, D0t, delta, api.Options(x_planes=8), work, reps=2)
+        ms_x, ix, Xx = _timed_refine(api, At, X0t, D0t, delta, api.Options(xi=1.0), work, reps=2)
+        rec = {"n": n, "delta": delta,
+               "proposed_xi1": {"ms": ms_x, "status": ix["status_name"], "iters": ix["iters"],
+                                "products": ix["products"], "forward_error": _forward_error(Xx, Qht, Qlt)["two"]},
+               "proposed": {"ms": ms_p, "status": ip["status_name"], "iters": ip["iters"], "products": ip["products"],
+                            "forward_error": _forward_error(Xp, Qht, Qlt)["two"]},
+               "previous_8_planes": {"ms": ms_q, "status": iq["status_name"], "iters": iq["iters"],
+                                     "products": iq["products"], "forward_error": _forward_error(Xq, Qht, Qlt)["two"]},
+               "product_ratio": iq["products"] / max(ip["products"], 1), "time_ratio": ms_q / ms_p}
+        out["exact_truth_n4096_cond1e10"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -634,6 +695,8 @@ def main():
         run_batched(args)
     elif args.workload == "configs":
         run_configs(args)
+    elif args.workload == "previous":
+        run_previous(args)
     else:
         run_ours(args)
 

@@ -76,6 +76,10 @@ typedef struct {
   double cluster_omega;  /* >= 0: |lam_j - lam_i| <= omega is a cluster pair (0: only equal
                             estimates); < 0: Ogita-Aishima threshold
                             2 (||W||_F + max|lam| ||diag R||_2) each iteration              */
+  int x_planes;          /* 0: X^(1) from the Sec. 3 truncation (beta rule).  1..8: X is kept at
+                            x_planes digit planes (rounded to the last plane's grid, beta =
+                            54 - 7 x_planes) with no truncation rule: the "previous study"
+                            form of Sec. 4 (both operands sliced; 8 planes = full FP64 width) */
 } frx_opts;
 
 /* Per-call report of frx_refine (host struct). */

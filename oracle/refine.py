@@ -57,6 +57,8 @@ class Options:
     max_iter: int = 10
     xi_stop: float | None = None  # None: n
     cluster: object = 0.0        # threshold omega (float) or "auto"
+    x_planes: int = 0            # > 0: X kept at x_planes digit planes, no truncation rule
+                                 # (the "previous study" of Sec. 4: both operands sliced)
 
 
 def ceil_log2_sqrt(n: int) -> int:
@@ -132,7 +134,9 @@ def plan(A, X, lam_prev, delta, opts: Options, omega_prev=0.0):
     f = oz.col_exponents(X)
     g, Lam = min_gap(lam_prev, omega_prev)
     S2 = sum_pow4(f)
-    beta = beta_rule(n, delta, g, Lam, S2, opts)
+    # previous-study form: X represented by x_planes digit planes, i.e. rounded to the grid
+    # of plane x_planes, which is the tau grid of beta = 54 - 7 x_planes
+    beta = 54 - 7 * opts.x_planes if opts.x_planes > 0 else beta_rule(n, delta, g, Lam, S2, opts)
     alpha = alpha_rule(n, beta, opts)
     sX = -(-(54 - beta) // 7)
     eA = oz.row_exponents(A)
@@ -156,7 +160,12 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
     beta, sX, kV, f, eA = p["beta"], p["sX"], p["kV"], p["f"], p["eA"]
 
     # X^(1) (eq. tau, eq. x) and V = A X^(1) (line 1, eq. mat_mul)
-    X1, _ = oz.tau_truncate_cols(X, beta, f)
+    if opts.x_planes > 0:
+        # the sum of the x_planes digit planes of X (exact: X minus the slicing residual)
+        _, _, resid = oz.slice_cols(X, opts.x_planes, f)
+        X1 = X - resid
+    else:
+        X1, _ = oz.tau_truncate_cols(X, beta, f)
     V = oz.ozaki_product(A, X1, kV, sX, kV + 1, eL=eA, eR=f, exact=exact)
     Vh, Vl = V["hi"], V["lo"]
 

@@ -36,11 +36,12 @@ class Options:
     max_iter: int = 10
     xi_stop: float = 0.0
     cluster_omega: float = 0.0   # < 0: automatic Ogita-Aishima threshold
+    x_planes: int = 0            # > 0: X kept at x_planes digit planes (previous-study form)
 
     def to_c(self) -> _lib.Opts:
         return _lib.Opts(self.slices_A, self.xi, int(self.beta_ceil), int(self.theory_alpha),
                          self.beta_override, self.k_cap, self.max_iter, self.xi_stop,
-                         self.cluster_omega)
+                         self.cluster_omega, self.x_planes)
 
 
 def _ptr(t):

@@ -158,6 +158,7 @@ struct DebugOut {
 int validate_opts(const frx_opts& o) {
   if (o.k_cap < 1 || o.k_cap > MAX_PLANES || o.max_iter < 1 || o.slices_A < 0 || o.slices_A > o.k_cap)
     return FRX_E_ARG;
+  if (o.x_planes < 0 || o.x_planes > 8) return FRX_E_ARG;
   return FRX_OK;
 }
 
@@ -172,6 +173,7 @@ PlanOpts plan_opts(const frx_opts& o, double delta, int64_t n, int max_iter) {
   p.max_iter = max_iter;
   p.xi_stop = o.xi_stop;
   p.cluster_omega = o.cluster_omega;
+  p.x_planes = o.x_planes;
   p.delta = delta;
   p.n = n;
   return p;
@@ -587,6 +589,7 @@ void frx_default_opts(frx_opts* o) {
   o->max_iter = 10;
   o->xi_stop = 0.0;
   o->cluster_omega = 0.0;
+  o->x_planes = 0;
 }
 
 const char* frx_status_string(int st) {

@@ -24,6 +24,21 @@ __device__ __forceinline__ int bitlen_u128(u128 a) {
 
 __device__ __forceinline__ u128 abs_i128(i128 v) { return v < 0 ? (u128)0 - (u128)v : (u128)v; }
 
+// an upper bound on the bit length of |v| (exact for v >= 0, at most one more for v < 0):
+// the bit length of v XOR its sign mask, plus one for negatives
+__device__ __forceinline__ int bitlen_bound_i128(i128 v) {
+  const u64 hi = (u64)(v >> 64), lo = (u64)v, sm = (u64)((i64)hi >> 63);
+  const u64 h = hi ^ sm, l = lo ^ sm;
+  return (h ? 128 - __clzll((long long)h) : 64 - __clzll((long long)l)) + (int)(sm & 1);
+}
+
+// full signed 64 x 64 -> 128-bit product
+__device__ __forceinline__ i128 mul_i64(i64 a, i64 b) {
+  const u64 lo = (u64)a * (u64)b;
+  const u64 hi = (u64)__mul64hi(a, b);
+  return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
 // Bits of RN-even((-1)^neg * a * 2^c) for a > 0.  False when the result is subnormal or
 // overflows (the caller then takes a general path).  Works on the 64-bit halves: the top
 // 64 bits of a and a sticky bit for the rest decide the rounding exactly.

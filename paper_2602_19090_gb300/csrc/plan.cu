@@ -272,7 +272,9 @@ __global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, Pla
   const int64_t n = o.n;
   double g = p->g, Lam = p->Lam;
   int beta;
-  if (o.beta_override >= 0) {
+  if (o.x_planes > 0) {
+    beta = 54 - DIGIT_BITS * o.x_planes;   // X kept at x_planes planes (previous-study form)
+  } else if (o.beta_override >= 0) {
     beta = min(max(o.beta_override, 3), 47);
   } else if (g <= 0.0 || Lam <= 0.0 || S2 <= 0.0) {
     beta = 3;

@@ -96,6 +96,7 @@ struct PlanOpts {
   double xi;
   int beta_ceil, theory_alpha, beta_override, k_cap, max_iter;
   double xi_stop, cluster_omega;
+  int x_planes;
   double delta;
   int64_t n;
 };

@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
   __shared__ u64 redu[32];
   __shared__ i128 redi[32];
   __shared__ int redt[32];
+  __shared__ int redb[32][4];
   const int64_t j = blockIdx.x;
   const int64_t n = a.n;
   const int fj = a.f[j];
@@ -515,6 +516,7 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
   const int nb = a.V.groups;
   u128 nn = 0;
   int tb = -(1 << 30);
+  int bmmax = 0, bnmax = 0, emin = 1 << 30, emax = -(1 << 30);   // bounds for pass 3
   // pass 1
   for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)FRX_RPT_RESIDUAL * blockDim.x) {
     double xv[FRX_RPT_RESIDUAL];
@@ -545,8 +547,16 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
       const i64 m = grid_mantissa(xv[k], gj);
       const u64 am = m < 0 ? (u64)0 - (u64)m : (u64)m;
       nn += (u128)am * am;
+      const int bm = am ? bitlen_u64(am) : 0;
+      const int bn = N != 0 ? bitlen_bound_i128(N) : 0;
+      bmmax = bm > bmmax ? bm : bmmax;
+      bnmax = bn > bnmax ? bn : bnmax;
+      if (ei[k] != EZERO) {
+        emin = ei[k] < emin ? ei[k] : emin;
+        emax = ei[k] > emax ? ei[k] : emax;
+      }
       if (N != 0 && m != 0) {
-        const int t = bitlen_u64(am) + bitlen_u128(abs_i128(N)) + ei[k] + cbase;
+        const int t = bm + bn + ei[k] + cbase;
         tb = t > tb ? t : tb;
       }
     }
@@ -560,29 +570,48 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
       const u128 sum = (((u128)hi << 64) | lo) + (((u128)hi2 << 64) | lo2);
       lo = (u64)sum;
       hi = (u64)(sum >> 64);
-      const int t2 = __shfl_xor_sync(0xffffffffu, tb, o);
-      tb = t2 > tb ? t2 : tb;
+      tb = max(tb, __shfl_xor_sync(0xffffffffu, tb, o));
+      bmmax = max(bmmax, __shfl_xor_sync(0xffffffffu, bmmax, o));
+      bnmax = max(bnmax, __shfl_xor_sync(0xffffffffu, bnmax, o));
+      emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     }
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
       redi[wi] = (i128)(((u128)hi << 64) | lo);
       redt[wi] = tb;
+      redb[wi][0] = bmmax;
+      redb[wi][1] = bnmax;
+      redb[wi][2] = emin;
+      redb[wi][3] = emax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       u128 tot = 0;
-      int tm = -(1 << 30);
+      int tm = -(1 << 30), b0 = 0, b1 = 0, e0 = 1 << 30, e1 = -(1 << 30);
       for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
         tot += (u128)redi[k];
-        tm = redt[k] > tm ? redt[k] : tm;
+        tm = max(tm, redt[k]);
+        b0 = max(b0, redb[k][0]);
+        b1 = max(b1, redb[k][1]);
+        e0 = min(e0, redb[k][2]);
+        e1 = max(e1, redb[k][3]);
       }
       redi[0] = (i128)tot;
       redt[0] = tm;
+      redb[0][0] = b0;
+      redb[0][1] = b1;
+      redb[0][2] = e0;
+      redb[0][3] = e1;
     }
     __syncthreads();
   }
   const u128 nn_tot = (u128)redi[0];
   const int T = redt[0];
+  bmmax = redb[0][0];
+  bnmax = redb[0][1];
+  emin = redb[0][2];
+  emax = redb[0][3];
   __syncthreads();
   // pass 2: x^T v on the grid 2^(lsb + gj)
   int lg = 0;
@@ -627,25 +656,29 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
   }
   const double lam = __longlong_as_double((long long)redu[0]);
   __syncthreads();
-  // pass 3: Res = N 2^c - (m L) 2^(gj + qL), rounded once
+  // pass 3: Res = N 2^c - (m L) 2^(gj + qL), rounded once.  The aligned difference fits
+  // 128 bits for every row when the block-wide bounds say so; otherwise per row.
   i64 L = 0;
   int qL = 0;
   if (lam != 0.0) decompose(lam, L, qL);
+  const int bL = L ? bitlen_u64(L < 0 ? (u64)0 - (u64)L : (u64)L) : 0;
+  const int gq = gj + qL;
+  const int dmax = emax > -(1 << 29) ? gq - (emin + cbase) : 0, dmin = emax > -(1 << 29) ? gq - (emax + cbase) : 0;
+  const bool safe = dmin >= -60 && dmax <= 60 && bmmax + bL + (dmax > 0 ? dmax : 0) <= 125 &&
+                    bnmax + (dmin < 0 ? -dmin : 0) <= 125 && bnmax <= 125 && bmmax + bL <= 125;
   u64 mx = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     const double xi = x[i];
     const int ei = a.eA[i];
     const i128 N = ncol[i];
-    const i128 ML = (i128)grid_mantissa(xi, gj) * (i128)L;
-    const int c = ei == EZERO ? gj + qL : ei + cbase;
-    const int d = (gj + qL) - c;
+    const i128 ML = mul_i64(grid_mantissa(xi, gj), L);
+    const int c = ei == EZERO ? gq : ei + cbase;
+    const int d = gq - c;
     double res;
     bool done = false;
-    if (d >= 0) {
-      if (bitlen_u128(abs_i128(ML)) + d <= 125 && bitlen_u128(abs_i128(N)) <= 125)
-        done = rn_scaled(N - (ML << d), c, res);
-    } else if (bitlen_u128(abs_i128(N)) - d <= 125 && bitlen_u128(abs_i128(ML)) <= 125) {
-      done = rn_scaled((N << (-d)) - ML, gj + qL, res);
+    if (safe || (d >= 0 ? (bitlen_u128(abs_i128(ML)) + d <= 125 && bitlen_u128(abs_i128(N)) <= 125)
+                        : (bitlen_u128(abs_i128(N)) - d <= 125 && bitlen_u128(abs_i128(ML)) <= 125))) {
+      done = d >= 0 ? rn_scaled(N - (ML << d), c, res) : rn_scaled((N << (-d)) - ML, gq, res);
     }
     if (!done) {
       const dd v = gather_dd_general(a.V, i, j, ei, fj);

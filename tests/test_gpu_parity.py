@@ -175,6 +175,13 @@ def test_refine_step_parity_several_tiles(api, n, cond, variant):
     _step_compare(api, A, X0, D0, 1e-12, orf.Options(), api.Options())
 
 
+@pytest.mark.parametrize("xp", [3, 8])
+def test_refine_step_parity_previous_study_form(api, xp):
+    # X kept at xp digit planes (no truncation rule): beta = 54 - 7 xp, below 3 for xp = 8
+    A, X0, D0, lam = synth.refine_workload(257, 1e6, "spd", case=257)
+    _step_compare(api, A, X0, D0, 1e-12, orf.Options(x_planes=xp), api.Options(x_planes=xp))
+
+
 def test_refine_converges_like_the_oracle(api):
     g = G()
     A, X0, D0 = synth.workload0()

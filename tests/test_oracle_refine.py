@@ -214,3 +214,22 @@ def test_start_outside_the_basin_still_converges():
     assert hist[1]["step"] > 0.5 * hist[0]["step"]  # ... and the second step is as large
     assert res["status"] == "converged"
     assert fe(X) <= 1e-14
+
+
+def test_previous_study_form_keeps_x_at_its_planes():
+    # x_planes = 8 keeps X at 8 digit planes (56 bits on the column grid): every entry within
+    # 2^(f-3) of the column maximum is unchanged, smaller ones are rounded to 2^(f-55)
+    A, X0, D0 = synth.workload0()
+    hist = []
+    rf.refine(A, X0, D0, 1e-14, rf.Options(x_planes=8, max_iter=1), history=hist)
+    p = rf.plan(A, X0, D0, 1e-14, rf.Options(x_planes=8))
+    assert p["sX"] == 8 and p["beta"] == -2
+    X1 = X0 - oz.slice_cols(X0, 8, p["f"])[2]
+    big = np.abs(X0) >= np.ldexp(1.0, p["f"] - 3)[None, :]
+    assert np.array_equal(X1[big], X0[big])
+    assert np.all(np.abs(X1 - X0) <= np.ldexp(1.0, p["f"] - 56)[None, :])
+    # three planes: the tau grid of beta = 33
+    p3 = rf.plan(A, X0, D0, 1e-14, rf.Options(x_planes=3))
+    X13 = X0 - oz.slice_cols(X0, 3, p3["f"])[2]
+    T, _ = oz.tau_truncate_cols(X0, 33, p3["f"])
+    assert p3["sX"] == 3 and np.array_equal(X13, T)
