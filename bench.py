@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--sample-rows", type=int, default=8)
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
-    p.add_argument("--workload", choices=["refine", "batched", "configs", "previous"], default="refine",
+    p.add_argument("--workload", choices=["refine", "batched", "configs", "previous", "gemm"], default="refine",
                    help="refine: one n=4096 refinement per step; batched: 256 matrices, n in [32, 512]; "
                         "configs: the n=2048 variants and the n=8192 forward-error sweep")
     p.add_argument("--count", type=int, default=256)
@@ -654,6 +654,59 @@ def run_previous(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gemm_sweep(args):
+    """ozaki_gemm over n = 1024/4096/8192, phi = 0.5/2/4, k = 4/8/12/18 planes, both product
+    sets: time (CUDA events, best of 3), TFLOPS-eq = 2 n^3 / time, the slice-product kernel's own
+    rate, and the error against the same product at 18 planes with all pairs (126 bits of each
+    operand), relative to |A||B|; a DGEMM's error on the same scale is given for context."""
+    import torch
+
+    from paper_2602_19090_gb300 import api, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    out = {"metric": "ozaki_gemm_sweep", "cases": []}
+    for n in (1024, 4096, 8192):
+        for phi in (0.5, 2.0, 4.0):
+            # column-major operands, so that the timed calls do no layout copies
+            A = api.colmajor(torch.from_numpy(synth.gemm_operand(n, n, phi, synth.seed_for(1, 10 + int(phi * 2)))).to(dev))[0]
+            B = api.colmajor(torch.from_numpy(synth.gemm_operand(n, n, phi, synth.seed_for(1, 20 + int(phi * 2)))).to(dev))[0]
+            work = api.workspace(api.ozaki_gemm_workspace_bytes(n, n, n, 18), dev)
+            Rh, Rl = api.ozaki_gemm(A, B, 18, "full", return_lo=True, work=work)
+            mag = torch.abs(A) @ torch.abs(B)
+            mag = torch.where(mag > 0, mag, torch.ones_like(mag))
+            D = A @ B
+            dgemm_err = float((((D - Rh) - Rl).abs() / mag).max())
+            for k in (4, 8, 12, 18):
+                for mode in ("triangular", "full"):
+                    C = api.ozaki_gemm(A, B, k, mode, work=work)
+                    torch.cuda.synchronize()
+                    best = 1e30
+                    api.profile_read(reset=True)
+                    api.profile_enable(True)
+                    for _ in range(3):
+                        s0 = torch.cuda.Event(enable_timing=True)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        s0.record()
+                        C = api.ozaki_gemm(A, B, k, mode, work=work)
+                        e0.record()
+                        torch.cuda.synchronize()
+                        best = min(best, s0.elapsed_time(e0))
+                    api.profile_enable(False)
+                    pr = api.profile_read(reset=True)
+                    products = k * (k + 1) // 2 if mode == "triangular" else k * k
+                    err = float((((C - Rh) - Rl).abs() / mag).max())
+                    rec = {"n": n, "phi": phi, "k": k, "mode": mode, "products": products, "ms": best,
+                           "tflops_eq": 2.0 * n ** 3 / (best * 1e-3) / 1e12,
+                           "gemm_kernel_tflops": pr["gemm_ops"] / (pr["gemm_ms"] * 1e-3) / 1e12 if pr["gemm_ms"] else None,
+                           "gemm_share": pr["gemm_ms"] / 3 / best if pr["gemm_ms"] else None,
+                           "max_err_rel_absAabsB": err, "dgemm_err_rel_absAabsB": dgemm_err}
+                    out["cases"].append(rec)
+                    print(json.dumps(rec), file=sys.stderr, flush=True)
+            del A, B, work, Rh, Rl, mag, D
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -697,6 +750,8 @@ def main():
         run_configs(args)
     elif args.workload == "previous":
         run_previous(args)
+    elif args.workload == "gemm":
+        run_gemm_sweep(args)
     else:
         run_ours(args)
 

@@ -167,6 +167,10 @@ def refine_step(A, X, D, delta, opts: Options | None = None, omega_prev: float =
     return info.as_dict(), out
 
 
+def ozaki_gemm_workspace_bytes(m: int, n: int, k: int, slices: int) -> int:
+    return _lib.load().frx_ozaki_gemm_workspace_bytes(m, n, k, slices)
+
+
 def ozaki_gemm(A, B, slices: int, mode: str = "full", return_lo: bool = False, work=None,
                stream=None):
     """C = A B by the Ozaki scheme with `slices` digit planes per operand."""

@@ -87,6 +87,7 @@ struct GemmWs {
   u64* rowmax;
   __nv_bfloat16 *Ap, *Bp;
   i64* groups;
+  int out_bytes;   // bytes per product entry of the exact-sum buffer
   int64_t pitch;
   size_t bytes;
 };
@@ -101,7 +102,10 @@ GemmWs carve_gemm(void* work, int64_t m, int64_t n, int64_t k, int slices) {
   w.rowmax = c.take<u64>(m);
   w.Ap = c.take<__nv_bfloat16>((size_t)slices * m * w.pitch);
   w.Bp = c.take<__nv_bfloat16>((size_t)slices * n * w.pitch);
-  w.groups = c.take<i64>((size_t)8 * m * n);
+  // exact sums: one int32 plane per anti-diagonal (at most 2 slices - 1 of them, full set),
+  // at least 64 bytes per entry for the int64 grouping used beyond the int32 bound
+  w.out_bytes = 4 * (2 * slices - 1) > 64 ? 4 * (2 * slices - 1) : 64;
+  w.groups = c.take<i64>((size_t)((w.out_bytes + 7) / 8) * m * n);
   w.bytes = c.off + 256;
   return w;
 }
@@ -683,6 +687,7 @@ int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_t ldb, d
   FRX_TRY(launch_slice_cols(B, ldb, k, n, ws.eB, slices, ws.Bp, n * ws.pitch, ws.pitch, s));
   int T = mode == FRX_MODE_FULL ? 2 * slices : slices + 1;
   PlaneGemm g = make_gemm(ws.Ap, m * ws.pitch, ws.Bp, n * ws.pitch, ws.pitch, m, n, k, slices, slices, T, ws.groups);
+  g.out_bytes_per_elem = ws.out_bytes;
   g.flags = ws.flags;
   FRX_TRY(plan_plane_gemm(g));
   FRX_TRY(launch_plane_gemm(g, s));

@@ -187,6 +187,23 @@ __device__ __forceinline__ int pair_hi(int t, int kL) { return kL < t - 1 ? kL :
 
 // BN_ = 128: int64 Horner groups of gs anti-diagonals, 64 columns per epilogue thread.
 // BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
+// Tile t of a group in banded raster order: bands of TILE_BAND tile rows, each walked
+// column by column, so the units in flight at one time (consecutive t) share A panels
+// across a band's width and B panels across its TILE_BAND rows, instead of sweeping whole
+// tile rows (where every B panel is re-read once per few rows).
+#ifndef FRX_TILE_BAND
+#define FRX_TILE_BAND 16
+#endif
+constexpr int TILE_BAND = FRX_TILE_BAND;
+
+__device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int bm, int bn, int& i0, int& j0) {
+  const int band = t / (TILE_BAND * ntn);
+  const int rows = min(TILE_BAND, ntm - band * TILE_BAND);
+  const int local = t - band * TILE_BAND * ntn;
+  i0 = (band * TILE_BAND + local % rows) * bm;
+  j0 = (local / rows) * bn;
+}
+
 template <int BN_, bool W32>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
@@ -260,7 +277,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int tiles = a.ntm * a.ntn;
       for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
         const int grp = gorder[u / tiles], tile = u % tiles;
-        const int i0 = (tile / a.ntn) * BM, j0 = (tile % a.ntn) * BN;
+        int i0, j0;
+        tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           for (int r = pair_lo(t, a.kR); r <= pair_hi(t, a.kL) && ok; ++r) {
@@ -386,7 +404,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int tiles = a.ntm * a.ntn;
     for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
       const int grp = gorder[u / tiles], tile = u % tiles;
-      const int i0 = (tile / a.ntn) * BM, j0 = (tile % a.ntn) * BN;
+      int i0, j0;
+        tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
       const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
       for (int t = t0; t <= t1 && ok; ++t) {
