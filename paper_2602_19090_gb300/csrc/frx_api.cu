@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "frx_internal.cuh"
+#include "grouped.cuh"
 #include "kernels.cuh"
 #include "refine_kernels.cuh"
 #include "plan_launch.cuh"
@@ -317,6 +318,7 @@ int ensure_attributes() {
   std::call_once(once, []() {
     st = set_refine_kernel_attributes();
     if (st == FRX_OK) st = set_plan_kernel_attributes();
+    if (st == FRX_OK) st = prepare_plane_gemm_grouped();
   });
   return st;
 }
@@ -385,72 +387,18 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
 }
 
 // ---------------------------------------------------------------------------
-// batched refinement: one CUDA graph per phase with an independent branch per problem
+// batched refinement: every stage of an iteration is one grouped launch over all problems
 // ---------------------------------------------------------------------------
-struct ForkPool {
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
-  cudaStream_t origin = nullptr;       // captures run here (the caller's stream may be the legacy one)
-  cudaEvent_t enter = nullptr, leave = nullptr;
-};
-
-int fork_pool(int k, ForkPool** out) {
-  static std::mutex mu;
-  static ForkPool pools[64];
-  int dev = 0;
-  FRX_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return FRX_E_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(mu);
-  ForkPool& p = pools[dev];
-  if (!p.fork) {
-    FRX_CUDA_TRY(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
-    FRX_CUDA_TRY(cudaEventCreateWithFlags(&p.enter, cudaEventDisableTiming));
-    FRX_CUDA_TRY(cudaEventCreateWithFlags(&p.leave, cudaEventDisableTiming));
-    FRX_CUDA_TRY(cudaStreamCreateWithFlags(&p.origin, cudaStreamNonBlocking));
-  }
-  while ((int)p.side.size() < k) {
-    cudaStream_t st;
-    cudaEvent_t ev;
-    FRX_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    FRX_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    p.side.push_back(st);
-    p.join.push_back(ev);
-  }
-  *out = &p;
-  return FRX_OK;
-}
-
-// capture body(b, stream) for b < count on `k` side streams forked from s, then tail(s)
-int capture_fanout(cudaStream_t s, ForkPool* pool, int k, int count, const std::function<int(int, cudaStream_t)>& body,
-                   const std::function<int(cudaStream_t)>& tail, cudaGraphExec_t* exec) {
-  cudaGraph_t graph = nullptr;
-  FRX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  int st = [&]() -> int {
-    FRX_CUDA_TRY(cudaEventRecord(pool->fork, s));
-    for (int q = 0; q < k; ++q) FRX_CUDA_TRY(cudaStreamWaitEvent(pool->side[q], pool->fork, 0));
-    for (int b = 0; b < count; ++b) FRX_TRY(body(b, pool->side[b % k]));
-    for (int q = 0; q < k; ++q) {
-      FRX_CUDA_TRY(cudaEventRecord(pool->join[q], pool->side[q]));
-      FRX_CUDA_TRY(cudaStreamWaitEvent(s, pool->join[q], 0));
-    }
-    if (tail) FRX_TRY(tail(s));
-    return FRX_OK;
-  }();
-  cudaError_t e = cudaStreamEndCapture(s, &graph);
-  if (st != FRX_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return st;
-  }
-  if (e != cudaSuccess) return FRX_E_CUDA;
-  e = cudaGraphInstantiate(exec, graph, 0);
-  cudaGraphDestroy(graph);
-  return e == cudaSuccess ? FRX_OK : FRX_E_CUDA;
-}
+// The launch sequence of one iteration is recorded once per problem (the same kernels in
+// the same order, with each problem's arguments); stage k of every problem then runs as one
+// launch whose blocks are the union of the problems' blocks, and the slice products of a
+// stage run in one persistent tensor-core launch.  An iteration is one captured CUDA graph.
+constexpr int BATCH_CHUNK = 2048;                      // problems per grouped launch
+constexpr size_t TABLE_BYTES_PER_PROBLEM = 16 * 1024;  // argument tables of all stages
 
 struct BatchLayout {
   std::vector<size_t> off;
-  size_t plans_off, done_off, gather_off, bytes;
+  size_t plans_off, done_off, gather_off, tables_off, tables_bytes, bytes;
 };
 
 BatchLayout batch_layout(const int64_t* n, int count, int kcap) {
@@ -460,77 +408,205 @@ BatchLayout batch_layout(const int64_t* n, int count, int kcap) {
     L.off.push_back(off);
     off += round_up((int64_t)carve_refine(nullptr, n[b], kcap).bytes, 256);
   }
+  const int chunk = count < BATCH_CHUNK ? count : BATCH_CHUNK;
   L.plans_off = off;
-  off += round_up(sizeof(DevPlan*) * (size_t)count, 256);
+  off += round_up(sizeof(DevPlan*) * (size_t)chunk, 256);
   L.done_off = off;
-  off += round_up(sizeof(int) * (size_t)count, 256);
+  off += round_up(sizeof(int) * (size_t)chunk, 256);
   L.gather_off = off;
-  off += round_up(sizeof(DevPlan) * (size_t)count, 256);
+  off += round_up(sizeof(DevPlan) * (size_t)chunk, 256);
+  L.tables_off = off;
+  L.tables_bytes = TABLE_BYTES_PER_PROBLEM * (size_t)chunk + 65536;
+  off += round_up((int64_t)L.tables_bytes, 256);
   L.bytes = off + 256;
   return L;
 }
 
-int refine_batched_impl(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
-                        double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, void* work,
-                        size_t work_bytes, frx_info* infos, cudaStream_t caller) {
-  BatchLayout L = batch_layout(n, count, o.k_cap);
-  if (!work || !aligned256(work) || work_bytes < L.bytes) return FRX_E_WORKSPACE;
-  FRX_TRY(ensure_attributes());
-  char* base = (char*)work;
+struct Stage {
+  int kind;
+  size_t tab_off, start_off;
+  long long blocks;
+  int threads;
+  size_t smem;
+};
+
+// stage k of a phase groups record k of every problem (same kind and argument size)
+int build_stages(const std::vector<std::vector<LaunchRecord>>& recs, std::vector<unsigned char>& blob,
+                 std::vector<Stage>& stages) {
+  const int count = (int)recs.size();
+  const size_t K = recs[0].size();
+  for (int b = 1; b < count; ++b)
+    if (recs[b].size() != K) return FRX_E_UNSUPPORTED;
+  for (size_t k = 0; k < K; ++k) {
+    Stage st;
+    st.kind = recs[0][k].kind;
+    const size_t sz = recs[0][k].args.size();
+    st.blocks = 0;
+    st.threads = 0;
+    st.smem = 0;
+    st.tab_off = (blob.size() + 63) / 64 * 64;
+    blob.resize(st.tab_off + sz * (size_t)count);
+    for (int b = 0; b < count; ++b) {
+      const LaunchRecord& r = recs[b][k];
+      if (r.kind != st.kind || r.args.size() != sz) return FRX_E_UNSUPPORTED;
+      memcpy(blob.data() + st.tab_off + sz * b, r.args.data(), sz);
+    }
+    st.start_off = (blob.size() + 7) / 8 * 8;
+    blob.resize(st.start_off + sizeof(long long) * (size_t)(count + 1));
+    long long* start = reinterpret_cast<long long*>(blob.data() + st.start_off);
+    for (int b = 0; b < count; ++b) {
+      const LaunchRecord& r = recs[b][k];
+      start[b] = st.blocks;
+      st.blocks += r.blocks;
+      st.threads = r.threads > st.threads ? r.threads : st.threads;
+      st.smem = r.smem > st.smem ? r.smem : st.smem;
+    }
+    start[count] = st.blocks;
+    if (st.kind == LK_RESIDUAL || st.kind == LK_CORRECTION || st.kind == LK_UPDATE) {
+      // one block per column: with every problem at n <= 1024 columns are short, and 128
+      // threads per block (up to 8 rows each) keep fewer threads idle at the same occupancy
+      long long most = 0;
+      for (int b = 0; b < count; ++b) most = recs[b][k].blocks > most ? recs[b][k].blocks : most;
+      if (most <= 1024) st.threads = 128;
+    }
+    stages.push_back(st);
+  }
+  return FRX_OK;
+}
+
+int launch_stage(const Stage& st, char* tables, int count, cudaStream_t s) {
+  const void* tab = tables + st.tab_off;
+  const long long* start = reinterpret_cast<const long long*>(tables + st.start_off);
+  switch (st.kind) {
+    case LK_GEMM:
+      return launch_plane_gemm_grouped(tab, count, s);
+    case LK_COL_EXPONENTS:
+    case LK_ROW_MAXBITS:
+    case LK_MAXBITS_TO_EXPONENTS:
+    case LK_SLICE_COLS:
+    case LK_SLICE_ROWS:
+    case LK_TRUNCATE_SLICE_X:
+    case LK_ZERO:
+    case LK_COPY:
+      return launch_grouped_scan(st.kind, tab, start, count, st.blocks, st.threads, st.smem, s);
+    case LK_RESIDUAL:
+    case LK_W_OFFDIAG:
+    case LK_CORRECTION:
+    case LK_UPDATE:
+      return launch_grouped_refine(st.kind, tab, start, count, st.blocks, st.threads, st.smem, s);
+    default:
+      return launch_grouped_plan(st.kind, tab, start, count, st.blocks, st.threads, st.smem, s);
+  }
+}
+
+// the library's own stream for the batched path (captures cannot use the legacy stream),
+// bridged to the caller's stream with events
+struct BatchStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t enter = nullptr, leave = nullptr;
+};
+
+int batch_stream(BatchStream** out) {
+  static std::mutex mu;
+  static BatchStream streams[64];
+  int dev = 0;
+  FRX_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return FRX_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  BatchStream& b = streams[dev];
+  if (!b.s) {
+    FRX_CUDA_TRY(cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking));
+    FRX_CUDA_TRY(cudaEventCreateWithFlags(&b.enter, cudaEventDisableTiming));
+    FRX_CUDA_TRY(cudaEventCreateWithFlags(&b.leave, cudaEventDisableTiming));
+  }
+  *out = &b;
+  return FRX_OK;
+}
+
+// record the three phases of every problem: setup, one iteration, finish
+int record_phases(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                  double* const* D, const int64_t* n, int count, const frx_opts& o, const std::vector<PlanOpts>& po,
+                  const std::vector<RefineWs>& ws, std::vector<std::vector<LaunchRecord>> (&rec)[3]) {
+  LaunchRecorder R;
+  LaunchRecorder*& active = active_recorder();
+  active = &R;
+  cudaStream_t none = nullptr;   // nothing is launched while recording
+  int st = [&]() -> int {
+    for (int b = 0; b < count; ++b) {
+      R.recs.clear();
+      FRX_TRY(record_bytes(ws[b].plan, nullptr, sizeof(DevPlan)));
+      FRX_TRY(record_bytes(ws[b].rowmax, nullptr, sizeof(u64) * (size_t)n[b]));
+      FRX_TRY(launch_col_exponents(A[b], lda[b], n[b], n[b], ws[b].eA, &ws[b].plan->flags, none));
+      FRX_TRY(launch_plan_init(ws[b].plan, ws[b].eA, D[b], ws[b].lam_prev, po[b], 0.0, none));
+      rec[0][b] = std::move(R.recs);
+      R.recs.clear();
+      FRX_TRY(enqueue_iteration(A[b], lda[b], X[b], ldx[b], n[b], o, po[b], ws[b], nullptr, none));
+      rec[1][b] = std::move(R.recs);
+      R.recs.clear();
+      FRX_TRY(record_bytes(D[b], ws[b].lam_prev, sizeof(double) * (size_t)n[b]));
+      rec[2][b] = std::move(R.recs);
+    }
+    return FRX_OK;
+  }();
+  active = nullptr;
+  return st;
+}
+
+int refine_batched_chunk(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                         double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, char* base,
+                         const BatchLayout& L, const size_t* off, frx_info* infos, cudaStream_t s) {
   std::vector<RefineWs> ws(count);
   std::vector<DevPlan*> hplans(count);
   std::vector<PlanOpts> po(count);
   for (int b = 0; b < count; ++b) {
-    ws[b] = carve_refine(base + L.off[b], n[b], o.k_cap);
+    ws[b] = carve_refine(base + off[b], n[b], o.k_cap);
     hplans[b] = ws[b].plan;
     po[b] = plan_opts(o, delta, n[b], o.max_iter);
   }
+  std::vector<std::vector<LaunchRecord>> rec[3];
+  for (int q = 0; q < 3; ++q) rec[q].resize(count);
+  FRX_TRY(record_phases(A, lda, X, ldx, D, n, count, o, po, ws, rec));
+  std::vector<unsigned char> blob;
+  std::vector<Stage> stages[3];
+  for (int q = 0; q < 3; ++q) FRX_TRY(build_stages(rec[q], blob, stages[q]));
+  if (blob.size() > L.tables_bytes) return FRX_E_UNSUPPORTED;
+  char* tables = base + L.tables_off;
   DevPlan** dplans = (DevPlan**)(base + L.plans_off);
   int* ddone = (int*)(base + L.done_off);
   DevPlan* gathered = (DevPlan*)(base + L.gather_off);
-  ForkPool* pool = nullptr;
-  FRX_TRY(fork_pool(count < 64 ? count : 64, &pool));
-  cudaStream_t s = pool->origin;
-  FRX_CUDA_TRY(cudaEventRecord(pool->enter, caller));
-  FRX_CUDA_TRY(cudaStreamWaitEvent(s, pool->enter, 0));
+  FRX_CUDA_TRY(cudaMemcpyAsync(tables, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
   FRX_CUDA_TRY(cudaMemcpyAsync(dplans, hplans.data(), sizeof(DevPlan*) * count, cudaMemcpyHostToDevice, s));
-  const int k = count < 64 ? count : 64;
-  cudaGraphExec_t g_setup = nullptr, g_iter = nullptr, g_end = nullptr;
+  for (const Stage& st : stages[0]) FRX_TRY(launch_stage(st, tables, count, s));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  FRX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int cst = [&]() -> int {
+    for (const Stage& st : stages[1]) FRX_TRY(launch_stage(st, tables, count, s));
+    return launch_collect_done(dplans, count, ddone, s);
+  }();
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (cst != FRX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return cst;
+  }
+  if (e != cudaSuccess) return FRX_E_CUDA;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return FRX_E_CUDA;
+  count_launches(-(int)(stages[1].size() + 1));   // captured, not launched: counted per replay
   int st = [&]() -> int {
-    FRX_TRY(capture_fanout(
-        s, pool, k, count,
-        [&](int b, cudaStream_t q) -> int {
-          FRX_CUDA_TRY(cudaMemsetAsync(ws[b].plan, 0, sizeof(DevPlan), q));
-          FRX_CUDA_TRY(cudaMemsetAsync(ws[b].rowmax, 0, sizeof(u64) * n[b], q));
-          FRX_TRY(launch_col_exponents(A[b], lda[b], n[b], n[b], ws[b].eA, &ws[b].plan->flags, q));
-          return launch_plan_init(ws[b].plan, ws[b].eA, D[b], ws[b].lam_prev, po[b], 0.0, q);
-        },
-        nullptr, &g_setup));
-    FRX_TRY(capture_fanout(
-        s, pool, k, count,
-        [&](int b, cudaStream_t q) -> int {
-          return enqueue_iteration(A[b], lda[b], X[b], ldx[b], n[b], o, po[b], ws[b], nullptr, q);
-        },
-        [&](cudaStream_t q) -> int { return launch_collect_done(dplans, count, ddone, q); }, &g_iter));
-    FRX_TRY(capture_fanout(
-        s, pool, k, count,
-        [&](int b, cudaStream_t q) -> int {
-          FRX_CUDA_TRY(
-              cudaMemcpyAsync(D[b], ws[b].lam_prev, sizeof(double) * n[b], cudaMemcpyDeviceToDevice, q));
-          return FRX_OK;
-        },
-        [&](cudaStream_t q) -> int { return launch_gather_plans(dplans, count, gathered, q); }, &g_end));
-    FRX_CUDA_TRY(cudaGraphLaunch(g_setup, s));
     std::vector<int> done(count);
     for (int it = 1; it <= o.max_iter; ++it) {
-      FRX_CUDA_TRY(cudaGraphLaunch(g_iter, s));
+      FRX_CUDA_TRY(cudaGraphLaunch(exec, s));
+      count_launches((long long)stages[1].size() + 1);   // the graph's kernels, per replay
       FRX_CUDA_TRY(cudaMemcpyAsync(done.data(), ddone, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
       FRX_CUDA_TRY(cudaStreamSynchronize(s));
       bool all = true;
       for (int b = 0; b < count; ++b) all &= done[b] != 0;
       if (all) break;
     }
-    FRX_CUDA_TRY(cudaGraphLaunch(g_end, s));
+    for (const Stage& sg : stages[2]) FRX_TRY(launch_stage(sg, tables, count, s));
+    FRX_TRY(launch_gather_plans(dplans, count, gathered, s));
     std::vector<DevPlan> hp(count);
     FRX_CUDA_TRY(cudaMemcpyAsync(hp.data(), gathered, sizeof(DevPlan) * count, cudaMemcpyDeviceToHost, s));
     FRX_CUDA_TRY(cudaStreamSynchronize(s));
@@ -567,12 +643,35 @@ int refine_batched_impl(const double* const* A, const int64_t* lda, double* cons
     profile_add_gemm_work(ops);
     return worst;
   }();
-  if (g_setup) cudaGraphExecDestroy(g_setup);
-  if (g_iter) cudaGraphExecDestroy(g_iter);
-  if (g_end) cudaGraphExecDestroy(g_end);
-  if (cudaEventRecord(pool->leave, s) != cudaSuccess || cudaStreamWaitEvent(caller, pool->leave, 0) != cudaSuccess)
-    return FRX_E_CUDA;
+  cudaGraphExecDestroy(exec);
   return st;
+}
+
+int refine_batched_impl(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                        double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, void* work,
+                        size_t work_bytes, frx_info* infos, cudaStream_t caller) {
+  BatchLayout L = batch_layout(n, count, o.k_cap);
+  if (!work || !aligned256(work) || work_bytes < L.bytes) return FRX_E_WORKSPACE;
+  FRX_TRY(ensure_attributes());
+  BatchStream* bs = nullptr;
+  FRX_TRY(batch_stream(&bs));
+  cudaStream_t s = bs->s;
+  FRX_CUDA_TRY(cudaEventRecord(bs->enter, caller));
+  FRX_CUDA_TRY(cudaStreamWaitEvent(s, bs->enter, 0));
+  int worst = FRX_OK;
+  for (int c0 = 0; c0 < count; c0 += BATCH_CHUNK) {
+    const int c = count - c0 < BATCH_CHUNK ? count - c0 : BATCH_CHUNK;
+    int st = refine_batched_chunk(A + c0, lda + c0, X + c0, ldx + c0, D + c0, n + c0, c, delta, o, (char*)work, L,
+                                  L.off.data() + c0, infos ? infos + c0 : nullptr, s);
+    if (st < 0) {
+      worst = st;
+      break;
+    }
+    if (worst >= 0 && st > worst) worst = st;
+  }
+  if (cudaEventRecord(bs->leave, s) != cudaSuccess || cudaStreamWaitEvent(caller, bs->leave, 0) != cudaSuccess)
+    return FRX_E_CUDA;
+  return worst;
 }
 
 }  // namespace

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 
 #include "frx_internal.cuh"
+#include "grouped.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
 
@@ -153,6 +154,19 @@ int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s) {
 // kernel (used to cross-check the two implementations bit for bit).
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) {
   if ((!g.dyn && g.d.groups == 0) || g.M == 0 || g.N == 0) return FRX_OK;
+  if (active_recorder()) {
+    // batched refinement: the product becomes one entry of a grouped tensor-core launch
+    std::vector<unsigned char> entry(tc_problem_bytes());
+    FRX_TRY(tc_problem_fill(g, g.flags, entry.data()));
+    LaunchRecord r;
+    r.kind = LK_GEMM;
+    r.args = std::move(entry);
+    r.blocks = 0;
+    r.threads = 0;
+    r.smem = 0;
+    active_recorder()->recs.push_back(std::move(r));
+    return FRX_OK;
+  }
   const char* env = getenv("FRX_GEMM");
   bool simt = env && env[0] == 's';
   GemmTimer timer(g, s);

@@ -173,6 +173,13 @@ struct TcArgs {
   const int* done;
 };
 
+// one problem of a grouped launch: its tensor maps and arguments (device table entry)
+struct TcProblem {
+  CUtensorMap mapL;
+  CUtensorMap mapR;
+  TcArgs a;
+};
+
 // per-launch scalars read once at kernel entry
 struct TcRun {
   int64_t M, N;
@@ -204,22 +211,11 @@ __device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int bm, int
   j0 = (local / rows) * bn;
 }
 
-template <int BN_, bool W32>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-    k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
-                    const __grid_constant__ TcArgs a0) {
-  constexpr int BN = BN_;
-  constexpr int STAGES = BN == 256 ? 4 : 6;
-  constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
-  constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
-  constexpr uint32_t TMEM_COLS = 2 * BN;
-  constexpr uint32_t IDESC = idesc_for(BN);
-  constexpr int NCOL = BN / 2;   // columns per epilogue thread
-  typedef typename std::conditional<W32, int, i64>::type Acc;
-  if (a0.done && *a0.done) return;
+// the product description of a launch's problem, resolved from its arguments
+__device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*& gorder) {
+  if (a0.done && *a0.done) return false;
   const GemmDesc* D = a0.dyn ? a0.dyn : &a0.d;
-  if (!D->active || D->units <= 0) return;
-  TcRun a;
+  if (!D->active || D->units <= 0) return false;
   a.M = a0.M;
   a.N = a0.N;
   a.nkb = a0.nkb;
@@ -235,7 +231,65 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   a.ogs = a0.ogs;
   a.ldo = a0.ldo;
   a.flags = a0.flags;
-  const int* gorder = D->gorder;
+  gorder = D->gorder;
+  return true;
+}
+
+// Unit sources of the kernel body.  A unit is (output tile, anti-diagonal group) of one
+// problem; unit(u, lu) makes `run`, `gorder` and the tensor maps describe the problem that
+// global unit u belongs to and sets lu to its index within that problem.
+struct SingleSrc {
+  TcRun run;
+  const int* gorder;
+  const CUtensorMap* mapL;
+  const CUtensorMap* mapR;
+  int* flags0;
+  __device__ int total() const { return run.units; }
+  __device__ void unit(int u, int& lu) { lu = u; }
+};
+
+constexpr int MAX_GROUPED = 2048;   // problems of one grouped launch
+
+struct GroupedSrc {
+  const TcProblem* probs;
+  const int* prefix;   // shared: units of problems 0..m-1
+  int count;
+  int cur;             // problem `run` currently describes
+  TcRun run;
+  const int* gorder;
+  const CUtensorMap* mapL;
+  const CUtensorMap* mapR;
+  int* flags0;
+  __device__ int total() const { return prefix[count]; }
+  __device__ void unit(int u, int& lu) {
+    int lo = 0, hi = count - 1;   // last m with prefix[m] <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    if (lo != cur) {
+      cur = lo;
+      tc_run_of(probs[lo].a, run, gorder);
+      mapL = &probs[lo].mapL;
+      mapR = &probs[lo].mapR;
+    }
+    lu = u - prefix[lo];
+  }
+};
+
+// BN_ = 128: int64 Horner groups of gs anti-diagonals, 64 columns per epilogue thread.
+// BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
+template <int BN_, bool W32, class Src>
+__device__ __forceinline__ void tc_body(Src& src) {
+  constexpr int BN = BN_;
+  constexpr int STAGES = BN == 256 ? 4 : 6;
+  constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
+  constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t IDESC = idesc_for(BN);
+  constexpr int NCOL = BN / 2;   // columns per epilogue thread
+  typedef typename std::conditional<W32, int, i64>::type Acc;
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
   unsigned char* tiles_smem = base;
@@ -268,15 +322,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&mapL) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&mapR) : "memory");
       int stage = 0;
       uint32_t phase = 0;
       long long issued = 0;
       bool ok = !*abort;
-      const int tiles = a.ntm * a.ntn;
-      for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-        const int grp = gorder[u / tiles], tile = u % tiles;
+      for (int u = blockIdx.x; u < src.total() && ok; u += gridDim.x) {
+        int lu;
+        src.unit(u, lu);
+        const TcRun& a = src.run;
+        const int* gorder = src.gorder;
+        const int tiles = a.ntm * a.ntn;
+        const int grp = gorder[lu / tiles], tile = lu % tiles;
         int i0, j0;
         tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
@@ -290,8 +346,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               }
               unsigned char* st = tiles_smem + stage * STAGE_BYTES;
               mbar_expect_tx(&sm->full[stage], STAGE_BYTES);
-              tma_load_3d(st, &mapL, kb * BK, i0, r - 1, &sm->full[stage]);
-              tma_load_3d(st + STAGE_A_BYTES, &mapR, kb * BK, j0, s - 1, &sm->full[stage]);
+              tma_load_3d(st, src.mapL, kb * BK, i0, r - 1, &sm->full[stage]);
+              tma_load_3d(st + STAGE_A_BYTES, src.mapR, kb * BK, j0, s - 1, &sm->full[stage]);
               ++issued;
               if (++stage == STAGES) {
                 stage = 0;
@@ -305,7 +361,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // every consumer (local MMA and, in a cluster, the peers') has released the stages
         // this CTA's copies filled: no arrival can target this CTA's barriers after it exits
         for (int q = 0; q < STAGES; ++q) {
-          if (!mbar_wait(&sm->empty[stage], phase ^ 1, abort, a.flags)) break;
+          if (!mbar_wait(&sm->empty[stage], phase ^ 1, abort, src.flags0)) break;
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
@@ -336,9 +392,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t acc_phase[2] = {0, 0};
       bool ok = true;
       bool any = false;
-      const int tiles = a.ntm * a.ntn;
-      for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-        const int grp = gorder[u / tiles];
+      for (int u = blockIdx.x; u < src.total() && ok; u += gridDim.x) {
+        int lu;
+        src.unit(u, lu);
+        const TcRun& a = src.run;
+        const int* gorder = src.gorder;
+        const int tiles = a.ntm * a.ntn;
+        const int grp = gorder[lu / tiles];
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           int rlo = pair_lo(t, a.kR), rhi = pair_hi(t, a.kL);
@@ -401,11 +461,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int buf = 0;
     uint32_t acc_phase[2] = {0, 0};
     bool ok = true;
-    const int tiles = a.ntm * a.ntn;
-    for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-      const int grp = gorder[u / tiles], tile = u % tiles;
+    for (int u = blockIdx.x; u < src.total() && ok; u += gridDim.x) {
+      int lu;
+      src.unit(u, lu);
+      const TcRun& a = src.run;
+      const int* gorder = src.gorder;
+      const int tiles = a.ntm * a.ntn;
+      const int grp = gorder[lu / tiles], tile = lu % tiles;
       int i0, j0;
-        tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
+      tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
       const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
       for (int t = t0; t <= t1 && ok; ++t) {
@@ -453,6 +517,54 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+
+template <int BN_, bool W32>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
+                    const __grid_constant__ TcArgs a0) {
+  SingleSrc src;
+  if (!tc_run_of(a0, src.run, src.gorder)) return;
+  src.mapL = &mapL;
+  src.mapR = &mapR;
+  src.flags0 = a0.flags;
+  if (threadIdx.x == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapL) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapR) : "memory");
+  }
+  tc_body<BN_, W32>(src);
+}
+
+// Many problems in one persistent launch (batched refinement): every CTA forms the prefix
+// of the problems' unit counts (0 for finished or inactive products) and walks the global
+// unit sequence.
+template <int BN_, bool W32>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_plane_gemm_tc_grouped(const TcProblem* __restrict__ probs, int count) {
+  __shared__ int prefix[MAX_GROUPED + 1];
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int m = 0; m < count; ++m) {
+      prefix[m] = acc;
+      TcRun r;
+      const int* g;
+      if (tc_run_of(probs[m].a, r, g)) acc += r.units;
+    }
+    prefix[count] = acc;
+  }
+  __syncthreads();
+  if (prefix[count] == 0) return;
+  GroupedSrc src;
+  src.probs = probs;
+  src.prefix = prefix;
+  src.count = count;
+  src.cur = -1;
+  src.gorder = nullptr;
+  src.mapL = src.mapR = nullptr;
+  src.flags0 = probs[0].a.flags;
+  memset(&src.run, 0, sizeof(src.run));
+  tc_body<BN_, W32>(src);
 }
 
 // ---------------------------------------------------------------------------
@@ -522,6 +634,50 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   unsigned grid = (unsigned)(units < sms ? units : sms);
   if (grid == 0) return FRX_OK;
   k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+size_t tc_problem_bytes() { return sizeof(TcProblem); }
+
+// one entry of a grouped launch's table (host memory), for a product with int32 planes
+int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry) {
+  if (!plane_gemm_tc_supported(g) || !g.d.word32) return FRX_E_UNSUPPORTED;
+  TcProblem* e = reinterpret_cast<TcProblem*>(host_entry);
+  memset(e, 0, sizeof(TcProblem));
+  if (!make_map(&e->mapL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
+  if (!make_map(&e->mapR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, 256)) return FRX_E_CUDA;
+  e->a.M = g.M;
+  e->a.N = g.N;
+  e->a.nkb = (int)((g.K + BK - 1) / BK);
+  e->a.out = (void*)g.out;
+  e->a.ogs = g.ogs;
+  e->a.ldo = g.ldo;
+  e->a.flags = flags;
+  e->a.d = g.d;
+  e->a.dyn = g.dyn;
+  e->a.done = g.done;
+  return FRX_OK;
+}
+
+// shared-memory attribute of the grouped kernel (before any stream capture)
+int prepare_plane_gemm_grouped() {
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plane_gemm_tc_grouped<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_bytes(256)));
+  return FRX_OK;
+}
+
+// all problems of `table` (device memory, `count` entries) in one persistent launch
+int launch_plane_gemm_grouped(const void* table, int count, cudaStream_t s) {
+  if (count <= 0) return FRX_OK;
+  if (count > MAX_GROUPED || ((uintptr_t)table & 63)) return FRX_E_UNSUPPORTED;
+  const size_t smem = smem_bytes(256);
+  int dev = 0, sms = 0;
+  FRX_CUDA_TRY(cudaGetDevice(&dev));
+  FRX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  k_plane_gemm_tc_grouped<256, true>
+      <<<(unsigned)sms, NUM_THREADS, smem, s>>>(reinterpret_cast<const TcProblem*>(table), count);
+  count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }

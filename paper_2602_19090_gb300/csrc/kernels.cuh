@@ -62,6 +62,14 @@ int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s);
 int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s);
 int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s);
 bool plane_gemm_tc_supported(const PlaneGemm& g);
+// grouped slice products: a device table of per-problem entries (tensor maps + arguments,
+// 64-byte aligned, tc_problem_bytes() each) run in one persistent launch
+size_t tc_problem_bytes();
+int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry);
+int launch_plane_gemm_grouped(const void* table, int count, cudaStream_t s);
+int prepare_plane_gemm_grouped();
+// a zero (src == nullptr) or copy of 8-byte words recorded as a grouped-launch entry
+int record_bytes(void* dst, const void* src, size_t bytes);
 
 // refine_kernels.cu
 int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR, double* Ch, int64_t ldh,

@@ -6,6 +6,7 @@
 #include "kernels.cuh"
 #include "plan.cuh"
 #include "profile.cuh"
+#include "grouped.cuh"
 #include "plan_launch.cuh"
 
 namespace frx {
@@ -161,7 +162,7 @@ __device__ void raise(DevPlan* p, int st) {
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA, const double* D,
+__device__ __forceinline__ void plan_init_impl(DevPlan* p, const int32_t* eA, const double* D,
                                                   double* lam_prev, PlanOpts o, double omega_prev) {
   extern __shared__ double sbuf[];
   __shared__ int redi[32];
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA,
 }
 
 // beta, alpha, s_X, k_V and the V product (Alg. 1 line 1 with Sec. 3 and Sec. 4.1)
-__global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, PlanOpts o) {
+__device__ __forceinline__ void plan_v_impl(DevPlan* p, const int32_t* f, PlanOpts o) {
   __shared__ int redi[32];
   __shared__ double redd[32];
   __shared__ unsigned long long s2lo[32], s2hi[32];
@@ -310,12 +311,12 @@ __global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, Pla
 }
 
 // after the A planes for this iteration are written
-__global__ void k_plan_mark_sliced(DevPlan* p) {
+__device__ __forceinline__ void plan_mark_sliced_impl(DevPlan* p) {
   if (threadIdx.x == 0 && !p->done && p->kV > p->sliced_kA) p->sliced_kA = p->kV;
 }
 
 // k_W and the W product (Alg. 1 line 4)
-__global__ void __launch_bounds__(PT) k_plan_w(DevPlan* p, const int32_t* h, PlanOpts o) {
+__device__ __forceinline__ void plan_w_impl(DevPlan* p, const int32_t* h, PlanOpts o) {
   __shared__ int redi[32];
   if (p->done) return;
   int hm = EZERO;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(PT) k_plan_w(DevPlan* p, const int32_t* h, Pla
 }
 
 // cluster threshold omega (fixed, or the Ogita-Aishima form from ||W_off||_F and ||diag R||_2)
-__global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, PlanOpts o) {
+__device__ __forceinline__ void plan_omega_impl(DevPlan* p, const double* r, PlanOpts o) {
   __shared__ double redd[32];
   if (p->done) return;
   if (o.cluster_omega >= 0) {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, 
 }
 
 // k_U and the update product (Alg. 1 line 6)
-__global__ void __launch_bounds__(PT) k_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
+__device__ __forceinline__ void plan_u_impl(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
   __shared__ int redi[32];
   if (p->done) return;
   int rm = EZERO, em = EZERO;
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(PT) k_plan_u(DevPlan* p, const int32_t* rho, c
 }
 
 // stopping test (reading R7): est = step^2 max|lam| / (xi_stop gap) <= delta
-__global__ void __launch_bounds__(PT) k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, PlanOpts o) {
+__device__ __forceinline__ void plan_end_impl(DevPlan* p, const double* lam_new, double* lam_prev, PlanOpts o) {
   extern __shared__ double sbuf[];
   __shared__ double redd[32];
   if (p->done) return;
@@ -445,16 +446,52 @@ static size_t sort_smem(int64_t n) {
   return (size_t)m * sizeof(double);
 }
 
-int set_plan_kernel_attributes() {
-  int bytes = (int)sort_smem(FRX_MAX_N);
-  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plan_init, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plan_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  return FRX_OK;
+
+// ---- kernels: single problem (one block) and grouped bodies ----------------------------
+struct PlanArgs {
+  DevPlan* p;
+  const int32_t* e0;     // eA (init), f (v), h (w), rho (u)
+  const int32_t* e1;     // eta (u)
+  const double* d0;      // D (init), r (omega), lam_new (end)
+  double* d1;            // lam_prev (init, end)
+  PlanOpts o;
+  double omega_prev;
+  unsigned gx;
+};
+
+__global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev,
+                                                  PlanOpts o, double omega_prev) {
+  plan_init_impl(p, eA, D, lam_prev, o, omega_prev);
+}
+__global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, PlanOpts o) { plan_v_impl(p, f, o); }
+__global__ void k_plan_mark_sliced(DevPlan* p) { plan_mark_sliced_impl(p); }
+__global__ void __launch_bounds__(PT) k_plan_w(DevPlan* p, const int32_t* h, PlanOpts o) { plan_w_impl(p, h, o); }
+__global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, PlanOpts o) {
+  plan_omega_impl(p, r, o);
+}
+__global__ void __launch_bounds__(PT) k_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
+  plan_u_impl(p, rho, eta, o);
+}
+__global__ void __launch_bounds__(PT) k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, PlanOpts o) {
+  plan_end_impl(p, lam_new, lam_prev, o);
+}
+
+__device__ __forceinline__ void plan_init_body(PlanArgs a, unsigned, unsigned) {
+  plan_init_impl(a.p, a.e0, a.d0, a.d1, a.o, a.omega_prev);
+}
+__device__ __forceinline__ void plan_v_body(PlanArgs a, unsigned, unsigned) { plan_v_impl(a.p, a.e0, a.o); }
+__device__ __forceinline__ void plan_mark_sliced_body(PlanArgs a, unsigned, unsigned) { plan_mark_sliced_impl(a.p); }
+__device__ __forceinline__ void plan_w_body(PlanArgs a, unsigned, unsigned) { plan_w_impl(a.p, a.e0, a.o); }
+__device__ __forceinline__ void plan_omega_body(PlanArgs a, unsigned, unsigned) { plan_omega_impl(a.p, a.d0, a.o); }
+__device__ __forceinline__ void plan_u_body(PlanArgs a, unsigned, unsigned) { plan_u_impl(a.p, a.e0, a.e1, a.o); }
+__device__ __forceinline__ void plan_end_body(PlanArgs a, unsigned, unsigned) {
+  plan_end_impl(a.p, a.d0, a.d1, a.o);
 }
 
 int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev, const PlanOpts& o,
                      double omega_prev, cudaStream_t s) {
   size_t sm = sort_smem(o.n);
+  if (record_launch(LK_PLAN_INIT, PlanArgs{p, eA, nullptr, D, lam_prev, o, omega_prev, 1u}, 1, PT, sm)) return FRX_OK;
   k_plan_init<<<1, PT, sm, s>>>(p, eA, D, lam_prev, o, omega_prev);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -462,6 +499,7 @@ int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam
 }
 
 int launch_plan_v(DevPlan* p, const int32_t* f, const PlanOpts& o, cudaStream_t s) {
+  if (record_launch(LK_PLAN_V, PlanArgs{p, f, nullptr, nullptr, nullptr, o, 0.0, 1u}, 1, PT, 0)) return FRX_OK;
   k_plan_v<<<1, PT, 0, s>>>(p, f, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -469,6 +507,9 @@ int launch_plan_v(DevPlan* p, const int32_t* f, const PlanOpts& o, cudaStream_t 
 }
 
 int launch_plan_mark_sliced(DevPlan* p, cudaStream_t s) {
+  PlanOpts none{};
+  if (record_launch(LK_PLAN_MARK_SLICED, PlanArgs{p, nullptr, nullptr, nullptr, nullptr, none, 0.0, 1u}, 1, 32, 0))
+    return FRX_OK;
   k_plan_mark_sliced<<<1, 32, 0, s>>>(p);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -476,6 +517,7 @@ int launch_plan_mark_sliced(DevPlan* p, cudaStream_t s) {
 }
 
 int launch_plan_w(DevPlan* p, const int32_t* h, const PlanOpts& o, cudaStream_t s) {
+  if (record_launch(LK_PLAN_W, PlanArgs{p, h, nullptr, nullptr, nullptr, o, 0.0, 1u}, 1, PT, 0)) return FRX_OK;
   k_plan_w<<<1, PT, 0, s>>>(p, h, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -483,6 +525,7 @@ int launch_plan_w(DevPlan* p, const int32_t* h, const PlanOpts& o, cudaStream_t 
 }
 
 int launch_plan_omega(DevPlan* p, const double* r, const PlanOpts& o, cudaStream_t s) {
+  if (record_launch(LK_PLAN_OMEGA, PlanArgs{p, nullptr, nullptr, r, nullptr, o, 0.0, 1u}, 1, PT, 0)) return FRX_OK;
   k_plan_omega<<<1, PT, 0, s>>>(p, r, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -490,6 +533,7 @@ int launch_plan_omega(DevPlan* p, const double* r, const PlanOpts& o, cudaStream
 }
 
 int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const PlanOpts& o, cudaStream_t s) {
+  if (record_launch(LK_PLAN_U, PlanArgs{p, rho, eta, nullptr, nullptr, o, 0.0, 1u}, 1, PT, 0)) return FRX_OK;
   k_plan_u<<<1, PT, 0, s>>>(p, rho, eta, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -498,6 +542,7 @@ int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const Plan
 
 int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const PlanOpts& o, cudaStream_t s) {
   size_t sm = sort_smem(o.n);
+  if (record_launch(LK_PLAN_END, PlanArgs{p, nullptr, nullptr, lam_new, lam_prev, o, 0.0, 1u}, 1, PT, sm)) return FRX_OK;
   k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
@@ -528,6 +573,41 @@ int launch_gather_plans(DevPlan* const* plans, int count, DevPlan* out, cudaStre
   k_gather_plans<<<count, 128, 0, s>>>(plans, count, out);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+
+int launch_grouped_plan(int kind, const void* tab, const long long* start, int count, long long blocks, int threads,
+                        size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return FRX_OK;
+  const unsigned grid = (unsigned)blocks;
+  const PlanArgs* t = (const PlanArgs*)tab;
+  switch (kind) {
+    case LK_PLAN_INIT: k_grouped<PlanArgs, plan_init_body, PT, 1><<<grid, PT, smem, s>>>(t, start, count); break;
+    case LK_PLAN_V: k_grouped<PlanArgs, plan_v_body, PT, 1><<<grid, PT, 0, s>>>(t, start, count); break;
+    case LK_PLAN_MARK_SLICED:
+      k_grouped<PlanArgs, plan_mark_sliced_body, 32, 1><<<grid, 32, 0, s>>>(t, start, count);
+      break;
+    case LK_PLAN_W: k_grouped<PlanArgs, plan_w_body, PT, 1><<<grid, PT, 0, s>>>(t, start, count); break;
+    case LK_PLAN_OMEGA: k_grouped<PlanArgs, plan_omega_body, PT, 1><<<grid, PT, 0, s>>>(t, start, count); break;
+    case LK_PLAN_U: k_grouped<PlanArgs, plan_u_body, PT, 1><<<grid, PT, 0, s>>>(t, start, count); break;
+    case LK_PLAN_END: k_grouped<PlanArgs, plan_end_body, PT, 1><<<grid, PT, smem, s>>>(t, start, count); break;
+    default: return FRX_E_UNSUPPORTED;
+  }
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+
+int set_plan_kernel_attributes() {
+  int bytes = (int)sort_smem(FRX_MAX_N);
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plan_init, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plan_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<PlanArgs, plan_init_body, PT, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<PlanArgs, plan_end_body, PT, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return FRX_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "frx_internal.cuh"
+#include "grouped.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
 
@@ -69,6 +70,11 @@ GemmTimer::~GemmTimer() {
     std::lock_guard<std::mutex> lk(mu);
     pending.push_back({a_, b_});
   }
+}
+
+LaunchRecorder*& active_recorder() {
+  static thread_local LaunchRecorder* r = nullptr;
+  return r;
 }
 
 }  // namespace frx

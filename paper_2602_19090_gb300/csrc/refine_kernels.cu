@@ -4,6 +4,7 @@
 // (line 5, with the Ogita-Aishima cluster rule) and the update by pair arithmetic
 // (line 6, Sec. 2.2).
 #include "frx_internal.cuh"
+#include "grouped.cuh"
 #include "intround.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
@@ -361,12 +362,12 @@ __device__ u64 block_max_u64(u64 v, u64* red) {
 // ---- lines 2-4 (inner part): one block per column j --------------------------------
 // smem: n double-doubles (V column).  x^T x is exact in integers (X1 lies on the grid
 // 2^(f_j + beta - 53)); x^T v is accumulated with TwoProduct/TwoSum (Dot2 form).
-__device__ __noinline__ void residual_general(ResidualArgs a) {
+__device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
   extern __shared__ __align__(16) dd vcol[];
   __shared__ dd redd[32];
   __shared__ u64 redu[32];
   __shared__ i128 redi[32];
-  const int64_t j = blockIdx.x;
+  const int64_t j = jcol;
   const int64_t n = a.n;
   const int fj = a.f[j];
   const int gj = fj + a.beta - 53;
@@ -493,12 +494,12 @@ __device__ __noinline__ void residual_general(ResidualArgs a) {
 // bound 2^T on the terms of x^T v; pass 2 accumulates x^T v on the fixed grid 2^(T + log2 n
 // - 126) (every term truncated once: relative error below 2^(2 log2 n - 126) of the largest
 // term); pass 3 rounds Res = V - x lambda once from its exact integer value.
-__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(ResidualArgs a) {
+__device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsigned) {
   if (a.done && *a.done) return;
   a.V = resolve(a.V);
   if (a.beta_dyn) a.beta = *a.beta_dyn;
   if (!(a.V.word32 && a.V.exact128 && a.V.groups <= MP_RESIDUAL)) {
-    residual_general(a);
+    residual_general(a, bx);
     return;
   }
   extern __shared__ __align__(16) dd vcol[];
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
   __shared__ i128 redi[32];
   __shared__ int redt[32];
   __shared__ int redb[32][4];
-  const int64_t j = blockIdx.x;
+  const int64_t j = bx;
   const int64_t n = a.n;
   const int fj = a.f[j];
   const int gj = fj + a.beta - 53;
@@ -695,12 +696,12 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(Re
 }
 
 // ---- ||off-diagonal W||_F^2 (for the automatic cluster threshold) ------------------
-__global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) {
+__device__ __forceinline__ void w_offdiag_body(CorrectionArgs a, unsigned bx, unsigned) {
   if (a.done && *a.done) return;
   a.W = resolve(a.W);
   if (a.W.groups == 0) return;
   __shared__ double red[32];
-  const int64_t j = blockIdx.x;
+  const int64_t j = bx;
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) {
     if (i == j) continue;
@@ -722,7 +723,7 @@ __device__ __noinline__ double gather_d_general(GroupArgs g, int64_t i, int64_t 
   return gather_d(g, i, j, eLi, eRj);
 }
 
-__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_CORRECTION) k_correction(CorrectionArgs a) {
+__device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, unsigned) {
   if (a.done && *a.done) return;
   a.W = resolve(a.W);
   if (a.omega_dyn) a.omega = *a.omega_dyn;
@@ -731,7 +732,7 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_CORRECTION) k_correctio
   __shared__ dd redd[32];
   __shared__ int clist[64];
   __shared__ int ccount;
-  const int64_t j = blockIdx.x;
+  const int64_t j = bx;
   const int64_t n = a.n;
   const double lj = a.lam[j];
   const int hj = a.h[j];
@@ -911,12 +912,12 @@ __device__ __forceinline__ void accumulate_dx2(double xn, double xo, float& d2f,
 // X(:, j) <- RN(X1(:, j) + U(:, j)) (Alg. 1 line 6, one rounding); ||X_new - X_old||_F^2
 // partial per column.  One block per column; exact sums and their rounding run on the
 // integer pipes.
-__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_UPDATE) k_update(UpdateArgs a) {
+__device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned) {
   if (a.done && *a.done) return;
   a.U = resolve(a.U);
   if (a.beta_dyn) a.beta = *a.beta_dyn;
   __shared__ double red[32];
-  const int64_t j = blockIdx.x;
+  const int64_t j = bx;
   const int ej = a.eta[j];
   const bool none = a.U.groups == 0 || ej == EZERO;
   const bool fast = a.U.word32 && a.U.exact128 && a.U.groups <= MP_UPDATE;
@@ -958,6 +959,18 @@ __global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_UPDATE) k_update(Update
   if (threadIdx.x == 0) atomicAdd(a.norms + 2, d2);
 }
 
+// ---- single-problem kernels (one block per column) ---------------------------------
+__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_RESIDUAL) k_residual(ResidualArgs a) {
+  residual_body(a, blockIdx.x, 0);
+}
+__global__ void __launch_bounds__(256) k_w_offdiag_norm2(CorrectionArgs a) { w_offdiag_body(a, blockIdx.x, 0); }
+__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_CORRECTION) k_correction(CorrectionArgs a) {
+  correction_body(a, blockIdx.x, 0);
+}
+__global__ void __launch_bounds__(ELEM_THREADS, FRX_MINB_UPDATE) k_update(UpdateArgs a) {
+  update_body(a, blockIdx.x, 0);
+}
+
 // ---------------------------------------------------------------------------
 GroupArgs group_args(const PlaneGemm& g) {
   GroupArgs ga;
@@ -989,33 +1002,78 @@ int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR
 int set_refine_kernel_attributes() {
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(sizeof(dd) * (size_t)FRX_MAX_N)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<ResidualArgs, residual_body, ELEM_THREADS, FRX_MINB_RESIDUAL>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(dd) * (size_t)FRX_MAX_N)));
   return FRX_OK;
 }
 
-int launch_residual(const ResidualArgs& a, cudaStream_t s) {
+int launch_residual(const ResidualArgs& a0, cudaStream_t s) {
+  ResidualArgs a = a0;
+  a.gx = (unsigned)a.n;
   size_t smem = sizeof(dd) * (size_t)a.n;
+  if (record_launch(LK_RESIDUAL, a, a.n, elem_threads(a.n), smem)) return FRX_OK;
   k_residual<<<(unsigned)a.n, elem_threads(a.n), smem, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
-int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s) {
+int launch_w_offdiag_norm2(const CorrectionArgs& a0, cudaStream_t s) {
+  CorrectionArgs a = a0;
+  a.gx = (unsigned)a.n;
+  if (record_launch(LK_W_OFFDIAG, a, a.n, 256, 0)) return FRX_OK;
   k_w_offdiag_norm2<<<(unsigned)a.n, 256, 0, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
-int launch_correction(const CorrectionArgs& a, cudaStream_t s) {
+int launch_correction(const CorrectionArgs& a0, cudaStream_t s) {
+  CorrectionArgs a = a0;
+  a.gx = (unsigned)a.n;
+  if (record_launch(LK_CORRECTION, a, a.n, elem_threads(a.n), 0)) return FRX_OK;
   k_correction<<<(unsigned)a.n, elem_threads(a.n), 0, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
 
-int launch_update(const UpdateArgs& a, cudaStream_t s) {
+int launch_update(const UpdateArgs& a0, cudaStream_t s) {
+  UpdateArgs a = a0;
+  a.gx = (unsigned)a.n;
+  if (record_launch(LK_UPDATE, a, a.n, elem_threads(a.n), 0)) return FRX_OK;
   k_update<<<(unsigned)a.n, elem_threads(a.n), 0, s>>>(a);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
+
+
+int launch_grouped_refine(int kind, const void* tab, const long long* start, int count, long long blocks,
+                          int threads, size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return FRX_OK;
+  const unsigned grid = (unsigned)blocks;
+  threads = threads < 32 ? 32 : (threads > ELEM_THREADS ? ELEM_THREADS : threads);
+  switch (kind) {
+    case LK_RESIDUAL:
+      k_grouped<ResidualArgs, residual_body, ELEM_THREADS, FRX_MINB_RESIDUAL>
+          <<<grid, threads, smem, s>>>((const ResidualArgs*)tab, start, count);
+      break;
+    case LK_W_OFFDIAG:
+      k_grouped<CorrectionArgs, w_offdiag_body, 256, 1><<<grid, 256, 0, s>>>((const CorrectionArgs*)tab, start, count);
+      break;
+    case LK_CORRECTION:
+      k_grouped<CorrectionArgs, correction_body, ELEM_THREADS, FRX_MINB_CORRECTION>
+          <<<grid, threads, 0, s>>>((const CorrectionArgs*)tab, start, count);
+      break;
+    case LK_UPDATE:
+      k_grouped<UpdateArgs, update_body, ELEM_THREADS, FRX_MINB_UPDATE>
+          <<<grid, threads, 0, s>>>((const UpdateArgs*)tab, start, count);
+      break;
+    default:
+      return FRX_E_UNSUPPORTED;
+  }
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;

@@ -31,6 +31,7 @@ struct ResidualArgs {
   const int* done;
   double* Vh;            // optional debug copies (ld = n)
   double* Vl;
+  unsigned gx;           // blocks of the single launch (one per column)
 };
 
 struct CorrectionArgs {
@@ -52,6 +53,7 @@ struct CorrectionArgs {
   int* ccount;           // out: cluster pairs found
   int* flags;
   double* Wout;          // optional debug copy (ld = n)
+  unsigned gx;
 };
 
 struct UpdateArgs {
@@ -68,6 +70,7 @@ struct UpdateArgs {
   double* X;             // in: X_old, out: X_new
   int64_t ldx;
   double* norms;
+  unsigned gx;
 };
 
 GroupArgs group_args(const PlaneGemm& g);
