@@ -72,6 +72,14 @@ def colmajor(t: torch.Tensor):
     return c, max(1, c.shape[0]), True
 
 
+def symmetric_colmajor(A: torch.Tensor):
+    """(tensor, ld, copied) for a symmetric matrix: a contiguous row-major square matrix is
+    passed as it is, since A = A^T makes its row-major layout the column-major one."""
+    if A.dim() == 2 and A.shape[0] == A.shape[1] and A.is_contiguous():
+        return A, max(1, A.shape[1]), False
+    return colmajor(A)
+
+
 def empty_colmajor(m, n, device="cuda"):
     return torch.empty((n, m), dtype=torch.float64, device=device).t()
 
@@ -92,7 +100,7 @@ def refine(A, X, D, delta, opts: Options | None = None, work=None, stream=None):
         _f64_cuda(t, nm)
     n = A.shape[0]
     o = (opts or Options()).to_c()
-    Ac, lda, _ = colmajor(A)
+    Ac, lda, _ = symmetric_colmajor(A)
     Xc, ldx, xcopy = colmajor(X)
     if work is None:
         work = workspace(lib.frx_refine_workspace_bytes(n, C.byref(o)), A.device)
@@ -112,7 +120,7 @@ def refine_batched(As, Xs, Ds, delta, opts: Options | None = None, work=None, st
     lib = _lib.load()
     count = len(As)
     o = (opts or Options()).to_c()
-    cols = [colmajor(A) for A in As]
+    cols = [symmetric_colmajor(A) for A in As]
     xcols = [colmajor(X) for X in Xs]
     for t in list(As) + list(Xs) + list(Ds):
         _f64_cuda(t, "batched operand")
@@ -147,7 +155,7 @@ def refine_step(A, X, D, delta, opts: Options | None = None, omega_prev: float =
     lib = _lib.load()
     n = A.shape[0]
     o = (opts or Options()).to_c()
-    Ac, lda, _ = colmajor(A)
+    Ac, lda, _ = symmetric_colmajor(A)
     Xc, ldx, xcopy = colmajor(X)
     if work is None:
         work = workspace(lib.frx_refine_workspace_bytes(n, C.byref(o)), A.device)
