@@ -80,6 +80,9 @@ typedef struct {
                             x_planes digit planes (rounded to the last plane's grid, beta =
                             54 - 7 x_planes) with no truncation rule: the "previous study"
                             form of Sec. 4 (both operands sliced; 8 planes = full FP64 width) */
+  int sparse_rule;       /* 0: the dense Sec. 4.1 beta rule.  1: the sparse-matrix rule of Sec. 4
+                            (xi = min(k, sqrt n)^2, alpha = 53 - beta + ceil(log2 k)) with k the
+                            largest number of nonzeros in a row of A, counted on the device   */
 } frx_opts;
 
 /* Per-call report of frx_refine (host struct). */

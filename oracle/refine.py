@@ -59,6 +59,8 @@ class Options:
     cluster: object = 0.0        # threshold omega (float) or "auto"
     x_planes: int = 0            # > 0: X kept at x_planes digit planes, no truncation rule
                                  # (the "previous study" of Sec. 4: both operands sliced)
+    sparse_rule: bool = False    # the sparse-matrix rule of Sec. 4: beta with min(k, sqrt n)
+                                 # in place of sqrt n, alpha with ceil(log2 k); k = max row nnz
 
 
 def ceil_log2_sqrt(n: int) -> int:
@@ -136,8 +138,16 @@ def plan(A, X, lam_prev, delta, opts: Options, omega_prev=0.0):
     S2 = sum_pow4(f)
     # previous-study form: X represented by x_planes digit planes, i.e. rounded to the grid
     # of plane x_planes, which is the tau grid of beta = 54 - 7 x_planes
-    beta = 54 - 7 * opts.x_planes if opts.x_planes > 0 else beta_rule(n, delta, g, Lam, S2, opts)
-    alpha = alpha_rule(n, beta, opts)
+    kmax = max(int(np.max(np.count_nonzero(A, axis=1))), 1)
+    if opts.x_planes > 0:
+        beta = 54 - 7 * opts.x_planes
+    elif opts.sparse_rule:
+        # Sec. 4 (sparse matrices): gamma min(k, sqrt n) sqrt(1 / S2) / (0.75 u) with
+        # gamma = sqrt(delta gap / max|lam|) is the Sec. 4.1 form with xi = min(k, sqrt n)^2
+        beta = beta_rule(n, delta, g, Lam, S2, dataclasses.replace(opts, xi=float(min(kmax * kmax, n))))
+    else:
+        beta = beta_rule(n, delta, g, Lam, S2, opts)
+    alpha = 53 - beta + ceil_log2_int(kmax) if opts.sparse_rule else alpha_rule(n, beta, opts)
     sX = -(-(54 - beta) // 7)
     eA = oz.row_exponents(A)
     eAmax = int(np.max(eA))

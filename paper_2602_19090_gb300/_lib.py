@@ -14,7 +14,7 @@ class Opts(C.Structure):
     _fields_ = [("slices_A", C.c_int), ("xi", C.c_double), ("beta_ceil", C.c_int),
                 ("theory_alpha", C.c_int), ("beta_override", C.c_int), ("k_cap", C.c_int),
                 ("max_iter", C.c_int), ("xi_stop", C.c_double), ("cluster_omega", C.c_double),
-                ("x_planes", C.c_int)]
+                ("x_planes", C.c_int), ("sparse_rule", C.c_int)]
 
 
 class Info(C.Structure):

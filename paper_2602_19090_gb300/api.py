@@ -37,11 +37,12 @@ class Options:
     xi_stop: float = 0.0
     cluster_omega: float = 0.0   # < 0: automatic Ogita-Aishima threshold
     x_planes: int = 0            # > 0: X kept at x_planes digit planes (previous-study form)
+    sparse_rule: bool = False    # the sparse-matrix beta rule (k = max nonzeros in a row of A)
 
     def to_c(self) -> _lib.Opts:
         return _lib.Opts(self.slices_A, self.xi, int(self.beta_ceil), int(self.theory_alpha),
                          self.beta_override, self.k_cap, self.max_iter, self.xi_stop,
-                         self.cluster_omega, self.x_planes)
+                         self.cluster_omega, self.x_planes, int(self.sparse_rule))
 
 
 def _ptr(t):

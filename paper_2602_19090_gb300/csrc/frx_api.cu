@@ -164,6 +164,7 @@ int validate_opts(const frx_opts& o) {
   if (o.k_cap < 1 || o.k_cap > MAX_PLANES || o.max_iter < 1 || o.slices_A < 0 || o.slices_A > o.k_cap)
     return FRX_E_ARG;
   if (o.x_planes < 0 || o.x_planes > 8) return FRX_E_ARG;
+  if (o.sparse_rule != 0 && o.sparse_rule != 1) return FRX_E_ARG;
   return FRX_OK;
 }
 
@@ -179,6 +180,7 @@ PlanOpts plan_opts(const frx_opts& o, double delta, int64_t n, int max_iter) {
   p.xi_stop = o.xi_stop;
   p.cluster_omega = o.cluster_omega;
   p.x_planes = o.x_planes;
+  p.sparse_rule = o.sparse_rule;
   p.delta = delta;
   p.n = n;
   return p;
@@ -349,7 +351,7 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
       FRX_TRY(ensure_attributes());
       FRX_CUDA_TRY(cudaMemsetAsync(ws.plan, 0, sizeof(DevPlan), s));
       FRX_CUDA_TRY(cudaMemsetAsync(ws.rowmax, 0, sizeof(u64) * n, s));
-      FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s));
+      FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s, nullptr, &ws.plan->rownnz));
       FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));
       for (int it = 1; it <= max_iter; ++it) {
         FRX_TRY(enqueue_iteration(A, lda, X, ldx, n, o, po, ws, dbg, s));
@@ -536,7 +538,8 @@ int record_phases(const double* const* A, const int64_t* lda, double* const* X, 
       R.recs.clear();
       FRX_TRY(record_bytes(ws[b].plan, nullptr, sizeof(DevPlan)));
       FRX_TRY(record_bytes(ws[b].rowmax, nullptr, sizeof(u64) * (size_t)n[b]));
-      FRX_TRY(launch_col_exponents(A[b], lda[b], n[b], n[b], ws[b].eA, &ws[b].plan->flags, none));
+      FRX_TRY(launch_col_exponents(A[b], lda[b], n[b], n[b], ws[b].eA, &ws[b].plan->flags, none, nullptr,
+                                    &ws[b].plan->rownnz));
       FRX_TRY(launch_plan_init(ws[b].plan, ws[b].eA, D[b], ws[b].lam_prev, po[b], 0.0, none));
       rec[0][b] = std::move(R.recs);
       R.recs.clear();
@@ -693,6 +696,7 @@ void frx_default_opts(frx_opts* o) {
   o->xi_stop = 0.0;
   o->cluster_omega = 0.0;
   o->x_planes = 0;
+  o->sparse_rule = 0;
 }
 
 const char* frx_status_string(int st) {

@@ -17,8 +17,9 @@ struct SliceDyn {
 };
 
 // scan_slice.cu
+// nnz_max (optional): atomic max of the columns' nonzero counts
 int launch_col_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, int* flags,
-                         cudaStream_t s, const int* done = nullptr);
+                         cudaStream_t s, const int* done = nullptr, int* nnz_max = nullptr);
 int launch_row_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, u64* scratch,
                          int* flags, cudaStream_t s, const int* done = nullptr);
 int launch_slice_cols(const double* M, int64_t ld, int64_t K, int64_t N, const int32_t* e, int nplanes,

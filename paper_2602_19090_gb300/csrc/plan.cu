@@ -280,7 +280,9 @@ __device__ __forceinline__ void plan_v_impl(DevPlan* p, const int32_t* f, PlanOp
   } else if (g <= 0.0 || Lam <= 0.0 || S2 <= 0.0) {
     beta = 3;
   } else {
-    double xi = o.xi > 0 ? o.xi : (double)n;
+    // Sec. 4.1 uses xi = n; the sparse-matrix rule of Sec. 4 has min(k, sqrt n)^2
+    const double kk = (double)(p->rownnz > 0 ? p->rownnz : 1);
+    double xi = o.sparse_rule ? (kk * kk < (double)n ? kk * kk : (double)n) : (o.xi > 0 ? o.xi : (double)n);
     double q = __ddiv_rn(__dsqrt_rn(__ddiv_rn(__dmul_rn(__dmul_rn(xi, o.delta), g), __dmul_rn(Lam, S2))),
                          0.75 * U53);
     int b = o.beta_ceil ? dceil_log2(q) : dfloor_log2(q);
@@ -288,7 +290,8 @@ __device__ __forceinline__ void plan_v_impl(DevPlan* p, const int32_t* f, PlanOp
   }
   p->iter += 1;
   p->beta = beta;
-  p->alpha = o.theory_alpha ? 53 - beta + dceil_log2_int(n) : 53 - beta + dceil_log2_sqrt(n);
+  p->alpha = o.sparse_rule ? 53 - beta + dceil_log2_int(p->rownnz > 0 ? p->rownnz : 1)
+            : (o.theory_alpha ? 53 - beta + dceil_log2_int(n) : 53 - beta + dceil_log2_sqrt(n));
   p->sX = (54 - beta + 6) / 7;
   p->fmax = fmx;
   p->S2 = S2;

@@ -97,6 +97,7 @@ struct PlanOpts {
   int beta_ceil, theory_alpha, beta_override, k_cap, max_iter;
   double xi_stop, cluster_omega;
   int x_planes;
+  int sparse_rule;
   double delta;
   int64_t n;
 };
@@ -107,6 +108,7 @@ struct DevPlan {
   int beta, alpha, sX, kV, kW, kU, sliced_kA, eAmax, fmax;
   int clustered, have_prev_step;
   int noncontract;  // consecutive iterations whose step exceeded half the previous one
+  int rownnz;       // largest number of nonzeros in a row of A (atomic max of the A scan)
   long long products;
   double g, Lam, S2, omega, step, prev_step, est, normE;
   double norms[4];  // [0] ||E~||_F^2, [1] ||W_off||_F^2, [2] ||dX||_F^2

@@ -16,6 +16,7 @@ struct ColExpArgs {
   int32_t* e;
   int* flags;
   const int* done;
+  int* nnz_max;   // optional: atomic max of the columns' nonzero counts
   unsigned gx;
 };
 
@@ -74,20 +75,27 @@ __device__ __forceinline__ void col_exponents_body(ColExpArgs a, unsigned bx, un
   const double* col = a.M + j * a.ld;
   u64 mx = 0;
   bool bad = false;
+  int nz = 0;
   for (int64_t i = threadIdx.x; i < a.rows; i += blockDim.x) {
     u64 ab = double_to_bits(col[i]) & 0x7fffffffffffffffull;
     bad |= nonfinite_absbits(ab);
+    nz += ab != 0;
     mx = ab > mx ? ab : mx;
   }
+
   for (int o = 16; o > 0; o >>= 1) {
     u64 other = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = other > mx ? other : mx;
   }
   __shared__ u64 red[8];
-  __shared__ int sbad;
-  if (threadIdx.x == 0) sbad = 0;
+  __shared__ int sbad, snz;
+  if (threadIdx.x == 0) sbad = snz = 0;
   __syncthreads();
   if (bad) atomicOr(&sbad, 1);
+  if (a.nnz_max) {
+    for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    if ((threadIdx.x & 31) == 0 && nz) atomicAdd(&snz, nz);
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -95,6 +103,7 @@ __device__ __forceinline__ void col_exponents_body(ColExpArgs a, unsigned bx, un
     mx = red[0] > mx ? red[0] : mx;
     a.e[j] = sbad ? EZERO : (mx == 0 ? EZERO : ceil_log2_absbits(mx));
     if (sbad) atomicOr(a.flags, FLAG_NONFINITE);
+    if (a.nnz_max && snz) atomicMax(a.nnz_max, snz);
   }
 }
 
@@ -281,9 +290,9 @@ __global__ void __launch_bounds__(256) k_truncate_slice_x(TruncArgs a) {
 // host launchers (each records its launch instead while a recorder is active)
 // ---------------------------------------------------------------------------
 int launch_col_exponents(const double* M, int64_t ld, int64_t rows, int64_t cols, int32_t* e, int* flags,
-                         cudaStream_t s, const int* done) {
+                         cudaStream_t s, const int* done, int* nnz_max) {
   if (cols == 0) return FRX_OK;
-  ColExpArgs a{M, ld, rows, cols, e, flags, done, (unsigned)cols};
+  ColExpArgs a{M, ld, rows, cols, e, flags, done, nnz_max, (unsigned)cols};
   if (record_launch(LK_COL_EXPONENTS, a, cols, 256, 0)) return FRX_OK;
   k_col_exponents<<<(unsigned)cols, 256, 0, s>>>(a);
   count_launches(1);

@@ -210,3 +210,19 @@ def hadamard_workload(n: int, cond: float, seed: int, rel: float = 1e-8, variant
     info = dict(scale_exp=-S, min_gap=float(gaps.min()), max_abs=float(np.abs(lam).max()),
                 cond=float(np.abs(lam).max() / np.abs(lam).min()))
     return A, X0, D0, lam, Qh, Ql, info
+
+
+def banded_workload(n: int, bw: int, seed: int, rel: float = 1e-8):
+    """Sparse stand-in (the paper's ELSES matrices are not available): a symmetric band matrix
+    with half-bandwidth bw (k = 2 bw + 1 nonzeros in an interior row), entries N(0, 1) inside
+    the band, exactly symmetric.  The start is its FP64 eigenvector basis (numpy eigh) perturbed
+    by `rel` and re-orthonormalised, as in ``initial_guess``.  Returns (A, X0, D0, lam)."""
+    g = rng(seed)
+    A = np.zeros((n, n))
+    for d in range(bw + 1):
+        v = g.standard_normal(n - d)
+        A[np.arange(n - d), np.arange(d, n)] = v
+        A[np.arange(d, n), np.arange(n - d)] = v
+    lam, Q = np.linalg.eigh(A)
+    X0, D0 = initial_guess(Q, lam, seed, rel)
+    return np.ascontiguousarray(A), X0, D0, lam

@@ -40,7 +40,7 @@ def test_host_only_calls(lib):
     assert lib.frx_status_string(-3) == b"delta must exceed 2^-53"
     o = _lib.Opts()
     lib.frx_default_opts(ctypes.byref(o))
-    assert (o.slices_A, o.k_cap, o.max_iter, o.beta_override, o.x_planes) == (0, 16, 10, -1, 0)
+    assert (o.slices_A, o.k_cap, o.max_iter, o.beta_override, o.x_planes, o.sparse_rule) == (0, 16, 10, -1, 0, 0)
     assert lib.frx_refine_workspace_bytes(0, None) == 0
     assert lib.frx_refine_workspace_bytes(64, None) > 64 * 64 * 8 * 3
     assert lib.frx_refine_workspace_bytes(12289, None) == 0
@@ -63,6 +63,10 @@ def test_argument_errors_before_any_device_work(lib):
     o = _lib.Opts()
     lib.frx_default_opts(ctypes.byref(o))
     o.x_planes = 9                  # more planes than FP64 width needs
+    st = lib.frx_refine(p, 4, p, 4, p, 4, 1e-10, ctypes.byref(o), p, 1 << 20, None, None)
+    assert st == -1
+    lib.frx_default_opts(ctypes.byref(o))
+    o.sparse_rule = 2
     st = lib.frx_refine(p, 4, p, 4, p, 4, 1e-10, ctypes.byref(o), p, 1 << 20, None, None)
     assert st == -1
     st = lib.frx_ozaki_gemm(p, 4, p, 4, p, 4, None, 4, 4, 4, 0, 0, p, 1 << 20, None)

@@ -182,6 +182,13 @@ def test_refine_step_parity_previous_study_form(api, xp):
     _step_compare(api, A, X0, D0, 1e-12, orf.Options(x_planes=xp), api.Options(x_planes=xp))
 
 
+def test_refine_step_parity_sparse_rule(api):
+    # Sec. 4's sparse-matrix beta rule; k (max nonzeros in a row of A) is counted on the device
+    A, X0, D0, lam = synth.banded_workload(300, 2, 12)
+    info, oi = _step_compare(api, A, X0, D0, 1e-12, orf.Options(sparse_rule=True), api.Options(sparse_rule=True))
+    assert info["alpha"] == oi["alpha"]
+
+
 def test_refine_converges_like_the_oracle(api):
     g = G()
     A, X0, D0 = synth.workload0()

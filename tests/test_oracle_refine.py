@@ -233,3 +233,25 @@ def test_previous_study_form_keeps_x_at_its_planes():
     X13 = X0 - oz.slice_cols(X0, 3, p3["f"])[2]
     T, _ = oz.tau_truncate_cols(X0, 33, p3["f"])
     assert p3["sX"] == 3 and np.array_equal(X13, T)
+
+
+def test_sparse_rule_is_the_paper_formula():
+    # Sec. 4 (sparse matrices): beta = floor(log2(gamma min(k, sqrt n) / (0.75 u) sqrt(1 / S2))),
+    # gamma = sqrt(delta gap / max|lam|), alpha = 53 - beta + ceil(log2 k), k = max row nonzeros
+    n, bw, delta = 300, 2, 1e-12
+    A, X0, D0, lam = synth.banded_workload(n, bw, 11)
+    assert np.max(np.count_nonzero(A, axis=1)) == 2 * bw + 1
+    p = rf.plan(A, X0, D0, delta, rf.Options(sparse_rule=True))
+    k = 2 * bw + 1
+    s = np.sort(D0)
+    gap = np.min(np.diff(s))
+    Lam = np.max(np.abs(D0))
+    f = oz.col_exponents(X0)
+    S2 = math.fsum(math.ldexp(1.0, 2 * int(e)) for e in f)
+    gamma = math.sqrt(delta * gap / Lam)
+    q = gamma * min(k, math.sqrt(n)) / (0.75 * U) * math.sqrt(1.0 / S2)
+    beta = min(max(math.floor(math.log2(q)), 3), 47)
+    assert p["beta"] == beta
+    assert p["alpha"] == 53 - beta + 3
+    # denser than the dense rule: min(k, sqrt n)^2 = 25 < n keeps more bits of X (smaller beta)
+    assert p["beta"] < rf.plan(A, X0, D0, delta, rf.Options())["beta"]
