@@ -5,16 +5,18 @@
 // tcgen05.mma (.kind::f16, bf16 x bf16 -> f32 in TMEM).  Every product is an integer
 // of magnitude <= 2^12, so an FP32 accumulator holds exact integers as long as the
 // accumulated count stays <= 2^11 terms per lane (|sum| <= 2^23); the accumulator is
-// therefore drained into int64 every CHUNK_KB k-blocks (and at the end of every
-// anti-diagonal t) and the int64 sums are combined in Horner form per group:
-//   R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
+// therefore drained into integer registers every CHUNK_KB k-blocks (and at the end of
+// every anti-diagonal t).  With BN = 256 each anti-diagonal's exact sum S_t is stored as
+// one int32 plane (while pairs * K * 4096 < 2^31); otherwise BN = 128 and the int64 sums
+// are combined in Horner form per group: R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
 //
 // Persistent: one CTA per SM walks the units (output tile of 128 x BN, group of
-// anti-diagonals) in a static round-robin, groups ordered by decreasing work.  BN = 256
-// with int32 per-t planes, else 128 with int64 groups.  Warp roles:
+// anti-diagonals), groups ordered by decreasing work and tiles in bands of TILE_BAND tile
+// rows.  A grouped variant walks the units of many problems (the batched refinement).
+// Warp roles:
 //   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
 //   warp 1       TMEM allocator and single-thread MMA issuer
-//   warps 2..9   epilogue: tcgen05.ld of the FP32 accumulator, exact int64 sums
+//   warps 2..9   epilogue: tcgen05.ld of the FP32 accumulator, exact integer sums
 // Pipeline: 4-6 smem stages (A 16 KB + B BN * 128 bytes), two TMEM accumulators of BN
 // columns each.  Every mbarrier wait is bounded by the global timer; on expiry the
 // CTA raises FLAG_TIMEOUT, drains what it issued and returns.

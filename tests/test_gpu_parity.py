@@ -301,3 +301,26 @@ def test_ozaki_gemm_more_than_65535_columns(api):
     mag = np.abs(A) @ np.abs(B)
     assert np.all(np.abs((Ch - o["hi"]) + (Cl - o["lo"])) <= mag * 2.0 ** -100)
     assert np.all(np.abs(Ch - C_ref) <= np.spacing(np.abs(C_ref)))
+
+
+def test_refine_batched_more_problems_than_one_grouped_launch(api):
+    # 2100 small problems: more than one chunk of grouped launches (2048); a sample of them
+    # must equal single-matrix calls bit for bit
+    g = G()
+    rng = synth.rng(synth.seed_for(3, 77))
+    sizes = rng.integers(8, 17, size=2100)
+    probs = []
+    for b, nn in enumerate(sizes):
+        A, Q, lam = synth.symmetric_matrix(int(nn), 1e3, synth.seed_for(3, 5000 + b))
+        X0, D0 = synth.initial_guess(Q, lam, synth.seed_for(3, 5000 + b))
+        probs.append((A, X0, D0))
+    As = [g.to_dev(p[0]) for p in probs]
+    Xb = [g.to_dev(p[1]) for p in probs]
+    Db = [g.to_dev(p[2]) for p in probs]
+    infos = api.refine_batched(As, Xb, Db, 1e-12)
+    assert all(i["status"] >= 0 for i in infos)
+    for b in (0, 1, 2047, 2048, 2099):
+        Xs, Ds = g.to_dev(probs[b][1]), g.to_dev(probs[b][2])
+        ref = api.refine(As[b], Xs, Ds, 1e-12)
+        assert infos[b]["iters"] == ref["iters"] and infos[b]["products"] == ref["products"]
+        assert np.array_equal(Xb[b].cpu().numpy(), Xs.cpu().numpy())
