@@ -1,0 +1,101 @@
+"""Edge cases of the CUDA path: the smallest problems, degenerate matrices, the largest
+sizes the library accepts, and the int64-group form of the slice products."""
+import numpy as np
+import pytest
+
+from oracle import ozaki as oz
+from oracle import refine as orf
+from paper_2602_19090_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2602_19090_gb300 import api as a
+    return a
+
+
+def G():
+    from tests import gpu_util
+    return gpu_util
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_refine_smallest_problems_match_the_oracle(api, n):
+    g = G()
+    A, Q, lam = synth.symmetric_matrix(n, 1e2, 40 + n)
+    X0, D0 = synth.initial_guess(Q, lam, 40 + n)
+    Xo, lo, oi = orf.refine(A, X0, D0, 1e-13, orf.Options())
+    Xt, Dt = g.to_dev(X0), g.to_dev(D0)
+    info = api.refine(g.to_dev(A), Xt, Dt, 1e-13)
+    assert info["status"] == 0 and oi["status"] == "converged"
+    assert info["iters"] == oi["iters"]
+    assert np.max(np.abs(Xt.cpu().numpy() - Xo)) <= 4 * U * np.max(np.abs(Xo))
+
+
+def test_diagonal_matrix_identity_start_is_a_fixed_point(api):
+    # A = diag(d) with distinct d: X = I, lambda = d are exact; one step must return them
+    g = G()
+    n = 70
+    d = np.arange(1, n + 1, dtype=np.float64)[::-1] * 0.75
+    A = np.diag(d)
+    info, mats = api.refine_step(g.to_dev(A), g.to_dev(np.eye(n)), g.to_dev(d.copy()), 1e-13)
+    assert np.array_equal(mats["X1"].cpu().numpy(), np.eye(n))
+    Xt = g.to_dev(np.eye(n))
+    Dt = g.to_dev(d.copy())
+    info = api.refine(g.to_dev(A), Xt, Dt, 1e-13)
+    assert info["status"] == 0
+    assert np.array_equal(Xt.cpu().numpy(), np.eye(n))
+    assert np.array_equal(Dt.cpu().numpy(), d)
+
+
+def test_zero_matrix_is_handled(api):
+    # all eigenvalues equal (zero): every pair is a cluster pair (up to 64 per column are kept
+    # on the device), no gap exists, so no estimate can certify convergence: the iteration runs
+    # to its limit and leaves the exact eigenvectors unchanged
+    g = G()
+    n = 16
+    Xt = g.to_dev(np.eye(n))
+    Dt = g.to_dev(np.zeros(n))
+    info = api.refine(g.to_dev(np.zeros((n, n))), Xt, Dt, 1e-12, api.Options(max_iter=3))
+    assert info["status"] == 1
+    assert np.array_equal(Xt.cpu().numpy(), np.eye(n))
+
+
+def test_largest_accepted_size(api):
+    # n = 12288 (the library's limit): diagonal A with distinct entries and a perturbed
+    # identity start converge to the identity (the exact eigenvectors)
+    import torch
+    g = G()
+    n = 12288
+    d = np.linspace(1.0, 2.0, n)
+    dev = g.dev()
+    A = torch.diag(torch.from_numpy(d)).to(dev)
+    rng = synth.rng(synth.seed_for(2, 12288))
+    X = torch.eye(n, dtype=torch.float64, device=dev) + torch.from_numpy(
+        rng.standard_normal((n, n)) * (1e-9 / np.sqrt(n))).to(dev)
+    D = torch.from_numpy(d * (1.0 + 1e-9 * rng.standard_normal(n))).to(dev)
+    info = api.refine(A, X, D, 1e-12)
+    assert info["status"] == 0
+    err = (X.abs() - torch.eye(n, dtype=torch.float64, device=dev)).abs().max().item()
+    assert err <= 1e-12
+    dd = torch.from_numpy(d).to(dev)
+    assert ((D - dd).abs() <= 2 * U * dd.abs()).all()
+
+
+def test_ozaki_gemm_longest_inner_dimension_int64_groups(api):
+    # k = 65536 (the limit) with 8 planes, all pairs: up to 8 pairs per anti-diagonal make
+    # 8 * 65536 * 4096 = 2^31, beyond int32, so the int64 Horner groups are used
+    g = G()
+    m, K, n, k = 136, 65536, 130, 8
+    A = synth.gemm_operand(m, K, 1.0, 330)
+    B = synth.gemm_operand(K, n, 1.0, 331)
+    Ch, Cl = api.ozaki_gemm(g.to_dev(A), g.to_dev(B), k, "full", return_lo=True)
+    C_ref, o = oz.ozaki_gemm(A, B, k, "full")
+    Ch, Cl = Ch.cpu().numpy(), Cl.cpu().numpy()
+    mag = np.abs(A) @ np.abs(B)
+    assert np.all(np.abs((Ch - o["hi"]) + (Cl - o["lo"])) <= mag * 2.0 ** -100)
+    assert np.all(np.abs(Ch - C_ref) <= np.spacing(np.abs(C_ref)))
