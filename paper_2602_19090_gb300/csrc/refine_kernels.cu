@@ -295,7 +295,9 @@ __global__ void __launch_bounds__(256) k_groups_to_dd(GroupArgs ga, const int32_
   if (!done && ga.word32 && ga.exact128 && ga.groups <= 16) {
     int32_t pl[16];
     load_planes<16>(ga, i, j, true, pl);
-    done = dd_from_i128(horner<16>(pl, ga.groups), ei + ej + 2 - DIGIT_BITS * ga.tmax, v);
+    const i128 S = horner<16>(pl, ga.groups);
+    const int ex = ei + ej + 2 - DIGIT_BITS * ga.tmax;
+    done = Cl ? dd_from_i128(S, ex, v) : rn_scaled(S, ex, v.h);   // the low word only when asked
   }
   if (!done) v = gather_dd(ga, i, j, ei, ej);
   Ch[i + j * ldh] = v.h;
