@@ -71,6 +71,9 @@ def parse():
                    help="refine: one n=4096 refinement per step; batched: 256 matrices, n in [32, 512]; "
                         "configs: the n=2048 variants and the n=8192 forward-error sweep")
     p.add_argument("--count", type=int, default=256)
+    p.add_argument("--sweep-n", default="1024,4096,8192", help="matrix orders of the ozaki_gemm sweep")
+    p.add_argument("--tile-n", type=int, default=0, choices=[0, 128, 256],
+                   help="output tile width of the slice products (0: the library's autotuner)")
     return p.parse_args()
 
 
@@ -390,6 +393,8 @@ def run_batched(args):
         Dflat.copy_(D0flat)
         return api.refine_batched(As, Xs, Ds, delta, work=work)
 
+    api.set_tile_n(args.tile_n)
+
     for _ in range(args.warmup):
         infos = one()
     api.profile_read(reset=True)
@@ -433,6 +438,8 @@ def run_batched(args):
                                f"start perturbed 1e-8, delta={delta:g}", "count": args.count,
                    "n_min": int(sizes.min()), "n_max": int(sizes.max()), "delta": delta},
         "statuses": stats, "gpu_launches": prof["kernel_launches"],
+        "tile_n": {"used": api.last_tile_n(), "policy": "forced" if args.tile_n else "autotuned",
+                   "tuner": api.tune_stats()},
         "fp64_loop": ({"seconds": fp64_ms / 1e3, "matrices_per_s": args.count * 1e3 / fp64_ms, "statuses": fstats,
                        "speedup_ours": fp64_ms / ms} if fp64_ms else None),
         "clocks": clk,
@@ -672,8 +679,10 @@ def run_gemm_sweep(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
+    api.set_tile_n(args.tile_n)
     out = {"metric": "ozaki_gemm_sweep", "cases": []}
-    for n in (1024, 4096, 8192):
+    sizes = tuple(int(v) for v in args.sweep_n.split(","))
+    for n in sizes:
         for phi in (0.5, 2.0, 4.0):
             # column-major operands, so that the timed calls do no layout copies
             A = api.colmajor(torch.from_numpy(synth.gemm_operand(n, n, phi, synth.seed_for(1, 10 + int(phi * 2)))).to(dev))[0]
@@ -707,6 +716,7 @@ def run_gemm_sweep(args):
                            "tflops_eq": 2.0 * n ** 3 / (best * 1e-3) / 1e12,
                            "gemm_kernel_tflops": pr["gemm_ops"] / (pr["gemm_ms"] * 1e-3) / 1e12 if pr["gemm_ms"] else None,
                            "gemm_share": pr["gemm_ms"] / 3 / best if pr["gemm_ms"] else None,
+                           "tile_n": api.last_tile_n(),
                            "max_err_rel_absAabsB": err, "dgemm_err_rel_absAabsB": dgemm_err}
                     out["cases"].append(rec)
                     print(json.dumps(rec), file=sys.stderr, flush=True)

@@ -250,6 +250,27 @@ def plane_products(Lp, Rp, K, kL, kR, T, stream=None):
     return out, gs
 
 
+def set_tile_n(tile_n: int) -> int:
+    """Force the slice products' output tile width (128 or 256); 0 restores autotuning.
+    Returns the previous setting."""
+    st = _lib.load().frx_set_tile_n(int(tile_n))
+    if st < 0:
+        raise FrxError(st, "frx_set_tile_n")
+    return st
+
+
+def last_tile_n() -> int:
+    """Tile width of the last slice-product launch made by this host thread."""
+    return _lib.load().frx_last_tile_n()
+
+
+def tune_stats(clear: bool = False) -> dict:
+    """Autotuner decisions: taken by timing, by the cost model, and cache hits."""
+    m, d, h = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _lib.load().frx_tune_stats(C.byref(m), C.byref(d), C.byref(h), 1 if clear else 0)
+    return {"measured": m.value, "modelled": d.value, "hits": h.value}
+
+
 def profile_enable(on: bool = True):
     """Time every slice-product GEMM launch with CUDA events on its stream."""
     _lib.load().frx_profile_enable(1 if on else 0)

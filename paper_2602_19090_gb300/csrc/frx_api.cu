@@ -42,7 +42,7 @@ struct RefineWs {
   DevPlan* plan;
   double* lam_prev;
   int* flags;      // [0] flags, [1] cluster count
-  double* norms;   // [0] ||E||^2, [1] ||W_off||^2, [2] ||dX||^2
+  double* colsq;   // per-column squared norms [3][n]: E~, off-diagonal W, X_new - X_old
   int32_t *eA, *f, *h, *eta, *rho;
   u64* rowmax;
   double *lam, *r;
@@ -51,6 +51,7 @@ struct RefineWs {
   i64* groups;
   int64_t pitch, ps;
   size_t bytes;
+  int tile_n;      // output tile width of the slice products (set by the autotuner)
 };
 
 RefineWs carve_refine(void* work, int64_t n, int kcap) {
@@ -61,13 +62,13 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   w.plan = c.take<DevPlan>(1);
   w.lam_prev = c.take<double>(n);
   w.flags = c.take<int>(4);
-  w.norms = c.take<double>(4);
   w.eA = c.take<int32_t>(n);
   w.f = c.take<int32_t>(n);
   w.h = c.take<int32_t>(n);
   w.eta = c.take<int32_t>(n);
   w.rho = c.take<int32_t>(n);
   w.rowmax = c.take<u64>(n);
+  w.colsq = c.take<double>(3 * n);
   w.lam = c.take<double>(n);
   w.r = c.take<double>(n);
   w.X1 = c.take<double>(n * n);
@@ -79,6 +80,7 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   w.X1rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
   w.groups = c.take<i64>((size_t)8 * n * n);   // 64 bytes per entry: 8 int64 groups or 16 int32 planes
   w.bytes = c.off + 256;
+  w.tile_n = 256;
   return w;
 }
 
@@ -128,6 +130,7 @@ int check_flags(const int* dflags, cudaStream_t s) {
   if (f & FLAG_NONFINITE) return FRX_E_NONFINITE;
   if (f & FLAG_TIMEOUT) return FRX_E_TIMEOUT;
   if (f & FLAG_RANGE) return FRX_E_RANGE;
+  if (f & FLAG_CONFIG) return FRX_E_UNSUPPORTED;
   return FRX_OK;
 }
 
@@ -195,6 +198,17 @@ PlaneGemm dyn_gemm(const __nv_bfloat16* L, int capL, const __nv_bfloat16* R, int
   g.d.groups = 1;
   g.dyn = dyn;
   g.done = &ws.plan->done;
+  g.flags = &ws.plan->flags;
+  g.tile_n = ws.tile_n;
+  return g;
+}
+
+// the representative product the autotuner times for a refinement of order n: 8 planes of
+// A (fewer when k_cap is smaller) against 7 planes of X^(1), the triangular set r + s <= kL + 1
+PlaneGemm tuning_gemm(const RefineWs& ws, int64_t n, int kcap) {
+  const int kL = kcap < 8 ? kcap : 8, kR = 7;
+  PlaneGemm g = make_gemm(ws.Ap, ws.ps, ws.Xp, ws.ps, ws.pitch, n, n, n, kL, kR, kL + 1, ws.groups);
+  g.out_bytes_per_elem = 64;
   g.flags = &ws.plan->flags;
   return g;
 }
@@ -269,12 +283,12 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   ca.E = ws.E;
   ca.lde = n;
   ca.eta = ws.eta;
-  ca.norms = P->norms;
+  ca.norms = ws.colsq;
   ca.ccount = &P->ccount;
   ca.flags = flags;
   ca.Wout = dbg ? dbg->W : nullptr;
   if (o.cluster_omega < 0) FRX_TRY(launch_w_offdiag_norm2(ca, s));
-  FRX_TRY(launch_plan_omega(P, ws.r, po, s));
+  FRX_TRY(launch_plan_omega(P, ws.r, ws.colsq, po, s));
   FRX_TRY(launch_correction(ca, s));
   // S11: U = X^(1) E~ (rows of X^(1), columns of E~), X <- RN(X^(1) + U)
   FRX_TRY(launch_row_exponents(ws.X1, n, n, n, ws.rho, ws.rowmax, flags, s, done));
@@ -306,10 +320,10 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   ua.ld1 = n;
   ua.X = X;
   ua.ldx = ldx;
-  ua.norms = P->norms;
+  ua.norms = ws.colsq;
   FRX_TRY(launch_update(ua, s));
   // S12: stopping test
-  FRX_TRY(launch_plan_end(P, ws.lam, ws.lam_prev, po, s));
+  FRX_TRY(launch_plan_end(P, ws.lam, ws.lam_prev, ws.colsq, po, s));
   return FRX_OK;
 }
 
@@ -351,6 +365,9 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
       FRX_TRY(ensure_attributes());
       FRX_CUDA_TRY(cudaMemsetAsync(ws.plan, 0, sizeof(DevPlan), s));
       FRX_CUDA_TRY(cudaMemsetAsync(ws.rowmax, 0, sizeof(u64) * n, s));
+      PlaneGemm rep = tuning_gemm(ws, n, o.k_cap);
+      FRX_TRY(plan_plane_gemm(rep));
+      FRX_TRY(tune_tile_refine(rep, s, ws.tile_n));
       FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s, nullptr, &ws.plan->rownnz));
       FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));
       for (int it = 1; it <= max_iter; ++it) {
@@ -430,6 +447,7 @@ struct Stage {
   long long blocks;
   int threads;
   size_t smem;
+  int variant;   // slice products: output tile width
 };
 
 // stage k of a phase groups record k of every problem (same kind and argument size)
@@ -446,11 +464,12 @@ int build_stages(const std::vector<std::vector<LaunchRecord>>& recs, std::vector
     st.blocks = 0;
     st.threads = 0;
     st.smem = 0;
+    st.variant = recs[0][k].variant;
     st.tab_off = (blob.size() + 63) / 64 * 64;
     blob.resize(st.tab_off + sz * (size_t)count);
     for (int b = 0; b < count; ++b) {
       const LaunchRecord& r = recs[b][k];
-      if (r.kind != st.kind || r.args.size() != sz) return FRX_E_UNSUPPORTED;
+      if (r.kind != st.kind || r.args.size() != sz || r.variant != st.variant) return FRX_E_UNSUPPORTED;
       memcpy(blob.data() + st.tab_off + sz * b, r.args.data(), sz);
     }
     st.start_off = (blob.size() + 7) / 8 * 8;
@@ -481,7 +500,7 @@ int launch_stage(const Stage& st, char* tables, int count, cudaStream_t s) {
   const long long* start = reinterpret_cast<const long long*>(tables + st.start_off);
   switch (st.kind) {
     case LK_GEMM:
-      return launch_plane_gemm_grouped(tab, count, s);
+      return launch_plane_gemm_grouped(tab, count, st.variant, s);
     case LK_COL_EXPONENTS:
     case LK_ROW_MAXBITS:
     case LK_MAXBITS_TO_EXPONENTS:
@@ -528,8 +547,9 @@ int batch_stream(BatchStream** out) {
 // record the three phases of every problem: setup, one iteration, finish
 int record_phases(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
                   double* const* D, const int64_t* n, int count, const frx_opts& o, const std::vector<PlanOpts>& po,
-                  const std::vector<RefineWs>& ws, std::vector<std::vector<LaunchRecord>> (&rec)[3]) {
+                  const std::vector<RefineWs>& ws, int tile_n, std::vector<std::vector<LaunchRecord>> (&rec)[3]) {
   LaunchRecorder R;
+  R.tile_n = tile_n;
   LaunchRecorder*& active = active_recorder();
   active = &R;
   cudaStream_t none = nullptr;   // nothing is launched while recording
@@ -566,9 +586,25 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
     hplans[b] = ws[b].plan;
     po[b] = plan_opts(o, delta, n[b], o.max_iter);
   }
+  // tile width of the grouped slice products: cached per batch signature (the sorted orders),
+  // else timed on representative products over the problems' plane buffers
+  int tile_n = 256;
+  {
+    std::vector<PlaneGemm> reps(count);
+    std::vector<long long> key = {3, count, o.k_cap};
+    std::vector<int64_t> sorted(n, n + count);
+    std::sort(sorted.begin(), sorted.end());
+    key.insert(key.end(), sorted.begin(), sorted.end());
+    for (int b = 0; b < count; ++b) {
+      reps[b] = tuning_gemm(ws[b], n[b], o.k_cap);
+      FRX_TRY(plan_plane_gemm(reps[b]));
+    }
+    FRX_TRY(tune_tile_grouped(reps, key, base + L.tables_off, s, tile_n));
+  }
+  for (int b = 0; b < count; ++b) ws[b].tile_n = tile_n;
   std::vector<std::vector<LaunchRecord>> rec[3];
   for (int q = 0; q < 3; ++q) rec[q].resize(count);
-  FRX_TRY(record_phases(A, lda, X, ldx, D, n, count, o, po, ws, rec));
+  FRX_TRY(record_phases(A, lda, X, ldx, D, n, count, o, po, ws, tile_n, rec));
   std::vector<unsigned char> blob;
   std::vector<Stage> stages[3];
   for (int q = 0; q < 3; ++q) FRX_TRY(build_stages(rec[q], blob, stages[q]));

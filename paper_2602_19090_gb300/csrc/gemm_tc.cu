@@ -173,6 +173,7 @@ struct TcArgs {
   GemmDesc d;
   const GemmDesc* dyn;
   const int* done;
+  int bn;        // tile width the right operand's tensor map was encoded for
 };
 
 // one problem of a grouped launch: its tensor maps and arguments (device table entry)
@@ -213,11 +214,18 @@ __device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int bm, int
   j0 = (local / rows) * bn;
 }
 
-// the product description of a launch's problem, resolved from its arguments
+// the product description of a launch's problem, resolved from its arguments; the tiling
+// (128 x BN tiles, units = tiles x groups) belongs to the kernel variant, not to the plan
+template <int BN, bool W32>
 __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*& gorder) {
   if (a0.done && *a0.done) return false;
   const GemmDesc* D = a0.dyn ? a0.dyn : &a0.d;
-  if (!D->active || D->units <= 0) return false;
+  if (!D->active || D->groups <= 0) return false;
+  if (a0.bn != BN || D->word32 != (W32 ? 1 : 0)) {
+    // the tensor map's box or the exact-sum layout does not fit this variant: no product
+    if (a0.flags) atomicOr(a0.flags, FLAG_CONFIG);
+    return false;
+  }
   a.M = a0.M;
   a.N = a0.N;
   a.nkb = a0.nkb;
@@ -226,9 +234,9 @@ __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*
   a.tmax = D->tmax;
   a.gs = D->gs;
   a.groups = D->groups;
-  a.ntm = D->ntm;
-  a.ntn = D->ntn;
-  a.units = D->units;
+  a.ntm = (int)((a0.M + BM - 1) / BM);
+  a.ntn = (int)((a0.N + BN - 1) / BN);
+  a.units = a.ntm * a.ntn * D->groups;
   a.out = a0.out;
   a.ogs = a0.ogs;
   a.ldo = a0.ldo;
@@ -252,6 +260,7 @@ struct SingleSrc {
 
 constexpr int MAX_GROUPED = 2048;   // problems of one grouped launch
 
+template <int BN, bool W32>
 struct GroupedSrc {
   const TcProblem* probs;
   const int* prefix;   // shared: units of problems 0..m-1
@@ -272,7 +281,7 @@ struct GroupedSrc {
     }
     if (lo != cur) {
       cur = lo;
-      tc_run_of(probs[lo].a, run, gorder);
+      tc_run_of<BN, W32>(probs[lo].a, run, gorder);
       mapL = &probs[lo].mapL;
       mapR = &probs[lo].mapR;
     }
@@ -527,7 +536,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
                     const __grid_constant__ TcArgs a0) {
   SingleSrc src;
-  if (!tc_run_of(a0, src.run, src.gorder)) return;
+  if (!tc_run_of<BN_, W32>(a0, src.run, src.gorder)) return;
   src.mapL = &mapL;
   src.mapR = &mapR;
   src.flags0 = a0.flags;
@@ -551,13 +560,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       prefix[m] = acc;
       TcRun r;
       const int* g;
-      if (tc_run_of(probs[m].a, r, g)) acc += r.units;
+      if (tc_run_of<BN_, W32>(probs[m].a, r, g)) acc += r.units;
     }
     prefix[count] = acc;
   }
   __syncthreads();
   if (prefix[count] == 0) return;
-  GroupedSrc src;
+  GroupedSrc<BN_, W32> src;
   src.probs = probs;
   src.prefix = prefix;
   src.count = count;
@@ -613,6 +622,14 @@ bool plane_gemm_tc_supported(const PlaneGemm& g) {
   return get_encode() != nullptr;
 }
 
+// the streaming multiprocessors of the current device (persistent grids)
+int sm_count(int& sms) {
+  int dev = 0;
+  FRX_CUDA_TRY(cudaGetDevice(&dev));
+  FRX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return FRX_OK;
+}
+
 template <int BN, bool W32>
 int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   // tensor maps span the allocated planes (g.d.kL, g.d.kR: the capacity when d comes from the device)
@@ -626,29 +643,28 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
     attr_err = cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   FRX_CUDA_TRY(attr_err);
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    FRX_CUDA_TRY(cudaGetDevice(&dev));
-    FRX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  int64_t units = a.dyn ? (int64_t)sms : (int64_t)a.d.units;
+  int sms = 0;
+  FRX_TRY(sm_count(sms));
+  const int64_t units =
+      a.dyn ? (int64_t)sms : ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups;
   unsigned grid = (unsigned)(units < sms ? units : sms);
   if (grid == 0) return FRX_OK;
   k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
   FRX_CUDA_TRY(cudaGetLastError());
+  last_tile_n() = BN;
   return FRX_OK;
 }
 
 size_t tc_problem_bytes() { return sizeof(TcProblem); }
 
-// one entry of a grouped launch's table (host memory), for a product with int32 planes
-int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry) {
-  if (!plane_gemm_tc_supported(g) || !g.d.word32) return FRX_E_UNSUPPORTED;
+// one entry of a grouped launch's table (host memory), for a product with int32 planes and
+// output tiles of 128 x bn
+int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int bn) {
+  if (!plane_gemm_tc_supported(g) || !g.d.word32 || (bn != 128 && bn != 256)) return FRX_E_UNSUPPORTED;
   TcProblem* e = reinterpret_cast<TcProblem*>(host_entry);
   memset(e, 0, sizeof(TcProblem));
   if (!make_map(&e->mapL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
-  if (!make_map(&e->mapR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, 256)) return FRX_E_CUDA;
+  if (!make_map(&e->mapR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, bn)) return FRX_E_CUDA;
   e->a.M = g.M;
   e->a.N = g.N;
   e->a.nkb = (int)((g.K + BK - 1) / BK);
@@ -659,32 +675,39 @@ int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry) {
   e->a.d = g.d;
   e->a.dyn = g.dyn;
   e->a.done = g.done;
+  e->a.bn = bn;
   return FRX_OK;
 }
 
-// shared-memory attribute of the grouped kernel (before any stream capture)
+// shared-memory attributes of the grouped kernels (before any stream capture)
 int prepare_plane_gemm_grouped() {
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_plane_gemm_tc_grouped<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem_bytes(256)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_plane_gemm_tc_grouped<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_bytes(128)));
   return FRX_OK;
 }
 
-// all problems of `table` (device memory, `count` entries) in one persistent launch
-int launch_plane_gemm_grouped(const void* table, int count, cudaStream_t s) {
+// all problems of `table` (device memory, `count` entries filled for tile width bn) in one
+// persistent launch
+int launch_plane_gemm_grouped(const void* table, int count, int bn, cudaStream_t s) {
   if (count <= 0) return FRX_OK;
-  if (count > MAX_GROUPED || ((uintptr_t)table & 63)) return FRX_E_UNSUPPORTED;
-  const size_t smem = smem_bytes(256);
-  int dev = 0, sms = 0;
-  FRX_CUDA_TRY(cudaGetDevice(&dev));
-  FRX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  k_plane_gemm_tc_grouped<256, true>
-      <<<(unsigned)sms, NUM_THREADS, smem, s>>>(reinterpret_cast<const TcProblem*>(table), count);
+  if (count > MAX_GROUPED || ((uintptr_t)table & 63) || (bn != 128 && bn != 256)) return FRX_E_UNSUPPORTED;
+  int sms = 0;
+  FRX_TRY(sm_count(sms));
+  const TcProblem* tab = reinterpret_cast<const TcProblem*>(table);
+  if (bn == 256)
+    k_plane_gemm_tc_grouped<256, true><<<(unsigned)sms, NUM_THREADS, smem_bytes(256), s>>>(tab, count);
+  else
+    k_plane_gemm_tc_grouped<128, true><<<(unsigned)sms, NUM_THREADS, smem_bytes(128), s>>>(tab, count);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
+  last_tile_n() = bn;
   return FRX_OK;
 }
 
-int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
+// bn: output tile width (int32 planes: 128 or 256; int64 groups always use 128)
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int bn, cudaStream_t s) {
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
@@ -696,8 +719,14 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s) {
   a.d = g.d;
   a.dyn = g.dyn;
   a.done = g.done;
-  if (g.d.word32) return launch_variant<256, true>(g, a, s);
-  return launch_variant<128, false>(g, a, s);
+  if (!g.d.word32) {
+    a.bn = 128;
+    return launch_variant<128, false>(g, a, s);
+  }
+  if (bn != 128 && bn != 256) return FRX_E_UNSUPPORTED;
+  a.bn = bn;
+  if (bn == 256) return launch_variant<256, true>(g, a, s);
+  return launch_variant<128, true>(g, a, s);
 }
 
 }  // namespace frx

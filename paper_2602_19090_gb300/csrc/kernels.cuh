@@ -1,12 +1,14 @@
 // Launchers of the frx kernels (host-side declarations).
 #pragma once
 
+#include <vector>
+
 #include "frx_internal.cuh"
 #include "plan.cuh"
 
 namespace frx {
 
-enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_RANGE = 4 };
+enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_RANGE = 4, FLAG_CONFIG = 8 };
 
 // optional device-side parameters of the slicing kernels (null: use the launch arguments)
 struct SliceDyn {
@@ -51,6 +53,7 @@ struct PlaneGemm {
   int64_t ogs, ldo;
   int* flags;   // device status word (timeouts), may be null
   int out_bytes_per_elem;
+  int tile_n;   // output tile width of the tensor-core kernel (0: the autotuner decides)
   __host__ __device__ int32_t* out32() const { return reinterpret_cast<int32_t*>(out); }
 };
 
@@ -61,16 +64,24 @@ int pairs_in(int kL, int kR, int T);
 // gemm_simt.cu / gemm_tc.cu
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s);
 int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s);
-int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, cudaStream_t s);
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int bn, cudaStream_t s);
 bool plane_gemm_tc_supported(const PlaneGemm& g);
 // grouped slice products: a device table of per-problem entries (tensor maps + arguments,
 // 64-byte aligned, tc_problem_bytes() each) run in one persistent launch
 size_t tc_problem_bytes();
-int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry);
-int launch_plane_gemm_grouped(const void* table, int count, cudaStream_t s);
+int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int bn);
+int launch_plane_gemm_grouped(const void* table, int count, int bn, cudaStream_t s);
 int prepare_plane_gemm_grouped();
 // a zero (src == nullptr) or copy of 8-byte words recorded as a grouped-launch entry
 int record_bytes(void* dst, const void* src, size_t bytes);
+
+// autotune.cu: output tile width (128 or 256) of the tensor-core products
+int tile_policy();
+int tune_tile_single(const PlaneGemm& g, int kind, cudaStream_t s, int& bn);
+int tune_tile_refine(const PlaneGemm& rep, cudaStream_t s, int& bn);
+int tune_tile_grouped(const std::vector<PlaneGemm>& gs, const std::vector<long long>& key, void* table,
+                      cudaStream_t s, int& bn);
+int& last_tile_n();
 
 // refine_kernels.cu
 int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR, double* Ch, int64_t ldh,

@@ -350,7 +350,17 @@ __device__ __forceinline__ void plan_w_impl(DevPlan* p, const int32_t* h, PlanOp
 }
 
 // cluster threshold omega (fixed, or the Ogita-Aishima form from ||W_off||_F and ||diag R||_2)
-__device__ __forceinline__ void plan_omega_impl(DevPlan* p, const double* r, PlanOpts o) {
+// sum of n per-column partials in a fixed order (strided per thread, then a fixed tree), so
+// that the norms and the decisions taken from them repeat bit for bit from run to run
+__device__ __forceinline__ double sum_columns(const double* c, int64_t n, double* redd) {
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += PT) s = __dadd_rn(s, c[i]);
+  return bsum_d(s, redd);
+}
+
+// colsq: per-column squared norms [3][n] written by the correction, off-diagonal-W and
+// update kernels (E~, W_off, X_new - X_old)
+__device__ __forceinline__ void plan_omega_impl(DevPlan* p, const double* r, const double* colsq, PlanOpts o) {
   __shared__ double redd[32];
   if (p->done) return;
   if (o.cluster_omega >= 0) {
@@ -360,7 +370,11 @@ __device__ __forceinline__ void plan_omega_impl(DevPlan* p, const double* r, Pla
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < o.n; i += PT) s = __fma_rn(r[i], r[i], s);
   s = bsum_d(s, redd);
-  if (threadIdx.x == 0) p->omega = 2.0 * (__dsqrt_rn(p->norms[1]) + p->Lam * __dsqrt_rn(s));
+  const double w2 = sum_columns(colsq + o.n, o.n, redd);
+  if (threadIdx.x == 0) {
+    p->norms[1] = w2;
+    p->omega = 2.0 * (__dsqrt_rn(w2) + p->Lam * __dsqrt_rn(s));
+  }
 }
 
 // k_U and the update product (Alg. 1 line 6)
@@ -399,7 +413,8 @@ __device__ __forceinline__ void plan_u_impl(DevPlan* p, const int32_t* rho, cons
 }
 
 // stopping test (reading R7): est = step^2 max|lam| / (xi_stop gap) <= delta
-__device__ __forceinline__ void plan_end_impl(DevPlan* p, const double* lam_new, double* lam_prev, PlanOpts o) {
+__device__ __forceinline__ void plan_end_impl(DevPlan* p, const double* lam_new, double* lam_prev,
+                                              const double* colsq, PlanOpts o) {
   extern __shared__ double sbuf[];
   __shared__ double redd[32];
   if (p->done) return;
@@ -407,13 +422,18 @@ __device__ __forceinline__ void plan_end_impl(DevPlan* p, const double* lam_new,
   double g, Lam;
   gap_of(lam_new, o.n, omega, sbuf, redd, g, Lam);
   for (int64_t i = threadIdx.x; i < o.n; i += PT) lam_prev[i] = lam_new[i];
+  const double e2 = sum_columns(colsq, o.n, redd);
+  __syncthreads();
+  const double dx2 = sum_columns(colsq + 2 * o.n, o.n, redd);
   if (threadIdx.x != 0) return;
+  p->norms[0] = e2;
+  p->norms[2] = dx2;
   if (p->flags & FLAG_NONFINITE) {
     raise(p, FRX_E_NONFINITE);
     return;
   }
-  if (p->flags & (FLAG_TIMEOUT | FLAG_RANGE)) {
-    raise(p, (p->flags & FLAG_TIMEOUT) ? FRX_E_TIMEOUT : FRX_E_RANGE);
+  if (p->flags & (FLAG_TIMEOUT | FLAG_RANGE | FLAG_CONFIG)) {
+    raise(p, (p->flags & FLAG_TIMEOUT) ? FRX_E_TIMEOUT : (p->flags & FLAG_RANGE) ? FRX_E_RANGE : FRX_E_UNSUPPORTED);
     return;
   }
   double step = __dsqrt_rn(p->norms[2]);
@@ -460,6 +480,7 @@ struct PlanArgs {
   PlanOpts o;
   double omega_prev;
   unsigned gx;
+  const double* colsq;   // per-column squared norms (omega, end)
 };
 
 __global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev,
@@ -469,14 +490,15 @@ __global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA,
 __global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, PlanOpts o) { plan_v_impl(p, f, o); }
 __global__ void k_plan_mark_sliced(DevPlan* p) { plan_mark_sliced_impl(p); }
 __global__ void __launch_bounds__(PT) k_plan_w(DevPlan* p, const int32_t* h, PlanOpts o) { plan_w_impl(p, h, o); }
-__global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, PlanOpts o) {
-  plan_omega_impl(p, r, o);
+__global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, const double* colsq, PlanOpts o) {
+  plan_omega_impl(p, r, colsq, o);
 }
 __global__ void __launch_bounds__(PT) k_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
   plan_u_impl(p, rho, eta, o);
 }
-__global__ void __launch_bounds__(PT) k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, PlanOpts o) {
-  plan_end_impl(p, lam_new, lam_prev, o);
+__global__ void __launch_bounds__(PT)
+    k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const double* colsq, PlanOpts o) {
+  plan_end_impl(p, lam_new, lam_prev, colsq, o);
 }
 
 __device__ __forceinline__ void plan_init_body(PlanArgs a, unsigned, unsigned) {
@@ -485,10 +507,12 @@ __device__ __forceinline__ void plan_init_body(PlanArgs a, unsigned, unsigned) {
 __device__ __forceinline__ void plan_v_body(PlanArgs a, unsigned, unsigned) { plan_v_impl(a.p, a.e0, a.o); }
 __device__ __forceinline__ void plan_mark_sliced_body(PlanArgs a, unsigned, unsigned) { plan_mark_sliced_impl(a.p); }
 __device__ __forceinline__ void plan_w_body(PlanArgs a, unsigned, unsigned) { plan_w_impl(a.p, a.e0, a.o); }
-__device__ __forceinline__ void plan_omega_body(PlanArgs a, unsigned, unsigned) { plan_omega_impl(a.p, a.d0, a.o); }
+__device__ __forceinline__ void plan_omega_body(PlanArgs a, unsigned, unsigned) {
+  plan_omega_impl(a.p, a.d0, a.colsq, a.o);
+}
 __device__ __forceinline__ void plan_u_body(PlanArgs a, unsigned, unsigned) { plan_u_impl(a.p, a.e0, a.e1, a.o); }
 __device__ __forceinline__ void plan_end_body(PlanArgs a, unsigned, unsigned) {
-  plan_end_impl(a.p, a.d0, a.d1, a.o);
+  plan_end_impl(a.p, a.d0, a.d1, a.colsq, a.o);
 }
 
 int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev, const PlanOpts& o,
@@ -527,9 +551,10 @@ int launch_plan_w(DevPlan* p, const int32_t* h, const PlanOpts& o, cudaStream_t 
   return FRX_OK;
 }
 
-int launch_plan_omega(DevPlan* p, const double* r, const PlanOpts& o, cudaStream_t s) {
-  if (record_launch(LK_PLAN_OMEGA, PlanArgs{p, nullptr, nullptr, r, nullptr, o, 0.0, 1u}, 1, PT, 0)) return FRX_OK;
-  k_plan_omega<<<1, PT, 0, s>>>(p, r, o);
+int launch_plan_omega(DevPlan* p, const double* r, const double* colsq, const PlanOpts& o, cudaStream_t s) {
+  if (record_launch(LK_PLAN_OMEGA, PlanArgs{p, nullptr, nullptr, r, nullptr, o, 0.0, 1u, colsq}, 1, PT, 0))
+    return FRX_OK;
+  k_plan_omega<<<1, PT, 0, s>>>(p, r, colsq, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
@@ -543,10 +568,12 @@ int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const Plan
   return FRX_OK;
 }
 
-int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const PlanOpts& o, cudaStream_t s) {
+int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const double* colsq, const PlanOpts& o,
+                    cudaStream_t s) {
   size_t sm = sort_smem(o.n);
-  if (record_launch(LK_PLAN_END, PlanArgs{p, nullptr, nullptr, lam_new, lam_prev, o, 0.0, 1u}, 1, PT, sm)) return FRX_OK;
-  k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, o);
+  if (record_launch(LK_PLAN_END, PlanArgs{p, nullptr, nullptr, lam_new, lam_prev, o, 0.0, 1u, colsq}, 1, PT, sm))
+    return FRX_OK;
+  k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, colsq, o);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;

@@ -701,9 +701,12 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
 __device__ __forceinline__ void w_offdiag_body(CorrectionArgs a, unsigned bx, unsigned) {
   if (a.done && *a.done) return;
   a.W = resolve(a.W);
-  if (a.W.groups == 0) return;
-  __shared__ double red[32];
   const int64_t j = bx;
+  if (a.W.groups == 0) {
+    if (threadIdx.x == 0) a.norms[a.n + j] = 0.0;
+    return;
+  }
+  __shared__ double red[32];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) {
     if (i == j) continue;
@@ -711,7 +714,7 @@ __device__ __forceinline__ void w_offdiag_body(CorrectionArgs a, unsigned bx, un
     s += w * w;
   }
   s = block_sum_d(s, red);
-  if (threadIdx.x == 0) atomicAdd(a.norms + 1, s);
+  if (threadIdx.x == 0) a.norms[a.n + j] = s;
 }
 
 // ---- line 5: E~ column j, its exponent, ||E~||_F^2 -----------------------------------
@@ -813,7 +816,7 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
   const double s2 = block_sum_d(__fma_rn((double)s2f, 0x1p-64, s2d), red);
   mx = block_max_u64(mx, redu);
   if (threadIdx.x == 0) {
-    atomicAdd(a.norms + 0, s2);
+    a.norms[j] = s2;
     a.eta[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
   }
 }
@@ -958,7 +961,7 @@ __device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned)
     }
   }
   const double d2 = block_sum_d(__fma_rn((double)d2f, 0x1p-64, d2d), red);
-  if (threadIdx.x == 0) atomicAdd(a.norms + 2, d2);
+  if (threadIdx.x == 0) a.norms[2 * a.n + j] = d2;
 }
 
 // ---- single-problem kernels (one block per column) ---------------------------------

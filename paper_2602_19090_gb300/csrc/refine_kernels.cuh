@@ -49,7 +49,7 @@ struct CorrectionArgs {
   double* E;             // out: E~
   int64_t lde;
   int32_t* eta;          // out: column exponents of E~
-  double* norms;         // [0] += ||E~||_F^2, [1] += ||W_offdiag||_F^2, [2] += ||dX||_F^2
+  double* norms;         // per-column squared norms [3][n]: E~(:, j), W_offdiag(:, j) (this kernel writes [0], [1])
   int* ccount;           // out: cluster pairs found
   int* flags;
   double* Wout;          // optional debug copy (ld = n)
@@ -69,7 +69,7 @@ struct UpdateArgs {
   int64_t ld1;
   double* X;             // in: X_old, out: X_new
   int64_t ldx;
-  double* norms;
+  double* norms;         // per-column squared norms [3][n]: this kernel writes [2] (X_new - X_old)(:, j)
   unsigned gx;
 };
 
