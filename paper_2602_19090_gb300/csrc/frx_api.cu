@@ -450,9 +450,11 @@ struct Stage {
   int variant;   // slice products: output tile width
 };
 
-// stage k of a phase groups record k of every problem (same kind and argument size)
-int build_stages(const std::vector<std::vector<LaunchRecord>>& recs, std::vector<unsigned char>& blob,
-                 std::vector<Stage>& stages) {
+// stage k of a phase groups record k of every problem (same kind and argument size); the
+// slice-product stages list the problems in `gemm_order` (largest first, so that the
+// persistent kernel's units come roughly in decreasing order of work), the others in batch order
+int build_stages(const std::vector<std::vector<LaunchRecord>>& recs, const std::vector<int>& gemm_order,
+                 std::vector<unsigned char>& blob, std::vector<Stage>& stages) {
   const int count = (int)recs.size();
   const size_t K = recs[0].size();
   for (int b = 1; b < count; ++b)
@@ -468,7 +470,8 @@ int build_stages(const std::vector<std::vector<LaunchRecord>>& recs, std::vector
     st.tab_off = (blob.size() + 63) / 64 * 64;
     blob.resize(st.tab_off + sz * (size_t)count);
     for (int b = 0; b < count; ++b) {
-      const LaunchRecord& r = recs[b][k];
+      const int src = st.kind == LK_GEMM ? gemm_order[b] : b;
+      const LaunchRecord& r = recs[src][k];
       if (r.kind != st.kind || r.args.size() != sz || r.variant != st.variant) return FRX_E_UNSUPPORTED;
       memcpy(blob.data() + st.tab_off + sz * b, r.args.data(), sz);
     }
@@ -605,9 +608,12 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
   std::vector<std::vector<LaunchRecord>> rec[3];
   for (int q = 0; q < 3; ++q) rec[q].resize(count);
   FRX_TRY(record_phases(A, lda, X, ldx, D, n, count, o, po, ws, tile_n, rec));
+  std::vector<int> gemm_order(count);
+  for (int b = 0; b < count; ++b) gemm_order[b] = b;
+  std::stable_sort(gemm_order.begin(), gemm_order.end(), [&](int x, int y) { return n[x] > n[y]; });
   std::vector<unsigned char> blob;
   std::vector<Stage> stages[3];
-  for (int q = 0; q < 3; ++q) FRX_TRY(build_stages(rec[q], blob, stages[q]));
+  for (int q = 0; q < 3; ++q) FRX_TRY(build_stages(rec[q], gemm_order, blob, stages[q]));
   if (blob.size() > L.tables_bytes) return FRX_E_UNSUPPORTED;
   char* tables = base + L.tables_off;
   DevPlan** dplans = (DevPlan**)(base + L.plans_off);

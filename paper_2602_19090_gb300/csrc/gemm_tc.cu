@@ -11,8 +11,8 @@
 // are combined in Horner form per group: R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
 //
 // Persistent: one CTA per SM walks the units (output tile of 128 x BN, group of
-// anti-diagonals), groups ordered by decreasing work and tiles in bands of TILE_BAND tile
-// rows.  A grouped variant walks the units of many problems (the batched refinement).
+// anti-diagonals) in serpentine rounds, groups ordered by decreasing work and tiles in bands
+// of TILE_BAND tile rows.  A grouped variant walks the units of many problems (the batched refinement).
 // Warp roles:
 //   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
 //   warp 1       TMEM allocator and single-thread MMA issuer
@@ -214,6 +214,15 @@ __device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int bm, int
   j0 = (local / rows) * bn;
 }
 
+// The unit this CTA takes in round r of the persistent loop.  Rounds alternate direction
+// (serpentine): units come in decreasing order of work, so a CTA that took one of the longest
+// units of a round takes one of the shortest of the next, which evens out the CTAs' totals
+// where plain round-robin would give the first CTAs the longest unit of every round.
+__device__ __forceinline__ int unit_of_round(int r) {
+  const int P = (int)gridDim.x, c = (int)blockIdx.x;
+  return (r & 1) ? (r + 1) * P - 1 - c : r * P + c;
+}
+
 // the product description of a launch's problem, resolved from its arguments; the tiling
 // (128 x BN tiles, units = tiles x groups) belongs to the kernel variant, not to the plan
 template <int BN, bool W32>
@@ -337,7 +346,9 @@ __device__ __forceinline__ void tc_body(Src& src) {
       uint32_t phase = 0;
       long long issued = 0;
       bool ok = !*abort;
-      for (int u = blockIdx.x; u < src.total() && ok; u += gridDim.x) {
+      for (int rnd = 0; (long long)rnd * gridDim.x < src.total() && ok; ++rnd) {
+        const int u = unit_of_round(rnd);
+        if (u >= src.total()) continue;
         int lu;
         src.unit(u, lu);
         const TcRun& a = src.run;
@@ -403,7 +414,9 @@ __device__ __forceinline__ void tc_body(Src& src) {
       uint32_t acc_phase[2] = {0, 0};
       bool ok = true;
       bool any = false;
-      for (int u = blockIdx.x; u < src.total() && ok; u += gridDim.x) {
+      for (int rnd = 0; (long long)rnd * gridDim.x < src.total() && ok; ++rnd) {
+        const int u = unit_of_round(rnd);
+        if (u >= src.total()) continue;
         int lu;
         src.unit(u, lu);
         const TcRun& a = src.run;
@@ -472,7 +485,9 @@ __device__ __forceinline__ void tc_body(Src& src) {
     int buf = 0;
     uint32_t acc_phase[2] = {0, 0};
     bool ok = true;
-    for (int u = blockIdx.x; u < src.total() && ok; u += gridDim.x) {
+    for (int rnd = 0; (long long)rnd * gridDim.x < src.total() && ok; ++rnd) {
+      const int u = unit_of_round(rnd);
+      if (u >= src.total()) continue;
       int lu;
       src.unit(u, lu);
       const TcRun& a = src.run;
