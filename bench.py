@@ -72,8 +72,8 @@ def parse():
                         "configs: the n=2048 variants and the n=8192 forward-error sweep")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--sweep-n", default="1024,4096,8192", help="matrix orders of the ozaki_gemm sweep")
-    p.add_argument("--tile-n", type=int, default=0, choices=[0, 128, 256],
-                   help="output tile width of the slice products (0: the library's autotuner)")
+    p.add_argument("--tile", default="auto", choices=["auto", "128x128", "128x256", "256x256"],
+                   help="tile configuration of the slice products (auto: the library's autotuner)")
     return p.parse_args()
 
 
@@ -205,6 +205,7 @@ def run_ours(args):
     D = torch.empty_like(D0t)
     opts = api.Options()
     work = api.workspace(api.refine_workspace_bytes(n, opts), dev)
+    api.set_tile(args.tile)
 
     def one():
         X.copy_(X0t)
@@ -281,6 +282,7 @@ def run_ours(args):
                      "peak_source": f"{src} bf16_tflops (burst; sustained {pk.get('bf16_tflops_sustained')})",
                      "gemm_share_of_step": prof["gemm_ms"] / (ms * args.steps) if ms else None},
         "gpu_launches": prof["kernel_launches"],
+        "tile": {"used": api.last_tile(), "policy": "autotuned" if args.tile == "auto" else "forced"},
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(A_h.numel() * 8 + X0_h.numel() * 8 + D0_h.numel() * 8),
                 "d2h_bytes_per_step": int(Xo_h.numel() * 8 + Do_h.numel() * 8)},
         "clocks": clk,
@@ -393,7 +395,7 @@ def run_batched(args):
         Dflat.copy_(D0flat)
         return api.refine_batched(As, Xs, Ds, delta, work=work)
 
-    api.set_tile_n(args.tile_n)
+    api.set_tile(args.tile)
 
     for _ in range(args.warmup):
         infos = one()
@@ -438,8 +440,8 @@ def run_batched(args):
                                f"start perturbed 1e-8, delta={delta:g}", "count": args.count,
                    "n_min": int(sizes.min()), "n_max": int(sizes.max()), "delta": delta},
         "statuses": stats, "gpu_launches": prof["kernel_launches"],
-        "tile_n": {"used": api.last_tile_n(), "policy": "forced" if args.tile_n else "autotuned",
-                   "tuner": api.tune_stats()},
+        "tile": {"used": api.last_tile(), "policy": "autotuned" if args.tile == "auto" else "forced",
+                 "tuner": api.tune_stats()},
         "fp64_loop": ({"seconds": fp64_ms / 1e3, "matrices_per_s": args.count * 1e3 / fp64_ms, "statuses": fstats,
                        "speedup_ours": fp64_ms / ms} if fp64_ms else None),
         "clocks": clk,
@@ -679,7 +681,7 @@ def run_gemm_sweep(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    api.set_tile_n(args.tile_n)
+    api.set_tile(args.tile)
     out = {"metric": "ozaki_gemm_sweep", "cases": []}
     sizes = tuple(int(v) for v in args.sweep_n.split(","))
     for n in sizes:
@@ -716,7 +718,7 @@ def run_gemm_sweep(args):
                            "tflops_eq": 2.0 * n ** 3 / (best * 1e-3) / 1e12,
                            "gemm_kernel_tflops": pr["gemm_ops"] / (pr["gemm_ms"] * 1e-3) / 1e12 if pr["gemm_ms"] else None,
                            "gemm_share": pr["gemm_ms"] / 3 / best if pr["gemm_ms"] else None,
-                           "tile_n": api.last_tile_n(),
+                           "tile": api.last_tile(),
                            "max_err_rel_absAabsB": err, "dgemm_err_rel_absAabsB": dgemm_err}
                     out["cases"].append(rec)
                     print(json.dumps(rec), file=sys.stderr, flush=True)

@@ -261,25 +261,36 @@ FRX_API void frx_profile_enable(int on);
 FRX_API int frx_profile_read(frx_profile* out, int reset);
 
 /*
- * Tile-width autotuner of the slice products (no counterpart in the paper; it changes
- * the time of a product, never its result: every tile sum is exact).
- *   The tensor-core kernel covers a product's m x n output with 128 x 256 or 128 x 128
- *   tiles.  The first time a product shape is seen (frx_ozaki_gemm: m, n, k, planes and
- *   pair bound; frx_refine: n and the plane capacities; frx_refine_batched: the sorted
- *   orders of the batch), a cost model picks 256 when those tiles cover the output with
- *   under 3% padding and leave at least 4 units per SM; otherwise both widths are timed
- *   with CUDA events on the call's stream (4 launches each, one stream synchronisation)
- *   and the faster is cached for the shape, process-wide.  On a stream under capture
- *   nothing is timed or cached: the model's estimate is used.
- *   frx_set_tile_n(w): w = 0 autotunes (default); 128 or 256 forces that width.  Returns
- *     the previous setting, or FRX_E_ARG for another w.  Process-wide.
- *   frx_last_tile_n(): the width of the last slice-product launch made by the calling
- *     host thread (0 before any).
+ * Tile autotuner of the slice products (no counterpart in the paper; it changes the time of
+ * a product, never its result: every tile sum is exact).
+ *   The tensor-core kernel covers a product's m x n output with one of three tile
+ *   configurations:
+ *     FRX_TILE_128x128, FRX_TILE_128x256  one CTA per tile;
+ *     FRX_TILE_256x256  a pair of CTAs (a 2-CTA cluster) per 256 x 256 super-tile, each CTA
+ *                       computing one 128-row half and loading half of the shared B panel,
+ *                       which it multicasts to both (offered when m > 128; batched calls use
+ *                       one CTA per tile).
+ *   The first time a product shape is seen (frx_ozaki_gemm: m, n, k, planes and pair bound;
+ *   frx_refine: n and the plane capacities; frx_refine_batched: the sorted orders of the
+ *   batch), a cost model settles it when 128 x 256 tiles cover the output with under 3%
+ *   padding and leave at least 4 units per SM; otherwise every offered configuration is
+ *   timed with CUDA events on the call's stream (4 launches each, one stream
+ *   synchronisation) and the fastest is cached for the shape, process-wide.  On a stream
+ *   under capture nothing is timed or cached: the model's estimate is used.
+ *   frx_set_tile(t): FRX_TILE_AUTO (0, default) autotunes; another FRX_TILE_* forces that
+ *     configuration where it is offered (FRX_TILE_128x256 elsewhere).  Returns the previous
+ *     setting, or FRX_E_ARG for another value.  Process-wide.
+ *   frx_last_tile(): the configuration of the last slice-product launch made by the calling
+ *     host thread (FRX_TILE_AUTO before any).
  *   frx_tune_stats: decisions taken by timing and by the model, and cache hits, since the
  *     last clear (clear != 0 also empties the cache).  Any pointer may be NULL.
  */
-FRX_API int frx_set_tile_n(int tile_n);
-FRX_API int frx_last_tile_n(void);
+#define FRX_TILE_AUTO 0
+#define FRX_TILE_128x128 1
+#define FRX_TILE_128x256 2
+#define FRX_TILE_256x256 3
+FRX_API int frx_set_tile(int tile);
+FRX_API int frx_last_tile(void);
 FRX_API int frx_tune_stats(long long* measured, long long* modelled, long long* hits, int clear);
 
 #ifdef __cplusplus

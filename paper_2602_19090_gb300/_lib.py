@@ -63,8 +63,8 @@ _SIGS = {
                                         c_i64, C.c_int, C.c_int, c_p]),
     "frx_profile_enable": (None, [C.c_int]),
     "frx_profile_read": (C.c_int, [C.POINTER(Profile), C.c_int]),
-    "frx_set_tile_n": (C.c_int, [C.c_int]),
-    "frx_last_tile_n": (C.c_int, []),
+    "frx_set_tile": (C.c_int, [C.c_int]),
+    "frx_last_tile": (C.c_int, []),
     "frx_tune_stats": (C.c_int, [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                  C.POINTER(C.c_longlong), C.c_int]),
 }

@@ -250,18 +250,23 @@ def plane_products(Lp, Rp, K, kL, kR, T, stream=None):
     return out, gs
 
 
-def set_tile_n(tile_n: int) -> int:
-    """Force the slice products' output tile width (128 or 256); 0 restores autotuning.
-    Returns the previous setting."""
-    st = _lib.load().frx_set_tile_n(int(tile_n))
+TILES = {"auto": 0, "128x128": 1, "128x256": 2, "256x256": 3}
+TILE_NAMES = {v: k for k, v in TILES.items()}
+
+
+def set_tile(tile) -> str:
+    """Force the slice products' tile configuration ("128x128", "128x256", or "256x256" for
+    pairs of CTAs); "auto" restores the autotuner.  Returns the previous setting's name."""
+    code = TILES[tile] if isinstance(tile, str) else int(tile)
+    st = _lib.load().frx_set_tile(code)
     if st < 0:
-        raise FrxError(st, "frx_set_tile_n")
-    return st
+        raise FrxError(st, "frx_set_tile")
+    return TILE_NAMES[st]
 
 
-def last_tile_n() -> int:
-    """Tile width of the last slice-product launch made by this host thread."""
-    return _lib.load().frx_last_tile_n()
+def last_tile() -> str:
+    """Tile configuration of the last slice-product launch made by this host thread."""
+    return TILE_NAMES[_lib.load().frx_last_tile()]
 
 
 def tune_stats(clear: bool = False) -> dict:

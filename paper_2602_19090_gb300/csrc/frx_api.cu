@@ -51,7 +51,7 @@ struct RefineWs {
   i64* groups;
   int64_t pitch, ps;
   size_t bytes;
-  int tile_n;      // output tile width of the slice products (set by the autotuner)
+  int tile;        // tile configuration of the slice products (set by the autotuner)
 };
 
 RefineWs carve_refine(void* work, int64_t n, int kcap) {
@@ -80,7 +80,7 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   w.X1rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
   w.groups = c.take<i64>((size_t)8 * n * n);   // 64 bytes per entry: 8 int64 groups or 16 int32 planes
   w.bytes = c.off + 256;
-  w.tile_n = 256;
+  w.tile = TILE_128x256;
   return w;
 }
 
@@ -199,7 +199,7 @@ PlaneGemm dyn_gemm(const __nv_bfloat16* L, int capL, const __nv_bfloat16* R, int
   g.dyn = dyn;
   g.done = &ws.plan->done;
   g.flags = &ws.plan->flags;
-  g.tile_n = ws.tile_n;
+  g.tile = ws.tile;
   return g;
 }
 
@@ -367,7 +367,7 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
       FRX_CUDA_TRY(cudaMemsetAsync(ws.rowmax, 0, sizeof(u64) * n, s));
       PlaneGemm rep = tuning_gemm(ws, n, o.k_cap);
       FRX_TRY(plan_plane_gemm(rep));
-      FRX_TRY(tune_tile_refine(rep, s, ws.tile_n));
+      FRX_TRY(tune_tile_refine(rep, s, ws.tile));
       FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s, nullptr, &ws.plan->rownnz));
       FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));
       for (int it = 1; it <= max_iter; ++it) {
@@ -550,9 +550,9 @@ int batch_stream(BatchStream** out) {
 // record the three phases of every problem: setup, one iteration, finish
 int record_phases(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
                   double* const* D, const int64_t* n, int count, const frx_opts& o, const std::vector<PlanOpts>& po,
-                  const std::vector<RefineWs>& ws, int tile_n, std::vector<std::vector<LaunchRecord>> (&rec)[3]) {
+                  const std::vector<RefineWs>& ws, int tile, std::vector<std::vector<LaunchRecord>> (&rec)[3]) {
   LaunchRecorder R;
-  R.tile_n = tile_n;
+  R.tile = tile;
   LaunchRecorder*& active = active_recorder();
   active = &R;
   cudaStream_t none = nullptr;   // nothing is launched while recording
@@ -589,9 +589,9 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
     hplans[b] = ws[b].plan;
     po[b] = plan_opts(o, delta, n[b], o.max_iter);
   }
-  // tile width of the grouped slice products: cached per batch signature (the sorted orders),
+  // tile configuration of the grouped slice products: cached per batch signature (the sorted orders),
   // else timed on representative products over the problems' plane buffers
-  int tile_n = 256;
+  int tile = TILE_128x256;
   {
     std::vector<PlaneGemm> reps(count);
     std::vector<long long> key = {3, count, o.k_cap};
@@ -602,12 +602,12 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
       reps[b] = tuning_gemm(ws[b], n[b], o.k_cap);
       FRX_TRY(plan_plane_gemm(reps[b]));
     }
-    FRX_TRY(tune_tile_grouped(reps, key, base + L.tables_off, s, tile_n));
+    FRX_TRY(tune_tile_grouped(reps, key, base + L.tables_off, s, tile));
   }
-  for (int b = 0; b < count; ++b) ws[b].tile_n = tile_n;
+  for (int b = 0; b < count; ++b) ws[b].tile = tile;
   std::vector<std::vector<LaunchRecord>> rec[3];
   for (int q = 0; q < 3; ++q) rec[q].resize(count);
-  FRX_TRY(record_phases(A, lda, X, ldx, D, n, count, o, po, ws, tile_n, rec));
+  FRX_TRY(record_phases(A, lda, X, ldx, D, n, count, o, po, ws, tile, rec));
   std::vector<int> gemm_order(count);
   for (int b = 0; b < count; ++b) gemm_order[b] = b;
   std::stable_sort(gemm_order.begin(), gemm_order.end(), [&](int x, int y) { return n[x] > n[y]; });

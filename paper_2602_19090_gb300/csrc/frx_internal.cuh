@@ -84,6 +84,9 @@ __host__ __device__ inline double pow2(int k) {
 //   d_r = RNE(rho_{r-1} / w_r), rho_r = rho_{r-1} - d_r w_r (round half to even),
 //   which is the sigma-trick fl((sigma + rho) - sigma) with ulp(sigma) = w_r.
 // ---------------------------------------------------------------------------
+// x == +-0 tested on its bits (an integer instruction, not a compare on the FP64 pipe)
+__host__ __device__ inline bool is_zero(double x) { return (double_to_bits(x) << 1) == 0; }
+
 __host__ __device__ inline void decompose(double x, i64& P, int& q) {
   u64 b = double_to_bits(x);
   int bexp = (int)((b >> 52) & 0x7ff);

@@ -157,25 +157,25 @@ int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) {
   if (active_recorder()) {
     // batched refinement: the product becomes one entry of a grouped tensor-core launch
     std::vector<unsigned char> entry(tc_problem_bytes());
-    const int bn = active_recorder()->tile_n;
-    FRX_TRY(tc_problem_fill(g, g.flags, entry.data(), bn));
+    const int tile = active_recorder()->tile;
+    FRX_TRY(tc_problem_fill(g, g.flags, entry.data(), tile));
     LaunchRecord r;
     r.kind = LK_GEMM;
     r.args = std::move(entry);
     r.blocks = 0;
     r.threads = 0;
     r.smem = 0;
-    r.variant = bn;
+    r.variant = tile;
     active_recorder()->recs.push_back(std::move(r));
     return FRX_OK;
   }
   const char* env = getenv("FRX_GEMM");
   bool simt = env && env[0] == 's';
   if (!simt && plane_gemm_tc_supported(g)) {
-    int bn = g.tile_n;
-    if (!bn) FRX_TRY(tune_tile_single(g, 1, s, bn));
+    int tile = g.tile;
+    if (tile == TILE_AUTO) FRX_TRY(tune_tile_single(g, 1, s, tile));
     GemmTimer timer(g, s);
-    return launch_plane_gemm_tc(g, g.flags, bn, s);
+    return launch_plane_gemm_tc(g, g.flags, tile, s);
   }
   GemmTimer timer(g, s);
   return launch_plane_gemm_simt(g, s);

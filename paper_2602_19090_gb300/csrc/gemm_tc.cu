@@ -11,8 +11,8 @@
 // are combined in Horner form per group: R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
 //
 // Persistent: one CTA per SM walks the units (output tile of 128 x BN, group of
-// anti-diagonals) in serpentine rounds, groups ordered by decreasing work and tiles in bands
-// of TILE_BAND tile rows.  A grouped variant walks the units of many problems (the batched refinement).
+// anti-diagonals) in rounds (serpentine when there are few), groups ordered by decreasing work
+// and tiles in bands of TILE_BAND tile rows.  A grouped variant walks the units of many problems (the batched refinement).
 // Warp roles:
 //   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
 //   warp 1       TMEM allocator and single-thread MMA issuer
@@ -115,6 +115,29 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// the same copy into the same shared-memory offset of every CTA of the cluster in `mask`,
+// completing bytes on the mbarrier at the same offset in each of them
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                               uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
+      "[%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// every thread of every CTA of the cluster: release this CTA's prior shared-memory writes
+// (barrier initialisation) and wait for the other CTAs
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart (SBO), version 1
 __device__ __forceinline__ uint64_t smem_desc(const void* tile) {
   uint64_t addr = smem_u32(tile);
@@ -146,6 +169,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// arrive, once the MMAs issued so far complete, on the mbarrier at this offset in every CTA
+// of the cluster in `mask`
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -174,6 +207,7 @@ struct TcArgs {
   const GemmDesc* dyn;
   const int* done;
   int bn;        // tile width the right operand's tensor map was encoded for
+  int cl;        // CTAs per super-tile (2: the map's box is half the tile width)
 };
 
 // one problem of a grouped launch: its tensor maps and arguments (device table entry)
@@ -214,23 +248,31 @@ __device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int bm, int
   j0 = (local / rows) * bn;
 }
 
-// The unit this CTA takes in round r of the persistent loop.  Rounds alternate direction
-// (serpentine): units come in decreasing order of work, so a CTA that took one of the longest
-// units of a round takes one of the shortest of the next, which evens out the CTAs' totals
-// where plain round-robin would give the first CTAs the longest unit of every round.
-__device__ __forceinline__ int unit_of_round(int r) {
-  const int P = (int)gridDim.x, c = (int)blockIdx.x;
-  return (r & 1) ? (r + 1) * P - 1 - c : r * P + c;
+// The unit this CTA takes in round r of the persistent loop.  With few rounds, rounds
+// alternate direction (serpentine): units come in decreasing order of work, so a CTA that took
+// one of the longest units of a round takes one of the shortest of the next, which evens out
+// the CTAs' totals where plain round-robin would give the first CTAs the longest unit of every
+// round.  With many rounds the imbalance is confined to the short units of the tail, and plain
+// round-robin keeps the units in flight a contiguous window (better L2 reuse of the panels).
+constexpr int SERPENTINE_MAX_ROUNDS = 16;
+
+// (per cluster of CL CTAs: both CTAs of a pair walk the same units)
+template <int CL>
+__device__ __forceinline__ int unit_of_round(int r, bool serp) {
+  const int P = (int)gridDim.x / CL, c = (int)blockIdx.x / CL;
+  return (serp && (r & 1)) ? (r + 1) * P - 1 - c : r * P + c;
 }
 
 // the product description of a launch's problem, resolved from its arguments; the tiling
 // (128 x BN tiles, units = tiles x groups) belongs to the kernel variant, not to the plan
-template <int BN, bool W32>
+// With CL = 2 a pair of CTAs (a cluster) computes a 256 x BN super-tile, one 128-row half
+// each; ntm then counts super-tile rows.
+template <int BN, bool W32, int CL = 1>
 __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*& gorder) {
   if (a0.done && *a0.done) return false;
   const GemmDesc* D = a0.dyn ? a0.dyn : &a0.d;
   if (!D->active || D->groups <= 0) return false;
-  if (a0.bn != BN || D->word32 != (W32 ? 1 : 0)) {
+  if (a0.bn != BN || a0.cl != CL || D->word32 != (W32 ? 1 : 0)) {
     // the tensor map's box or the exact-sum layout does not fit this variant: no product
     if (a0.flags) atomicOr(a0.flags, FLAG_CONFIG);
     return false;
@@ -243,7 +285,7 @@ __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*
   a.tmax = D->tmax;
   a.gs = D->gs;
   a.groups = D->groups;
-  a.ntm = (int)((a0.M + BM - 1) / BM);
+  a.ntm = (int)(((a0.M + BM - 1) / BM + CL - 1) / CL);
   a.ntn = (int)((a0.N + BN - 1) / BN);
   a.units = a.ntm * a.ntn * D->groups;
   a.out = a0.out;
@@ -300,9 +342,15 @@ struct GroupedSrc {
 
 // BN_ = 128: int64 Horner groups of gs anti-diagonals, 64 columns per epilogue thread.
 // BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
-template <int BN_, bool W32, class Src>
+// CL = 2: the CTA is one half of a pair (a 2-CTA cluster) working on 256 x BN super-tiles; both
+// halves need the same B panel, so each loads half of it and multicasts that half to both, and
+// each MMA releases a stage in both CTAs (a stage is refilled only once both have consumed it).
+template <int BN_, bool W32, int CL, class Src>
 __device__ __forceinline__ void tc_body(Src& src) {
   constexpr int BN = BN_;
+  static_assert(CL == 1 || CL == 2, "pairs of CTAs at most");
+  constexpr uint32_t HALF_B_BYTES = (BN / 2) * BK * 2;
+  constexpr uint16_t PAIR_MASK = 0x3;
   constexpr int STAGES = BN == 256 ? 4 : 6;
   constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
   constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
@@ -318,7 +366,7 @@ __device__ __forceinline__ void tc_body(Src& src) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&sm->full[s], 1);
-      mbar_init(&sm->empty[s], 1);
+      mbar_init(&sm->empty[s], CL);   // one release per consuming CTA
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->acc_full[b], 1);
@@ -336,6 +384,9 @@ __device__ __forceinline__ void tc_body(Src& src) {
   fence_before();
   __syncthreads();
   fence_after();
+  // the peer may signal this CTA's barriers only once they are initialised
+  if (CL > 1) cluster_sync_all();
+  const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
   const uint32_t tmem = sm->tmem_base;
   volatile int* abort = &sm->abort;
 
@@ -346,8 +397,10 @@ __device__ __forceinline__ void tc_body(Src& src) {
       uint32_t phase = 0;
       long long issued = 0;
       bool ok = !*abort;
-      for (int rnd = 0; (long long)rnd * gridDim.x < src.total() && ok; ++rnd) {
-        const int u = unit_of_round(rnd);
+      const int P = (int)gridDim.x / CL;
+      const bool serp = src.total() <= SERPENTINE_MAX_ROUNDS * P;
+      for (int rnd = 0; (long long)rnd * P < src.total() && ok; ++rnd) {
+        const int u = unit_of_round<CL>(rnd, serp);
         if (u >= src.total()) continue;
         int lu;
         src.unit(u, lu);
@@ -356,7 +409,8 @@ __device__ __forceinline__ void tc_body(Src& src) {
         const int tiles = a.ntm * a.ntn;
         const int grp = gorder[lu / tiles], tile = lu % tiles;
         int i0, j0;
-        tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
+        tile_origin(tile, a.ntm, a.ntn, BM * CL, BN, i0, j0);
+        i0 += (int)rank * BM;
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           for (int r = pair_lo(t, a.kR); r <= pair_hi(t, a.kL) && ok; ++r) {
@@ -367,9 +421,13 @@ __device__ __forceinline__ void tc_body(Src& src) {
                 break;
               }
               unsigned char* st = tiles_smem + stage * STAGE_BYTES;
-              mbar_expect_tx(&sm->full[stage], STAGE_BYTES);
+              mbar_expect_tx(&sm->full[stage], STAGE_BYTES);   // own A tile + the whole B tile
               tma_load_3d(st, src.mapL, kb * BK, i0, r - 1, &sm->full[stage]);
-              tma_load_3d(st + STAGE_A_BYTES, src.mapR, kb * BK, j0, s - 1, &sm->full[stage]);
+              if (CL == 1)
+                tma_load_3d(st + STAGE_A_BYTES, src.mapR, kb * BK, j0, s - 1, &sm->full[stage]);
+              else
+                tma_load_3d_mc(st + STAGE_A_BYTES + rank * HALF_B_BYTES, src.mapR, kb * BK,
+                               j0 + (int)rank * (BN / 2), s - 1, &sm->full[stage], PAIR_MASK);
               ++issued;
               if (++stage == STAGES) {
                 stage = 0;
@@ -414,8 +472,10 @@ __device__ __forceinline__ void tc_body(Src& src) {
       uint32_t acc_phase[2] = {0, 0};
       bool ok = true;
       bool any = false;
-      for (int rnd = 0; (long long)rnd * gridDim.x < src.total() && ok; ++rnd) {
-        const int u = unit_of_round(rnd);
+      const int P = (int)gridDim.x / CL;
+      const bool serp = src.total() <= SERPENTINE_MAX_ROUNDS * P;
+      for (int rnd = 0; (long long)rnd * P < src.total() && ok; ++rnd) {
+        const int u = unit_of_round<CL>(rnd, serp);
         if (u >= src.total()) continue;
         int lu;
         src.unit(u, lu);
@@ -448,7 +508,8 @@ __device__ __forceinline__ void tc_body(Src& src) {
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
                 mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), IDESC, (cnt > 0 || kk > 0) ? 1u : 0u);
-              mma_commit(&sm->empty[stage]);
+              if (CL == 1) mma_commit(&sm->empty[stage]);
+              else mma_commit_mc(&sm->empty[stage], PAIR_MASK);
               any = true;
               if (++stage == STAGES) {
                 stage = 0;
@@ -485,8 +546,10 @@ __device__ __forceinline__ void tc_body(Src& src) {
     int buf = 0;
     uint32_t acc_phase[2] = {0, 0};
     bool ok = true;
-    for (int rnd = 0; (long long)rnd * gridDim.x < src.total() && ok; ++rnd) {
-      const int u = unit_of_round(rnd);
+    const int P = (int)gridDim.x / CL;
+    const bool serp = src.total() <= SERPENTINE_MAX_ROUNDS * P;
+    for (int rnd = 0; (long long)rnd * P < src.total() && ok; ++rnd) {
+      const int u = unit_of_round<CL>(rnd, serp);
       if (u >= src.total()) continue;
       int lu;
       src.unit(u, lu);
@@ -495,7 +558,8 @@ __device__ __forceinline__ void tc_body(Src& src) {
       const int tiles = a.ntm * a.ntn;
       const int grp = gorder[lu / tiles], tile = lu % tiles;
       int i0, j0;
-      tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
+      tile_origin(tile, a.ntm, a.ntn, BM * CL, BN, i0, j0);
+      i0 += (int)rank * BM;
       const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
       for (int t = t0; t <= t1 && ok; ++t) {
@@ -543,15 +607,19 @@ __device__ __forceinline__ void tc_body(Src& src) {
   __syncthreads();
   fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  // neither CTA of a pair leaves while the other may still write to its shared memory
+  if (CL > 1) cluster_sync_all();
 }
 
 
-template <int BN_, bool W32>
+// CL = 2 is launched as 2-CTA clusters (both CTAs of a cluster take the same early exit: they
+// read the same arguments)
+template <int BN_, bool W32, int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
                     const __grid_constant__ TcArgs a0) {
   SingleSrc src;
-  if (!tc_run_of<BN_, W32>(a0, src.run, src.gorder)) return;
+  if (!tc_run_of<BN_, W32, CL>(a0, src.run, src.gorder)) return;
   src.mapL = &mapL;
   src.mapR = &mapR;
   src.flags0 = a0.flags;
@@ -559,7 +627,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapL) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapR) : "memory");
   }
-  tc_body<BN_, W32>(src);
+  tc_body<BN_, W32, CL>(src);
 }
 
 // Many problems in one persistent launch (batched refinement): every CTA forms the prefix
@@ -590,7 +658,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   src.mapL = src.mapR = nullptr;
   src.flags0 = probs[0].a.flags;
   memset(&src.run, 0, sizeof(src.run));
-  tc_body<BN_, W32>(src);
+  tc_body<BN_, W32, 1>(src);
 }
 
 // ---------------------------------------------------------------------------
@@ -645,37 +713,86 @@ int sm_count(int& sms) {
   return FRX_OK;
 }
 
-template <int BN, bool W32>
+// clusters of CL CTAs of this variant that can be resident at once (the persistent grid)
+template <int BN, bool W32, int CL>
+int resident_clusters(size_t smem, int sms, int& out) {
+  if (CL == 1) {
+    out = sms;
+    return FRX_OK;
+  }
+  static std::once_flag once;
+  static int n = 0;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [&]() {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(CL * (sms / CL)));
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    err = cudaOccupancyMaxActiveClusters(&n, k_plane_gemm_tc<BN, W32, CL>, &cfg);
+  });
+  FRX_CUDA_TRY(err);
+  out = n > 0 ? n : sms / CL;
+  return FRX_OK;
+}
+
+template <int BN, bool W32, int CL>
 int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
-  // tensor maps span the allocated planes (g.d.kL, g.d.kR: the capacity when d comes from the device)
+  // tensor maps span the allocated planes (g.d.kL, g.d.kR: the capacity when d comes from the
+  // device); a pair's CTAs each load half of the B tile
   CUtensorMap mL, mR;
   if (!make_map(&mL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
-  if (!make_map(&mR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, BN)) return FRX_E_CUDA;
+  if (!make_map(&mR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, BN / CL)) return FRX_E_CUDA;
   size_t smem = smem_bytes(BN);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&]() {
-    attr_err = cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_err =
+        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   FRX_CUDA_TRY(attr_err);
-  int sms = 0;
+  int sms = 0, clusters = 0;
   FRX_TRY(sm_count(sms));
-  const int64_t units =
-      a.dyn ? (int64_t)sms : ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups;
-  unsigned grid = (unsigned)(units < sms ? units : sms);
+  FRX_TRY((resident_clusters<BN, W32, CL>(smem, sms, clusters)));
+  const int64_t units = a.dyn ? (int64_t)clusters
+                              : (((g.M + BM - 1) / BM + CL - 1) / CL) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups;
+  const unsigned grid = (unsigned)(CL * (units < clusters ? units : clusters));
   if (grid == 0) return FRX_OK;
-  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  if (CL == 1) {
+    k_plane_gemm_tc<BN, W32, CL><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FRX_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_plane_gemm_tc<BN, W32, CL>, mL, mR, a));
+  }
   FRX_CUDA_TRY(cudaGetLastError());
-  last_tile_n() = BN;
   return FRX_OK;
 }
 
 size_t tc_problem_bytes() { return sizeof(TcProblem); }
 
 // one entry of a grouped launch's table (host memory), for a product with int32 planes and
-// output tiles of 128 x bn
-int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int bn) {
-  if (!plane_gemm_tc_supported(g) || !g.d.word32 || (bn != 128 && bn != 256)) return FRX_E_UNSUPPORTED;
+// one CTA per output tile (TILE_128x128 or TILE_128x256)
+int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int tile) {
+  if (!plane_gemm_tc_supported(g) || !g.d.word32 || (tile != TILE_128x128 && tile != TILE_128x256))
+    return FRX_E_UNSUPPORTED;
+  const int bn = tile_bn(tile);
   TcProblem* e = reinterpret_cast<TcProblem*>(host_entry);
   memset(e, 0, sizeof(TcProblem));
   if (!make_map(&e->mapL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
@@ -691,6 +808,7 @@ int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int bn) {
   e->a.dyn = g.dyn;
   e->a.done = g.done;
   e->a.bn = bn;
+  e->a.cl = 1;
   return FRX_OK;
 }
 
@@ -703,11 +821,13 @@ int prepare_plane_gemm_grouped() {
   return FRX_OK;
 }
 
-// all problems of `table` (device memory, `count` entries filled for tile width bn) in one
+// all problems of `table` (device memory, `count` entries filled for `tile`) in one
 // persistent launch
-int launch_plane_gemm_grouped(const void* table, int count, int bn, cudaStream_t s) {
+int launch_plane_gemm_grouped(const void* table, int count, int tile, cudaStream_t s) {
   if (count <= 0) return FRX_OK;
-  if (count > MAX_GROUPED || ((uintptr_t)table & 63) || (bn != 128 && bn != 256)) return FRX_E_UNSUPPORTED;
+  if (count > MAX_GROUPED || ((uintptr_t)table & 63) || (tile != TILE_128x128 && tile != TILE_128x256))
+    return FRX_E_UNSUPPORTED;
+  const int bn = tile_bn(tile);
   int sms = 0;
   FRX_TRY(sm_count(sms));
   const TcProblem* tab = reinterpret_cast<const TcProblem*>(table);
@@ -717,12 +837,13 @@ int launch_plane_gemm_grouped(const void* table, int count, int bn, cudaStream_t
     k_plane_gemm_tc_grouped<128, true><<<(unsigned)sms, NUM_THREADS, smem_bytes(128), s>>>(tab, count);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
-  last_tile_n() = bn;
+  last_tile() = tile;
   return FRX_OK;
 }
 
-// bn: output tile width (int32 planes: 128 or 256; int64 groups always use 128)
-int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int bn, cudaStream_t s) {
+// tile: TILE_128x128, TILE_128x256 or TILE_256x256 for int32 planes (int64 groups always use
+// 128 x 128 tiles)
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int tile, cudaStream_t s) {
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
@@ -734,14 +855,25 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int bn, cudaStream_t s)
   a.d = g.d;
   a.dyn = g.dyn;
   a.done = g.done;
+  a.cl = 1;
   if (!g.d.word32) {
     a.bn = 128;
-    return launch_variant<128, false>(g, a, s);
+    last_tile() = TILE_128x128;
+    return launch_variant<128, false, 1>(g, a, s);
   }
-  if (bn != 128 && bn != 256) return FRX_E_UNSUPPORTED;
-  a.bn = bn;
-  if (bn == 256) return launch_variant<256, true>(g, a, s);
-  return launch_variant<128, true>(g, a, s);
+  last_tile() = tile;
+  a.bn = tile_bn(tile);
+  switch (tile) {
+    case TILE_128x128:
+      return launch_variant<128, true, 1>(g, a, s);
+    case TILE_128x256:
+      return launch_variant<256, true, 1>(g, a, s);
+    case TILE_256x256:
+      a.cl = 2;
+      return launch_variant<256, true, 2>(g, a, s);
+    default:
+      return FRX_E_UNSUPPORTED;
+  }
 }
 
 }  // namespace frx

@@ -65,12 +65,12 @@ struct LaunchRecord {
   long long blocks;
   int threads;
   size_t smem;
-  int variant = 0;   // slice products: the output tile width the entry was filled for
+  int variant = 0;   // slice products: the tile configuration the entry was filled for
 };
 
 struct LaunchRecorder {
   std::vector<LaunchRecord> recs;
-  int tile_n = 256;  // tile width of the slice products recorded
+  int tile = 2;      // tile configuration of the slice products recorded (128 x 256)
 };
 
 // the calling host thread's active recorder (nullptr: launchers issue their kernels)

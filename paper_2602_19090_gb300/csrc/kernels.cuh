@@ -10,6 +10,12 @@ namespace frx {
 
 enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_RANGE = 4, FLAG_CONFIG = 8 };
 
+// Output tile configurations of the tensor-core products (the values of frx_set_tile):
+// 128 x 128 or 128 x 256 tiles per CTA, or 256 x 256 super-tiles per pair of CTAs (a 2-CTA
+// cluster sharing the B panel)
+enum : int { TILE_AUTO = 0, TILE_128x128 = 1, TILE_128x256 = 2, TILE_256x256 = 3 };
+inline int tile_bn(int cfg) { return cfg == TILE_128x128 ? 128 : 256; }
+
 // optional device-side parameters of the slicing kernels (null: use the launch arguments)
 struct SliceDyn {
   const int* nplanes = nullptr;  // planes to produce
@@ -53,7 +59,7 @@ struct PlaneGemm {
   int64_t ogs, ldo;
   int* flags;   // device status word (timeouts), may be null
   int out_bytes_per_elem;
-  int tile_n;   // output tile width of the tensor-core kernel (0: the autotuner decides)
+  int tile;     // output tile configuration of the tensor-core kernel (TILE_AUTO: the autotuner decides)
   __host__ __device__ int32_t* out32() const { return reinterpret_cast<int32_t*>(out); }
 };
 
@@ -64,24 +70,24 @@ int pairs_in(int kL, int kR, int T);
 // gemm_simt.cu / gemm_tc.cu
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s);
 int launch_plane_gemm_simt(const PlaneGemm& g, cudaStream_t s);
-int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int bn, cudaStream_t s);
+int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int tile, cudaStream_t s);
 bool plane_gemm_tc_supported(const PlaneGemm& g);
 // grouped slice products: a device table of per-problem entries (tensor maps + arguments,
 // 64-byte aligned, tc_problem_bytes() each) run in one persistent launch
 size_t tc_problem_bytes();
-int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int bn);
-int launch_plane_gemm_grouped(const void* table, int count, int bn, cudaStream_t s);
+int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int tile);
+int launch_plane_gemm_grouped(const void* table, int count, int tile, cudaStream_t s);
 int prepare_plane_gemm_grouped();
 // a zero (src == nullptr) or copy of 8-byte words recorded as a grouped-launch entry
 int record_bytes(void* dst, const void* src, size_t bytes);
 
-// autotune.cu: output tile width (128 or 256) of the tensor-core products
+// autotune.cu: output tile configuration (TILE_*) of the tensor-core products
 int tile_policy();
-int tune_tile_single(const PlaneGemm& g, int kind, cudaStream_t s, int& bn);
-int tune_tile_refine(const PlaneGemm& rep, cudaStream_t s, int& bn);
+int tune_tile_single(const PlaneGemm& g, int kind, cudaStream_t s, int& tile);
+int tune_tile_refine(const PlaneGemm& rep, cudaStream_t s, int& tile);
 int tune_tile_grouped(const std::vector<PlaneGemm>& gs, const std::vector<long long>& key, void* table,
-                      cudaStream_t s, int& bn);
-int& last_tile_n();
+                      cudaStream_t s, int& tile);
+int& last_tile();
 
 // refine_kernels.cu
 int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR, double* Ch, int64_t ldh,

@@ -185,7 +185,7 @@ __device__ __forceinline__ double i128_scaled_rn(i128 S, int ex) {
 
 // integer m with x = m * 2^G (x on the grid 2^G, |m| < 2^62)
 __device__ __forceinline__ i64 grid_mantissa(double x, int G) {
-  if (x == 0.0) return 0;
+  if (is_zero(x)) return 0;
   i64 P;
   int q;
   decompose(x, P, q);
@@ -267,7 +267,7 @@ constexpr int MP_UPDATE = 12;
 __device__ __forceinline__ bool dd_from_i128(i128 N, int ex, dd& out) {
   double h;
   if (!rn_scaled(N, ex, h)) return false;
-  if (h == 0.0) {
+  if (is_zero(h)) {
     out = dd{0.0, 0.0};
     return true;
   }
@@ -451,7 +451,7 @@ __device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
   }
   i64 L = 0;
   int qL = 0;
-  if (lam != 0.0) decompose(lam, L, qL);
+  if (!is_zero(lam)) decompose(lam, L, qL);
   u64 mx = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     double xi = x[i];
@@ -663,7 +663,7 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   // 128 bits for every row when the block-wide bounds say so; otherwise per row.
   i64 L = 0;
   int qL = 0;
-  if (lam != 0.0) decompose(lam, L, qL);
+  if (!is_zero(lam)) decompose(lam, L, qL);
   const int bL = L ? bitlen_u64(L < 0 ? (u64)0 - (u64)L : (u64)L) : 0;
   const int gq = gj + qL;
   const int dmax = emax > -(1 << 29) ? gq - (emin + cbase) : 0, dmin = emax > -(1 << 29) ? gq - (emax + cbase) : 0;
@@ -826,7 +826,7 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
 // sum is rounded on x1's grid with round-half-even on the combined integer.  Returns false
 // when the result leaves x1's binade (then the caller takes the general path).
 __device__ __forceinline__ bool add_small_rn(double x1, i64 N, int c, double& out) {
-  if (x1 == 0.0) return false;
+  if (is_zero(x1)) return false;
   i64 P;
   int q;
   decompose(x1, P, q);
@@ -880,7 +880,7 @@ __device__ __noinline__ double update_general(const UpdateArgs& a, double x1, in
 // RN(x1 + N 2^c) exactly in 128-bit integers; false when the aligned sum would not fit
 // or the result leaves the normal range
 __device__ __forceinline__ bool add_exact_rn(double x1, i128 N, int c, double& out) {
-  if (x1 == 0.0) return rn_scaled(N, c, out);
+  if (is_zero(x1)) return rn_scaled(N, c, out);
   i64 P;
   int q;
   decompose(x1, P, q);

@@ -48,17 +48,17 @@ def test_host_only_calls(lib):
     assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 18) > 0
 
 
-def test_tile_width_policy_is_host_only(lib):
+def test_tile_policy_is_host_only(lib):
     # the autotuner's switch and counters touch no device
-    assert lib.frx_set_tile_n(64) == -1
-    assert lib.frx_set_tile_n(128) == 0
-    assert lib.frx_set_tile_n(256) == 128
-    assert lib.frx_set_tile_n(0) == 256
+    assert lib.frx_set_tile(4) == -1 and lib.frx_set_tile(-1) == -1
+    assert lib.frx_set_tile(1) == 0
+    assert lib.frx_set_tile(3) == 1
+    assert lib.frx_set_tile(0) == 3
     m, d, h = ctypes.c_longlong(-1), ctypes.c_longlong(-1), ctypes.c_longlong(-1)
     assert lib.frx_tune_stats(ctypes.byref(m), ctypes.byref(d), ctypes.byref(h), 1) == 0
     assert lib.frx_tune_stats(ctypes.byref(m), ctypes.byref(d), ctypes.byref(h), 0) == 0
     assert (m.value, d.value, h.value) == (0, 0, 0)
-    assert lib.frx_last_tile_n() == 0
+    assert lib.frx_last_tile() == 0
 
 
 def test_argument_errors_before_any_device_work(lib):
