@@ -420,6 +420,9 @@ def run_batched(args):
     # per-matrix native-FP64 loop (cuBLAS DGEMM), once
     fstats, fp64_ms = {}, None
     if not args.no_fp64:
+        # one untimed pass first: cuBLAS loads its FP64 kernels for each new shape on first use
+        for A, x0, d0 in zip(As, X0s, D0s):
+            fp64_refine.refine(A, x0.clone(), d0.clone(), delta)
         torch.cuda.synchronize()
         s2 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
