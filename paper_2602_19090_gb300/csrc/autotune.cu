@@ -138,8 +138,13 @@ void store(const std::vector<long long>& key, int tile, bool measured) {
 // decide for `key` among `cands` from the model or by timing launch(cfg) for each; prepare()
 // runs once before the first timed launch
 template <class P, class F>
-int decide(const std::vector<long long>& key, const Shape& sh, const std::vector<int>& cands, P prepare, F launch,
-           cudaStream_t s, int& tile) {
+int decide(const std::vector<long long>& shape_key, const Shape& sh, const std::vector<int>& cands, P prepare,
+           F launch, cudaStream_t s, int& tile) {
+  // decisions belong to a device (a process may drive devices of different kinds)
+  int dev = 0;
+  FRX_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<long long> key = shape_key;
+  key.push_back(dev);
   const int forced = g_policy.load();
   if (forced != TILE_AUTO) {
     // a forced pair configuration falls back to single-CTA tiles where pairs are not offered

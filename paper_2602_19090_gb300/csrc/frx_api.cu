@@ -327,16 +327,16 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   return FRX_OK;
 }
 
-// dynamic shared memory limits of the refinement kernels, set once before any launch or capture
+// dynamic shared memory limits of the refinement kernels, set once per device before any
+// launch or capture
 int ensure_attributes() {
-  static std::once_flag once;
-  static int st = FRX_OK;
-  std::call_once(once, []() {
-    st = set_refine_kernel_attributes();
+  static PerDevice pd;
+  return once_per_device(pd, [](int) {
+    int st = set_refine_kernel_attributes();
     if (st == FRX_OK) st = set_plan_kernel_attributes();
     if (st == FRX_OK) st = prepare_plane_gemm_grouped();
+    return st;
   });
-  return st;
 }
 
 int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* D, int64_t n, double delta,

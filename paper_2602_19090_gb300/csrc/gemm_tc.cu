@@ -768,10 +768,9 @@ int resident_clusters(size_t smem, int sms, int& out) {
     out = sms;
     return FRX_OK;
   }
-  static std::once_flag once;
-  static int n = 0;
-  static cudaError_t err = cudaSuccess;
-  std::call_once(once, [&]() {
+  static PerDevice pd;
+  static int n[FRX_MAX_DEVICES] = {};
+  FRX_TRY(once_per_device(pd, [&](int dev) -> int {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(CL * (sms / CL)));
     cfg.blockDim = dim3(NUM_THREADS);
@@ -783,10 +782,12 @@ int resident_clusters(size_t smem, int sms, int& out) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    err = cudaOccupancyMaxActiveClusters(&n, k_plane_gemm_tc<BN, W32, CL>, &cfg);
-  });
-  FRX_CUDA_TRY(err);
-  out = n > 0 ? n : sms / CL;
+    FRX_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n[dev], k_plane_gemm_tc<BN, W32, CL>, &cfg));
+    return FRX_OK;
+  }));
+  int dev = 0;
+  FRX_CUDA_TRY(cudaGetDevice(&dev));
+  out = n[dev] > 0 ? n[dev] : sms / CL;
   return FRX_OK;
 }
 
@@ -798,13 +799,12 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   if (!make_map(&mL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
   if (!make_map(&mR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, BN / CL)) return FRX_E_CUDA;
   size_t smem = smem_bytes(BN);
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&]() {
-    attr_err =
-        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  FRX_CUDA_TRY(attr_err);
+  static PerDevice pd;
+  FRX_TRY(once_per_device(pd, [&](int) -> int {
+    FRX_CUDA_TRY(
+        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return FRX_OK;
+  }));
   int sms = 0, clusters = 0;
   FRX_TRY(sm_count(sms));
   FRX_TRY((resident_clusters<BN, W32, CL>(smem, sms, clusters)));

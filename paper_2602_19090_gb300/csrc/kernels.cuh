@@ -1,6 +1,7 @@
 // Launchers of the frx kernels (host-side declarations).
 #pragma once
 
+#include <mutex>
 #include <vector>
 
 #include "frx_internal.cuh"
@@ -9,6 +10,24 @@
 namespace frx {
 
 enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_RANGE = 4, FLAG_CONFIG = 8 };
+
+// One-time setup per CUDA device: kernel attributes and occupancy figures belong to a device,
+// so a process that drives several devices sets them on each.  f() runs once per device and
+// its status is returned for the current device on every call.
+constexpr int FRX_MAX_DEVICES = 64;
+struct PerDevice {
+  std::once_flag once[FRX_MAX_DEVICES];
+  int status[FRX_MAX_DEVICES] = {};
+};
+
+template <class F>
+int once_per_device(PerDevice& pd, F f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FRX_E_CUDA;
+  if (dev < 0 || dev >= FRX_MAX_DEVICES) return FRX_E_UNSUPPORTED;
+  std::call_once(pd.once[dev], [&]() { pd.status[dev] = f(dev); });
+  return pd.status[dev];
+}
 
 // Output tile configurations of the tensor-core products (the values of frx_set_tile):
 // 128 x 128 or 128 x 256 tiles per CTA, or 256 x 256 super-tiles per pair of CTAs (a 2-CTA
