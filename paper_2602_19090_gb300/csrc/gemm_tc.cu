@@ -6,13 +6,19 @@
 // of magnitude <= 2^12, so an FP32 accumulator holds exact integers as long as the
 // accumulated count stays <= 2^11 terms per lane (|sum| <= 2^23); the accumulator is
 // therefore drained into integer registers every CHUNK_KB k-blocks (and at the end of
-// every anti-diagonal t).  With BN = 256 each anti-diagonal's exact sum S_t is stored as
-// one int32 plane (while pairs * K * 4096 < 2^31); otherwise BN = 128 and the int64 sums
-// are combined in Horner form per group: R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
+// every anti-diagonal t).  With int32 planes each anti-diagonal's exact sum S_t is stored
+// as one plane (while pairs * K * 4096 < 2^31); otherwise BN = 128 and the int64 sums are
+// combined in Horner form per group: R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
 //
-// Persistent: one CTA per SM walks the units (output tile of 128 x BN, group of
-// anti-diagonals) in rounds (serpentine when there are few), groups ordered by decreasing work
-// and tiles in bands of TILE_BAND tile rows.  A grouped variant walks the units of many problems (the batched refinement).
+// Tile configurations (int32 planes): 128 x 128 or 128 x 256 output tiles per CTA, or
+// 256 x 256 super-tiles per pair of CTAs (a 2-CTA cluster: each CTA computes one 128-row
+// half, loads half of the shared B panel and multicasts it to both).  The configuration
+// changes no result; the autotuner picks it.
+//
+// Persistent: one CTA (or pair) per SM walks the units (output tile, anti-diagonal group)
+// in rounds (serpentine when there are few), groups ordered by decreasing work and tiles in
+// bands of TILE_BAND tile rows.  A grouped variant walks the units of many problems (the
+// batched refinement).
 // Warp roles:
 //   warp 0       TMA producer (3-D tensor maps over the plane stacks, 128B swizzle)
 //   warp 1       TMEM allocator and single-thread MMA issuer
