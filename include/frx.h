@@ -127,8 +127,11 @@ FRX_API size_t frx_refine_workspace_bytes(int64_t n, const frx_opts* opts);
  *   opts  (in,host) options, or NULL for the defaults.
  *   info  (out,host) may be NULL.
  * Errors: FRX_E_ARG, FRX_E_DELTA, FRX_E_NONFINITE, FRX_E_WORKSPACE, FRX_E_UNSUPPORTED
- * (n > FRX_MAX_N), FRX_E_RANGE, FRX_E_CUDA.  Synchronises `stream` several times per
- * iteration (the plan of each iteration is computed on the host).
+ * (n > FRX_MAX_N), FRX_E_RANGE, FRX_E_TIMEOUT, FRX_E_CUDA.  The plan of each iteration
+ * (beta, alpha, plane counts, the stopping test) is computed on the device; the host
+ * synchronises `stream` once per iteration to read the finish flag, and once more at the end
+ * to read the report.  The first call for a new n may time the tile configurations of the
+ * slice products (see frx_set_tile).
  */
 FRX_API int frx_refine(const double* A, int64_t lda, double* X, int64_t ldx, double* D, int64_t n,
                double delta, const frx_opts* opts, void* work, size_t work_bytes,
@@ -157,11 +160,13 @@ FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx
 /*
  * Batched refinement of `count` independent symmetric problems of possibly different
  * orders (each as in frx_refine, with the same delta and options).  A, X, D, lda, ldx and
- * n are HOST arrays of length `count` holding device pointers and sizes.  One iteration of
- * the whole batch is captured once into a CUDA graph (one independent branch per problem)
- * and replayed until every problem has converged, stagnated or reached max_iter; each
+ * n are HOST arrays of length `count` holding device pointers and sizes.  Every stage of
+ * an iteration runs as one grouped launch over all problems (the slice products as one
+ * persistent tensor-core launch); the iteration is captured once into a CUDA graph and
+ * replayed until every problem has converged, stagnated or reached max_iter.  Each
  * problem's plan lives on the device, so the host reads only an array of finish flags per
- * iteration.  `infos` (host, `count` entries) may be NULL.
+ * iteration.  Problems are processed in chunks of 2048.  Results equal those of
+ * frx_refine on each problem, bit for bit.  `infos` (host, `count` entries) may be NULL.
  * Returns FRX_OK if every problem converged, else the largest soft status (1, 2), or the
  * first hard error (< 0; the per-problem statuses are then in infos when it is not NULL).
  * The call must not be made while `stream` is being captured.
