@@ -165,8 +165,10 @@ FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx
  * persistent tensor-core launch); the iteration is captured once into a CUDA graph and
  * replayed until every problem has converged, stagnated or reached max_iter.  Each
  * problem's plan lives on the device, so the host reads only an array of finish flags per
- * iteration.  Problems are processed in chunks of 2048.  Results equal those of
- * frx_refine on each problem, bit for bit.  `infos` (host, `count` entries) may be NULL.
+ * iteration.  Problems are processed in chunks of 2048.  The refined X and D, the
+ * iteration and product counts equal those of frx_refine on each problem, bit for bit (the
+ * reported norms may differ in their last bits: columns are summed with another block
+ * size).  `infos` (host, `count` entries) may be NULL.
  * Returns FRX_OK if every problem converged, else the largest soft status (1, 2), or the
  * first hard error (< 0; the per-problem statuses are then in infos when it is not NULL).
  * The call must not be made while `stream` is being captured.
