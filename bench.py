@@ -449,8 +449,29 @@ def run_batched(args):
                        "speedup_ours": fp64_ms / ms} if fp64_ms else None),
         "clocks": clk,
     }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_batched(probs, delta)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_batched(probs, delta, budget_s=15.0):
+    """The CPU oracle's full refinement of the batch's matrices in order, until about
+    `budget_s` seconds have passed (at least one matrix): matrices/s over that sample."""
+    from oracle import refine as orf
+    t0 = time.perf_counter()
+    done, sizes = 0, []
+    for A, X0, D0 in probs:
+        orf.refine(A, X0, D0, delta, orf.Options())
+        done += 1
+        sizes.append(int(A.shape[0]))
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": done / t, "unit": "matrices/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"full oracle refinement of the batch's first {done} matrices (n = {sizes}) took "
+                       f"{t:.1f} s; the slice products use numpy's multithreaded FP64 BLAS, the rest is "
+                       f"single-threaded numpy")}
 
 
 def _timed_refine(api, A, X0, D0, delta, opts, work, reps=1):
@@ -726,6 +747,22 @@ def run_gemm_sweep(args):
                     out["cases"].append(rec)
                     print(json.dumps(rec), file=sys.stderr, flush=True)
             del A, B, work, Rh, Rl, mag, D
+    if not args.no_cpu_baseline:
+        # the CPU oracle's ozaki_gemm on one case of the sweep (n = 1024, phi = 2, 8 planes)
+        from oracle import ozaki as oz
+        n = 1024
+        A = synth.gemm_operand(n, n, 2.0, synth.seed_for(1, 14))
+        B = synth.gemm_operand(n, n, 2.0, synth.seed_for(1, 24))
+        base = {}
+        for mode in ("triangular", "full"):
+            t0 = time.perf_counter()
+            oz.ozaki_gemm(A, B, 8, mode)
+            t = time.perf_counter() - t0
+            base[mode] = {"seconds": t, "tflops_eq": 2.0 * n ** 3 / t / 1e12}
+        out["cpu_baseline"] = {"value": base["triangular"]["tflops_eq"], "unit": "TFLOPS-eq", "cores": os.cpu_count(),
+                               "kind": "oracle", "per_mode": base,
+                               "sample": "oracle ozaki_gemm, n = 1024, phi = 2, 8 planes per operand (the slice "
+                                         "products use numpy's multithreaded FP64 BLAS, exact for these sums)"}
     print(json.dumps(out), flush=True)
 
 
