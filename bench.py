@@ -567,6 +567,9 @@ def run_configs(args):
                        max_abs_diff_vs_fp64=float((Xb - X).abs().max()))
             out["variants_n2048"].append(rec)
             print(json.dumps(rec), file=sys.stderr, flush=True)
+            if not args.no_cpu_baseline and cond == 1e4 and variant == "spd" and delta == 1e-14:
+                # the CPU oracle beside the n = 2048 refinement, on the headline's sampled V product
+                out["cpu_baseline_n2048"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], args.sample_rows)
         del At, X0t, D0t
     del work
 
