@@ -266,7 +266,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 digit planes, int64 exact sums, f64/dd elsewhere",
+        "vs_baseline": None, "dtype": "bf16 digit planes, exact int32 plane sums, f64/dd elsewhere",
         "data": "synthetic",
         "config": {"workload": f"refine n={n} SPD geometric cond {args.cond:g}, start perturbed 1e-8, "
                                f"delta={delta:g}", "n": n, "cond": args.cond, "delta": delta,
@@ -438,7 +438,7 @@ def run_batched(args):
         "value": job_throughput(ws, args.count, ms),
         "unit": "matrices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16 digit planes, int64 exact sums, f64/dd elsewhere", "data": "synthetic",
+        "dtype": "bf16 digit planes, exact int32 plane sums, f64/dd elsewhere", "data": "synthetic",
         "config": {"workload": f"batched: {args.count} matrices, n ~ U[32, 512], cond log-uniform [1e2, 1e12], "
                                f"start perturbed 1e-8, delta={delta:g}", "count": args.count,
                    "n_min": int(sizes.min()), "n_max": int(sizes.max()), "delta": delta},
