@@ -268,6 +268,16 @@ FRX_API void frx_profile_enable(int on);
 FRX_API int frx_profile_read(frx_profile* out, int reset);
 
 /*
+ * Self-test of the bounded device waits.  Every wait of the tensor-core kernels on an
+ * mbarrier gives up after 2 s (by the global timer), raises a flag and returns, so that a call
+ * whose device work stalls reports FRX_E_TIMEOUT instead of hanging.  This call runs one such
+ * wait on a barrier that nothing completes and returns what a stalled call returns:
+ * FRX_E_TIMEOUT, after about 2 s.  `work`: at least 256 bytes of device scratch, 256-byte
+ * aligned.  Synchronises `stream`; the context stays usable afterwards.
+ */
+FRX_API int frx_check_wait_timeout(void* work, size_t work_bytes, void* stream);
+
+/*
  * Tile autotuner of the slice products (no counterpart in the paper; it changes the time of
  * a product, never its result: every tile sum is exact).
  *   The tensor-core kernel covers a product's m x n output with one of three tile

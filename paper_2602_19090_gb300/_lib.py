@@ -63,6 +63,7 @@ _SIGS = {
                                         c_i64, C.c_int, C.c_int, c_p]),
     "frx_profile_enable": (None, [C.c_int]),
     "frx_profile_read": (C.c_int, [C.POINTER(Profile), C.c_int]),
+    "frx_check_wait_timeout": (C.c_int, [c_p, C.c_size_t, c_p]),
     "frx_set_tile": (C.c_int, [C.c_int]),
     "frx_last_tile": (C.c_int, []),
     "frx_tune_stats": (C.c_int, [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),

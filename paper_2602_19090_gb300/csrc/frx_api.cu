@@ -809,6 +809,15 @@ int frx_refine_batched(const double* const* A, const int64_t* lda, double* const
   return refine_batched_impl(A, lda, X, ldx, D, n, count, delta, o, work, work_bytes, infos, s);
 }
 
+int frx_check_wait_timeout(void* work, size_t work_bytes, void* stream) {
+  if (!work || !aligned256(work) || work_bytes < 256) return FRX_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* flags = (int*)work;
+  FRX_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  FRX_TRY(launch_wait_timeout(flags, s));
+  return check_flags(flags, s);
+}
+
 size_t frx_ozaki_gemm_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices) {
   if (m < 1 || n < 1 || k < 1 || slices < 1 || slices > MAX_PLANES) return 0;
   return carve_gemm(nullptr, m, n, k, slices).bytes;

@@ -715,6 +715,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   tc_body<BN_, W32, 1>(src);
 }
 
+// A wait that nothing completes (no thread ever arrives on the barrier): the bounded wait of
+// the slice-product kernels must give up after its limit, raise FLAG_TIMEOUT and return, so
+// that the host reads an error status and the context stays usable.
+__global__ void k_wait_timeout(int* flags) {
+  __shared__ uint64_t bar;
+  __shared__ int abort;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, &abort, flags);   // phase 0 never completes
+}
+
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -840,6 +855,13 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
 }
 
 size_t tc_problem_bytes() { return sizeof(TcProblem); }
+
+int launch_wait_timeout(int* dflags, cudaStream_t s) {
+  k_wait_timeout<<<1, 32, 0, s>>>(dflags);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
+}
 
 // one entry of a grouped launch's table (host memory), for a product with int32 planes and
 // one CTA per output tile (TILE_128x128 or TILE_128x256)

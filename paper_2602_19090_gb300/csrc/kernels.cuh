@@ -97,6 +97,8 @@ size_t tc_problem_bytes();
 int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int tile);
 int launch_plane_gemm_grouped(const void* table, int count, int tile, cudaStream_t s);
 int prepare_plane_gemm_grouped();
+// a device wait that nothing completes (self-test of the bounded waits)
+int launch_wait_timeout(int* dflags, cudaStream_t s);
 // a zero (src == nullptr) or copy of 8-byte words recorded as a grouped-launch entry
 int record_bytes(void* dst, const void* src, size_t bytes);
 

@@ -48,6 +48,11 @@ def test_host_only_calls(lib):
     assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 18) > 0
 
 
+def test_wait_self_test_checks_its_scratch_first(lib):
+    assert lib.frx_check_wait_timeout(None, 256, None) == -5
+    assert lib.frx_check_wait_timeout(ctypes.c_void_p(256), 128, None) == -5
+
+
 def test_tile_policy_is_host_only(lib):
     # the autotuner's switch and counters touch no device
     assert lib.frx_set_tile(4) == -1 and lib.frx_set_tile(-1) == -1

@@ -99,3 +99,27 @@ def test_ozaki_gemm_longest_inner_dimension_int64_groups(api):
     mag = np.abs(A) @ np.abs(B)
     assert np.all(np.abs((Ch - o["hi"]) + (Cl - o["lo"])) <= mag * 2.0 ** -100)
     assert np.all(np.abs(Ch - C_ref) <= np.spacing(np.abs(C_ref)))
+
+
+def test_bounded_wait_reports_timeout_and_the_context_survives(api):
+    # a device wait on an mbarrier that nothing completes gives up after its limit (2 s),
+    # the call reports FRX_E_TIMEOUT, and the next call on the same context works
+    import ctypes
+    import time
+
+    import torch
+    from paper_2602_19090_gb300 import _lib
+    g = G()
+    lib = _lib.load()
+    work = api.workspace(256, g.dev())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    t0 = time.perf_counter()
+    st = lib.frx_check_wait_timeout(ctypes.c_void_p(work.data_ptr()), 256, stream)
+    elapsed = time.perf_counter() - t0
+    assert st == -6
+    assert 1.5 < elapsed < 60
+    A = synth.gemm_operand(70, 90, 1.0, 340)
+    B = synth.gemm_operand(90, 50, 1.0, 341)
+    C = api.ozaki_gemm(g.to_dev(A), g.to_dev(B), 8, "full").cpu().numpy()
+    C_ref, _ = oz.ozaki_gemm(A, B, 8, "full")
+    assert np.all(np.abs(C - C_ref) <= np.spacing(np.abs(C_ref)))
