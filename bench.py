@@ -638,7 +638,7 @@ def run_configs(args):
 
 def run_previous(args):
     """The proposed truncation of X (Sec. 3, beta rule) against the "previous study" form in
-    which X is sliced at full FP64 width (8 digit planes), at the settings of the paper's
+    which X is sliced at full FP64 width (7 digit planes), at the settings of the paper's
     convergence figures (cond 1e10, n = 1024/4096/8192, delta = 1e-8/1e-10/1e-12): products,
     iterations and time of both, and their ratio (the paper's 4/3 - 2x claim counts products)."""
     import torch
@@ -660,7 +660,7 @@ def run_previous(args):
         work = api.workspace(api.refine_workspace_bytes(n), dev)
         for delta in (1e-8, 1e-10, 1e-12):
             ms_p, ip, Xp = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work, reps=2)
-            ms_q, iq, Xq = _timed_refine(api, At, X0t, D0t, delta, api.Options(x_planes=8), work, reps=2)
+            ms_q, iq, Xq = _timed_refine(api, At, X0t, D0t, delta, api.Options(x_planes=7), work, reps=2)
             ms_x, ix, Xx = _timed_refine(api, At, X0t, D0t, delta, api.Options(xi=1.0), work, reps=2)
             rec = {"n": n, "delta": delta,
                    "proposed_xi1": {"ms": ms_x, "status": ix["status_name"], "iters": ix["iters"],
@@ -682,7 +682,7 @@ def run_previous(args):
     work = api.workspace(api.refine_workspace_bytes(n), dev)
     for delta in (1e-8, 1e-10, 1e-12):
         ms_p, ip, Xp = _timed_refine(api, At, X0t, D0t, delta, api.Options(), work, reps=2)
-        ms_q, iq, Xq = _timed_refine(api, At, X0t, D0t, delta, api.Options(x_planes=8), work, reps=2)
+        ms_q, iq, Xq = _timed_refine(api, At, X0t, D0t, delta, api.Options(x_planes=7), work, reps=2)
         ms_x, ix, Xx = _timed_refine(api, At, X0t, D0t, delta, api.Options(xi=1.0), work, reps=2)
         rec = {"n": n, "delta": delta,
                "proposed_xi1": {"ms": ms_x, "status": ix["status_name"], "iters": ix["iters"],
@@ -698,9 +698,9 @@ def run_previous(args):
 
 
 def run_gemm_sweep(args):
-    """ozaki_gemm over n = 1024/4096/8192, phi = 0.5/2/4, k = 4/8/12/18 planes, both product
+    """ozaki_gemm over n = 1024/4096/8192, phi = 0.5/2/4, k = 4/8/12/16 planes, both product
     sets: time (CUDA events, best of 3), TFLOPS-eq = 2 n^3 / time, the slice-product kernel's own
-    rate, and the error against the same product at 18 planes with all pairs (126 bits of each
+    rate, and the error against the same product at 16 planes with all pairs (128 bits of each
     operand), relative to |A||B|; a DGEMM's error on the same scale is given for context."""
     import torch
 
@@ -716,13 +716,13 @@ def run_gemm_sweep(args):
             # column-major operands, so that the timed calls do no layout copies
             A = api.colmajor(torch.from_numpy(synth.gemm_operand(n, n, phi, synth.seed_for(1, 10 + int(phi * 2)))).to(dev))[0]
             B = api.colmajor(torch.from_numpy(synth.gemm_operand(n, n, phi, synth.seed_for(1, 20 + int(phi * 2)))).to(dev))[0]
-            work = api.workspace(api.ozaki_gemm_workspace_bytes(n, n, n, 18), dev)
-            Rh, Rl = api.ozaki_gemm(A, B, 18, "full", return_lo=True, work=work)
+            work = api.workspace(api.ozaki_gemm_workspace_bytes(n, n, n, 16), dev)
+            Rh, Rl = api.ozaki_gemm(A, B, 16, "full", return_lo=True, work=work)
             mag = torch.abs(A) @ torch.abs(B)
             mag = torch.where(mag > 0, mag, torch.ones_like(mag))
             D = A @ B
             dgemm_err = float((((D - Rh) - Rl).abs() / mag).max())
-            for k in (4, 8, 12, 18):
+            for k in (4, 8, 12, 16):
                 for mode in ("triangular", "full"):
                     C = api.ozaki_gemm(A, B, k, mode, work=work)
                     torch.cuda.synchronize()

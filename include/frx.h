@@ -7,11 +7,11 @@
  * the Sec. 3 modification (X^ is replaced by its beta-truncated first slice X^(1),
  * eq. tau / eq. x, and A X^(1) is formed by n_A error-free slice products,
  * eq. mat_mul) and the Sec. 4.1 choice of alpha and beta.  The error-free slices
- * of Sec. 2.3 (eq. sigma, eq. a) are taken on a fixed 7-bit digit grid so that
- * every slice is an integer digit in [-64, 64]: slice r of a row (or column) whose
- * maximum magnitude v satisfies 2^(e-1) < v <= 2^e has weight 2^(e + 1 - 7r).
- * Slice products run on the tensor cores with exact integer accumulation and are
- * recombined in double-double.
+ * of Sec. 2.3 (eq. sigma, eq. a) are taken on a fixed 8-bit digit grid so that
+ * every slice is an integer digit in [-128, 128] (exact in bfloat16): slice r of a row
+ * (or column) whose maximum magnitude v satisfies 2^(e-1) < v <= 2^e has weight
+ * 2^(e + 1 - 8r).  Slice products run on the tensor cores with exact integer
+ * accumulation and are recombined in double-double.
  *
  * Conventions for every call below:
  *  - Matrices are FP64, column-major, with a leading dimension ld >= rows
@@ -70,16 +70,16 @@ typedef struct {
   int theory_alpha;      /* 0: alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1);
                             1: alpha = 53 - beta + ceil(log2 n) (eq. proposed_beta)           */
   int beta_override;     /* < 0: use the rule; else a fixed beta (clamped to [3, 47])          */
-  int k_cap;             /* largest number of digit planes per operand, 1..18                  */
+  int k_cap;             /* largest number of digit planes per operand, 1..16                  */
   int max_iter;          /* iteration limit (>= 1)                                           */
   double xi_stop;        /* <= 0: n.  Stop when step^2 * max|lam| / (xi_stop * gap) <= delta  */
   double cluster_omega;  /* >= 0: |lam_j - lam_i| <= omega is a cluster pair (0: only equal
                             estimates); < 0: Ogita-Aishima threshold
                             2 (||W||_F + max|lam| ||diag R||_2) each iteration              */
-  int x_planes;          /* 0: X^(1) from the Sec. 3 truncation (beta rule).  1..8: X is kept at
+  int x_planes;          /* 0: X^(1) from the Sec. 3 truncation (beta rule).  1..7: X is kept at
                             x_planes digit planes (rounded to the last plane's grid, beta =
-                            54 - 7 x_planes) with no truncation rule: the "previous study"
-                            form of Sec. 4 (both operands sliced; 8 planes = full FP64 width) */
+                            54 - 8 x_planes) with no truncation rule: the "previous study"
+                            form of Sec. 4 (both operands sliced; 7 planes = full FP64 width) */
   int sparse_rule;       /* 0: the dense Sec. 4.1 beta rule.  1: the sparse-matrix rule of Sec. 4
                             (xi = min(k, sqrt n)^2, alpha = 53 - beta + ceil(log2 k)) with k the
                             largest number of nonzeros in a row of A, counted on the device   */
@@ -185,13 +185,15 @@ FRX_API size_t frx_ozaki_gemm_workspace_bytes(int64_t m, int64_t n, int64_t k, i
 /*
  * C = A B by the Ozaki scheme (Sec. 2.3): A (m x k) is split by rows and B (k x n)
  * by columns into `slices` digit planes each (eq. sigma/tau, eq. a/x on the fixed
- * 7-bit grid); the products of the selected plane pairs (FRX_MODE_FULL: all
+ * 8-bit grid); the products of the selected plane pairs (FRX_MODE_FULL: all
  * slices^2; FRX_MODE_TRIANGULAR: r + s <= slices + 1) are exact integer matrices,
  * recombined exactly per anti-diagonal and rounded: C = RN(C_hi + C_lo).
  *   C_lo (out, optional) receives the low word of the double-double result
  *   (ld = ldc).  When the planes hold A and B exactly and mode is FULL, C_hi + C_lo
  *   equals the exact product to about 2^-104 relative.
- * slices in [1, 18]; m, n, k in [1, 2^20] with k <= 65536; A, B finite.
+ * slices in [1, 16]; m, n, k in [1, 2^20] with k <= 65536; A, B finite.  The exact sums
+ * are int32 planes while (pairs per anti-diagonal) * k * 2^14 < 2^31, int64 groups beyond
+ * (slower).
  */
 FRX_API int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_t ldb,
                    double* C, int64_t ldc, double* C_lo, int64_t m, int64_t n, int64_t k,
@@ -229,7 +231,7 @@ FRX_API int frx_ozaki_gemm_static(const double* A, int64_t lda, const double* B,
  *     column for axis 1; pitch >= the other dimension, multiple of 8; the pad is zero).
  *   frx_plane_products: the exact anti-diagonal sums of the slice products grouped
  *     into int64 words: out[g * n * m + j * m + i] = sum over t in group g of
- *     2^(7 (t_last(g) - t)) * sum_{r + s = t, r <= kL, s <= kR, t <= T} (L_r R_s)_ij,
+ *     2^(8 (t_last(g) - t)) * sum_{r + s = t, r <= kL, s <= kR, t <= T} (L_r R_s)_ij,
  *     groups of `frx_group_size(...)` consecutive t starting at t = 2.
  */
 FRX_API size_t frx_exponents_workspace_bytes(int64_t rows);

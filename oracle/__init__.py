@@ -8,7 +8,7 @@ It is a plain, slow, independent restatement of the paper in numpy:
 
 * ``ddarith``  -- TwoSum, pair arithmetic (Sec. 2.2) and double-double helpers.
 * ``ozaki``    -- the error-free splitting of Sec. 2.3 (eq. sigma, tau, a, x) on a
-  fixed 7-bit digit grid, exact integer slice products, recombination.
+  fixed 8-bit digit grid, exact integer slice products, recombination.
 * ``refine``   -- Algorithm 1 with the Sec. 3 modification (X <- X^(1), n_A-slice
   accurate product) and the Sec. 4.1 choice of alpha and beta; stopping test.
 * ``truth``    -- reference eigenvectors of a stored matrix by double-double

@@ -4,16 +4,17 @@ ORACLE: test infrastructure only.
 
 Reading of eq. sigma and eq. a used throughout (the "digit grid"):
 for a vector with maximum magnitude v > 0 let e = ceil(log2 v) (so v <= 2^e);
-slice r of an entry is taken on the grid w_r = 2^(e + 1 - 7r).  This is the
-paper's sigma-trick a^(r) = fl((sigma + a_res) - sigma) with a fixed
-sigma_r = 0.75 * 2^(e + 54 - 7r) (ulp(sigma_r) = w_r) instead of a rescan of the
-residual's maximum, so every slice is an integer digit d with |d| <= 64 times
-w_r, i.e. it fits a signed 8-bit integer and is exact in bfloat16.  Residuals
-obey |res_r| <= w_r / 2 = 2^(e - 7r), the analogue of eq. minamihata.
+slice r of an entry is taken on the grid w_r = 2^(e + 1 - 8r) (DIGIT_BITS = 8
+bits per slice).  This is the paper's sigma-trick a^(r) = fl((sigma + a_res) - sigma)
+with a fixed sigma_r = 0.75 * 2^(e + 54 - 8r) (ulp(sigma_r) = w_r) instead of a
+rescan of the residual's maximum, so every slice is an integer digit d with
+|d| <= 128 times w_r, exact in bfloat16 (whose 8-bit significand holds every
+integer up to 256).  Residuals obey |res_r| <= w_r / 2 = 2^(e - 8r), the analogue
+of eq. minamihata.
 A zero vector gets exponent EZERO and all-zero digits (sigma = 0 in eq. sigma).
 
 A product C = L R with L sliced by rows (exponents eL_i) and R by columns (eR_j)
-is  C_ij = sum_{(r,s)} 2^(eL_i + eR_j + 2 - 7(r+s)) * sum_k dL_r[i,k] dR_s[k,j],
+is  C_ij = sum_{(r,s)} 2^(eL_i + eR_j + 2 - 8(r+s)) * sum_k dL_r[i,k] dR_s[k,j],
 the inner sums being exact integers (eq. after alp_beta: every slice product is
 exact).  The pair set keeps r + s <= T (T = kL + kR: all pairs; T = k + 1: the
 triangular k(k+1)/2 form cited after eq. alp_beta).
@@ -27,7 +28,9 @@ import numpy as np
 from . import ddarith as dd
 
 EZERO = -(1 << 30)   # exponent of an all-zero vector
-DIGIT_BITS = 7       # bits per digit plane (|digit| <= 64)
+DIGIT_BITS = 8       # bits per digit plane (|digit| <= 2^(DIGIT_BITS - 1) = 128)
+DIGIT_MAX = 1 << (DIGIT_BITS - 1)
+MAX_PLANES = 16      # planes per operand (128 bits)
 
 
 def ceil_log2(m):
@@ -52,7 +55,7 @@ def col_exponents(M):
 
 
 def plane_weight(e, r):
-    """w_r = 2^(e + 1 - 7r); 0 for a zero vector."""
+    """w_r = 2^(e + 1 - DIGIT_BITS r); 0 for a zero vector."""
     e = np.asarray(e, dtype=np.int64)
     w = np.ldexp(1.0, np.where(e == EZERO, 0, e + 1 - DIGIT_BITS * r))
     return np.where(e == EZERO, 0.0, w)
@@ -88,7 +91,7 @@ def slice_cols(M, k, f=None):
 
 
 def sigma_trick_slice(res, e, r):
-    """Eq. a with sigma_r = 0.75 * 2^(e + 54 - 7r): fl((sigma + res) - sigma), per row."""
+    """Eq. a with sigma_r = 0.75 * 2^(e + 54 - DIGIT_BITS r): fl((sigma + res) - sigma), per row."""
     e = np.asarray(e, dtype=np.int64)
     sig = np.where(e == EZERO, 0.0, 0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + 54 - DIGIT_BITS * r)))
     sig = sig[:, None]
@@ -117,14 +120,14 @@ def pair_set(kL, kR, T):
 def slice_products(dL, dR, pairs):
     """S_t = sum over pairs with r + s = t of dL_r @ dR_s, exact int64 matrices.
 
-    Every entry of dL_r @ dR_s is a sum of K integer terms of magnitude <= 64 * 64 = 2^12,
-    so all its partial sums are integers of magnitude <= K * 2^12.  While that bound is
+    Every entry of dL_r @ dR_s is a sum of K integer terms of magnitude <= 128 * 128 = 2^14,
+    so all its partial sums are integers of magnitude <= K * 2^14.  While that bound is
     below 2^53 an FP64 matrix product is exact whatever its summation order, and the
     library routine evaluates it; otherwise the products are taken in int64.
     """
     S = {}
     K = dL.shape[-1]
-    exact_f64 = K * 4096 < 2 ** 53
+    exact_f64 = K * DIGIT_MAX * DIGIT_MAX < 2 ** 53
     if exact_f64:
         fL = dL.astype(np.float64)
         fR = dR.astype(np.float64)
@@ -147,7 +150,7 @@ def _scale_exponents(eL, eR, t):
 
 
 def recombine_dd(S, eL, eR, shape):
-    """sum_t S_t * 2^(eL_i + eR_j + 2 - 7t) as a double-double.
+    """sum_t S_t * 2^(eL_i + eR_j + 2 - DIGIT_BITS t) as a double-double.
 
     Terms are added from the least significant t upwards with TwoSum; each term
     is exact in FP64 (|S_t| < 2^53 is asserted).

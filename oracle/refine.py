@@ -7,7 +7,7 @@ One iteration (Algorithm 1 with the Sec. 3 modification, eq. mat_mul):
          xi = n), alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1), using the
          previous eigenvalue estimates (the circularity is broken by lagging them);
   X1     = fl((tau_j + x_ij) - tau_j), tau_j = 0.75 2^ceil(log2 w_j) 2^beta (eq. tau, x);
-  V      = accurate A X1 from exact 7-bit digit-plane products (line 1, eq. mat_mul);
+  V      = accurate A X1 from exact 8-bit digit-plane products (line 1, eq. mat_mul);
   r_i    = 1 - x1_i^T x1_i                                            (line 2);
   lam_i  = x1_i^T v_i / (1 - r_i)                                     (line 3);
   W      = X1^T (V - X1 diag(lam))                                    (line 4);
@@ -15,14 +15,19 @@ One iteration (Algorithm 1 with the Sec. 3 modification, eq. mat_mul):
   X      <- RN(X1 + X1 E~) by pair arithmetic                         (line 6, Sec. 2.2).
 
 Readings where the paper is silent (each also listed in the design notes):
-* digit planes: 7-bit digits on a fixed grid (see ``ozaki``); X1 is exactly the
-  first s_X = ceil((54 - beta) / 7) planes' worth of bits, so V's products are
+* digit planes: 8-bit digits on a fixed grid (see ``ozaki``); X1 is exactly the
+  first s_X = ceil((54 - beta) / 8) planes' worth of bits, so V's products are
   all exact and only the truncation of A to k_V planes (and of the pair set to
   r + s <= k_V + 1) is approximate;
 * slice counts (the paper sweeps n_A by hand): k = smallest k with
-  (2^(7k - eL - eR - 6) tau)^2 >= n^3, i.e. 64 n^1.5 2^(eL+eR) 2^(-7k) <= tau,
-  where eL, eR are the operands' largest exponents and tau = delta * g for V and
-  W, delta for the update product;  a fixed k_V may be forced (``slices_A``);
+  (2^(8k - eL - eR - 7) tau)^2 >= n^3, i.e. 128 n^1.5 2^(eL+eR) 2^(-8k) <= tau
+  (the first dropped anti-diagonal's digits are at most 128 = 2^7 on the grid
+  2^(eL + eR + 2 - 8(k + 1))), where eL, eR are the operands' largest exponents and
+  tau = delta * g for V and W, delta for the update product;  a fixed k_V may be
+  forced (``slices_A``);
+* the slice products' exact int32 sums need pairs * n * 2^14 < 2^31: the update
+  product (up to k_U pairs per anti-diagonal) takes at most floor((2^17 - 1) / n)
+  planes (16 for n < 8192); V's and W's pairs are at most s_X <= 7;
 * beta is clamped to [3, 47] (tau-trick valid, X1 keeps at least one plane);
 * stopping test: ||E~|| cannot fall below ||X^(2)|| (every step re-corrects the
   truncated tail), so the test uses the observed step d_k = ||X_k - X_{k-1}||_F:
@@ -115,15 +120,21 @@ def alpha_rule(n, beta, opts: Options) -> int:
 
 
 def slices_for(n, eL, eR, tau, k_cap):
-    """Smallest k >= 1 with (2^(7k - eL - eR - 6) * tau)^2 >= n^3, capped."""
+    """Smallest k >= 1 with (2^(8k - eL - eR - 7) * tau)^2 >= n^3, capped."""
     if eL == oz.EZERO or eR == oz.EZERO:
         return 0
     n3 = float(n) ** 3
     for k in range(1, k_cap + 1):
-        v = math.ldexp(tau, 7 * k - int(eL) - int(eR) - 6)
+        v = math.ldexp(tau, oz.DIGIT_BITS * k - int(eL) - int(eR) - (oz.DIGIT_BITS - 1))
         if v * v >= n3:
             return k
     return k_cap
+
+
+def int32_planes(n):
+    """Largest k with k * n * 2^14 < 2^31 (exact int32 sums of up to k pairs of products
+    of two 8-bit digits over n terms)."""
+    return (2 ** 31 - 1) // (n * oz.DIGIT_MAX * oz.DIGIT_MAX)
 
 
 def sum_pow4(f):
@@ -137,10 +148,10 @@ def plan(A, X, lam_prev, delta, opts: Options, omega_prev=0.0):
     g, Lam = min_gap(lam_prev, omega_prev)
     S2 = sum_pow4(f)
     # previous-study form: X represented by x_planes digit planes, i.e. rounded to the grid
-    # of plane x_planes, which is the tau grid of beta = 54 - 7 x_planes
+    # of plane x_planes, which is the tau grid of beta = 54 - 8 x_planes
     kmax = max(int(np.max(np.count_nonzero(A, axis=1))), 1)
     if opts.x_planes > 0:
-        beta = 54 - 7 * opts.x_planes
+        beta = 54 - oz.DIGIT_BITS * opts.x_planes
     elif opts.sparse_rule:
         # Sec. 4 (sparse matrices): gamma min(k, sqrt n) sqrt(1 / S2) / (0.75 u) with
         # gamma = sqrt(delta gap / max|lam|) is the Sec. 4.1 form with xi = min(k, sqrt n)^2
@@ -148,7 +159,7 @@ def plan(A, X, lam_prev, delta, opts: Options, omega_prev=0.0):
     else:
         beta = beta_rule(n, delta, g, Lam, S2, opts)
     alpha = 53 - beta + ceil_log2_int(kmax) if opts.sparse_rule else alpha_rule(n, beta, opts)
-    sX = -(-(54 - beta) // 7)
+    sX = -(-(54 - beta) // oz.DIGIT_BITS)
     eA = oz.row_exponents(A)
     eAmax = int(np.max(eA))
     fmax = int(np.max(f))
@@ -223,7 +234,7 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
     # line 6: X <- accsum(X1, X1 E~): U = X1 E~ (rows of X1, columns of E~)
     rho = oz.row_exponents(X1)
     eta = oz.col_exponents(E)
-    kU = slices_for(n, int(np.max(rho)), int(np.max(eta)), delta, opts.k_cap)
+    kU = min(slices_for(n, int(np.max(rho)), int(np.max(eta)), delta, opts.k_cap), int32_planes(n))
     if kU > 0:
         Up = oz.ozaki_product(X1, E, kU, kU, kU + 1, eL=rho, eR=eta, exact=exact)
         ch, cl = dd.pair_add(X1, Up["hi"], Up["lo"])

@@ -166,7 +166,8 @@ struct DebugOut {
 int validate_opts(const frx_opts& o) {
   if (o.k_cap < 1 || o.k_cap > MAX_PLANES || o.max_iter < 1 || o.slices_A < 0 || o.slices_A > o.k_cap)
     return FRX_E_ARG;
-  if (o.x_planes < 0 || o.x_planes > 8) return FRX_E_ARG;
+  // x_planes digit planes of X: at most ceil(56 / DIGIT_BITS), the full FP64 width
+  if (o.x_planes < 0 || o.x_planes > (56 + DIGIT_BITS - 1) / DIGIT_BITS) return FRX_E_ARG;
   if (o.sparse_rule != 0 && o.sparse_rule != 1) return FRX_E_ARG;
   return FRX_OK;
 }
@@ -204,9 +205,9 @@ PlaneGemm dyn_gemm(const __nv_bfloat16* L, int capL, const __nv_bfloat16* R, int
 }
 
 // the representative product the autotuner times for a refinement of order n: 8 planes of
-// A (fewer when k_cap is smaller) against 7 planes of X^(1), the triangular set r + s <= kL + 1
+// A (fewer when k_cap is smaller) against 5 planes of X^(1), the triangular set r + s <= kL + 1
 PlaneGemm tuning_gemm(const RefineWs& ws, int64_t n, int kcap) {
-  const int kL = kcap < 8 ? kcap : 8, kR = 7;
+  const int kL = kcap < 8 ? kcap : 8, kR = 5;
   PlaneGemm g = make_gemm(ws.Ap, ws.ps, ws.Xp, ws.ps, ws.pitch, n, n, n, kL, kR, kL + 1, ws.groups);
   g.out_bytes_per_elem = 64;
   g.flags = &ws.plan->flags;

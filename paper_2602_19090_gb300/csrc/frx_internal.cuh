@@ -10,8 +10,10 @@
 namespace frx {
 
 constexpr int EZERO = -(1 << 30);   // exponent of an all-zero row or column
-constexpr int DIGIT_BITS = 7;       // 7-bit digits: |d| <= 64
-constexpr int MAX_PLANES = 18;   // digit planes per operand (7 bits each: 126 bits)
+constexpr int DIGIT_BITS = 8;                        // 8-bit digits: |d| <= 2^7 (exact in bf16)
+constexpr int DIGIT_MAX = 1 << (DIGIT_BITS - 1);     // 128
+constexpr int PRODUCT_BITS = 2 * (DIGIT_BITS - 1);   // |d_L d_R| <= 2^14
+constexpr int MAX_PLANES = 16;                       // digit planes per operand (128 bits)
 
 typedef unsigned long long u64;
 typedef long long i64;
@@ -140,17 +142,18 @@ __device__ __forceinline__ double exact_double(i64 P, int q) {
 }
 
 // Digits of x = P 2^q on the fixed grid of exponent e, computed plane by plane instead of
-// through the sequential remainder.  After r round-half-even digits the partial sum is the
-// round-half-even multiple Q_r 2^(s_r) of P, s_r = e + 1 - 7r - q (a tie leaves Q_r even,
-// since Q_r = 128 Q_(r-1) + d_r with d_r chosen even), so d_r = Q_r - 128 Q_(r-1); as
-// |d_r| <= 64 it depends only on Q_r mod 256 and Q_(r-1) mod 2 (Q_0 = 0 because |x| < 2^e).
-// The digits of -x are those of x negated.
+// through the sequential remainder.  With b = DIGIT_BITS: after r round-half-even digits
+// the partial sum is the round-half-even multiple Q_r 2^(s_r) of P, s_r = e + 1 - b r - q
+// (a tie leaves Q_r even, since Q_r = 2^b Q_(r-1) + d_r with d_r chosen even), so
+// d_r = Q_r - 2^b Q_(r-1); as |d_r| <= 2^(b-1) it depends only on Q_r mod 2^(b+1) and
+// Q_(r-1) mod 2 (Q_0 = 0 because |x| < 2^e).  The digits of -x are those of x negated.
 //
 // The value is placed once on the grid one bit below the last plane's LSB:
-// A = |P| 2^(q - g), g = e - 7K (bits shifted out only set a sticky flag; A < 2^(7K)).
-// Plane r = K - j then has its LSB at bit p = 1 + 7j of A, a constant in the unrolled loop,
-// and its sticky bit is "trailing zeros of A < p - 1".  L lanes (values) share e and K;
-// emit(r, d) receives plane r's digits of all lanes, from r = 1 down to r = K.
+// A = |P| 2^(q - g), g = e - b K (bits shifted out only set a sticky flag; A < 2^(b K),
+// which fits 128 bits for K <= MAX_PLANES).  Plane r = K - j then has its LSB at bit
+// p = 1 + b j of A, a constant in the unrolled loop, and its sticky bit is "trailing zeros
+// of A < p - 1".  L lanes (values) share e and K; emit(r, d) receives plane r's digits of
+// all lanes, from r = 1 down to r = K.
 template <int L, class Emit>
 __device__ __forceinline__ void for_each_digit(const i64 (&P)[L], const int (&q)[L], int e, int K, Emit emit) {
   unsigned __int128 A[L];
@@ -166,7 +169,8 @@ __device__ __forceinline__ void for_each_digit(const i64 (&P)[L], const int (&q)
     if (a != 0) {
       const int sh = q[l] - (e - DIGIT_BITS * K);
       if (sh >= 0) {
-        A[l] = sh <= 74 ? (unsigned __int128)a << sh : (unsigned __int128)0;
+        // |x| < 2^e bounds bitlen(a) + sh by b K <= 128, so the shift stays in range
+        A[l] = sh < 128 ? (unsigned __int128)a << sh : (unsigned __int128)0;
       } else if (sh > -64) {
         A[l] = a >> (-sh);
         sticky0[l] = (a & ((1ull << (-sh)) - 1)) != 0;
@@ -185,14 +189,15 @@ __device__ __forceinline__ void for_each_digit(const i64 (&P)[L], const int (&q)
       int d[L];
 #pragma unroll
       for (int l = 0; l < L; ++l) {
-        const unsigned t8 = (unsigned)(A[l] >> p) & 0xffu;
+        constexpr unsigned MASK = (2u << DIGIT_BITS) - 1u;   // b + 1 bits: Q_r mod 2^(b+1)
+        const unsigned tq = (unsigned)(A[l] >> p) & MASK;
         const unsigned rb = (unsigned)(A[l] >> (p - 1)) & 1u;
         const unsigned st = (sticky0[l] || tz[l] < p - 1) ? 1u : 0u;
-        const unsigned q8 = (t8 + (rb & (st | (t8 & 1u)))) & 0xffu;
-        int v = (int)((q8 - (par[l] << 7)) & 0xffu);
-        v = v >= 128 ? v - 256 : v;
+        const unsigned qr = (tq + (rb & (st | (tq & 1u)))) & MASK;
+        int v = (int)((qr - (par[l] << DIGIT_BITS)) & MASK);
+        v = v >= (1 << DIGIT_BITS) ? v - (2 << DIGIT_BITS) : v;
         d[l] = neg[l] ? -v : v;
-        par[l] = q8 & 1u;
+        par[l] = qr & 1u;
       }
       emit(K - j, d);
     }

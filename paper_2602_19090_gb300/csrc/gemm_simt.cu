@@ -1,8 +1,9 @@
-// Exact digit-plane products on the CUDA cores (dp4a), grouped by anti-diagonal.
-// Sec. 2.3: every slice product A^(r) X^(s) is exact; here the slices are 7-bit
-// integer digits, so the products are exact integer matrices (int32 per pair,
-// int64 per anti-diagonal group).  Used for small problems and as the
-// cross-check of the tensor-core path.
+// Exact digit-plane products on the CUDA cores, grouped by anti-diagonal.
+// Sec. 2.3: every slice product A^(r) X^(s) is exact; here the slices are 8-bit
+// integer digits (|d| <= 128), so the products are exact integer matrices (int32 per pair:
+// |sum| <= K 2^14 < 2^31 for K <= 2^16; int64 per anti-diagonal group).  Used where the
+// tensor-core kernel's alignment rules are not met and as the cross-check of the
+// tensor-core path.
 #include <stdlib.h>
 
 #include "frx_internal.cuh"
@@ -35,24 +36,13 @@ __device__ __forceinline__ int bf16_digit(unsigned short b) {
   return (int)__uint_as_float((unsigned)b << 16);
 }
 
-// 8 bf16 digits -> two int8x4 words
-__device__ __forceinline__ void pack8(uint4 v, int& w0, int& w1) {
-  unsigned short h[8];
-  memcpy(h, &v, 16);
-  int d[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) d[i] = bf16_digit(h[i]) & 0xff;
-  w0 = d[0] | (d[1] << 8) | (d[2] << 16) | (d[3] << 24);
-  w1 = d[4] | (d[5] << 8) | (d[6] << 16) | (d[7] << 24);
-}
-
 __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
   if (g.done && *g.done) return;
   const GemmDesc& d = g.dyn ? *g.dyn : g.d;
   if (!d.active) return;
   const int kL = d.kL, kR = d.kR, tmax = d.tmax, gs = d.gs, groups = d.groups, word32 = d.word32;
-  __shared__ __align__(16) int As[BK / 4][BM];
-  __shared__ __align__(16) int Bs[BK / 4][BN];
+  __shared__ __align__(16) int As[BK][BM];
+  __shared__ __align__(16) int Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
@@ -91,24 +81,25 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
             va = *reinterpret_cast<const uint4*>(Lp + (i0 + lrow) * g.pitch + k0 + lk);
           if (j0 + lrow < g.N && k0 + lk < g.pitch)
             vb = *reinterpret_cast<const uint4*>(Rp + (j0 + lrow) * g.pitch + k0 + lk);
-          int a0, a1, b0, b1;
-          pack8(va, a0, a1);
-          pack8(vb, b0, b1);
-          As[lk / 4][lrow] = a0;
-          As[lk / 4 + 1][lrow] = a1;
-          Bs[lk / 4][lrow] = b0;
-          Bs[lk / 4 + 1][lrow] = b1;
-          __syncthreads();
+          unsigned short ha[8], hb[8];
+          memcpy(ha, &va, 16);
+          memcpy(hb, &vb, 16);
 #pragma unroll
-          for (int qd = 0; qd < BK / 4; ++qd) {
-            int4 av = *reinterpret_cast<const int4*>(&As[qd][ty * 4]);
-            int4 bv = *reinterpret_cast<const int4*>(&Bs[qd][tx * 4]);
-            int ar[4] = {av.x, av.y, av.z, av.w};
-            int br[4] = {bv.x, bv.y, bv.z, bv.w};
+          for (int q = 0; q < 8; ++q) {
+            As[lk + q][lrow] = bf16_digit(ha[q]);
+            Bs[lk + q][lrow] = bf16_digit(hb[q]);
+          }
+          __syncthreads();
+#pragma unroll 8
+          for (int kk = 0; kk < BK; ++kk) {
+            const int4 av = *reinterpret_cast<const int4*>(&As[kk][ty * 4]);
+            const int4 bv = *reinterpret_cast<const int4*>(&Bs[kk][tx * 4]);
+            const int ar[4] = {av.x, av.y, av.z, av.w};
+            const int br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] = __dp4a(ar[a], br[b], acc[a][b]);
+              for (int b = 0; b < 4; ++b) acc[a][b] += ar[a] * br[b];
           }
           __syncthreads();
         }
@@ -120,7 +111,7 @@ __global__ void __launch_bounds__(256) k_plane_gemm_simt(PlaneGemm g) {
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) racc[a][b] = racc[a][b] * 128 + tacc[a][b];
+        for (int b = 0; b < 4; ++b) racc[a][b] = racc[a][b] * (1 << DIGIT_BITS) + tacc[a][b];
     }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {

@@ -1,14 +1,15 @@
 // Exact digit-plane products on the 5th-generation tensor cores (sm_103a).
 //
 // Sec. 2.3 multiplies error-free slices so that every slice product is exact.  The
-// slices here are integer digits in [-64, 64] stored as bfloat16, multiplied by
-// tcgen05.mma (.kind::f16, bf16 x bf16 -> f32 in TMEM).  Every product is an integer
-// of magnitude <= 2^12, so an FP32 accumulator holds exact integers as long as the
-// accumulated count stays <= 2^11 terms per lane (|sum| <= 2^23); the accumulator is
-// therefore drained into integer registers every CHUNK_KB k-blocks (and at the end of
-// every anti-diagonal t).  With int32 planes each anti-diagonal's exact sum S_t is stored
-// as one plane (while pairs * K * 4096 < 2^31); otherwise BN = 128 and the int64 sums are
-// combined in Horner form per group: R_g = sum_{t in g} 2^(7 (t_last - t)) S_t.
+// slices here are integer digits in [-128, 128] stored as bfloat16 (exact: its 8-bit
+// significand holds every integer up to 256), multiplied by tcgen05.mma (.kind::f16,
+// bf16 x bf16 -> f32 in TMEM).  Every product is an integer of magnitude <= 2^14, so an
+// FP32 accumulator holds exact integers as long as the accumulated count stays <= 2^10
+// terms per lane (|sum| <= 2^24); the accumulator is therefore drained into integer
+// registers every CHUNK_KB k-blocks (and at the end of every anti-diagonal t).  With int32
+// planes each anti-diagonal's exact sum S_t is stored as one plane (while
+// pairs * K * 2^14 < 2^31); otherwise BN = 128 and the int64 sums are combined in Horner
+// form per group: R_g = sum_{t in g} 2^(8 (t_last - t)) S_t.
 //
 // Tile configurations (int32 planes): 128 x 128 or 128 x 256 output tiles per CTA, or
 // 256 x 256 super-tiles per pair of CTAs (a 2-CTA cluster: each CTA computes one 128-row
@@ -44,7 +45,8 @@ namespace {
 
 constexpr int BM = 128, BK = 64;   // BK bf16 = 128 bytes = one swizzle row
 constexpr int MAX_STAGES = 6;
-constexpr int CHUNK_KB = 32;                 // 32 * 64 = 2048 products per accumulation
+constexpr int CHUNK_KB = (1 << (24 - PRODUCT_BITS)) / BK;   // 16 * 64 = 1024 products: |sum| <= 2^24
+static_assert(CHUNK_KB >= 1, "a k-block of products must stay exact in FP32");
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = 32 * (2 + NUM_EPI_WARPS);
 constexpr uint32_t STAGE_A_BYTES = BM * BK * 2;
@@ -593,7 +595,7 @@ __device__ __forceinline__ void tc_body(Src& src) {
         int chunks = (total + CHUNK_KB - 1) / CHUNK_KB;
         if constexpr (!W32) {
 #pragma unroll
-          for (int c = 0; c < NCOL; ++c) R[c] <<= 7;
+          for (int c = 0; c < NCOL; ++c) R[c] <<= DIGIT_BITS;
         }
         for (int ch = 0; ch < chunks; ++ch) {
           if (!mbar_wait(&sm->acc_full[buf], acc_phase[buf], abort, a.flags)) {

@@ -38,12 +38,13 @@ __device__ int dceil_log2_int(int64_t n) {
   return bl;
 }
 
-// smallest k >= 1 with (2^(7k - eL - eR - 6) tau)^2 >= n^3, capped; 0 if an operand is zero
+// smallest k >= 1 with (2^(b k - eL - eR - (b - 1)) tau)^2 >= n^3 (b = DIGIT_BITS), capped; 0 if
+// an operand is zero
 __device__ int dslices_for(int64_t n, int eL, int eR, double tau, int kcap) {
   if (eL == EZERO || eR == EZERO) return 0;
   double n3 = __dmul_rn(__dmul_rn((double)n, (double)n), (double)n);
   for (int k = 1; k <= kcap; ++k) {
-    double v = ldexp(tau, 7 * k - eL - eR - 6);
+    double v = ldexp(tau, DIGIT_BITS * k - eL - eR - (DIGIT_BITS - 1));
     if (__dmul_rn(v, v) >= n3) return k;
   }
   return kcap;
@@ -292,7 +293,7 @@ __device__ __forceinline__ void plan_v_impl(DevPlan* p, const int32_t* f, PlanOp
   p->beta = beta;
   p->alpha = o.sparse_rule ? 53 - beta + dceil_log2_int(p->rownnz > 0 ? p->rownnz : 1)
             : (o.theory_alpha ? 53 - beta + dceil_log2_int(n) : 53 - beta + dceil_log2_sqrt(n));
-  p->sX = (54 - beta + 6) / 7;
+  p->sX = (54 - beta + DIGIT_BITS - 1) / DIGIT_BITS;
   p->fmax = fmx;
   p->S2 = S2;
   int kV = o.slices_A > 0 ? o.slices_A : dslices_for(n, p->eAmax, fmx, __dmul_rn(o.delta, g), o.k_cap);
@@ -389,7 +390,10 @@ __device__ __forceinline__ void plan_u_impl(DevPlan* p, const int32_t* rho, cons
   rm = bmax_int(rm, redi);
   em = bmax_int(em, redi);
   if (threadIdx.x != 0) return;
+  // the exact int32 sums need kU n 2^14 < 2^31 (up to kU pairs per anti-diagonal)
+  const int cap = (int)(((1ll << 31) - 1) / ((long long)o.n << PRODUCT_BITS));
   int kU = dslices_for(o.n, rm, em, o.delta, o.k_cap);
+  kU = kU < cap ? kU : cap;
   p->kU = kU;
   GemmDesc d;
   d.kL = kU;

@@ -38,7 +38,7 @@ __host__ __device__ inline int gemm_desc_layout(GemmDesc& d, int64_t K, int out_
     int c = hi - lo + 1;
     pmax = c > pmax ? c : pmax;
   }
-  unsigned long long smax = (unsigned long long)pmax * (unsigned long long)K * 4096ull;
+  unsigned long long smax = (unsigned long long)pmax * (unsigned long long)K << PRODUCT_BITS;
   int bs = 0;
   for (unsigned long long v = smax; v; v >>= 1) ++bs;  // smax < 2^bs
   if (bs > 61) return FRX_E_UNSUPPORTED;
@@ -49,7 +49,7 @@ __host__ __device__ inline int gemm_desc_layout(GemmDesc& d, int64_t K, int out_
     d.groups = d.tmax - 1;
     return FRX_OK;
   }
-  d.gs = (61 - bs) / 7 + 1;
+  d.gs = (61 - bs) / DIGIT_BITS + 1;
   d.groups = (d.tmax - 1 + d.gs - 1) / d.gs;
   if (d.groups > MAX_GROUPS) return FRX_E_UNSUPPORTED;
   if (out_bytes_per_elem > 0 && d.groups * 8 > out_bytes_per_elem) return FRX_E_UNSUPPORTED;

@@ -82,11 +82,12 @@ __device__ __forceinline__ i128 double_to_i128(double h) {
   return (b >> 63) ? -(i128)v : (i128)v;
 }
 
-// sum_g R_g 2^(7 (tlast[G-1] - tlast[g])), exact (caller checks ga.exact128)
+// sum_g R_g 2^(b (tlast[G-1] - tlast[g])) (b = DIGIT_BITS), exact (caller checks ga.exact128)
 __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, int64_t j) {
   if (ga.word32 && ga.groups <= 16) {
     // one int32 plane per anti-diagonal: all loads issued first, then Horner with the
-    // constant shift 7 in int64 chunks of four planes (|chunk| < 2^(31 + 21)), merged in 128 bits
+    // constant shift b in int64 chunks of four planes (|chunk| < 2^(31 + 3b + 1) <= 2^56),
+    // merged in 128 bits
     const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
     int32_t v[16];
 #pragma unroll
@@ -99,15 +100,15 @@ __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, i
       i64 c = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (q < len) c = (c << 7) + (i64)v[g + q];
-      N = g ? (N << (7 * len)) + (i128)c : (i128)c;
+        if (q < len) c = (c << DIGIT_BITS) + (i64)v[g + q];
+      N = g ? (N << (DIGIT_BITS * len)) + (i128)c : (i128)c;
     }
     return N;
   }
   if (ga.word32) {
     const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
     i128 N = 0;
-    for (int g = 0; g < ga.groups; ++g) N = (N << 7) + (i128)p[g * ga.ogs];
+    for (int g = 0; g < ga.groups; ++g) N = (N << DIGIT_BITS) + (i128)p[g * ga.ogs];
     return N;
   }
   i128 N = 0;
@@ -118,21 +119,23 @@ __device__ __forceinline__ i128 combine_groups(const GroupArgs& ga, int64_t i, i
   return N;
 }
 
-// int32 planes in chunks of at most 13 (|chunk| < 2^(31 + 84)): each chunk is exact in 128
-// bits and converted to a double-double; chunks are added most significant first
+// int32 planes in chunks of at most W32_CHUNK (|chunk| < 2^(31 + b (W32_CHUNK - 1) + 1) <= 2^120):
+// each chunk is exact in 128 bits and converted to a double-double; chunks are added most
+// significant first
+constexpr int W32_CHUNK = (120 - 32) / DIGIT_BITS + 1;
 __device__ __forceinline__ dd gather_dd_w32_chunked(const GroupArgs& ga, int64_t i, int64_t j, int eLi, int eRj) {
   dd acc{0.0, 0.0};
   if (eLi == EZERO || eRj == EZERO) return acc;
   const int32_t* p = reinterpret_cast<const int32_t*>(ga.out) + j * ga.ldo + i;
   int g = 0;
   while (g < ga.groups) {
-    int len = ga.groups - g < 13 ? ga.groups - g : 13;
+    int len = ga.groups - g < W32_CHUNK ? ga.groups - g : W32_CHUNK;
     i128 N = 0;
     for (int q = 0; q < len; q += 4) {
       int l4 = len - q < 4 ? len - q : 4;
       i64 c = 0;
-      for (int u = 0; u < l4; ++u) c = (c << 7) + (i64)p[(g + q + u) * ga.ogs];
-      N = q ? (N << (7 * l4)) + (i128)c : (i128)c;
+      for (int u = 0; u < l4; ++u) c = (c << DIGIT_BITS) + (i64)p[(g + q + u) * ga.ogs];
+      N = q ? (N << (DIGIT_BITS * l4)) + (i128)c : (i128)c;
     }
     int ex = eLi + eRj + 2 - DIGIT_BITS * (g + len + 1);   // plane g has t = g + 2
     double h = i128_to_double_rn(N);
@@ -240,7 +243,7 @@ __device__ __forceinline__ void load_planes(const GroupArgs& g, int64_t i, int64
   for (int q = 0; q < MP; ++q) v[q] = (valid && q < g.groups) ? __ldg(p + q * g.ogs) : 0;
 }
 
-// sum_q v_q 2^(7 (groups - 1 - q)) exactly (|result| < 2^127 when the product's
+// sum_q v_q 2^(b (groups - 1 - q)) exactly (b = DIGIT_BITS; |result| < 2^127 when the product's
 // exact128 flag holds): Horner in int64 chunks of four planes, merged in 128 bits
 template <int MP>
 __device__ __forceinline__ i128 horner(const int32_t (&v)[MP], int groups) {
@@ -252,8 +255,8 @@ __device__ __forceinline__ i128 horner(const int32_t (&v)[MP], int groups) {
       i64 c = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (q < len && g + q < MP) c = (c << 7) + (i64)v[g + q];
-      N = g ? (N << (7 * len)) + (i128)c : (i128)c;
+        if (q < len && g + q < MP) c = (c << DIGIT_BITS) + (i64)v[g + q];
+      N = g ? (N << (DIGIT_BITS * len)) + (i128)c : (i128)c;
     }
   }
   return N;
@@ -856,11 +859,11 @@ __device__ __forceinline__ bool add_small_rn(double x1, i64 N, int c, double& ou
 __device__ __noinline__ double update_general(const UpdateArgs& a, double x1, int64_t i, int64_t j, int ri, int ej) {
   int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
   double xn;
-  if (a.U.word32 && a.U.groups <= 5) {
-    // the anti-diagonal planes combine exactly in int64 (31 + 28 bits)
+  if (a.U.word32 && a.U.groups <= (62 - 31) / DIGIT_BITS + 1) {
+    // the anti-diagonal planes combine exactly in int64 (31 + 8 (groups - 1) + 1 <= 63 bits)
     const int32_t* p = reinterpret_cast<const int32_t*>(a.U.out) + j * a.U.ldo + i;
     i64 N = 0;
-    for (int q = 0; q < a.U.groups; ++q) N = (N << 7) + (i64)p[q * a.U.ogs];
+    for (int q = 0; q < a.U.groups; ++q) N = (N << DIGIT_BITS) + (i64)p[q * a.U.ogs];
     if (add_small_rn(x1, N, c, xn)) return xn;
   }
   if (a.U.exact128) {
@@ -988,7 +991,7 @@ GroupArgs group_args(const PlaneGemm& g) {
   ga.tmax = g.d.tmax;
   ga.word32 = g.d.word32;
   // |R_g| < 2^31 (int32 planes) or 2^62 (int64 groups); the combination spans
-  // 7 (tmax - t_last(0)) more bits and must stay below 2^127
+  // DIGIT_BITS (tmax - t_last(0)) more bits and must stay below 2^127
   int t0 = 2 + g.d.gs - 1 < g.d.tmax ? 2 + g.d.gs - 1 : g.d.tmax;
   ga.exact128 = ga.groups > 0 && (g.d.word32 ? 31 : 62) + DIGIT_BITS * (g.d.tmax - t0) + 1 <= 127;
   return ga;

@@ -31,7 +31,7 @@ def group_sums(S, kL, kR, T, gs):
         for t in range(t0, t1 + 1):
             St = S.get(t)
             St = St.astype(object) if St is not None else 0
-            acc = St if acc is None else acc * 128 + St
+            acc = St if acc is None else acc * 256 + St     # 8-bit digits: planes 2^8 apart
         groups.append(acc)
         t0 = t1 + 1
     return groups

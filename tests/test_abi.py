@@ -44,8 +44,8 @@ def test_host_only_calls(lib):
     assert lib.frx_refine_workspace_bytes(0, None) == 0
     assert lib.frx_refine_workspace_bytes(64, None) > 64 * 64 * 8 * 3
     assert lib.frx_refine_workspace_bytes(12289, None) == 0
-    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 19) == 0
-    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 18) > 0
+    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 17) == 0
+    assert lib.frx_ozaki_gemm_workspace_bytes(10, 10, 10, 16) > 0
 
 
 def test_wait_self_test_checks_its_scratch_first(lib):
@@ -80,7 +80,7 @@ def test_argument_errors_before_any_device_work(lib):
     assert st == -5
     o = _lib.Opts()
     lib.frx_default_opts(ctypes.byref(o))
-    o.x_planes = 9                  # more planes than FP64 width needs
+    o.x_planes = 8                  # more planes than FP64 width needs (7 x 8 bits)
     st = lib.frx_refine(p, 4, p, 4, p, 4, 1e-10, ctypes.byref(o), p, 1 << 20, None, None)
     assert st == -1
     lib.frx_default_opts(ctypes.byref(o))
@@ -92,11 +92,12 @@ def test_argument_errors_before_any_device_work(lib):
 
 
 def test_group_size_keeps_sums_exact(lib):
-    # groups of gs anti-diagonals: max|S_t| * 2^(7 (gs - 1)) * 128/127 < 2^62
+    # groups of gs anti-diagonals: max|S_t| * 2^(8 (gs - 1)) * 256/255 < 2^62, where
+    # max|S_t| = pairs * K * 128^2 (8-bit digits)
     for kL, kR, T, K in ((8, 6, 9, 64), (16, 8, 17, 12288), (16, 16, 32, 65536), (3, 3, 4, 5)):
         gs = lib.frx_group_size(kL, kR, T, K)
         pmax = max(sum(1 for r in range(1, kL + 1) if 1 <= t - r <= kR and t <= T)
                    for t in range(2, min(T, kL + kR) + 1))
-        smax = pmax * K * 4096
-        assert smax * 2 ** (7 * (gs - 1)) * 128 / 127 < 2 ** 62
-        assert smax * 2 ** (7 * gs) * 128 / 127 >= 2 ** 61    # not needlessly small
+        smax = pmax * K * 16384
+        assert smax * 2 ** (8 * (gs - 1)) * 256 / 255 < 2 ** 62
+        assert smax * 2 ** (8 * gs) * 256 / 255 >= 2 ** 61    # not needlessly small

@@ -88,7 +88,7 @@ def test_largest_accepted_size(api):
 
 def test_ozaki_gemm_longest_inner_dimension_int64_groups(api):
     # k = 65536 (the limit) with 8 planes, all pairs: up to 8 pairs per anti-diagonal make
-    # 8 * 65536 * 4096 = 2^31, beyond int32, so the int64 Horner groups are used
+    # 8 * 65536 * 2^14 = 2^33, beyond int32, so the int64 Horner groups are used
     g = G()
     m, K, n, k = 136, 65536, 130, 8
     A = synth.gemm_operand(m, K, 1.0, 330)

@@ -56,17 +56,17 @@ def test_tc_matches_simt(api, m, n, K, kL, kR, T):
 
 
 def test_tc_worst_case_digits(api):
-    # every digit +64 (all-ones matrix): FP32 chunk sums reach 2048 * 4096 = 2^23 exactly
+    # every digit +128 (all-ones matrix): FP32 chunk sums reach 1024 * 2^14 = 2^24 exactly
     from tests import gpu_util as g
     K = 4096 + 64
     Lt = g.to_dev(np.ones((256, K)))
     Lp = api.slice_planes(Lt, 0, api.exponents(Lt, 0), 3)
     ref, got = _both(api, Lp, Lp.clone(), K, 3, 3, 6)
     assert np.array_equal(ref, got)
-    # only plane 1 is nonzero (digit 64), so group 0 holds S_2 shifted to its last t
+    # only plane 1 is nonzero (digit 128), so group 0 holds S_2 shifted to its last t
     gs = api.group_size(3, 3, 6, K)
     t_last = min(2 + gs - 1, 6)
-    assert ref[0, 0, 0] == 64 * 64 * K * 2 ** (7 * (t_last - 2))
+    assert ref[0, 0, 0] == 128 * 128 * K * 2 ** (8 * (t_last - 2))
 
 
 @pytest.mark.parametrize("m,k,n,slices,mode", [(300, 513, 260, 6, "full"), (1024, 2048, 512, 8, "triangular"),

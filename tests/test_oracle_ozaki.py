@@ -31,17 +31,17 @@ def test_slices_round_trip_digits_and_residual_bound(phi):
     M[3, :] = 0.0                                  # zero row: sigma = 0 (eq. sigma)
     k = 6
     d, e, res = oz.slice_rows(M, k)
-    assert np.all(np.abs(d) <= 64)
+    assert np.all(np.abs(d) <= 128)                  # 8-bit digits: |d| <= 2^7
     assert np.all(d[:, 3, :] == 0)
     for i in range(M.shape[0]):
         for j in range(M.shape[1]):
             acc = F(0)
             for r in range(1, k + 1):
                 if e[i] != oz.EZERO:
-                    acc += d[r - 1, i, j] * F(2) ** int(e[i] + 1 - 7 * r)
+                    acc += d[r - 1, i, j] * F(2) ** int(e[i] + 1 - 8 * r)
             assert acc + F(res[i, j]) == F(M[i, j])              # exact split
             if e[i] != oz.EZERO:
-                assert abs(F(res[i, j])) <= F(2) ** int(e[i] - 7 * k)   # |res_k| <= w_k / 2
+                assert abs(F(res[i, j])) <= F(2) ** int(e[i] - 8 * k)   # |res_k| <= w_k / 2
 
 
 def test_digit_rule_is_the_sigma_trick():
@@ -50,18 +50,19 @@ def test_digit_rule_is_the_sigma_trick():
     d, e, _ = oz.slice_rows(M, 7)
     res = M.copy()
     for r in range(1, 8):
-        w = np.ldexp(1.0, e + 1 - 7 * r)[:, None]
+        w = np.ldexp(1.0, e + 1 - 8 * r)[:, None]
         sl = oz.sigma_trick_slice(res, e, r)
         assert np.array_equal(d[r - 1] * w, sl)
         res = res - sl
 
 
 def test_ties_go_to_even_digit():
-    # e = 0 (max 1.0): w_1 = 2^-6; 2.5 w_1 -> digit 2, 3.5 w_1 -> 4
-    x = np.array([[1.0, 2.5 * 2.0 ** -6, 3.5 * 2.0 ** -6, -2.5 * 2.0 ** -6]])
+    # e = 0 (max 1.0): w_1 = 2^-7; 1.0 is the largest digit, 128; 2.5 w_1 -> digit 2,
+    # 3.5 w_1 -> 4
+    x = np.array([[1.0, 2.5 * 2.0 ** -7, 3.5 * 2.0 ** -7, -2.5 * 2.0 ** -7]])
     d, e, _ = oz.slice_rows(x, 1)
     assert e[0] == 0
-    assert list(d[0, 0]) == [64, 2, 4, -2]
+    assert list(d[0, 0]) == [128, 2, 4, -2]
 
 
 @pytest.mark.parametrize("beta", [3, 10, 17, 30, 47])
@@ -82,19 +83,19 @@ def test_tau_truncation(beta):
 
 
 def test_slice_products_fp64_route_is_exact_at_the_extremes():
-    # all digits +-64 with K = 2048: partial sums reach K * 2^12 = 2^23; and a random sign
+    # all digits +-128 with K = 2048: partial sums reach K * 2^14 = 2^25; and a random sign
     # pattern checked against Python integers term by term on a few entries
     K = 2048
-    dL = np.full((2, 3, K), 64, dtype=np.int64)
-    dR = np.full((2, K, 4), 64, dtype=np.int64)
-    dR[1] = -64
+    dL = np.full((2, 3, K), 128, dtype=np.int64)
+    dR = np.full((2, K, 4), 128, dtype=np.int64)
+    dR[1] = -128
     S = oz.slice_products(dL, dR, oz.pair_set(2, 2, 4))
-    assert int(S[2][0, 0]) == K * 4096
-    assert int(S[3][0, 0]) == 0          # (1,2) gives -K 2^12, (2,1) gives +K 2^12
-    assert int(S[4][0, 0]) == -K * 4096
+    assert int(S[2][0, 0]) == K * 16384
+    assert int(S[3][0, 0]) == 0          # (1,2) gives -K 2^14, (2,1) gives +K 2^14
+    assert int(S[4][0, 0]) == -K * 16384
     g = np.random.default_rng(13)
-    dL = g.integers(-64, 65, (2, 3, 5000))
-    dR = g.integers(-64, 65, (2, 5000, 3))
+    dL = g.integers(-128, 129, (2, 3, 5000))
+    dR = g.integers(-128, 129, (2, 5000, 3))
     S = oz.slice_products(dL, dR, oz.pair_set(2, 2, 4))
     for i in range(3):
         for j in range(3):
@@ -105,8 +106,8 @@ def test_slice_products_fp64_route_is_exact_at_the_extremes():
 
 def test_slice_products_brute_force():
     g = np.random.default_rng(12)
-    dL = g.integers(-64, 65, (3, 4, 6))
-    dR = g.integers(-64, 65, (3, 6, 5))
+    dL = g.integers(-128, 129, (3, 4, 6))
+    dR = g.integers(-128, 129, (3, 6, 5))
     pairs = oz.pair_set(3, 3, 4)
     S = oz.slice_products(dL, dR, pairs)
     assert set(S) == {2, 3, 4}
@@ -129,7 +130,7 @@ def _exact_product(A, B):
 def test_ozaki_gemm_enough_slices_is_correctly_rounded():
     A = synth.gemm_operand(6, 9, 0.5, 21)
     B = synth.gemm_operand(9, 5, 0.5, 22)
-    # exponent spread is small; 12 planes (84 bits) capture both operands exactly
+    # exponent spread is small; 12 planes (96 bits) capture both operands exactly
     _, eA, resA = oz.slice_rows(A, 12)
     _, eB, resB = oz.slice_cols(B, 12)
     assert np.all(resA == 0) and np.all(resB == 0)
@@ -152,7 +153,10 @@ def test_triangular_truncation_bound(k):
     K = A.shape[1]
     for i in range(7):
         for j in range(6):
-            bound = (k + 1) * K * F(2) ** int(eA[i] + eB[j] - 7 * k)
+            # dropped pairs (r + s >= k + 2: |a_r b_s| <= 2^(eA + eB + 16 - 8(r + s)), at most k
+            # per anti-diagonal, decaying by 2^-8) and the two residual terms (each below
+            # 2^(eA + eB - 8k) per product term): (1.004 k + 2.01) K 2^(eA + eB - 8k)
+            bound = (k + 3) * K * F(2) ** int(eA[i] + eB[j] - 8 * k)
             assert abs(F(out["hi"][i, j]) + F(out["lo"][i, j]) - ex[i][j]) <= bound
 
 

@@ -42,9 +42,9 @@ def test_slice_rule_definition():
         for eL, eR in ((0, -3), (-2, -30), (1, 1)):
             for tau in (1e-22, 3.4e-23, 1e-14):
                 k = rf.slices_for(n, eL, eR, tau, 40)
-                assert 64 * n ** 1.5 * 2.0 ** (eL + eR - 7 * k) <= tau * (1 + 1e-12)
+                assert 128 * n ** 1.5 * 2.0 ** (eL + eR - 8 * k) <= tau * (1 + 1e-12)
                 if k > 1:
-                    assert 64 * n ** 1.5 * 2.0 ** (eL + eR - 7 * (k - 1)) > tau * (1 - 1e-12)
+                    assert 128 * n ** 1.5 * 2.0 ** (eL + eR - 8 * (k - 1)) > tau * (1 - 1e-12)
 
 
 def test_w_identity():
@@ -132,12 +132,12 @@ def test_workload0_reaches_delta():
     assert tr.forward_error(Xh, Xl, X) <= 1e-14
 
 
-def test_workload0_fixed_eight_planes_floor():
-    # 8 planes of A (56 bits) cannot resolve gaps of 3.4e-9 to 1e-14: the error stalls
-    # near 2^-56 / gap and the stopping test reports stagnation rather than convergence.
+def test_workload0_fixed_56_bit_a_floor():
+    # 7 planes of A (56 bits) cannot resolve gaps of 3.4e-9 to 1e-14: the error stalls
+    # near 2^-56 / gap and the iteration does not converge.
     A, X0, D0 = synth.workload0()
     Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
-    X, lam, info = rf.refine(A, X0, D0, 1e-14, rf.Options(slices_A=8, max_iter=3))
+    X, lam, info = rf.refine(A, X0, D0, 1e-14, rf.Options(slices_A=7, max_iter=3))
     fe = tr.forward_error(Xh, Xl, X)
     assert info["status"] != "converged"
     assert 1e-10 < fe < 1e-8
@@ -217,21 +217,21 @@ def test_start_outside_the_basin_still_converges():
 
 
 def test_previous_study_form_keeps_x_at_its_planes():
-    # x_planes = 8 keeps X at 8 digit planes (56 bits on the column grid): every entry within
+    # x_planes = 7 keeps X at 7 digit planes (56 bits on the column grid): every entry within
     # 2^(f-3) of the column maximum is unchanged, smaller ones are rounded to 2^(f-55)
     A, X0, D0 = synth.workload0()
     hist = []
-    rf.refine(A, X0, D0, 1e-14, rf.Options(x_planes=8, max_iter=1), history=hist)
-    p = rf.plan(A, X0, D0, 1e-14, rf.Options(x_planes=8))
-    assert p["sX"] == 8 and p["beta"] == -2
-    X1 = X0 - oz.slice_cols(X0, 8, p["f"])[2]
+    rf.refine(A, X0, D0, 1e-14, rf.Options(x_planes=7, max_iter=1), history=hist)
+    p = rf.plan(A, X0, D0, 1e-14, rf.Options(x_planes=7))
+    assert p["sX"] == 7 and p["beta"] == -2
+    X1 = X0 - oz.slice_cols(X0, 7, p["f"])[2]
     big = np.abs(X0) >= np.ldexp(1.0, p["f"] - 3)[None, :]
     assert np.array_equal(X1[big], X0[big])
     assert np.all(np.abs(X1 - X0) <= np.ldexp(1.0, p["f"] - 56)[None, :])
-    # three planes: the tau grid of beta = 33
+    # three planes (24 bits): the tau grid of beta = 30
     p3 = rf.plan(A, X0, D0, 1e-14, rf.Options(x_planes=3))
     X13 = X0 - oz.slice_cols(X0, 3, p3["f"])[2]
-    T, _ = oz.tau_truncate_cols(X0, 33, p3["f"])
+    T, _ = oz.tau_truncate_cols(X0, 30, p3["f"])
     assert p3["sX"] == 3 and np.array_equal(X13, T)
 
 
