@@ -667,7 +667,7 @@ def run_previous(args):
                                     "products": ix["products"], "s_X": ix["s_X"], "err_est": ix["err_est"]},
                    "proposed": {"ms": ms_p, "status": ip["status_name"], "iters": ip["iters"],
                                 "products": ip["products"], "s_X": ip["s_X"], "k_V": ip["k_V"], "err_est": ip["err_est"]},
-                   "previous_8_planes": {"ms": ms_q, "status": iq["status_name"], "iters": iq["iters"],
+                   "previous_full_width": {"ms": ms_q, "status": iq["status_name"], "iters": iq["iters"],
                                          "products": iq["products"], "s_X": iq["s_X"], "k_V": iq["k_V"],
                                          "err_est": iq["err_est"]},
                    "product_ratio": iq["products"] / max(ip["products"], 1), "time_ratio": ms_q / ms_p,
@@ -689,7 +689,7 @@ def run_previous(args):
                                 "products": ix["products"], "forward_error": _forward_error(Xx, Qht, Qlt)["two"]},
                "proposed": {"ms": ms_p, "status": ip["status_name"], "iters": ip["iters"], "products": ip["products"],
                             "forward_error": _forward_error(Xp, Qht, Qlt)["two"]},
-               "previous_8_planes": {"ms": ms_q, "status": iq["status_name"], "iters": iq["iters"],
+               "previous_full_width": {"ms": ms_q, "status": iq["status_name"], "iters": iq["iters"],
                                      "products": iq["products"], "forward_error": _forward_error(Xq, Qht, Qlt)["two"]},
                "product_ratio": iq["products"] / max(ip["products"], 1), "time_ratio": ms_q / ms_p}
         out["exact_truth_n4096_cond1e10"].append(rec)
