@@ -98,6 +98,35 @@ def sigma_trick_slice(res, e, r):
     return (sig + res) - sig
 
 
+def slice_rows_adaptive(M, k, alpha):
+    """The paper's own splitting (eq. sigma and eq. a, Sec. 2.3), row by row, k slices.
+
+    Before every slice the residual's row maximum v_i^(r) is scanned again and
+    sigma_i^(r) = 0.75 * 2^ceil(log2 v_i^(r)) * 2^alpha (0 for a zero row); the slice is
+    a^(r) = fl((sigma + res) - sigma) and the residual res <- fl(res - a^(r)).  Each slice
+    keeps the bits of the residual from its leading one down to ulp(sigma), i.e. about
+    53 - alpha bits, so its width follows the data instead of a fixed grid.
+
+    Returns (slices FP64 [k, m, K], sigmas [k, m], residual [m, K]).
+    (The CUDA path keeps the fixed grid of ``slice_rows``: a per-slice rescan gives every
+    row its own slice exponents, which would break the anti-diagonal grouping of the exact
+    integer sums.  This function is the reference for comparing the two.)
+    """
+    M = np.asarray(M, dtype=np.float64)
+    res = M.copy()
+    slices = np.zeros((k,) + M.shape)
+    sigmas = np.zeros((k, M.shape[0]))
+    for r in range(k):
+        v = np.max(np.abs(res), axis=1) if M.shape[1] else np.zeros(M.shape[0])
+        e = ceil_log2(v)
+        sig = np.where(e == EZERO, 0.0, 0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + alpha)))
+        sl = (sig[:, None] + res) - sig[:, None]
+        res = res - sl
+        slices[r] = sl
+        sigmas[r] = sig
+    return slices, sigmas, res
+
+
 def tau_truncate_cols(X, beta, f=None):
     """Eq. tau / eq. x with s = 1: X^(1)_ij = fl((tau_j + x_ij) - tau_j),
 

@@ -170,3 +170,58 @@ def test_recombine_dd_matches_exact():
     mag = np.abs(A) @ np.abs(B)
     diff = np.abs((o1["hi"] - o2["hi"]) + (o1["lo"] - o2["lo"]))
     assert np.all(diff <= mag * 2.0 ** -100)
+
+
+def _ufp(x):
+    return F(2) ** (math.frexp(abs(float(x)))[1] - 1)
+
+
+@pytest.mark.parametrize("phi", [0.5, 4.0])
+def test_adaptive_slices_split_exactly_and_obey_eq_minamihata(phi):
+    # the paper's own splitting (eq. sigma with a rescan before every slice, eq. a): the
+    # slices and the residual add up to M exactly, and after slice r the residual is at most
+    # u * ufp(sigma_i^(r)) (eq. minamihata); a zero row gets sigma = 0 and zero slices
+    M = synth.gemm_operand(7, 19, phi, 50)
+    M[2, :] = 0.0
+    k, alpha = 3, 30
+    sl, sig, res = oz.slice_rows_adaptive(M, k, alpha)
+    assert np.all(sl[:, 2, :] == 0) and np.all(sig[:, 2] == 0)
+    for i in range(M.shape[0]):
+        for j in range(M.shape[1]):
+            rem = F(M[i, j])
+            for r in range(k):
+                rem -= F(sl[r, i, j])
+                if sig[r, i] != 0:
+                    assert abs(rem) <= U * _ufp(sig[r, i])
+            assert rem == F(res[i, j])
+
+
+def test_adaptive_slice_products_are_exact_under_eq_alp_beta():
+    # alpha + beta >= -log2 u + log2 n makes every slice product exact in FP64
+    n = 16
+    A = synth.gemm_operand(5, n, 2.0, 51)
+    X = synth.gemm_operand(n, 4, 2.0, 52)
+    alpha = 30
+    beta = 53 + 4 - alpha
+    sa, _, _ = oz.slice_rows_adaptive(A, 3, alpha)
+    sx, _, _ = oz.slice_rows_adaptive(X.T, 3, beta)
+    for r in range(3):
+        for s in range(3):
+            P = sa[r] @ sx[s].T
+            for i in range(5):
+                for j in range(4):
+                    exact = sum((F(sa[r, i, q]) * F(sx[s, j, q]) for q in range(n)), F(0))
+                    assert F(P[i, j]) == exact
+
+
+@pytest.mark.parametrize("phi", [0.5, 2.0, 4.0])
+def test_adaptive_slicing_needs_no_more_slices_than_the_fixed_grid(phi):
+    # alpha = 46 gives slices of at most 2^7 units of ulp(sigma), the width of the fixed
+    # 8-bit digit grid: the rescan starts every slice at the residual's leading bit, so it
+    # represents each row exactly with at most as many slices as the fixed grid's planes
+    M = synth.gemm_operand(24, 20, phi, 53)
+    for i in range(M.shape[0]):
+        row = M[i:i + 1]
+        kf = next(k for k in range(1, 20) if np.all(oz.slice_rows(row, k)[2] == 0))
+        ka = next(k for k in range(1, 20) if np.all(oz.slice_rows_adaptive(row, k, 46)[2] == 0))
+        assert ka <= kf
