@@ -168,7 +168,9 @@ FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx
  * iteration.  Problems are processed in chunks of 2048.  The refined X and D, the
  * iteration and product counts equal those of frx_refine on each problem, bit for bit (the
  * reported norms may differ in their last bits: columns are summed with another block
- * size).  `infos` (host, `count` entries) may be NULL.
+ * size).  `infos` (host, `count` entries) may be NULL.  Batched calls on one device from
+ * several host threads run one after another (they share the library's stream for the
+ * device).
  * Returns FRX_OK if every problem converged, else the largest soft status (1, 2), or the
  * first hard error (< 0; the per-problem statuses are then in infos when it is not NULL).
  * The call must not be made while `stream` is being captured.

@@ -526,9 +526,12 @@ int launch_stage(const Stage& st, char* tables, int count, cudaStream_t s) {
 
 // the library's own stream for the batched path (captures cannot use the legacy stream),
 // bridged to the caller's stream with events
+// One per device.  `busy` serialises batched calls on the device: they share the stream,
+// its events and the graph capture on it, which concurrent callers would interleave.
 struct BatchStream {
   cudaStream_t s = nullptr;
   cudaEvent_t enter = nullptr, leave = nullptr;
+  std::mutex busy;
 };
 
 int batch_stream(BatchStream** out) {
@@ -701,6 +704,7 @@ int refine_batched_impl(const double* const* A, const int64_t* lda, double* cons
   FRX_TRY(ensure_attributes());
   BatchStream* bs = nullptr;
   FRX_TRY(batch_stream(&bs));
+  std::lock_guard<std::mutex> serial(bs->busy);
   cudaStream_t s = bs->s;
   FRX_CUDA_TRY(cudaEventRecord(bs->enter, caller));
   FRX_CUDA_TRY(cudaStreamWaitEvent(s, bs->enter, 0));

@@ -123,3 +123,45 @@ def test_bounded_wait_reports_timeout_and_the_context_survives(api):
     C = api.ozaki_gemm(g.to_dev(A), g.to_dev(B), 8, "full").cpu().numpy()
     C_ref, _ = oz.ozaki_gemm(A, B, 8, "full")
     assert np.all(np.abs(C - C_ref) <= np.spacing(np.abs(C_ref)))
+
+
+def test_batched_calls_from_two_threads(api):
+    # two host threads run batched refinements on the same device at once (each with its
+    # own problems and scratch): the calls are serialised inside the library and each
+    # result equals the same call made alone
+    import threading
+
+    g = G()
+    sets = []
+    for base in (0, 100):
+        probs = [synth.refine_workload(nn, 1e3, "spd", case=base + nn) for nn in (40, 75, 130)]
+        sets.append(probs)
+    alone = []
+    for probs in sets:
+        Xs = [g.to_dev(p[1]) for p in probs]
+        api.refine_batched([g.to_dev(p[0]) for p in probs], Xs, [g.to_dev(p[2]) for p in probs], 1e-12)
+        alone.append([x.cpu().numpy() for x in Xs])
+    outs = [None, None]
+    errs = []
+
+    def run(k):
+        try:
+            import torch
+            torch.cuda.set_device(0)
+            probs = sets[k]
+            Xs = [g.to_dev(p[1]) for p in probs]
+            api.refine_batched([g.to_dev(p[0]) for p in probs], Xs, [g.to_dev(p[2]) for p in probs], 1e-12)
+            torch.cuda.synchronize()
+            outs[k] = [x.cpu().numpy() for x in Xs]
+        except Exception as e:   # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in (0, 1)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for k in (0, 1):
+        for a, b in zip(outs[k], alone[k]):
+            assert np.array_equal(a, b)
