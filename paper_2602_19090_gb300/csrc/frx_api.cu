@@ -534,12 +534,33 @@ int launch_stage(const Stage& st, char* tables, int count, cudaStream_t s) {
 
 // the library's own stream for the batched path (captures cannot use the legacy stream),
 // bridged to the caller's stream with events
+// Launch plan of one batched chunk: its recorded stages, their argument tables (pinned host
+// copy, uploaded into the caller's scratch on every call) and the instantiated iteration graph.
+// A later call with the same key (pointers, leading dimensions, orders, options, delta, scratch,
+// tile policy) reuses it and skips the recording, the tensor-map encoding and the capture.
+struct BatchPlan {
+  std::vector<unsigned char> key;
+  unsigned char* blob = nullptr;   // pinned
+  size_t blob_bytes = 0;
+  std::vector<DevPlan*> hplans;
+  std::vector<Stage> stages[3];
+  cudaGraphExec_t exec = nullptr;
+  long long last_use = 0;
+};
+
+#ifndef FRX_BATCH_PLAN_CACHE
+#define FRX_BATCH_PLAN_CACHE 4   // plans kept per device (0: none)
+#endif
+
 // One per device.  `busy` serialises batched calls on the device: they share the stream,
-// its events and the graph capture on it, which concurrent callers would interleave.
+// its events, the graph capture on it and the plan cache, which concurrent callers would
+// interleave.
 struct BatchStream {
   cudaStream_t s = nullptr;
   cudaEvent_t enter = nullptr, leave = nullptr;
   std::mutex busy;
+  std::vector<BatchPlan*> plans;
+  long long uses = 0;
 };
 
 int batch_stream(BatchStream** out) {
@@ -590,15 +611,22 @@ int record_phases(const double* const* A, const int64_t* lda, double* const* X, 
   return st;
 }
 
-int refine_batched_chunk(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
-                         double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, char* base,
-                         const BatchLayout& L, const size_t* off, frx_info* infos, cudaStream_t s) {
+template <class T>
+void key_append(std::vector<unsigned char>& k, const T& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+  k.insert(k.end(), p, p + sizeof(T));
+}
+
+// record, tune, build the argument tables and capture the iteration graph of a chunk
+int build_batch_plan(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                     double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, char* base,
+                     const BatchLayout& L, const size_t* off, cudaStream_t s, BatchPlan& plan) {
   std::vector<RefineWs> ws(count);
-  std::vector<DevPlan*> hplans(count);
   std::vector<PlanOpts> po(count);
+  plan.hplans.resize(count);
   for (int b = 0; b < count; ++b) {
     ws[b] = carve_refine(base + off[b], n[b], o.k_cap);
-    hplans[b] = ws[b].plan;
+    plan.hplans[b] = ws[b].plan;
     po[b] = plan_opts(o, delta, n[b], o.max_iter);
   }
   // tile configuration of the grouped slice products: cached per batch signature (the sorted orders),
@@ -624,21 +652,19 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
   for (int b = 0; b < count; ++b) gemm_order[b] = b;
   std::stable_sort(gemm_order.begin(), gemm_order.end(), [&](int x, int y) { return n[x] > n[y]; });
   std::vector<unsigned char> blob;
-  std::vector<Stage> stages[3];
-  for (int q = 0; q < 3; ++q) FRX_TRY(build_stages(rec[q], gemm_order, blob, stages[q]));
+  for (int q = 0; q < 3; ++q) FRX_TRY(build_stages(rec[q], gemm_order, blob, plan.stages[q]));
   if (blob.size() > L.tables_bytes) return FRX_E_UNSUPPORTED;
+  FRX_CUDA_TRY(cudaHostAlloc((void**)&plan.blob, blob.size() ? blob.size() : 1, cudaHostAllocDefault));
+  memcpy(plan.blob, blob.data(), blob.size());
+  plan.blob_bytes = blob.size();
+  // the iteration, captured once: every stage of it plus the collection of the finish flags
   char* tables = base + L.tables_off;
   DevPlan** dplans = (DevPlan**)(base + L.plans_off);
   int* ddone = (int*)(base + L.done_off);
-  DevPlan* gathered = (DevPlan*)(base + L.gather_off);
-  FRX_CUDA_TRY(cudaMemcpyAsync(tables, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
-  FRX_CUDA_TRY(cudaMemcpyAsync(dplans, hplans.data(), sizeof(DevPlan*) * count, cudaMemcpyHostToDevice, s));
-  for (const Stage& st : stages[0]) FRX_TRY(launch_stage(st, tables, count, s));
   cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
   FRX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int cst = [&]() -> int {
-    for (const Stage& st : stages[1]) FRX_TRY(launch_stage(st, tables, count, s));
+    for (const Stage& st : plan.stages[1]) FRX_TRY(launch_stage(st, tables, count, s));
     return launch_collect_done(dplans, count, ddone, s);
   }();
   cudaError_t e = cudaStreamEndCapture(s, &graph);
@@ -647,22 +673,97 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
     return cst;
   }
   if (e != cudaSuccess) return FRX_E_CUDA;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  e = cudaGraphInstantiate(&plan.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return FRX_E_CUDA;
-  count_launches(-(int)(stages[1].size() + 1));   // captured, not launched: counted per replay
+  count_launches(-(int)(plan.stages[1].size() + 1));   // captured, not launched: counted per replay
+  return FRX_OK;
+}
+
+void free_batch_plan(BatchPlan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->blob) cudaFreeHost(p->blob);
+  delete p;
+}
+
+int refine_batched_chunk(const double* const* A, const int64_t* lda, double* const* X, const int64_t* ldx,
+                         double* const* D, const int64_t* n, int count, double delta, const frx_opts& o, char* base,
+                         const BatchLayout& L, const size_t* off, frx_info* infos, BatchStream& bs) {
+  cudaStream_t s = bs.s;
+  // the plan's key: everything the recorded launches depend on
+  std::vector<unsigned char> key;
+  key_append(key, count);
+  key_append(key, base);
+  key_append(key, delta);
+  // the options field by field (the struct's padding bytes are not part of the key)
+  key_append(key, o.slices_A);
+  key_append(key, o.xi);
+  key_append(key, o.beta_ceil);
+  key_append(key, o.theory_alpha);
+  key_append(key, o.beta_override);
+  key_append(key, o.k_cap);
+  key_append(key, o.max_iter);
+  key_append(key, o.xi_stop);
+  key_append(key, o.cluster_omega);
+  key_append(key, o.x_planes);
+  key_append(key, o.sparse_rule);
+  key_append(key, tile_policy());
+  for (int b = 0; b < count; ++b) {
+    key_append(key, A[b]);
+    key_append(key, lda[b]);
+    key_append(key, X[b]);
+    key_append(key, ldx[b]);
+    key_append(key, D[b]);
+    key_append(key, n[b]);
+    key_append(key, off[b]);
+  }
+  BatchPlan* plan = nullptr;
+  for (BatchPlan* p : bs.plans)
+    if (p->key == key) plan = p;
+  bool owned = false;   // a plan not kept in the cache is freed at the end of the call
+  if (!plan) {
+    plan = new BatchPlan();
+    plan->key = key;
+    const int st = build_batch_plan(A, lda, X, ldx, D, n, count, delta, o, base, L, off, s, *plan);
+    if (st != FRX_OK) {
+      free_batch_plan(plan);
+      return st;
+    }
+    if (FRX_BATCH_PLAN_CACHE > 0) {
+      if ((int)bs.plans.size() >= FRX_BATCH_PLAN_CACHE) {
+        auto lru = std::min_element(bs.plans.begin(), bs.plans.end(),
+                                    [](BatchPlan* x, BatchPlan* y) { return x->last_use < y->last_use; });
+        free_batch_plan(*lru);
+        bs.plans.erase(lru);
+      }
+      bs.plans.push_back(plan);
+    } else {
+      owned = true;
+    }
+  }
+  plan->last_use = ++bs.uses;
+  char* tables = base + L.tables_off;
+  DevPlan** dplans = (DevPlan**)(base + L.plans_off);
+  int* ddone = (int*)(base + L.done_off);
+  DevPlan* gathered = (DevPlan*)(base + L.gather_off);
   int st = [&]() -> int {
+    // the argument tables live in the caller's scratch, which may have been reused since
+    FRX_CUDA_TRY(cudaMemcpyAsync(tables, plan->blob, plan->blob_bytes, cudaMemcpyHostToDevice, s));
+    FRX_CUDA_TRY(
+        cudaMemcpyAsync(dplans, plan->hplans.data(), sizeof(DevPlan*) * count, cudaMemcpyHostToDevice, s));
+    for (const Stage& sg : plan->stages[0]) FRX_TRY(launch_stage(sg, tables, count, s));
     std::vector<int> done(count);
     for (int it = 1; it <= o.max_iter; ++it) {
-      FRX_CUDA_TRY(cudaGraphLaunch(exec, s));
-      count_launches((long long)stages[1].size() + 1);   // the graph's kernels, per replay
+      FRX_CUDA_TRY(cudaGraphLaunch(plan->exec, s));
+      count_launches((long long)plan->stages[1].size() + 1);   // the graph's kernels, per replay
       FRX_CUDA_TRY(cudaMemcpyAsync(done.data(), ddone, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
       FRX_CUDA_TRY(cudaStreamSynchronize(s));
       bool all = true;
       for (int b = 0; b < count; ++b) all &= done[b] != 0;
       if (all) break;
     }
-    for (const Stage& sg : stages[2]) FRX_TRY(launch_stage(sg, tables, count, s));
+    for (const Stage& sg : plan->stages[2]) FRX_TRY(launch_stage(sg, tables, count, s));
     FRX_TRY(launch_gather_plans(dplans, count, gathered, s));
     std::vector<DevPlan> hp(count);
     FRX_CUDA_TRY(cudaMemcpyAsync(hp.data(), gathered, sizeof(DevPlan) * count, cudaMemcpyDeviceToHost, s));
@@ -700,7 +801,7 @@ int refine_batched_chunk(const double* const* A, const int64_t* lda, double* con
     profile_add_gemm_work(ops);
     return worst;
   }();
-  cudaGraphExecDestroy(exec);
+  if (owned) free_batch_plan(plan);
   return st;
 }
 
@@ -720,7 +821,7 @@ int refine_batched_impl(const double* const* A, const int64_t* lda, double* cons
   for (int c0 = 0; c0 < count; c0 += BATCH_CHUNK) {
     const int c = count - c0 < BATCH_CHUNK ? count - c0 : BATCH_CHUNK;
     int st = refine_batched_chunk(A + c0, lda + c0, X + c0, ldx + c0, D + c0, n + c0, c, delta, o, (char*)work, L,
-                                  L.off.data() + c0, infos ? infos + c0 : nullptr, s);
+                                  L.off.data() + c0, infos ? infos + c0 : nullptr, *bs);
     if (st < 0) {
       worst = st;
       break;

@@ -165,3 +165,43 @@ def test_batched_calls_from_two_threads(api):
     for k in (0, 1):
         for a, b in zip(outs[k], alone[k]):
             assert np.array_equal(a, b)
+
+
+def test_batched_plan_reuse_sees_new_data_and_a_clobbered_scratch(api):
+    # a repeated batched call with the same pointers, sizes and options reuses its launch plan
+    # (recorded stages, argument tables, iteration graph): with the scratch overwritten in
+    # between it must give the same bits, and with new data in the same buffers the result of
+    # the new data (equal to single-matrix calls on it)
+    import torch
+    g = G()
+    probs = [synth.refine_workload(nn, 1e3, "spd", case=600 + nn) for nn in (50, 90, 140)]
+    As = [g.to_dev(p[0]) for p in probs]
+    Xs = [api.colmajor(g.to_dev(p[1]))[0] for p in probs]   # passed without copies: same pointers
+    Ds = [g.to_dev(p[2]) for p in probs]
+    X0s = [x.clone() for x in Xs]
+    D0s = [d.clone() for d in Ds]
+    import ctypes as C
+    o = api.Options().to_c()
+    nn = (C.c_int64 * 3)(*[p[0].shape[0] for p in probs])
+    work = api.workspace(api._lib.load().frx_refine_batched_workspace_bytes(nn, 3, C.byref(o)), g.dev())
+    api.refine_batched(As, Xs, Ds, 1e-12, work=work)
+    first = [x.cpu().numpy() for x in Xs]
+    work.fill_(255)
+    for x, x0, d, d0 in zip(Xs, X0s, Ds, D0s):
+        x.copy_(x0)
+        d.copy_(d0)
+    api.refine_batched(As, Xs, Ds, 1e-12, work=work)
+    for a, b in zip(first, Xs):
+        assert np.array_equal(a, b.cpu().numpy())
+    # new starting eigenpairs in the same buffers
+    for k, (x, d) in enumerate(zip(Xs, Ds)):
+        A, Q, lam = synth.symmetric_matrix(probs[k][0].shape[0], 1e3, synth.seed_for(2, 600 + probs[k][0].shape[0]))
+        X1, D1 = synth.initial_guess(Q, lam, 77 + k, rel=1e-7)
+        x.copy_(torch.from_numpy(X1))
+        d.copy_(torch.from_numpy(D1))
+    starts = [(x.clone(), d.clone()) for x, d in zip(Xs, Ds)]
+    api.refine_batched(As, Xs, Ds, 1e-12, work=work)
+    for A, (x0, d0), x in zip(As, starts, Xs):
+        xs, ds = x0.clone(), d0.clone()
+        api.refine(A, xs, ds, 1e-12)
+        assert np.array_equal(xs.cpu().numpy(), x.cpu().numpy())
