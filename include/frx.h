@@ -170,7 +170,11 @@ FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx
  * reported norms may differ in their last bits: columns are summed with another block
  * size).  `infos` (host, `count` entries) may be NULL.  Batched calls on one device from
  * several host threads run one after another (they share the library's stream for the
- * device).
+ * device).  Launch plans: the library keeps, per device, the launch plans of the last 4
+ * distinct batched calls (recorded stages, a pinned host copy of their argument tables, the
+ * instantiated iteration graph) and reuses one when a call has the same pointers, leading
+ * dimensions, orders, options, delta and scratch; the tables are uploaded into the scratch
+ * on every call and all device work is redone.
  * Returns FRX_OK if every problem converged, else the largest soft status (1, 2), or the
  * first hard error (< 0; the per-problem statuses are then in infos when it is not NULL).
  * The call must not be made while `stream` is being captured.
