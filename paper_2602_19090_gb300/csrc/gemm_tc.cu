@@ -787,31 +787,33 @@ int sm_count(int& sms) {
 // clusters of CL CTAs of this variant that can be resident at once (the persistent grid)
 template <int BN, bool W32, int CL>
 int resident_clusters(size_t smem, int sms, int& out) {
-  if (CL == 1) {
+  if constexpr (CL == 1) {
+    (void)smem;
     out = sms;
     return FRX_OK;
-  }
-  static PerDevice pd;
-  static int n[FRX_MAX_DEVICES] = {};
-  FRX_TRY(once_per_device(pd, [&](int dev) -> int {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(CL * (sms / CL)));
-    cfg.blockDim = dim3(NUM_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    FRX_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n[dev], k_plane_gemm_tc<BN, W32, CL>, &cfg));
+  } else {
+    static PerDevice pd;
+    static int n[FRX_MAX_DEVICES] = {};
+    FRX_TRY(once_per_device(pd, [&](int dev) -> int {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(CL * (sms / CL)));
+      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CL;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      FRX_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n[dev], k_plane_gemm_tc<BN, W32, CL>, &cfg));
+      return FRX_OK;
+    }));
+    int dev = 0;
+    FRX_CUDA_TRY(cudaGetDevice(&dev));
+    out = n[dev] > 0 ? n[dev] : sms / CL;
     return FRX_OK;
-  }));
-  int dev = 0;
-  FRX_CUDA_TRY(cudaGetDevice(&dev));
-  out = n[dev] > 0 ? n[dev] : sms / CL;
-  return FRX_OK;
+  }
 }
 
 template <int BN, bool W32, int CL>
