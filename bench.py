@@ -57,14 +57,18 @@ def gemm_traffic():
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 40 for refine and batched, about a second of timed work "
+                        "so that the clock sampler sees it; 3 for the other workloads and the reference arm)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--cond", type=float, default=1e4)
     p.add_argument("--delta", type=float, default=1e-14)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--sample-rows", type=int, default=8)
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="CPU work of the oracle sample behind cpu_baseline (the reference arm's steps "
+                        "each time a fixed two-point sample instead)")
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
     p.add_argument("--workload", choices=["refine", "batched", "configs", "previous", "gemm"], default="refine",
@@ -74,7 +78,10 @@ def parse():
     p.add_argument("--sweep-n", default="1024,4096,8192", help="matrix orders of the ozaki_gemm sweep")
     p.add_argument("--tile", default="auto", choices=["auto", "128x128", "128x256", "256x256"],
                    help="tile configuration of the slice products (auto: the library's autotuner)")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = 40 if a.impl == "ours" and a.workload in ("refine", "batched") else 3
+    return a
 
 
 def peaks():
@@ -86,41 +93,73 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling around the timed region; the rows stamped inside it are kept."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 200
 
     def __init__(self, index):
         self.index = index
+        self.t0 = self.t1 = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # the sampler is running once its first row is out
+        t = time.time()
+        while self.p is not None and time.time() - t < 5.0 and os.path.getsize(self.f.name) == 0:
+            time.sleep(0.02)
+
+    def start(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.p is None:
             return None
+        time.sleep(1.5 * self.PERIOD_MS / 1e3)     # one more row after the region
         self.p.terminate()
         self.p.wait()
         rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
-        sm, mx, reasons = [], 0.0, set()
+        parsed = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                mx = max(mx, float(r[2]))
-                for nm, v in zip(names, r[5:9]):
-                    if v.strip().lower() == "active":
-                        reasons.add(nm)
+                parsed.append((self._stamp(r[0]), float(r[2]), float(r[3]),
+                               {nm for nm, v in zip(names, r[6:10]) if v.strip().lower() == "active"}))
             except (ValueError, IndexError):
                 pass
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [q for q in parsed if q[0] is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 <= q[0] <= self.t1]
+        where = "inside the timed region"
+        if not inside and self.t0 is not None and self.t1 is not None:
+            # a region shorter than the sampling period: the rows next to it on either side
+            pad = self.PERIOD_MS / 1e3
+            inside = [q for q in parsed if q[0] is not None and self.t0 - pad <= q[0] <= self.t1 + pad]
+            where = f"within {self.PERIOD_MS} ms of the timed region"
+        if not inside:
+            inside, where = parsed, "whole sampler run (no timestamps)"
+        sm = [q[1] for q in inside]
+        reasons = set().union(*[q[3] for q in inside]) if inside else set()
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max((q[2] for q in inside), default=None),
+                "reasons": sorted(reasons), "samples": len(sm), "samples_taken": where,
+                "region_s": (self.t1 - self.t0) if self.t0 is not None and self.t1 is not None else None}
 
 
 def dist_setup():
@@ -164,12 +203,14 @@ def job_throughput(ws, units_per_rank, ms_max):
     return ws * units_per_rank * 1e3 / ms_max
 
 
-def cpu_oracle_sample(A, X0, D0, delta, total_products, rows):
+def cpu_oracle_sample(A, X0, D0, delta, total_products, iters, rows=(64, 256), min_seconds=0.0):
     """Times the CPU oracle on a bounded sample and extrapolates to one full refinement.
 
-    Sample: the first iteration's V = A X^(1) product (all its slice pairs) on the
-    first `rows` rows of A; the full refinement is estimated as
-    t_sample * (n / rows) * (total slice products of the GPU run / products of V).
+    Sample: the oracle's plan of iteration 1 (scans, beta, the truncation of X) and its
+    V = A X^(1) product (all slice pairs) on the first r rows of A for increasing r (doubling
+    past the last entry of `rows` until `min_seconds` of CPU work have been spent).  A product
+    call costs a + b r (slicing X^(1) once, then r rows); a and b come from the last two calls.
+    The full refinement is estimated as iters * t_plan + (a + b n) * total_products / (V's pairs).
     """
     from oracle import ozaki as oz
     from oracle import refine as orf
@@ -177,14 +218,32 @@ def cpu_oracle_sample(A, X0, D0, delta, total_products, rows):
     t0 = time.perf_counter()
     p = orf.plan(A, X0, D0, delta, orf.Options())
     X1, _ = oz.tau_truncate_cols(X0, p["beta"], p["f"])
-    out = oz.ozaki_product(A[:rows], X1, p["kV"], p["sX"], p["kV"] + 1, eL=p["eA"][:rows], eR=p["f"])
-    t = time.perf_counter() - t0
+    t_plan = time.perf_counter() - t0
+    spent = t_plan
+    pts = []
+    seq = list(rows)
+    while seq:
+        r = min(int(seq.pop(0)), n)
+        t1 = time.perf_counter()
+        out = oz.ozaki_product(A[:r], X1, p["kV"], p["sX"], p["kV"] + 1, eL=p["eA"][:r], eR=p["f"])
+        dt = time.perf_counter() - t1
+        spent += dt
+        pts.append((r, dt))
+        if not seq and spent < min_seconds and r < n:
+            seq.append(2 * r)
     pv = len(out["pairs"])
-    est = t * (n / rows) * (total_products / pv)
+    (r1, u1), (r2, u2) = pts[-2], pts[-1]
+    b = max((u2 - u1) / (r2 - r1), 0.0)
+    a = max(u1 - b * r1, 0.0)
+    t_v = a + b * n
+    est = iters * t_plan + t_v * total_products / pv
     return {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle V = A X^(1) of iteration 1 ({pv} slice products) on {rows} of {n} rows "
-                       f"took {t:.1f} s; scaled by n/rows and by {total_products} total GPU slice "
-                       f"products / {pv}; the slice products use numpy's multithreaded FP64 BLAS "
+            "sample": (f"oracle plan of iteration 1 ({t_plan:.1f} s) and its V = A X^(1) product "
+                       f"({pv} slice products) on the first r of {n} rows, r = "
+                       f"{', '.join(str(q) for q, _ in pts)} ({', '.join(f'{u:.1f}' for _, u in pts)} s); "
+                       f"V on all rows = a + b n = {t_v:.1f} s from the last two; estimate = "
+                       f"{iters} x plan + V x ({total_products} slice products / {pv}); {spent:.1f} s "
+                       f"of CPU work in all; the slice products use numpy's multithreaded FP64 BLAS "
                        f"(exact for these integer sums), the rest of the oracle is single-threaded numpy")}
 
 
@@ -222,10 +281,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
+    clocks.start()
     s.record()
     infos = [one() for _ in range(args.steps)]
     e.record()
     torch.cuda.synchronize()
+    clocks.end()
     barrier(ws)
     clk = clocks.stop()
     api.profile_enable(False)
@@ -348,7 +409,8 @@ def run_ours(args):
                               "dgemm_tflops": 2 * n ** 3 / dgemm_ms / 1e9, **gl}
         del Ag, Bg, Agc, Bgc, ref, mag
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], args.sample_rows)
+        line["cpu_baseline"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], info["iters"],
+                                                 min_seconds=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -405,11 +467,13 @@ def run_batched(args):
     torch.cuda.synchronize()
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
+    clocks.start()
     s.record()
     for _ in range(args.steps):
         infos = one()
     e.record()
     torch.cuda.synchronize()
+    clocks.end()
     barrier(ws)
     clk = clocks.stop()
     prof = api.profile_read(reset=True)
@@ -569,7 +633,8 @@ def run_configs(args):
             print(json.dumps(rec), file=sys.stderr, flush=True)
             if not args.no_cpu_baseline and cond == 1e4 and variant == "spd" and delta == 1e-14:
                 # the CPU oracle beside the n = 2048 refinement, on the headline's sampled V product
-                out["cpu_baseline_n2048"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], args.sample_rows)
+                out["cpu_baseline_n2048"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], info["iters"],
+                                                              min_seconds=args.cpu_seconds)
         del At, X0t, D0t
     del work
 
@@ -780,12 +845,14 @@ def run_reference(args):
     from oracle import refine as orf
     p = orf.plan(A, X0, D0, delta, orf.Options())
     pv = len([1 for r in range(1, p["kV"] + 1) for s in range(1, p["sX"] + 1) if r + s <= p["kV"] + 1])
-    # stated estimate of one refinement's slice products: three iterations, each with the
-    # first iteration's V product count plus W and U products counted together as one more V
-    total = 3 * 2 * pv
+    # stated estimate of one refinement's slice products: two iterations (quadratic convergence
+    # from the 1e-8 start puts the second correction below delta), each with the first
+    # iteration's V product count plus W and U counted together as one more V
+    iters = 2
+    total = iters * 2 * pv
     vals = []
     for _ in range(args.warmup + args.steps):
-        vals.append(cpu_oracle_sample(A, X0, D0, delta, total, args.sample_rows))
+        vals.append(cpu_oracle_sample(A, X0, D0, delta, total, iters))
     v = vals[-args.steps:]
     value = statistics.median([x["value"] for x in v])
     cb = dict(v[-1])
