@@ -1,0 +1,72 @@
+"""Host-side logic of bench.py that needs no GPU: the clock record kept from the timed region,
+the fitted CPU-oracle sample, and the per-workload step defaults."""
+import datetime
+import sys
+import time
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def bench():
+    import bench as b
+    return b
+
+
+def _stamp(t):
+    return datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+
+
+def _fake_clocks(bench, tmp_path, rows, t0, t1):
+    # rows: (seconds after t0, SM MHz, sw_power_cap active?)
+    path = tmp_path / "clocks.csv"
+    with open(path, "w") as f:
+        for dt, mhz, cap in rows:
+            f.write(f"{_stamp(t0 + dt)}, 0, {mhz}, 2070, 900.00 W, 0x0, Not Active, Not Active, "
+                    f"Not Active, {'Active' if cap else 'Not Active'}\n")
+    c = bench.Clocks.__new__(bench.Clocks)
+    c.f = open(path)
+    c.p = type("P", (), {"terminate": lambda s: None, "wait": lambda s: None})()
+    c.t0, c.t1 = t0, t1
+    c.PERIOD_MS = 200
+    return c
+
+
+def test_clocks_keep_only_the_timed_region(bench, tmp_path, monkeypatch):
+    monkeypatch.setattr(time, "sleep", lambda s: None)
+    t0 = time.time()
+    c = _fake_clocks(bench, tmp_path, [(-0.4, 1100, False), (0.1, 2070, False), (0.3, 2050, True),
+                                       (0.5, 2070, False), (0.9, 900, False)], t0, t0 + 0.6)
+    rec = c.stop()
+    assert rec["samples"] == 3 and rec["samples_taken"] == "inside the timed region"
+    assert rec["sm_mhz"] == 2070 and rec["sm_max_mhz"] == 2070
+    assert rec["reasons"] == ["sw_power_cap"]
+
+
+def test_clocks_short_region_takes_the_adjacent_rows(bench, tmp_path, monkeypatch):
+    monkeypatch.setattr(time, "sleep", lambda s: None)
+    t0 = time.time()
+    c = _fake_clocks(bench, tmp_path, [(-0.15, 2040, False), (0.12, 2060, False), (0.6, 800, False)],
+                     t0, t0 + 0.05)
+    rec = c.stop()
+    assert rec["samples"] == 2 and rec["samples_taken"].startswith("within 200 ms")
+    assert rec["sm_mhz"] == 2050 and rec["reasons"] == []
+
+
+def test_step_defaults(bench, monkeypatch):
+    for argv, steps in ((["bench.py"], 40), (["bench.py", "--workload", "batched"], 40),
+                        (["bench.py", "--workload", "gemm"], 3), (["bench.py", "--impl", "reference"], 3),
+                        (["bench.py", "--steps", "7"], 7)):
+        monkeypatch.setattr(sys, "argv", argv)
+        assert bench.parse().steps == steps
+
+
+def test_oracle_sample_fits_fixed_and_per_row_cost(bench):
+    from paper_2602_19090_gb300 import synth
+    A, X0, D0, _ = synth.refine_workload(96, 1e4, "spd", case=3)
+    r = bench.cpu_oracle_sample(A, X0, D0, 1e-14, 100, 2, rows=(16, 32, 64))
+    assert r["kind"] == "oracle" and r["unit"] == "s" and r["value"] > 0
+    assert "r = 16, 32, 64" in r["sample"] and "2 x plan" in r["sample"]
+    # rows past n are clamped, and the doubling stops at n
+    r = bench.cpu_oracle_sample(A, X0, D0, 1e-14, 100, 2, rows=(32, 64), min_seconds=1e9)
+    assert "r = 32, 64, 96" in r["sample"]
