@@ -1,0 +1,144 @@
+"""Planted mistakes: the oracle's pins catch a plausible error anywhere in it.
+
+Each case copies the oracle's modules into a fresh package with ONE expression changed (a wrong
+sign, a dropped term, an index off by one, a transposed operand) and runs the pins of
+test_oracle_dd / test_oracle_ozaki / test_oracle_refine against the copy.  At least one pin
+must fail.  The stored regression of workload 0 is left out: it repeats the oracle's own
+output, so it would catch every change and pin nothing.  Everything runs on the CPU; the
+oracle itself is never modified.
+"""
+import os
+import sys
+import types
+
+import pytest
+
+from tests import test_oracle_dd as tdd
+from tests import test_oracle_ozaki as toz
+from tests import test_oracle_refine as trf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+MODULES = ("ddarith", "ozaki", "refine", "truth")
+
+# (module, original text, planted text, what the mistake is)
+MUTANTS = [
+    ("ddarith", "y = (a - (x - z)) + (b - z)", "y = (a - (x - z)) - (b - z)", "TwoSum: wrong sign"),
+    ("ddarith", "e = ((ah * bh - p) + ah * bl + al * bh) + al * bl", "e = ((ah * bh - p) + ah * bl + al * bh)",
+     "TwoProduct: dropped lo*lo term"),
+    ("ddarith", "    cl = bl + t\n", "    cl = bl\n", "pair arithmetic: dropped TwoSum error"),
+    ("ddarith", "    se = se + al\n", "    se = se\n", "dd + d: dropped low word"),
+    ("ozaki", "e + 1 - DIGIT_BITS * r))", "e - DIGIT_BITS * r))", "plane weight: exponent off by one"),
+    ("ozaki", "d = np.rint(res / ws)", "d = np.floor(res / ws)", "digits: truncation instead of round to nearest"),
+    ("ozaki", "S[t] = S[t] + P if t in S else P", "S[t] = P", "anti-diagonal sum: dropped pairs"),
+    ("ozaki", "if r + s <= T]", "if r + s < T]", "pair set: last anti-diagonal dropped"),
+    ("ozaki", "eL + eR + 2 - DIGIT_BITS * t", "eL + eR + 1 - DIGIT_BITS * t", "recombination: scale off by one"),
+    ("ozaki", "return np.transpose(d, (0, 2, 1)), f, res.T", "return d, f, res.T",
+     "column slicing: transposed digit planes"),
+    ("ozaki", "f + beta)))", "f + beta + 1)))", "tau: exponent off by one"),
+    ("ozaki", "hi, lo = dd.dd_add_d(hi, lo, term)", "hi, lo = dd.dd_add_d(hi, 0.0 * lo, term)",
+     "recombination: low word dropped"),
+    ("refine", "diff = lam[None, :] - lam[:, None]", "diff = lam[:, None] - lam[None, :]",
+     "correction: wrong sign of the eigenvalue gap"),
+    ("refine", "np.fill_diagonal(E, r / 2.0)", "np.fill_diagonal(E, r)", "correction: diagonal r instead of r/2"),
+    ("refine", "r = dd.dd_add_d(-nh, -nl, 1.0)[0]", "r = dd.dd_add_d(nh, nl, -1.0)[0]", "r: wrong sign"),
+    ("refine", "Wp = oz.ozaki_product(X1.T, Res,", "Wp = oz.ozaki_product(X1, Res,", "W: transposed operand"),
+    ("refine", "ch, cl = dd.pair_add(X1, Up[\"hi\"], Up[\"lo\"])", "ch, cl = dd.pair_add(X, Up[\"hi\"], Up[\"lo\"])",
+     "update: X instead of X^(1)"),
+    ("refine", "math.sqrt((xi * delta * g) / (Lam * S2)) / (0.75 * U)", "math.sqrt((xi * delta * g) / (Lam * S2)) / U",
+     "beta: dropped 0.75 of tau"),
+    ("refine", "return 53 - beta + ceil_log2_sqrt(n)", "return 53 - beta + ceil_log2_int(n)",
+     "alpha: log2 n for log2 sqrt n"),
+    ("refine", "- (oz.DIGIT_BITS - 1))", "- oz.DIGIT_BITS)", "slice rule: digit bound off by one bit"),
+    ("refine", "E[i, j] = -sh / 2.0", "E[i, j] = sh / 2.0", "cluster rule: wrong sign of r_ij"),
+    ("refine", "est = step_norm * step_norm * Lam_new", "est = step_norm * Lam_new", "stopping test: dropped square"),
+]
+
+
+def _mutant_package(module, old, new):
+    name = "oracle_mutant"
+    pkg = types.ModuleType(name)
+    pkg.__path__ = []
+    saved = {k: sys.modules.get(k) for k in [name] + [f"{name}.{m}" for m in MODULES]}
+    sys.modules[name] = pkg
+    try:
+        for m in MODULES:
+            path = os.path.join(ROOT, "oracle", m + ".py")
+            src = open(path).read()
+            if m == module:
+                assert src.count(old) == 1, (m, old)
+                src = src.replace(old, new)
+            mod = types.ModuleType(f"{name}.{m}")
+            mod.__package__ = name
+            mod.__file__ = path
+            sys.modules[mod.__name__] = mod
+            exec(compile(src, path, "exec"), mod.__dict__)
+            setattr(pkg, m, mod)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                sys.modules.pop(k, None)
+            else:
+                sys.modules[k] = v
+    return pkg
+
+
+def _pins():
+    """Every pin as a zero-argument call, cheapest first."""
+    calls = []
+    for mod in (tdd, toz, trf):
+        for nm in sorted(dir(mod)):
+            fn = getattr(mod, nm)
+            if not nm.startswith("test_") or not callable(fn) or nm == "test_golden_workload0_regression":
+                continue
+            marks = getattr(fn, "pytestmark", [])
+            params = [m for m in marks if m.name == "parametrize"]
+            if not params:
+                calls.append((f"{mod.__name__}.{nm}", fn, {}))
+                continue
+            argnames, values = params[0].args
+            names = [a.strip() for a in argnames.split(",")]
+            for v in values:
+                kw = dict(zip(names, v)) if len(names) > 1 else {names[0]: v}
+                calls.append((f"{mod.__name__}.{nm}{list(kw.values())}", fn, kw))
+    return calls
+
+
+def _fails(fn, kw):
+    try:
+        fn(**kw)
+    except pytest.skip.Exception:
+        return False
+    except Exception:          # an assertion or a crash: the pin rejects the copy
+        return True
+    return False
+
+
+def test_every_snippet_is_in_the_oracle():
+    for module, old, _, what in MUTANTS:
+        src = open(os.path.join(ROOT, "oracle", module + ".py")).read()
+        assert src.count(old) == 1, what
+
+
+def test_unchanged_copy_passes_every_pin(monkeypatch):
+    # the control: an unchanged copy fails no pin, so a failure below is the planted mistake's
+    pkg = _mutant_package(None, None, None)
+    _patch(monkeypatch, pkg)
+    failed = [nm for nm, fn, kw in _pins() if _fails(fn, kw)]
+    assert failed == []
+
+
+def _patch(monkeypatch, pkg):
+    monkeypatch.setattr(tdd, "dd", pkg.ddarith)
+    monkeypatch.setattr(toz, "oz", pkg.ozaki)
+    for attr, m in (("dd", pkg.ddarith), ("oz", pkg.ozaki), ("rf", pkg.refine), ("tr", pkg.truth)):
+        monkeypatch.setattr(trf, attr, m)
+
+
+@pytest.mark.parametrize("module,old,new,what", MUTANTS, ids=[m[3] for m in MUTANTS])
+def test_planted_mistake_is_caught(monkeypatch, module, old, new, what):
+    pkg = _mutant_package(module, old, new)
+    _patch(monkeypatch, pkg)
+    for nm, fn, kw in _pins():
+        if _fails(fn, kw):
+            return
+    pytest.fail(f"no pin catches: {what}")

@@ -19,7 +19,7 @@ def test_beta_alpha_worked_example():
     # 4096 * 1e-14 * 2.25e-7 / 64 = 1.44e-19; sqrt = 3.795e-10; / (0.75 * 2^-53) = 4.557e6;
     # log2 = 22.12 -> beta = 22 (floor), 23 (ceil);  alpha = 53 - 22 + ceil(log2 64) = 37
     # (theory: 53 - 22 + log2 4096 = 43);  X^(1) keeps bits 2^f ... 2^(f+22-53):
-    # 32 bit positions -> ceil(32 / 7) = 5 planes.
+    # 32 bit positions -> ceil(32 / 8) = 4 planes of 8-bit digits.
     o = rf.Options()
     assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, o) == 22
     assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, rf.Options(beta_rounding="ceil")) == 23
@@ -28,7 +28,7 @@ def test_beta_alpha_worked_example():
     X = np.full((4096, 3), 0.07)
     p = rf.plan(np.eye(3), X[:3], np.array([0.0, 2.25e-7, 1.0]), 1e-14, o)
     assert p["f"].tolist() == [-3, -3, -3]
-    assert -(-(54 - 22) // 7) == 5
+    assert -(-(54 - 22) // oz.DIGIT_BITS) == 4
 
 
 def test_ceil_log2_sqrt_exact():
@@ -132,6 +132,23 @@ def test_workload0_reaches_delta():
     assert tr.forward_error(Xh, Xl, X) <= 1e-14
 
 
+@pytest.mark.parametrize("n,cond,pert,delta", [(64, 1e8, 1e-8, 1e-14), (48, 1e4, 1e-6, 1e-14),
+                                                (64, 1e2, 1e-4, 1e-15)])
+def test_stop_within_one_iteration_of_the_truth(n, cond, pert, delta):
+    # the stopping estimate models the forward error after the step (the error model of
+    # Sec. 3.2, quadratic in the step): with quadratic convergence the iteration stops no later
+    # than one step after the true forward error first falls to delta, and never before it
+    A, Q, lam = synth.symmetric_matrix(n, cond, 7, "spd")
+    X0, D0 = synth.initial_guess(Q, lam, 7, pert)
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    hist = []
+    X, l, info = rf.refine(A, X0, D0, delta, rf.Options(), history=hist)
+    assert info["status"] == "converged"
+    fe = [tr.forward_error(Xh, Xl, h["X"]) for h in hist]
+    first = next(k for k, e in enumerate(fe, 1) if e <= delta)
+    assert first <= info["iters"] <= first + 1
+
+
 def test_workload0_fixed_56_bit_a_floor():
     # 7 planes of A (56 bits) cannot resolve gaps of 3.4e-9 to 1e-14: the error stalls
     # near 2^-56 / gap and the iteration does not converge.
@@ -163,6 +180,26 @@ def test_clusters_auto_rule_subspaces():
         assert tr.subspace_error(Xh, Xl, X, [i, i + 1]) <= 1e-12
         mask[i] = mask[i + 1] = False
     assert tr.forward_error(Xh[:, mask], Xl[:, mask], X[:, mask]) <= 1e-12
+
+
+def test_cluster_rule_restores_orthonormality_inside_a_cluster():
+    # the true eigenvectors are orthonormal; a start whose clustered columns are mixed by a
+    # non-orthogonal 2 x 2 (x_i^T x_j ~ 2e-6) is repaired by e~_ij = r_ij / 2 (R -> O(R^2) per
+    # step) while the subspace stays put, so both the subspace and X^T X = I hold to delta
+    n = 32
+    A, Q, lam = synth.symmetric_matrix(n, 1e2, 5, "clustered", cluster_pairs=2, cluster_gap=1e-10)
+    X0, D0 = synth.initial_guess(Q, lam, 5, 1e-8)
+    ci = np.nonzero(np.diff(np.sort(lam)) < 1e-9)[0]
+    for i in ci:
+        X0[:, [i, i + 1]] = X0[:, [i, i + 1]] @ np.array([[1.0, 1e-6], [1e-6, 1.0]])
+    Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
+    X, l, info = rf.refine(A, X0, D0, 1e-12, rf.Options(cluster="auto"))
+    assert info["status"] == "converged"
+    G = X.T @ X - np.eye(n)
+    for i in ci:
+        J = [i, i + 1]
+        assert np.abs(G[np.ix_(J, J)]).max() <= 1e-12
+        assert tr.subspace_error(Xh, Xl, X, J) <= 1e-12
 
 
 def test_truth_against_mpmath():
