@@ -331,7 +331,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"refine n={n} SPD geometric cond {args.cond:g}, start perturbed 1e-8, "
                                f"delta={delta:g}", "n": n, "cond": args.cond, "delta": delta,
-                   "per_gpu_matrices": 1, "l2": "inputs larger than L2 (A alone 134 MB)",
+                   "per_gpu_matrices": 1,
+                   "l2": (f"inputs larger than L2 (A alone {A.nbytes / 1e6:.0f} MB > 129 MB)" if A.nbytes > 129e6 else
+                          f"A is {A.nbytes / 1e6:.0f} MB, below the 129 MB L2; V's digit planes "
+                          f"({info['k_V']} x {4 * n * n / 1e6:.0f} MB) are not"),
                    "parallelism": f"replicas x{ws}"},
         "refine": {"status": info["status_name"], "iters": info["iters"], "err_est": info["err_est"],
                    "step": info["step"], "products": info["products"], "k_V": info["k_V"],
@@ -339,7 +342,9 @@ def run_ours(args):
         "refinements_per_s": job_throughput(ws, 1, ms),
         "roofline": {"bound": "tensor", "kernel": "slice-product GEMM (digit planes)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": gemm_traffic(),
+                     "frac": achieved / peak if peak else None,
+                     # the committed counters were taken on the default workload only
+                     "traffic": gemm_traffic() if (n, args.cond, delta) == (4096, 1e4, 1e-14) else None,
                      "peak_source": f"{src} bf16_tflops (burst; sustained {pk.get('bf16_tflops_sustained')})",
                      "gemm_share_of_step": prof["gemm_ms"] / (ms * args.steps) if ms else None},
         "gpu_launches": prof["kernel_launches"],
