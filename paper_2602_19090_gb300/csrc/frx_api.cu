@@ -1,5 +1,5 @@
 // C ABI of frx: argument checks, workspace layout, the host-side plan of each
-// iteration (Sec. 3.3 / Sec. 4.1) and the refinement driver (Algorithm 1 iterated).
+// iteration (Sec. 3.3 / Sec. 4.1) and the refinement loop (Algorithm 1 iterated).
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
