@@ -486,6 +486,43 @@ def run_batched(args):
     stats = {}
     for i in infos:
         stats[i["status_name"]] = stats.get(i["status_name"], 0) + 1
+
+    # end to end through the public API: every step copies all matrices, starting vectors and
+    # estimates in from pinned host memory and the refined X, D back
+    aoffs = np.concatenate([[0], np.cumsum([p[0].size for p in probs])]).astype(np.int64)
+    A_h = torch.from_numpy(np.concatenate([p[0].ravel() for p in probs])).pin_memory()
+    X0_h = X0flat.cpu().pin_memory()
+    D0_h = D0flat.cpu().pin_memory()
+    Xo_h = torch.empty_like(X0_h).pin_memory()
+    Do_h = torch.empty_like(D0_h).pin_memory()
+    Aflat = torch.empty(A_h.shape, dtype=torch.float64, device=dev)
+    Aviews = [Aflat[aoffs[b]:aoffs[b + 1]].view(int(p[0].shape[0]), int(p[0].shape[1])) for b, p in enumerate(probs)]
+
+    def one_e2e():
+        Aflat.copy_(A_h, non_blocking=True)
+        Xflat.copy_(X0_h, non_blocking=True)
+        Dflat.copy_(D0_h, non_blocking=True)
+        out = api.refine_batched(Aviews, Xs, Ds, delta, work=work)
+        Xo_h.copy_(Xflat, non_blocking=True)
+        Do_h.copy_(Dflat, non_blocking=True)
+        return out
+
+    one_e2e()        # untimed: these buffers get their own launch plan
+    torch.cuda.synchronize()
+    barrier(ws)
+    s2 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    s2.record()
+    for _ in range(args.steps):
+        one_e2e()
+    e2.record()
+    torch.cuda.synchronize()
+    e2e_ms = allmax(ws, s2.elapsed_time(e2)) / args.steps
+    e2e = {"value": job_throughput(ws, args.count, e2e_ms), "unit": "matrices/s",
+           "h2d_bytes_per_step": int((A_h.numel() + X0_h.numel() + D0_h.numel()) * 8),
+           "d2h_bytes_per_step": int((Xo_h.numel() + Do_h.numel()) * 8)}
+    del Aflat, Aviews
+
     # per-matrix native-FP64 loop (cuBLAS DGEMM), once
     fstats, fp64_ms = {}, None
     if not args.no_fp64:
@@ -510,8 +547,11 @@ def run_batched(args):
         "dtype": "bf16 digit planes, exact int32 plane sums, f64/dd elsewhere", "data": "synthetic",
         "config": {"workload": f"batched: {args.count} matrices, n ~ U[32, 512], cond log-uniform [1e2, 1e12], "
                                f"start perturbed 1e-8, delta={delta:g}", "count": args.count,
-                   "n_min": int(sizes.min()), "n_max": int(sizes.max()), "delta": delta},
+                   "n_min": int(sizes.min()), "n_max": int(sizes.max()), "delta": delta,
+                   "l2": (f"inputs larger than L2 (A, X and D of the batch: "
+                          f"{(sum(p[0].nbytes + p[1].nbytes + p[2].nbytes for p in probs)) / 1e6:.0f} MB > 129 MB)")},
         "statuses": stats, "gpu_launches": prof["kernel_launches"],
+        "e2e": e2e,
         "tile": {"used": api.last_tile(), "policy": "autotuned" if args.tile == "auto" else "forced",
                  "tuner": api.tune_stats()},
         "fp64_loop": ({"seconds": fp64_ms / 1e3, "matrices_per_s": args.count * 1e3 / fp64_ms, "statuses": fstats,
