@@ -1,5 +1,4 @@
 """Parity of the CUDA path with the CPU oracle (run on a GB300: pytest -m gpu)."""
-import math
 
 import numpy as np
 import pytest
@@ -247,7 +246,6 @@ def test_refine_rejects_bad_input(api):
 
 
 def test_fp64_comparator_reaches_delta():
-    import torch
     from paper_2602_19090_gb300 import fp64_refine
     g = G()
     A, X0, D0 = synth.workload0()
