@@ -90,7 +90,7 @@ typedef struct {
   int status;            /* same as the return value                                      */
   int iters;             /* iterations performed                                          */
   int beta, alpha;       /* last iteration's beta (eq. tau) and alpha (Sec. 4.1)           */
-  int s_X;               /* digit planes of X^(1) = ceil((54 - beta) / 7)                 */
+  int s_X;               /* digit planes of X^(1) = ceil((54 - beta) / 8)                 */
   int k_V, k_W, k_U;     /* slice counts of the three products of the last iteration      */
   long long products;    /* slice-pair products executed over all iterations              */
   double err_est;        /* est = step^2 * max|lam| / (xi_stop * gap), last iteration      */
@@ -177,6 +177,10 @@ FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx
  * on every call and all device work is redone.
  * Returns FRX_OK if every problem converged, else the largest soft status (1, 2), or the
  * first hard error (< 0; the per-problem statuses are then in infos when it is not NULL).
+ * Argument errors, checked before any device work: count < 1, a NULL array or pointer, an
+ * order below 1 or a leading dimension below it (FRX_E_ARG), delta <= u (FRX_E_DELTA), an
+ * order above FRX_MAX_N (FRX_E_UNSUPPORTED), scratch NULL, not 256-byte aligned or below
+ * frx_refine_batched_workspace_bytes (FRX_E_WORKSPACE).
  * The call must not be made while `stream` is being captured.
  */
 FRX_API size_t frx_refine_batched_workspace_bytes(const int64_t* n, int count, const frx_opts* opts);

@@ -117,9 +117,14 @@ def refine(A, X, D, delta, opts: Options | None = None, work=None, stream=None):
 
 
 def refine_batched(As, Xs, Ds, delta, opts: Options | None = None, work=None, stream=None):
-    """Batched in-place refinement of independent problems; returns a list of info dicts."""
+    """Batched in-place refinement of independent problems; returns a list of info dicts
+    (an empty list for an empty batch, which the library is not called for)."""
     lib = _lib.load()
     count = len(As)
+    if not (count == len(Xs) == len(Ds)):
+        raise ValueError("refine_batched: As, Xs and Ds must have the same length")
+    if count == 0:
+        return []
     o = (opts or Options()).to_c()
     cols = [symmetric_colmajor(A) for A in As]
     xcols = [colmajor(X) for X in Xs]

@@ -916,6 +916,8 @@ int frx_refine_batched(const double* const* A, const int64_t* lda, double* const
     if (!A[b] || !X[b] || !D[b] || n[b] < 1 || lda[b] < n[b] || ldx[b] < n[b]) return FRX_E_ARG;
     if (n[b] > FRX_MAX_N) return FRX_E_UNSUPPORTED;
   }
+  // the scratch is checked before any device call, as in frx_refine
+  if (!work || !aligned256(work) || work_bytes < batch_layout(n, count, o.k_cap).bytes) return FRX_E_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   FRX_CUDA_TRY(cudaStreamIsCapturing(s, &cs));

@@ -101,3 +101,60 @@ def test_group_size_keeps_sums_exact(lib):
         smax = pmax * K * 16384
         assert smax * 2 ** (8 * (gs - 1)) * 256 / 255 < 2 ** 62
         assert smax * 2 ** (8 * gs) * 256 / 255 >= 2 ** 61    # not needlessly small
+
+
+def test_batched_argument_errors_before_any_device_work(lib):
+    import ctypes as C
+    p = C.c_void_p(256)
+    P1 = C.c_void_p * 1
+    I1 = C.c_int64 * 1
+    A, ld, n = P1(256), I1(4), I1(4)
+    work, big = p, 1 << 20
+
+    def call(A=A, lda=ld, X=A, ldx=ld, D=A, n=n, count=1, delta=1e-10, work=work, wb=big):
+        return lib.frx_refine_batched(A, lda, X, ldx, D, n, count, delta, None, work, wb, None, None)
+
+    assert call(count=0) == -1 and call(count=-1) == -1
+    assert call(A=None) == -1 and call(n=None) == -1
+    assert call(A=P1(None)) == -1
+    assert call(lda=I1(3)) == -1 and call(n=I1(0)) == -1
+    assert call(delta=2.0 ** -53) == -3
+    assert call(n=I1(12289), lda=I1(12289), ldx=I1(12289)) == -7
+    # scratch: NULL, misaligned, one byte short of the documented size
+    need = lib.frx_refine_batched_workspace_bytes(n, 1, None)
+    assert need > 0 and lib.frx_refine_batched_workspace_bytes(n, 0, None) == 0
+    assert call(work=None, wb=0) == -5
+    assert call(work=C.c_void_p(256 + 8)) == -5
+    assert call(wb=need - 1) == -5
+
+
+def test_ozaki_gemm_limits_before_any_device_work(lib):
+    import ctypes as C
+    p = C.c_void_p(256)
+    # the allocation-free form: m, n, k <= 512 and slices <= 8
+    assert lib.frx_ozaki_gemm_static(p, 513, p, 513, p, 513, None, 513, 4, 4, 4, 0, None) == -7
+    assert lib.frx_ozaki_gemm_static(p, 8, p, 8, p, 8, None, 8, 8, 8, 9, 0, None) == -7
+    assert lib.frx_ozaki_gemm_static(p, 8, p, 8, p, 8, None, 0, 8, 8, 4, 0, None) == -1
+    # the general form: slices 1..16, a known mode, k <= 65536, enough scratch
+    assert lib.frx_ozaki_gemm(p, 8, p, 8, p, 8, None, 8, 8, 8, 17, 0, p, 1 << 30, None) == -1
+    assert lib.frx_ozaki_gemm(p, 8, p, 8, p, 8, None, 8, 8, 8, 4, 2, p, 1 << 30, None) == -1
+    assert lib.frx_ozaki_gemm(p, 8, p, 65537, p, 8, None, 8, 8, 65537, 4, 0, p, 1 << 30, None) == -7
+    need = lib.frx_ozaki_gemm_workspace_bytes(8, 8, 8, 4)
+    assert lib.frx_ozaki_gemm(p, 8, p, 8, p, 8, None, 8, 8, 8, 4, 0, p, need - 1, None) == -5
+
+
+def test_bit_level_calls_check_their_arguments(lib):
+    import ctypes as C
+    p, e = C.c_void_p(256), C.c_void_p(512)
+    assert lib.frx_exponents(p, 4, 4, 4, 2, e, p, 1 << 20, None) == -1      # axis 0 or 1
+    assert lib.frx_exponents(p, 3, 4, 4, 0, e, p, 1 << 20, None) == -1      # ld < rows
+    assert lib.frx_slice_planes(p, 4, 4, 4, 0, e, 17, p, 1 << 10, 8, None) == -1   # k <= 16
+    assert lib.frx_slice_planes(p, 4, 4, 4, 0, e, 4, p, 1 << 10, 7, None) == -1    # pitch % 8
+    assert lib.frx_plane_products(p, 1024, p, 1024, 8, 4, 4, 4, 0, 4, 5, p, None) == -1  # kL >= 1
+
+
+def test_binding_empty_batch_is_a_no_op(lib):
+    from paper_2602_19090_gb300 import api
+    assert api.refine_batched([], [], [], 1e-12) == []
+    with pytest.raises(ValueError):
+        api.refine_batched([], [None], [], 1e-12)
