@@ -158,3 +158,22 @@ def test_binding_empty_batch_is_a_no_op(lib):
     assert api.refine_batched([], [], [], 1e-12) == []
     with pytest.raises(ValueError):
         api.refine_batched([], [None], [], 1e-12)
+
+
+def test_workspace_sizes_grow_with_the_problem(lib):
+    import ctypes as C
+    from paper_2602_19090_gb300 import _lib
+    o = _lib.Opts()
+    lib.frx_default_opts(C.byref(o))
+    sizes = [lib.frx_refine_workspace_bytes(n, C.byref(o)) for n in (1, 2, 63, 64, 65, 1000, 4096, 12288)]
+    assert all(b > 0 for b in sizes)
+    assert sizes == sorted(sizes) and len(set(sizes[3:])) == len(sizes[3:])
+    o.k_cap = 8                       # fewer planes of A: less scratch
+    assert lib.frx_refine_workspace_bytes(4096, C.byref(o)) < sizes[6]
+    g = [lib.frx_ozaki_gemm_workspace_bytes(300, 200, 500, k) for k in range(1, 17)]
+    assert all(b > 0 for b in g) and g == sorted(g)
+    I = C.c_int64 * 3
+    one = lib.frx_refine_batched_workspace_bytes(I(100, 0, 0), 1, None)
+    three = lib.frx_refine_batched_workspace_bytes(I(100, 200, 50), 3, None)
+    assert 0 < one < three
+    assert lib.frx_refine_batched_workspace_bytes(I(100, 12289, 50), 3, None) == 0
