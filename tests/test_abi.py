@@ -177,3 +177,16 @@ def test_workspace_sizes_grow_with_the_problem(lib):
     three = lib.frx_refine_batched_workspace_bytes(I(100, 200, 50), 3, None)
     assert 0 < one < three
     assert lib.frx_refine_batched_workspace_bytes(I(100, 12289, 50), 3, None) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # no CPU fallback: without the CUDA library every entry point of the binding raises
+    from paper_2602_19090_gb300 import _lib, api
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libfrx.so"))
+    with pytest.raises(RuntimeError, match="library missing"):
+        _lib.load()
+    with pytest.raises(RuntimeError, match="library missing"):
+        api.refine_batched([], [], [], 1e-12)
+    with pytest.raises(RuntimeError, match="library missing"):
+        api.last_tile()
