@@ -225,3 +225,27 @@ def test_adaptive_slicing_needs_no_more_slices_than_the_fixed_grid(phi):
         kf = next(k for k in range(1, 20) if np.all(oz.slice_rows(row, k)[2] == 0))
         ka = next(k for k in range(1, 20) if np.all(oz.slice_rows_adaptive(row, k, 46)[2] == 0))
         assert ka <= kf
+
+
+def test_product_counts_printed_in_the_paper():
+    # tests/golden/paper_product_counts.json: the counts Sec. 2.3 and Sec. 4.1 print
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_product_counts.json")))
+    tri = g["triangular_products"]
+    for k, p, a in zip(tri["k"], tri["products"], tri["additions"]):
+        pairs = oz.pair_set(k, k, k + 1)
+        assert len(pairs) == p
+        # the exact sums add every product but the first of its anti-diagonal into it, then
+        # the anti-diagonals into each other: (pairs - diagonals) + (diagonals - 1) additions
+        diagonals = len({r + s for r, s in pairs})
+        assert (len(pairs) - diagonals) + (diagonals - 1) == a
+    prev = g["previous_study"]
+    assert len(oz.pair_set(prev["n_A"], prev["n_X"], prev["n_A"] + 1)) == prev["products"]
+    pro = g["proposed"]
+    n_eq = pro["equal_cost_n_A"]
+    # n_X = 1: the accurate A X^(1) takes n_A products (one per slice of A)
+    assert len(oz.pair_set(n_eq, pro["n_X"], n_eq + 1)) == n_eq
+    # both forms add the same two products per iteration, so the costs meet where the A X
+    # products do: n_A = the previous study's six
+    assert n_eq == prev["products"]
