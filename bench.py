@@ -76,7 +76,7 @@ def parse():
                         "configs: the n=2048 variants and the n=8192 forward-error sweep")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--sweep-n", default="1024,4096,8192", help="matrix orders of the ozaki_gemm sweep")
-    p.add_argument("--tile", default="auto", choices=["auto", "128x128", "128x256", "256x256"],
+    p.add_argument("--tile", default="auto", choices=["auto", "128x128", "128x256"],
                    help="tile configuration of the slice products (auto: the library's autotuner)")
     a = p.parse_args()
     if a.steps is None:

@@ -217,11 +217,16 @@ FRX_API int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_
  * Same arguments and results as frx_ozaki_gemm, minus `work`/`work_bytes`.
  *   Limits: m, n, k <= 512 and slices <= 8; larger sizes return FRX_E_UNSUPPORTED
  *   before any device work.
- *   Scratch: a fixed 24 MiB + 64 KiB array of device memory inside this library; every
- *   device that loads the library holds it until the process exits.  The call
- *   allocates nothing.  The first call on a device (with that device current) looks
- *   up the array's device address once; make that first call before any stream
- *   capture begins.  Call with the device that owns `stream` current.
+ *   Scratch: a fixed 24 MiB + 64 KiB array of device memory inside this library.  It is
+ *   reserved on a device when the library's code for this call is loaded there: with
+ *   CUDA's default lazy module loading at the first call on that device (with
+ *   CUDA_MODULE_LOADING=EAGER when the library is loaded), and it is held until the process
+ *   exits.  A caller whose framework later takes all free device memory must therefore make
+ *   one call on each device first.  The call allocates nothing.  Every call looks up the
+ *   array's device address on the current device (a host-side query); make the first call on
+ *   a device before any stream capture begins.  Call with the device that owns `stream`
+ *   current.  Like frx_ozaki_gemm, every call synchronises `stream` to read back its status
+ *   word.
  *   Sharing: every call uses the same array and leaves its contents behind (each call
  *   clears what it needs).  Calls whose GPU work overlaps (different streams or host
  *   threads without ordering) race on the array: order them, e.g. on one stream.
@@ -292,13 +297,8 @@ FRX_API int frx_check_wait_timeout(void* work, size_t work_bytes, void* stream);
 /*
  * Tile autotuner of the slice products (no counterpart in the paper; it changes the time of
  * a product, never its result: every tile sum is exact).
- *   The tensor-core kernel covers a product's m x n output with one of three tile
- *   configurations:
- *     FRX_TILE_128x128, FRX_TILE_128x256  one CTA per tile;
- *     FRX_TILE_256x256  a pair of CTAs (a 2-CTA cluster) per 256 x 256 super-tile, each CTA
- *                       computing one 128-row half and loading half of the shared B panel,
- *                       which it multicasts to both (offered when m > 128; batched calls use
- *                       one CTA per tile).
+ *   The tensor-core kernel covers a product's m x n output with one of two tile
+ *   configurations, one CTA per tile: FRX_TILE_128x128 or FRX_TILE_128x256.
  *   The first time a product shape is seen (frx_ozaki_gemm: m, n, k, planes and pair bound;
  *   frx_refine: n and the plane capacities; frx_refine_batched: the sorted orders of the
  *   batch), a cost model settles it when 128 x 256 tiles cover the output with under 3%
@@ -307,7 +307,7 @@ FRX_API int frx_check_wait_timeout(void* work, size_t work_bytes, void* stream);
  *   synchronisation) and the fastest is cached for the shape, process-wide.  On a stream
  *   under capture nothing is timed or cached: the model's estimate is used.
  *   frx_set_tile(t): FRX_TILE_AUTO (0, default) autotunes; another FRX_TILE_* forces that
- *     configuration where it is offered (FRX_TILE_128x256 elsewhere).  Returns the previous
+ *     configuration (int64 exact sums always use 128 x 128 tiles).  Returns the previous
  *     setting, or FRX_E_ARG for another value.  Process-wide.
  *   frx_last_tile(): the configuration of the last slice-product launch made by the calling
  *     host thread (FRX_TILE_AUTO before any).
@@ -317,7 +317,6 @@ FRX_API int frx_check_wait_timeout(void* work, size_t work_bytes, void* stream);
 #define FRX_TILE_AUTO 0
 #define FRX_TILE_128x128 1
 #define FRX_TILE_128x256 2
-#define FRX_TILE_256x256 3
 FRX_API int frx_set_tile(int tile);
 FRX_API int frx_last_tile(void);
 FRX_API int frx_tune_stats(long long* measured, long long* modelled, long long* hits, int clear);

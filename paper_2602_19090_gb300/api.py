@@ -255,13 +255,13 @@ def plane_products(Lp, Rp, K, kL, kR, T, stream=None):
     return out, gs
 
 
-TILES = {"auto": 0, "128x128": 1, "128x256": 2, "256x256": 3}
+TILES = {"auto": 0, "128x128": 1, "128x256": 2}
 TILE_NAMES = {v: k for k, v in TILES.items()}
 
 
 def set_tile(tile) -> str:
-    """Force the slice products' tile configuration ("128x128", "128x256", or "256x256" for
-    pairs of CTAs); "auto" restores the autotuner.  Returns the previous setting's name."""
+    """Force the slice products' tile configuration ("128x128" or "128x256"); "auto" restores
+    the autotuner.  Returns the previous setting's name."""
     code = TILES[tile] if isinstance(tile, str) else int(tile)
     st = _lib.load().frx_set_tile(code)
     if st < 0:

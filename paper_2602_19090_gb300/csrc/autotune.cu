@@ -1,11 +1,9 @@
 // Tile autotuner of the slice products.
 //
 // The persistent tensor-core kernel covers the M x N output of a product with 128 x 256 or
-// 128 x 128 tiles per CTA, or with 256 x 256 super-tiles per pair of CTAs (a 2-CTA cluster whose
-// halves share, by multicast, the B panel they both need).  Wide tiles read each A panel once
-// for more columns and pairs halve the B traffic from L2; narrow tiles waste less of a small or
-// ragged output and give the SMs more units to balance.  The choice changes no bit of the
-// result (every tile sum is exact), only the time.
+// 128 x 128 tiles per CTA.  Wide tiles read each A panel once for more columns; narrow tiles
+// waste less of a small or ragged output and give the SMs more units to balance.  The choice
+// changes no bit of the result (every tile sum is exact), only the time.
 //
 // A product (or a batch of products run as one grouped launch) is described by a key: the
 // output shape, inner dimension and plane counts, or for a batch its sorted sizes.  The first
@@ -27,8 +25,7 @@
 namespace frx {
 namespace {
 
-static_assert(TILE_AUTO == FRX_TILE_AUTO && TILE_128x128 == FRX_TILE_128x128 && TILE_128x256 == FRX_TILE_128x256 &&
-                  TILE_256x256 == FRX_TILE_256x256,
+static_assert(TILE_AUTO == FRX_TILE_AUTO && TILE_128x128 == FRX_TILE_128x128 && TILE_128x256 == FRX_TILE_128x256,
               "tile codes of the C ABI");
 
 constexpr int TUNE_REPS = 3;
@@ -46,16 +43,16 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // output area, and per tile configuration (index cfg - 1) the padded area and the CTA units
 // (one CTA's tile-and-anti-diagonal-group work items)
 struct Shape {
-  double area = 0.0, padded[3] = {0.0, 0.0, 0.0};
-  int64_t units[3] = {0, 0, 0};
+  double area = 0.0, padded[TILE_LAST] = {};
+  int64_t units[TILE_LAST] = {};
 };
 
 void add_shape(Shape& sh, int64_t M, int64_t N, int groups) {
   sh.area += (double)M * (double)N;
-  for (int c = TILE_128x128; c <= TILE_256x256; ++c) {
-    const int rows = c == TILE_256x256 ? 256 : 128, bn = tile_bn(c);
-    sh.padded[c - 1] += (double)(cdiv(M, rows) * rows) * (double)(cdiv(N, bn) * bn);
-    sh.units[c - 1] += cdiv(M, rows) * (rows / 128) * cdiv(N, bn) * (int64_t)groups;
+  for (int c = TILE_128x128; c <= TILE_LAST; ++c) {
+    const int bn = tile_bn(c);
+    sh.padded[c - 1] += (double)(cdiv(M, 128) * 128) * (double)(cdiv(N, bn) * bn);
+    sh.units[c - 1] += cdiv(M, 128) * cdiv(N, bn) * (int64_t)groups;
   }
 }
 
@@ -147,7 +144,6 @@ int decide(const std::vector<long long>& shape_key, const Shape& sh, const std::
   key.push_back(dev);
   const int forced = g_policy.load();
   if (forced != TILE_AUTO) {
-    // a forced pair configuration falls back to single-CTA tiles where pairs are not offered
     bool offered = false;
     for (int c : cands) offered |= c == forced;
     tile = offered ? forced : TILE_128x256;
@@ -182,12 +178,8 @@ int decide(const std::vector<long long>& shape_key, const Shape& sh, const std::
   return FRX_OK;
 }
 
-// candidates for one product: pairs of CTAs only when the output has at least two tile rows
-std::vector<int> single_candidates(int64_t M) {
-  std::vector<int> c = {TILE_128x256, TILE_128x128};
-  if (M > 128) c.push_back(TILE_256x256);
-  return c;
-}
+// candidates for one product
+std::vector<int> single_candidates() { return {TILE_128x256, TILE_128x128}; }
 
 // zero both operands' planes of a representative product (its timing reads defined digits)
 int zero_operands(const PlaneGemm& g, cudaStream_t s) {
@@ -214,7 +206,7 @@ int tune_single_impl(const PlaneGemm& g, int kind, P prepare, cudaStream_t s, in
   Shape sh;
   add_shape(sh, g.M, g.N, g.d.groups);
   std::vector<long long> key = {kind, g.M, g.N, g.K, g.d.kL, g.d.kR, g.d.T};
-  return decide(key, sh, single_candidates(g.M), prepare,
+  return decide(key, sh, single_candidates(), prepare,
                 [&](int c) { return launch_plane_gemm_tc(g, g.flags, c, s); }, s, tile);
 }
 
@@ -276,7 +268,7 @@ using namespace frx;
 extern "C" {
 
 int frx_set_tile(int tile) {
-  if (tile < TILE_AUTO || tile > TILE_256x256) return FRX_E_ARG;
+  if (tile < TILE_AUTO || tile > TILE_LAST) return FRX_E_ARG;
   return g_policy.exchange(tile);
 }
 

@@ -11,12 +11,11 @@
 // pairs * K * 2^14 < 2^31); otherwise BN = 128 and the int64 sums are combined in Horner
 // form per group: R_g = sum_{t in g} 2^(8 (t_last - t)) S_t.
 //
-// Tile configurations (int32 planes): 128 x 128 or 128 x 256 output tiles per CTA, or
-// 256 x 256 super-tiles per pair of CTAs (a 2-CTA cluster: each CTA computes one 128-row
-// half, loads half of the shared B panel and multicasts it to both).  The configuration
-// changes no result; the autotuner picks it.
+// Tile configurations (int32 planes): 128 x 128 or 128 x 256 output tiles per CTA.  The
+// configuration changes no result; the autotuner picks it.  Every CTA loads its own operand
+// tiles from this GPU's memory (no cluster launch).
 //
-// Persistent: one CTA (or pair) per SM walks the units (output tile, anti-diagonal group)
+// Persistent: one CTA per SM walks the units (output tile, anti-diagonal group)
 // in rounds (serpentine when there are few), groups ordered by decreasing work and tiles in
 // bands of TILE_BAND tile rows.  A grouped variant walks the units of many problems (the
 // batched refinement).
@@ -123,29 +122,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// the same copy into the same shared-memory offset of every CTA of the cluster in `mask`,
-// completing bytes on the mbarrier at the same offset in each of them
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                               uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
-      "[%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// every thread of every CTA of the cluster: release this CTA's prior shared-memory writes
-// (barrier initialisation) and wait for the other CTAs
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart (SBO), version 1
 __device__ __forceinline__ uint64_t smem_desc(const void* tile) {
   uint64_t addr = smem_u32(tile);
@@ -177,16 +153,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// arrive, once the MMAs issued so far complete, on the mbarrier at this offset in every CTA
-// of the cluster in `mask`
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -215,7 +181,6 @@ struct TcArgs {
   const GemmDesc* dyn;
   const int* done;
   int bn;        // tile width the right operand's tensor map was encoded for
-  int cl;        // CTAs per super-tile (2: the map's box is half the tile width)
 };
 
 // one problem of a grouped launch: its tensor maps and arguments (device table entry)
@@ -264,23 +229,19 @@ __device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int bm, int
 // round-robin keeps the units in flight a contiguous window (better L2 reuse of the panels).
 constexpr int SERPENTINE_MAX_ROUNDS = 16;
 
-// (per cluster of CL CTAs: both CTAs of a pair walk the same units)
-template <int CL>
 __device__ __forceinline__ int unit_of_round(int r, bool serp) {
-  const int P = (int)gridDim.x / CL, c = (int)blockIdx.x / CL;
+  const int P = (int)gridDim.x, c = (int)blockIdx.x;
   return (serp && (r & 1)) ? (r + 1) * P - 1 - c : r * P + c;
 }
 
 // the product description of a launch's problem, resolved from its arguments; the tiling
 // (128 x BN tiles, units = tiles x groups) belongs to the kernel variant, not to the plan
-// With CL = 2 a pair of CTAs (a cluster) computes a 256 x BN super-tile, one 128-row half
-// each; ntm then counts super-tile rows.
-template <int BN, bool W32, int CL = 1>
+template <int BN, bool W32>
 __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*& gorder) {
   if (a0.done && *a0.done) return false;
   const GemmDesc* D = a0.dyn ? a0.dyn : &a0.d;
   if (!D->active || D->groups <= 0) return false;
-  if (a0.bn != BN || a0.cl != CL || D->word32 != (W32 ? 1 : 0)) {
+  if (a0.bn != BN || D->word32 != (W32 ? 1 : 0)) {
     // the tensor map's box or the exact-sum layout does not fit this variant: no product
     if (a0.flags) atomicOr(a0.flags, FLAG_CONFIG);
     return false;
@@ -293,7 +254,7 @@ __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*
   a.tmax = D->tmax;
   a.gs = D->gs;
   a.groups = D->groups;
-  a.ntm = (int)(((a0.M + BM - 1) / BM + CL - 1) / CL);
+  a.ntm = (int)((a0.M + BM - 1) / BM);
   a.ntn = (int)((a0.N + BN - 1) / BN);
   a.units = a.ntm * a.ntn * D->groups;
   a.out = a0.out;
@@ -315,17 +276,15 @@ struct SingleSrc {
   int* flags0;
   int rnd, P;
   bool serp;
-  template <int CL>
   __device__ void begin() {
-    P = (int)gridDim.x / CL;
+    P = (int)gridDim.x;
     serp = run.units <= SERPENTINE_MAX_ROUNDS * P;
     rnd = 0;
   }
-  // the next unit of this CTA (or of its pair) in round order
-  template <int CL>
+  // the next unit of this CTA in round order
   __device__ bool next(int& lu) {
     while ((long long)rnd * P < run.units) {
-      const int u = unit_of_round<CL>(rnd++, serp);
+      const int u = unit_of_round(rnd++, serp);
       if (u < run.units) {
         lu = u;
         return true;
@@ -355,11 +314,7 @@ struct GroupedSrc {
   const CUtensorMap* mapR;
   int* flags0;
   int rnd;
-  template <int CL>
-  __device__ void begin() {
-    rnd = 0;
-  }
-  template <int CL>
+  __device__ void begin() { rnd = 0; }
   __device__ bool next(int& lu) {
     const int u = (int)blockIdx.x + rnd++ * (int)gridDim.x;
     if (u >= prefix[count]) return false;
@@ -382,15 +337,9 @@ struct GroupedSrc {
 
 // BN_ = 128: int64 Horner groups of gs anti-diagonals, 64 columns per epilogue thread.
 // BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
-// CL = 2: the CTA is one half of a pair (a 2-CTA cluster) working on 256 x BN super-tiles; both
-// halves need the same B panel, so each loads half of it and multicasts that half to both, and
-// each MMA releases a stage in both CTAs (a stage is refilled only once both have consumed it).
-template <int BN_, bool W32, int CL, class Src>
+template <int BN_, bool W32, class Src>
 __device__ __forceinline__ void tc_body(Src& src) {
   constexpr int BN = BN_;
-  static_assert(CL == 1 || CL == 2, "pairs of CTAs at most");
-  constexpr uint32_t HALF_B_BYTES = (BN / 2) * BK * 2;
-  constexpr uint16_t PAIR_MASK = 0x3;
   constexpr int STAGES = BN == 256 ? 4 : 6;
   constexpr uint32_t STAGE_B_BYTES = BN * BK * 2;
   constexpr uint32_t STAGE_BYTES = STAGE_A_BYTES + STAGE_B_BYTES;
@@ -406,7 +355,7 @@ __device__ __forceinline__ void tc_body(Src& src) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&sm->full[s], 1);
-      mbar_init(&sm->empty[s], CL);   // one release per consuming CTA
+      mbar_init(&sm->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->acc_full[b], 1);
@@ -424,9 +373,6 @@ __device__ __forceinline__ void tc_body(Src& src) {
   fence_before();
   __syncthreads();
   fence_after();
-  // the peer may signal this CTA's barriers only once they are initialised
-  if (CL > 1) cluster_sync_all();
-  const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
   const uint32_t tmem = sm->tmem_base;
   volatile int* abort = &sm->abort;
 
@@ -437,16 +383,15 @@ __device__ __forceinline__ void tc_body(Src& src) {
       uint32_t phase = 0;
       long long issued = 0;
       bool ok = !*abort;
-      src.template begin<CL>();
+      src.begin();
       int lu;
-      while (ok && src.template next<CL>(lu)) {
+      while (ok && src.next(lu)) {
         const TcRun& a = src.run;
         const int* gorder = src.gorder;
         const int tiles = a.ntm * a.ntn;
         const int grp = gorder[lu / tiles], tile = lu % tiles;
         int i0, j0;
-        tile_origin(tile, a.ntm, a.ntn, BM * CL, BN, i0, j0);
-        i0 += (int)rank * BM;
+        tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           for (int r = pair_lo(t, a.kR); r <= pair_hi(t, a.kL) && ok; ++r) {
@@ -457,13 +402,9 @@ __device__ __forceinline__ void tc_body(Src& src) {
                 break;
               }
               unsigned char* st = tiles_smem + stage * STAGE_BYTES;
-              mbar_expect_tx(&sm->full[stage], STAGE_BYTES);   // own A tile + the whole B tile
+              mbar_expect_tx(&sm->full[stage], STAGE_BYTES);
               tma_load_3d(st, src.mapL, kb * BK, i0, r - 1, &sm->full[stage]);
-              if (CL == 1)
-                tma_load_3d(st + STAGE_A_BYTES, src.mapR, kb * BK, j0, s - 1, &sm->full[stage]);
-              else
-                tma_load_3d_mc(st + STAGE_A_BYTES + rank * HALF_B_BYTES, src.mapR, kb * BK,
-                               j0 + (int)rank * (BN / 2), s - 1, &sm->full[stage], PAIR_MASK);
+              tma_load_3d(st + STAGE_A_BYTES, src.mapR, kb * BK, j0, s - 1, &sm->full[stage]);
               ++issued;
               if (++stage == STAGES) {
                 stage = 0;
@@ -474,8 +415,8 @@ __device__ __forceinline__ void tc_body(Src& src) {
         }
       }
       if (ok) {
-        // every consumer (local MMA and, in a cluster, the peers') has released the stages
-        // this CTA's copies filled: no arrival can target this CTA's barriers after it exits
+        // the MMA has released every stage this CTA's copies filled: no arrival can target
+        // this CTA's barriers after it exits
         for (int q = 0; q < STAGES; ++q) {
           if (!mbar_wait(&sm->empty[stage], phase ^ 1, abort, src.flags0)) break;
           if (++stage == STAGES) {
@@ -508,9 +449,9 @@ __device__ __forceinline__ void tc_body(Src& src) {
       uint32_t acc_phase[2] = {0, 0};
       bool ok = true;
       bool any = false;
-      src.template begin<CL>();
+      src.begin();
       int lu;
-      while (ok && src.template next<CL>(lu)) {
+      while (ok && src.next(lu)) {
         const TcRun& a = src.run;
         const int* gorder = src.gorder;
         const int tiles = a.ntm * a.ntn;
@@ -540,8 +481,7 @@ __device__ __forceinline__ void tc_body(Src& src) {
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
                 mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), IDESC, (cnt > 0 || kk > 0) ? 1u : 0u);
-              if (CL == 1) mma_commit(&sm->empty[stage]);
-              else mma_commit_mc(&sm->empty[stage], PAIR_MASK);
+              mma_commit(&sm->empty[stage]);
               any = true;
               if (++stage == STAGES) {
                 stage = 0;
@@ -578,16 +518,15 @@ __device__ __forceinline__ void tc_body(Src& src) {
     int buf = 0;
     uint32_t acc_phase[2] = {0, 0};
     bool ok = true;
-    src.template begin<CL>();
+    src.begin();
     int lu;
-    while (ok && src.template next<CL>(lu)) {
+    while (ok && src.next(lu)) {
       const TcRun& a = src.run;
       const int* gorder = src.gorder;
       const int tiles = a.ntm * a.ntn;
       const int grp = gorder[lu / tiles], tile = lu % tiles;
       int i0, j0;
-      tile_origin(tile, a.ntm, a.ntn, BM * CL, BN, i0, j0);
-      i0 += (int)rank * BM;
+      tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
       const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
       for (int t = t0; t <= t1 && ok; ++t) {
@@ -635,19 +574,15 @@ __device__ __forceinline__ void tc_body(Src& src) {
   __syncthreads();
   fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
-  // neither CTA of a pair leaves while the other may still write to its shared memory
-  if (CL > 1) cluster_sync_all();
 }
 
 
-// CL = 2 is launched as 2-CTA clusters (both CTAs of a cluster take the same early exit: they
-// read the same arguments)
-template <int BN_, bool W32, int CL>
+template <int BN_, bool W32>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
                     const __grid_constant__ TcArgs a0) {
   SingleSrc src;
-  if (!tc_run_of<BN_, W32, CL>(a0, src.run, src.gorder)) return;
+  if (!tc_run_of<BN_, W32>(a0, src.run, src.gorder)) return;
   src.mapL = &mapL;
   src.mapR = &mapR;
   src.flags0 = a0.flags;
@@ -655,7 +590,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapL) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapR) : "memory");
   }
-  tc_body<BN_, W32, CL>(src);
+  tc_body<BN_, W32>(src);
 }
 
 // In-place exclusive prefix sum of a[0..count-1] in shared memory, a[count] = the total, by
@@ -714,7 +649,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   src.mapL = src.mapR = nullptr;
   src.flags0 = probs[0].a.flags;
   memset(&src.run, 0, sizeof(src.run));
-  tc_body<BN_, W32, 1>(src);
+  tc_body<BN_, W32>(src);
 }
 
 // A wait that nothing completes (no thread ever arrives on the barrier): the bounded wait of
@@ -784,76 +719,26 @@ int sm_count(int& sms) {
   return FRX_OK;
 }
 
-// clusters of CL CTAs of this variant that can be resident at once (the persistent grid)
-template <int BN, bool W32, int CL>
-int resident_clusters(size_t smem, int sms, int& out) {
-  if constexpr (CL == 1) {
-    (void)smem;
-    out = sms;
-    return FRX_OK;
-  } else {
-    static PerDevice pd;
-    static int n[FRX_MAX_DEVICES] = {};
-    FRX_TRY(once_per_device(pd, [&](int dev) -> int {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)(CL * (sms / CL)));
-      cfg.blockDim = dim3(NUM_THREADS);
-      cfg.dynamicSmemBytes = smem;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = CL;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      FRX_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n[dev], k_plane_gemm_tc<BN, W32, CL>, &cfg));
-      return FRX_OK;
-    }));
-    int dev = 0;
-    FRX_CUDA_TRY(cudaGetDevice(&dev));
-    out = n[dev] > 0 ? n[dev] : sms / CL;
-    return FRX_OK;
-  }
-}
-
-template <int BN, bool W32, int CL>
+template <int BN, bool W32>
 int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   // tensor maps span the allocated planes (g.d.kL, g.d.kR: the capacity when d comes from the
-  // device); a pair's CTAs each load half of the B tile
+  // device)
   CUtensorMap mL, mR;
   if (!make_map(&mL, g.L, g.K, g.M, g.d.kL, g.pitch, g.Lps, BM)) return FRX_E_CUDA;
-  if (!make_map(&mR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, BN / CL)) return FRX_E_CUDA;
+  if (!make_map(&mR, g.R, g.K, g.N, g.d.kR, g.pitch, g.Rps, BN)) return FRX_E_CUDA;
   size_t smem = smem_bytes(BN);
   static PerDevice pd;
   FRX_TRY(once_per_device(pd, [&](int) -> int {
     FRX_CUDA_TRY(
-        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return FRX_OK;
   }));
-  int sms = 0, clusters = 0;
+  int sms = 0;
   FRX_TRY(sm_count(sms));
-  FRX_TRY((resident_clusters<BN, W32, CL>(smem, sms, clusters)));
-  const int64_t units = a.dyn ? (int64_t)clusters
-                              : (((g.M + BM - 1) / BM + CL - 1) / CL) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups;
-  const unsigned grid = (unsigned)(CL * (units < clusters ? units : clusters));
+  const int64_t units = a.dyn ? (int64_t)sms : ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups;
+  const unsigned grid = (unsigned)(units < sms ? units : sms);
   if (grid == 0) return FRX_OK;
-  if (CL == 1) {
-    k_plane_gemm_tc<BN, W32, CL><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(NUM_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    FRX_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_plane_gemm_tc<BN, W32, CL>, mL, mR, a));
-  }
+  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -888,7 +773,6 @@ int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int tile) 
   e->a.dyn = g.dyn;
   e->a.done = g.done;
   e->a.bn = bn;
-  e->a.cl = 1;
   return FRX_OK;
 }
 
@@ -921,8 +805,7 @@ int launch_plane_gemm_grouped(const void* table, int count, int tile, cudaStream
   return FRX_OK;
 }
 
-// tile: TILE_128x128, TILE_128x256 or TILE_256x256 for int32 planes (int64 groups always use
-// 128 x 128 tiles)
+// tile: TILE_128x128 or TILE_128x256 for int32 planes (int64 groups always use 128 x 128 tiles)
 int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int tile, cudaStream_t s) {
   TcArgs a;
   a.M = g.M;
@@ -935,22 +818,18 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int tile, cudaStream_t 
   a.d = g.d;
   a.dyn = g.dyn;
   a.done = g.done;
-  a.cl = 1;
   if (!g.d.word32) {
     a.bn = 128;
     last_tile() = TILE_128x128;
-    return launch_variant<128, false, 1>(g, a, s);
+    return launch_variant<128, false>(g, a, s);
   }
   last_tile() = tile;
   a.bn = tile_bn(tile);
   switch (tile) {
     case TILE_128x128:
-      return launch_variant<128, true, 1>(g, a, s);
+      return launch_variant<128, true>(g, a, s);
     case TILE_128x256:
-      return launch_variant<256, true, 1>(g, a, s);
-    case TILE_256x256:
-      a.cl = 2;
-      return launch_variant<256, true, 2>(g, a, s);
+      return launch_variant<256, true>(g, a, s);
     default:
       return FRX_E_UNSUPPORTED;
   }

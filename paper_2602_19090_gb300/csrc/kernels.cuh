@@ -30,9 +30,8 @@ int once_per_device(PerDevice& pd, F f) {
 }
 
 // Output tile configurations of the tensor-core products (the values of frx_set_tile):
-// 128 x 128 or 128 x 256 tiles per CTA, or 256 x 256 super-tiles per pair of CTAs (a 2-CTA
-// cluster sharing the B panel)
-enum : int { TILE_AUTO = 0, TILE_128x128 = 1, TILE_128x256 = 2, TILE_256x256 = 3 };
+// 128 x 128 or 128 x 256 tiles per CTA
+enum : int { TILE_AUTO = 0, TILE_128x128 = 1, TILE_128x256 = 2, TILE_LAST = TILE_128x256 };
 inline int tile_bn(int cfg) { return cfg == TILE_128x128 ? 128 : 256; }
 
 // optional device-side parameters of the slicing kernels (null: use the launch arguments)

@@ -3,13 +3,10 @@
 //
 // Some callers have no way to call cudaMalloc: a plugin running inside a host
 // framework that has already reserved the whole device memory for its own caching
-// allocator (a new cudaMalloc fails or fragments that pool), code that is handed only
-// a stream and no allocator, or a latency-critical loop where the implicit device
-// synchronisation of cudaMalloc/cudaFree is not acceptable.  This entry point takes
-// its scratch from a fixed array in device memory that is part of this library
-// (file-scope, see below), so it performs no allocation of its own.
-#include <mutex>
-
+// allocator (a new cudaMalloc fails or fragments that pool), or code that is handed
+// only a stream and no allocator.  This entry point takes its scratch from a fixed
+// array in device memory that is part of this library (file-scope, see below), so it
+// performs no allocation of its own.
 #include "frx_internal.cuh"
 
 namespace {
@@ -19,28 +16,21 @@ constexpr int64_t kStaticMaxDim = 512;
 constexpr int kStaticMaxSlices = 8;
 constexpr size_t kStaticScratchBytes = (size_t)24 * 1024 * 1024 + (size_t)64 * 1024;
 
-// The scratch itself: every device that loads this library holds these bytes until
-// the process exits.  In host code `g_static_scratch` names a host-side stand-in, not
-// device memory; the device address comes from cudaGetSymbolAddress below.
+// The scratch itself.  Its bytes are reserved on a device when this file's module is
+// loaded there: under CUDA's default lazy module loading that is the first call of
+// frx_ozaki_gemm_static on the device (CUDA_MODULE_LOADING=EAGER moves it to the
+// library's load), and it stays reserved until the process exits.  In host code
+// `g_static_scratch` names a host-side stand-in, not device memory; the device address
+// comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device.  Looked up on every call: the
+// lookup is a host-side query that enqueues no work, and it stays right after a
+// cudaDeviceReset, which reloads the module at another address.
 int scratch_on_current_device(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FRX_E_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return FRX_E_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t err = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (err != cudaSuccess || p == nullptr) return FRX_E_CUDA;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return FRX_E_CUDA;
+  *out = p;
   return FRX_OK;
 }
 

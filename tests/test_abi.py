@@ -55,10 +55,10 @@ def test_wait_self_test_checks_its_scratch_first(lib):
 
 def test_tile_policy_is_host_only(lib):
     # the autotuner's switch and counters touch no device
-    assert lib.frx_set_tile(4) == -1 and lib.frx_set_tile(-1) == -1
+    assert lib.frx_set_tile(3) == -1 and lib.frx_set_tile(-1) == -1
     assert lib.frx_set_tile(1) == 0
-    assert lib.frx_set_tile(3) == 1
-    assert lib.frx_set_tile(0) == 3
+    assert lib.frx_set_tile(2) == 1
+    assert lib.frx_set_tile(0) == 2
     m, d, h = ctypes.c_longlong(-1), ctypes.c_longlong(-1), ctypes.c_longlong(-1)
     assert lib.frx_tune_stats(ctypes.byref(m), ctypes.byref(d), ctypes.byref(h), 1) == 0
     assert lib.frx_tune_stats(ctypes.byref(m), ctypes.byref(d), ctypes.byref(h), 0) == 0
