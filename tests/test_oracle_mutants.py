@@ -51,6 +51,21 @@ MUTANTS = [
     ("refine", "- (oz.DIGIT_BITS - 1))", "- oz.DIGIT_BITS)", "slice rule: digit bound off by one bit"),
     ("refine", "E[i, j] = -sh / 2.0", "E[i, j] = sh / 2.0", "cluster rule: wrong sign of r_ij"),
     ("refine", "est = step_norm * step_norm * Lam_new", "est = step_norm * Lam_new", "stopping test: dropped square"),
+    ("refine", "    s = np.sort(lam)\n", "    s = lam\n", "min gap: estimates not sorted"),
+    ("refine", "g = float(np.min(gaps)) if gaps.size else Lam", "g = float(np.max(gaps)) if gaps.size else Lam",
+     "min gap: largest gap instead of the smallest"),
+    ("refine", "gaps = gaps[gaps > omega]", "gaps = gaps[gaps >= omega]", "min gap: gaps equal to omega kept"),
+    ("refine", "Lam = float(np.max(np.abs(lam)))", "Lam = float(np.max(lam))", "max |lam|: absolute value dropped"),
+    ("refine", "math.ldexp(1.0, 2 * int(x))", "math.ldexp(1.0, int(x))", "S2: 2^f instead of 2^(2f)"),
+    ("truth", "    Y = Xhat * s[None, :]\n", "    Y = Xhat\n", "forward error: no sign alignment"),
+    ("truth", "return float(np.linalg.norm(dh + dl, 2))", "return float(np.linalg.norm(dh + dl))",
+     "forward error: Frobenius norm for the 2-norm"),
+    ("truth", "dh, dl = dd.dd_add(Xh, Xl, -Y, np.zeros_like(Y))", "dh, dl = dd.dd_add(Xh, 0.0 * Xl, -Y, np.zeros_like(Y))",
+     "forward error: low word of X dropped"),
+    ("truth", "Qh, _ = np.linalg.qr(np.asarray(Xhat)[:, cols])", "Qh = np.asarray(Xhat)[:, cols]",
+     "subspace error: columns of X^ not orthonormalised"),
+    ("truth", "return float(np.linalg.norm(P, 2))", "return float(np.linalg.norm(P))",
+     "subspace error: Frobenius norm for the 2-norm"),
 ]
 
 

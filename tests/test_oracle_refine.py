@@ -292,3 +292,112 @@ def test_sparse_rule_is_the_paper_formula():
     assert p["alpha"] == 53 - beta + 3
     # denser than the dense rule: min(k, sqrt n)^2 = 25 < n keeps more bits of X (smaller beta)
     assert p["beta"] < rf.plan(A, X0, D0, delta, rf.Options())["beta"]
+
+
+def _plan_case(lam_prev, omega_prev=0.0, col_max=0.25):
+    # n = 4, X = col_max * I: every column maximum is col_max, so f_j = ceil(log2 col_max);
+    # A = I (only its exponents and nonzero counts enter the plan)
+    X = col_max * np.eye(4)
+    return rf.plan(np.eye(4), X, np.asarray(lam_prev, dtype=np.float64), 2.0 ** -30, rf.Options(), omega_prev)
+
+
+def test_plan_gap_and_beta_worked_by_hand():
+    # Sec. 3.3 / Sec. 4.1 through the oracle's plan, with every input chosen so that the
+    # result follows by hand:
+    #   estimates (unsorted) 0.5, -1, 0.5 + 2^-20, 2  ->  sorted -1, 0.5, 0.5 + 2^-20, 2
+    #   adjacent gaps 1.5, 2^-20, 1.5 - 2^-20  ->  smallest gap g = 2^-20;  max|lam| = 2
+    #   columns of X = 0.25 I: f_j = -2, sum_j 2^(2 f_j) = 4 * 2^-4 = 1/4
+    #   n delta g / (max|lam| S2) = 4 * 2^-30 * 2^-20 / (2 * 2^-2) = 2^-47;  sqrt = 2^-23.5
+    #   2^-23.5 / (0.75 * 2^-53) = 2^29.5 * 4/3 = 2^29.915  ->  beta = floor = 29
+    p = _plan_case([0.5, -1.0, 0.5 + 2.0 ** -20, 2.0])
+    assert p["g"] == 2.0 ** -20 and p["Lam"] == 2.0
+    assert p["f"].tolist() == [-2, -2, -2, -2] and p["S2"] == 0.25
+    assert p["beta"] == 29
+    # a gap at or below the cluster threshold omega = 2^-19 is not a gap: g = 1.5 - 2^-20;
+    #   4 * 2^-30 * (1.5 - 2^-20) / (2 * 2^-2) = 2^-27 (1.5 - 2^-20); log2 of its square root
+    #   = (0.58496 - 27) / 2 = -13.2075; + 53 + log2(4/3) = 40.2  ->  beta = 40
+    p = _plan_case([0.5, -1.0, 0.5 + 2.0 ** -20, 2.0], omega_prev=2.0 ** -19)
+    assert p["g"] == 1.5 - 2.0 ** -20 and p["beta"] == 40
+    # a repeated estimate gives a zero gap, which is excluded too: g = 1.5
+    p = _plan_case([0.5, -1.0, 0.5, 2.0])
+    assert p["g"] == 1.5 and p["beta"] == 40
+    # the largest magnitude is negative: max|lam| = 4 (not the largest value, 2);
+    #   4 * 2^-50 / (4 * 2^-2) = 2^-48, sqrt 2^-24, / (0.75 * 2^-53) = 2^29.415 -> beta = 29
+    p = _plan_case([0.5, -4.0, 0.5 + 2.0 ** -20, 2.0])
+    assert p["Lam"] == 4.0 and p["g"] == 2.0 ** -20 and p["beta"] == 29
+    # columns with maximum 2^-5 < 0.05 <= 2^-4: f_j = -4, S2 = 4 * 2^-8 = 2^-6, 16 times smaller:
+    #   beta = floor(29.915 + log2 sqrt 16) = floor(31.915) = 31
+    p = _plan_case([0.5, -1.0, 0.5 + 2.0 ** -20, 2.0], col_max=0.05)
+    assert p["S2"] == 2.0 ** -6 and p["beta"] == 31
+    # one estimate only: no gap exists and g = max|lam| (n = 1)
+    g, Lam = rf.min_gap(np.array([-3.0]))
+    assert g == 3.0 and Lam == 3.0
+
+
+def test_sum_pow4_against_fractions():
+    from fractions import Fraction
+    cases = ([-1, -3, 0, 5, -40], [0] + [-30] * 3, [-1074 // 2 + 3, 10, 10, -7], list(range(-20, 21)),
+             [oz.EZERO, -2, oz.EZERO, 3])
+    for f in cases:
+        exact = sum((Fraction(2) ** (2 * x) for x in f if x != oz.EZERO), Fraction(0))
+        assert rf.sum_pow4(np.array(f)) == float(exact)      # correctly rounded
+    assert rf.sum_pow4(np.array([3, 3])) == 128.0            # 2 * 2^6, not 2 * 2^3
+    assert rf.sum_pow4(np.array([oz.EZERO])) == 0.0
+
+
+def test_forward_error_closed_form():
+    # X = I (exact), X^ = I + diag(3e-7, 0, -4e-7, 0, 1e-7, 0) with column 1 sign-flipped:
+    # after the sign alignment of column 1 the difference is diagonal, so its 2-norm is the
+    # largest |d_j| = 4e-7 (the Frobenius norm would be 5.1e-7; without the alignment, 2)
+    n = 6
+    d = np.array([3e-7, 0.0, -4e-7, 0.0, 1e-7, 0.0])
+    Xhat = np.eye(n) + np.diag(d)
+    Xhat[:, 1] *= -1.0
+    fe = tr.forward_error(np.eye(n), np.zeros((n, n)), Xhat)
+    # 1 - fl(1 + d_j) is exact (Sterbenz), so the diagonal differences are known exactly
+    assert abs(fe - abs(1.0 - Xhat[2, 2])) <= 1e-9 * fe
+    assert abs(fe - 4e-7) <= 1e-16
+    # the low word of X counts: X = I + 2^-60 e_0 e_0^T held as (I, 2^-60 e_0 e_0^T), X^ = I
+    Xl = np.zeros((n, n))
+    Xl[0, 0] = 2.0 ** -60
+    assert tr.forward_error(np.eye(n), Xl, np.eye(n)) == 2.0 ** -60
+
+
+def test_forward_error_against_mpmath():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    n = 7
+    rng = np.random.default_rng(20260207)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Xl = rng.standard_normal((n, n)) * 1e-17 * np.abs(Q)
+    Xhat = Q + rng.standard_normal((n, n)) * 1e-9
+    flips = np.array([1, -1, 1, 1, -1, -1, 1], dtype=np.float64)
+    fe = tr.forward_error(Q, Xl, Xhat * flips[None, :])
+    D = mpmath.matrix(n, n)
+    for i in range(n):
+        for j in range(n):
+            D[i, j] = mpmath.mpf(float(Q[i, j])) + mpmath.mpf(float(Xl[i, j])) - mpmath.mpf(float(Xhat[i, j]))
+    s = mpmath.svd_r(D, compute_uv=False)
+    ref = float(max(s[i] for i in range(n)))
+    assert abs(fe - ref) <= 1e-6 * ref
+
+
+def test_subspace_error_closed_form():
+    # span(e0, e1) against the columns of X^ that tilt it by known principal angles:
+    # x^_0 = 2 (cos a e0 + sin a e3), x^_1 = 0.5 (cos b e1 + sin b e4): the angles are a and b, so
+    # ||sin Theta||_2 = max(sin a, sin b) whatever the columns' lengths (Frobenius would be
+    # sqrt(sin^2 a + sin^2 b))
+    n = 6
+    I = np.eye(n)
+    a, b = 0.3, 0.2
+    Xhat = np.eye(n)
+    Xhat[:, 0] = 2.0 * (np.cos(a) * I[:, 0] + np.sin(a) * I[:, 3])
+    Xhat[:, 1] = 0.5 * (np.cos(b) * I[:, 1] + np.sin(b) * I[:, 4])
+    se = tr.subspace_error(I, np.zeros((n, n)), Xhat, [0, 1])
+    assert abs(se - np.sin(a)) <= 1e-15
+    # a rotation and a scaling inside the subspace change no angle
+    c, s = np.cos(0.7), np.sin(0.7)
+    Xhat = np.eye(n)
+    Xhat[:, 0] = 3.0 * (c * I[:, 0] + s * I[:, 1])
+    Xhat[:, 1] = -s * I[:, 0] + c * I[:, 1]
+    assert tr.subspace_error(I, np.zeros((n, n)), Xhat, [0, 1]) <= 1e-15
