@@ -159,6 +159,91 @@ def _inv_sqrt_dd(n: int):
     return hi, lo
 
 
+def _scaled_dd(num: int, n: int, den: int = 1):
+    """num / (den sqrt(n)) for n = 2^p as a double-double."""
+    import decimal
+    with decimal.localcontext() as ctx:
+        ctx.prec = 60
+        v = decimal.Decimal(num) / (decimal.Decimal(den) * decimal.Decimal(n).sqrt())
+        hi = float(v)
+        lo = float(v - decimal.Decimal(hi))
+    return hi, lo
+
+
+def rotated_hadamard_workload(n: int, cond: float, seed: int, rel: float = 1e-8, variant: str = "spd"):
+    """Exact-truth workload for n = 2^p whose eigenvectors are not dyadic at any p.
+
+    Columns k and k + n/2 of the Sylvester Hadamard matrix H are rotated by the exact rotation
+    R5 / 5, R5 = [[3, -4], [4, 3]]: Q = H R / sqrt(n) with R block-diagonal in those pairs, so
+    every entry of Q is +-7 / (5 sqrt n) or +-1 / (5 sqrt n) (not an FP64 number).  With m_k
+    distinct positive integers (the geometric magnitudes of ``spectrum(n, cond)`` scaled by 2^S
+    and made distinct, as in ``hadamard_workload``) and s_k = +1 or seeded signs, the block
+    matrix M = R5 diag(s m) R5^T is an integer matrix, A = H M H 2^-S / n has exact FP64
+    entries (|sum| <= 49 sum m < 2^53), and A (H R5) = 25 (H R5) diag(s m) 2^-S exactly: the
+    eigenpairs of the stored A are lam_k = 25 s_k m_k 2^-S and the columns of Q.
+    Returns (A, X0, D0, lam, Qh, Ql, info) like ``hadamard_workload``.
+    """
+    p = n.bit_length() - 1
+    if n < 2 or (1 << p) != n:
+        raise ValueError("n must be a power of 2")
+    geom = spectrum(n, cond)
+    S = int(np.floor(np.log2(2.0 ** 52 / (49.0 * float(np.sum(geom))))))
+    m = np.maximum(np.rint(geom * 2.0 ** S), 1).astype(np.int64)
+    k = np.arange(n, dtype=np.int64)
+    m = np.maximum.accumulate(m - k) + k                     # strictly increasing
+    assert 49 * int(np.sum(m)) < (1 << 53)
+    if variant == "indefinite":
+        sgn = rng(seed + 7).integers(0, 2, size=n).astype(np.int64) * 2 - 1
+    elif variant == "spd":
+        sgn = np.ones(n, dtype=np.int64)
+    else:
+        raise ValueError(f"unknown variant {variant!r}")
+    # eigenvalue index j of H-column pair (a, a + n/2): a seeded assignment of the sorted
+    # magnitudes to the columns, so that each rotated pair mixes two unrelated eigenvalues
+    perm = rng(seed + 3).permutation(n)
+    sm = (sgn * m)[perm]                                     # s m of H-column k
+    h = n // 2
+    a, b = sm[:h], sm[h:]
+    M = np.zeros((n, n), dtype=np.int64)
+    idx = np.arange(h)
+    M[idx, idx] = 9 * a + 16 * b
+    M[idx + h, idx + h] = 16 * a + 9 * b
+    M[idx, idx + h] = 12 * (a - b)
+    M[idx + h, idx] = 12 * (a - b)
+    W = _fwht_rows(M)                                        # M H
+    W = _fwht_rows(np.ascontiguousarray(W.T)).T              # H M H
+    A = np.ascontiguousarray(W.astype(np.float64) * (2.0 ** -S / n))
+    del W, M
+    lam_all = 25.0 * sm.astype(np.float64) * 2.0 ** -S
+    order = np.argsort(lam_all, kind="stable")
+    lam = lam_all[order]
+    # H R5: column k (k < n/2) = 3 h_k + 4 h_{k+n/2}, column k + n/2 = -4 h_k + 3 h_{k+n/2}
+    Hm = _fwht_rows(np.eye(n, dtype=np.int64))
+    HR = np.empty((n, n), dtype=np.int64)
+    HR[:, :h] = 3 * Hm[:, :h] + 4 * Hm[:, h:]
+    HR[:, h:] = -4 * Hm[:, :h] + 3 * Hm[:, h:]
+    del Hm
+    HR = HR[:, order]
+    Qh = np.empty((n, n))
+    Ql = np.empty((n, n))
+    for v in (7, 1, -1, -7):
+        hi, lo = _scaled_dd(v, n, 5)
+        sel = HR == v
+        Qh[sel] = hi
+        Ql[sel] = lo
+    assert np.all(np.isin(HR, (7, 1, -1, -7)))
+    del HR
+    g = rng(seed + 1)
+    Y = Qh + g.standard_normal((n, n)) * (rel / (2.0 * np.sqrt(n)))
+    Qr, R = np.linalg.qr(Y)
+    X0 = np.ascontiguousarray(Qr * np.sign(np.diag(R)))
+    D0 = lam * (1.0 + rel * g.standard_normal(n))
+    gaps = np.diff(lam)
+    info = dict(scale_exp=-S, min_gap=float(gaps.min()), max_abs=float(np.abs(lam).max()),
+                cond=float(np.abs(lam).max() / np.abs(lam).min()))
+    return A, X0, D0, lam, Qh, Ql, info
+
+
 def hadamard_workload(n: int, cond: float, seed: int, rel: float = 1e-8, variant: str = "spd"):
     """Exact-truth workload for n = 2^p.
 

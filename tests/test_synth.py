@@ -35,6 +35,35 @@ def test_hadamard_workload_eigenpairs_are_exact(n, variant):
         assert np.all(lam > 0)
 
 
+@pytest.mark.parametrize("n,variant", [(8, "spd"), (64, "indefinite"), (128, "spd")])
+def test_rotated_hadamard_workload_eigenpairs_are_exact(n, variant):
+    A, X0, D0, lam, Qh, Ql, info = synth.rotated_hadamard_workload(n, 1e10, synth.seed_for(4, n), variant=variant)
+    assert np.array_equal(A, A.T)
+    # scaled by 2^S n, A is an integer matrix; Q 5 sqrt(n) = H R5 has entries +-7, +-1 and
+    # A (H R5) = (H R5) diag(lam) is checked in exact integer arithmetic (times 2^S n)
+    S = -info["scale_exp"]
+    Ai = A * (2.0 ** S * n)
+    assert np.array_equal(Ai, np.rint(Ai))
+    Ai = Ai.astype(np.int64).astype(object)
+    G = np.rint(Qh / np.abs(Qh).min()).astype(np.int64)      # H R5 (entries +-7, +-1)
+    assert set(np.unique(np.abs(G)).tolist()) == {1, 7}
+    # columns of H R5 are orthogonal with squared norm 25 n (so Q = H R5 / (5 sqrt n))
+    Go = G.astype(object)
+    assert np.array_equal(Go.T.dot(Go), np.eye(n, dtype=np.int64).astype(object) * (25 * n))
+    lam_i = lam * 2.0 ** S
+    assert np.array_equal(lam_i, np.rint(lam_i))
+    lam_i = lam_i.astype(np.int64).astype(object)
+    assert np.array_equal(Ai.dot(Go), Go * (lam_i * n)[None, :])
+    # Qh + Ql = G / (5 sqrt n) to double-double accuracy
+    for i, j in ((0, 0), (n - 1, n - 1), (1, n // 2)):
+        v = Fraction(float(Qh[i, j])) + Fraction(float(Ql[i, j]))
+        assert abs(v * v * 25 * n - G[i, j] ** 2) < Fraction(int(G[i, j]) ** 2, 2 ** 100)
+    assert np.all(np.diff(lam) > 0) and info["min_gap"] == float(np.min(np.diff(lam)))
+    if variant == "spd":
+        assert np.all(lam > 0)
+    assert abs(info["cond"] / 1e10 - 1) < 0.01
+
+
 def test_randsvd_like_matrix_is_symmetric_with_the_geometric_spectrum():
     n, cond = 96, 1e6
     A, Q, lam = synth.symmetric_matrix(n, cond, synth.seed_for(2, 9))
