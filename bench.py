@@ -66,9 +66,11 @@ def parse():
     p.add_argument("--cond", type=float, default=1e4)
     p.add_argument("--delta", type=float, default=1e-14)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0,
-                   help="CPU work of the oracle sample behind cpu_baseline (the reference arm's steps "
-                        "each time a fixed two-point sample instead)")
+    p.add_argument("--ref-budget", type=float, default=180.0,
+                   help="seconds of oracle refinements the reference arm may spend: it times full "
+                        "refinements one after another while the next one still fits, at least one")
+    p.add_argument("--no-truth", action="store_true",
+                   help="skip the exact-truth companion run that measures the forward error")
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
     p.add_argument("--workload", choices=["refine", "batched", "configs", "previous", "gemm"], default="refine",
@@ -203,48 +205,53 @@ def job_throughput(ws, units_per_rank, ms_max):
     return ws * units_per_rank * 1e3 / ms_max
 
 
-def cpu_oracle_sample(A, X0, D0, delta, total_products, iters, rows=(64, 256), min_seconds=0.0):
-    """Times the CPU oracle on a bounded sample and extrapolates to one full refinement.
+def cpu_oracle_refine(A, X0, D0, delta):
+    """Times one full refinement by the CPU oracle on the host cores, as the oracle stands:
+    Algorithm 1 iterated with the Sec. 3 / 4.1 rules and the stopping test, in double-double
+    with exact integer slice products.  Returns (cpu_baseline record, refined X, oracle info)."""
+    from oracle import refine as orf
+    t0 = time.perf_counter()
+    X, lam, info = orf.refine(A, X0.copy(), D0.copy(), delta, orf.Options())
+    dt = time.perf_counter() - t0
+    rec = {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"one full oracle refinement of the workload, timed whole: {info['iters']} iterations, "
+                      f"{info['products']} slice products, status {info['status']}; the slice products use "
+                      f"numpy's multithreaded FP64 BLAS on all host cores (exact for these integer sums), the "
+                      f"rest of the oracle is single-threaded numpy")}
+    return rec, X, info
 
-    Sample: the oracle's plan of iteration 1 (scans, beta, the truncation of X) and its
-    V = A X^(1) product (all slice pairs) on the first r rows of A for increasing r (doubling
-    past the last entry of `rows` until `min_seconds` of CPU work have been spent).  A product
-    call costs a + b r (slicing X^(1) once, then r rows); a and b come from the last two calls.
-    The full refinement is estimated as iters * t_plan + (a + b n) * total_products / (V's pairs).
-    """
+
+def oracle_warmup(A, X0, D0, delta):
+    """A bounded sample of the oracle's work (its plan and the V product on 64 rows): warms
+    numpy and the BLAS threads before the timed oracle refinements."""
     from oracle import ozaki as oz
     from oracle import refine as orf
-    n = A.shape[0]
-    t0 = time.perf_counter()
     p = orf.plan(A, X0, D0, delta, orf.Options())
     X1, _ = oz.tau_truncate_cols(X0, p["beta"], p["f"])
-    t_plan = time.perf_counter() - t0
-    spent = t_plan
-    pts = []
-    seq = list(rows)
-    while seq:
-        r = min(int(seq.pop(0)), n)
-        t1 = time.perf_counter()
-        out = oz.ozaki_product(A[:r], X1, p["kV"], p["sX"], p["kV"] + 1, eL=p["eA"][:r], eR=p["f"])
-        dt = time.perf_counter() - t1
-        spent += dt
-        pts.append((r, dt))
-        if not seq and spent < min_seconds and r < n:
-            seq.append(2 * r)
-    pv = len(out["pairs"])
-    (r1, u1), (r2, u2) = pts[-2], pts[-1]
-    b = max((u2 - u1) / (r2 - r1), 0.0)
-    a = max(u1 - b * r1, 0.0)
-    t_v = a + b * n
-    est = iters * t_plan + t_v * total_products / pv
-    return {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle plan of iteration 1 ({t_plan:.1f} s) and its V = A X^(1) product "
-                       f"({pv} slice products) on the first r of {n} rows, r = "
-                       f"{', '.join(str(q) for q, _ in pts)} ({', '.join(f'{u:.1f}' for _, u in pts)} s); "
-                       f"V on all rows = a + b n = {t_v:.1f} s from the last two; estimate = "
-                       f"{iters} x plan + V x ({total_products} slice products / {pv}); {spent:.1f} s "
-                       f"of CPU work in all; the slice products use numpy's multithreaded FP64 BLAS "
-                       f"(exact for these integer sums), the rest of the oracle is single-threaded numpy")}
+    oz.ozaki_product(A[:64], X1, p["kV"], p["sX"], p["kV"] + 1, eL=p["eA"][:64], eR=p["f"])
+
+
+def truth_companion(api, synth, dev, n, cond, delta, opts):
+    """The headline's refinement on an exact-truth matrix of the same order and condition:
+    rotated-Hadamard eigenvectors (not FP64 numbers) with a geometric spectrum, start perturbed
+    by 1e-8.  Returns the measured forward error ||X - X^||_2 and the run's report."""
+    import torch
+    A, X0, D0, lam, Qh, Ql, hinfo = synth.rotated_hadamard_workload(n, cond, synth.seed_for(2, 800))
+    At = torch.from_numpy(A).to(dev)
+    X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
+    D0t = torch.from_numpy(D0).to(dev)
+    Qht, Qlt = torch.from_numpy(Qh).to(dev), torch.from_numpy(Ql).to(dev)
+    work = api.workspace(api.refine_workspace_bytes(n, opts), dev)
+    _timed_refine(api, At, X0t, D0t, delta, opts, work)
+    ms, info, X = _timed_refine(api, At, X0t, D0t, delta, opts, work)
+    fe = _forward_error(X, Qht, Qlt)
+    fe0 = _forward_error(X0t, Qht, Qlt)
+    return {"value": fe["two"], "norm": "2-norm (power iteration), columns sign-aligned", "fro": fe["fro"],
+            "max_column": fe["maxcol"], "start": fe0["two"], "delta": delta, "ratio_to_delta": fe["two"] / delta,
+            "status": info["status_name"], "iters": info["iters"], "products": info["products"], "ms": ms,
+            "workload": (f"exact truth: eigenvectors H R / sqrt(n) (Sylvester Hadamard columns paired by the "
+                         f"3-4-5 rotation), n={n}, geometric spectrum cond {cond:g} scaled by 25 "
+                         f"(min gap {hinfo['min_gap']:.3g}), start perturbed 1e-8, delta={delta:g}")}
 
 
 def run_ours(args):
@@ -413,9 +420,17 @@ def run_ours(args):
         line["ozaki_gemm"] = {"n": n, "phi": 2.0, "slices": 8, "dgemm_ms": dgemm_ms,
                               "dgemm_tflops": 2 * n ** 3 / dgemm_ms / 1e9, **gl}
         del Ag, Bg, Agc, Bgc, ref, mag
+    if not args.no_truth:
+        line["forward_error"] = truth_companion(api, synth, dev, n, args.cond, delta, opts)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], info["iters"],
-                                                 min_seconds=args.cpu_seconds)
+        cb, Xo, io = cpu_oracle_refine(A, X0, D0, delta)
+        X.copy_(X0t)
+        D.copy_(D0t)
+        ig = api.refine(At, X, D, delta, opts, work=work)
+        cb["parity_vs_gpu"] = {"max_abs_diff_X": float(np.max(np.abs(X.cpu().numpy() - Xo))),
+                               "iters": [io["iters"], ig["iters"]], "products": [io["products"], ig["products"]],
+                               "status": [io["status"], ig["status_name"]]}
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -678,8 +693,7 @@ def run_configs(args):
             print(json.dumps(rec), file=sys.stderr, flush=True)
             if not args.no_cpu_baseline and cond == 1e4 and variant == "spd" and delta == 1e-14:
                 # the CPU oracle beside the n = 2048 refinement, on the headline's sampled V product
-                out["cpu_baseline_n2048"] = cpu_oracle_sample(A, X0, D0, delta, info["products"], info["iters"],
-                                                              min_seconds=args.cpu_seconds)
+                out["cpu_baseline_n2048"] = cpu_oracle_refine(A, X0, D0, delta)[0]
         del At, X0t, D0t
     del work
 
@@ -880,31 +894,33 @@ def run_gemm_sweep(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, timed on the host cores on this arm's
+    workload.  Each step is one full oracle refinement; warm-up steps are a bounded sample
+    (the oracle's plan and V product on 64 rows).  Full refinements are timed one after another
+    while the next still fits in --ref-budget seconds (at least one); `steps` reports how many
+    ran, so that steps x ms_per_step is the time actually spent."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2602_19090_gb300 import synth
     n, delta = args.n, args.delta
     A, X0, D0, lam = synth.refine_workload(n, args.cond, "spd", case=0)
-    # total slice products of one refinement as the GPU path schedules them (from its plan rule)
-    from oracle import refine as orf
-    p = orf.plan(A, X0, D0, delta, orf.Options())
-    pv = len([1 for r in range(1, p["kV"] + 1) for s in range(1, p["sX"] + 1) if r + s <= p["kV"] + 1])
-    # stated estimate of one refinement's slice products: two iterations (quadratic convergence
-    # from the 1e-8 start puts the second correction below delta), each with the first
-    # iteration's V product count plus W and U counted together as one more V
-    iters = 2
-    total = iters * 2 * pv
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_oracle_sample(A, X0, D0, delta, total, iters))
-    v = vals[-args.steps:]
-    value = statistics.median([x["value"] for x in v])
-    cb = dict(v[-1])
+    for _ in range(args.warmup):
+        oracle_warmup(A, X0, D0, delta)
+    recs = []
+    t_start = time.perf_counter()
+    for _ in range(max(args.steps, 1)):
+        rec, _, _ = cpu_oracle_refine(A, X0, D0, delta)
+        recs.append(rec)
+        if time.perf_counter() - t_start + rec["value"] > args.ref_budget:
+            break
+    value = statistics.mean([r["value"] for r in recs])
+    cb = dict(recs[-1])
     cb["value"] = value
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "steps": len(recs), "requested_steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "step_values_s": [r["value"] for r in recs],
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64/dd",
         "data": "synthetic",
         "config": {"workload": f"refine n={n} SPD geometric cond {args.cond:g}, start perturbed 1e-8, "

@@ -1,5 +1,6 @@
 """Host-side logic of bench.py that needs no GPU: the clock record kept from the timed region,
-the fitted CPU-oracle sample, and the per-workload step defaults."""
+the timed oracle refinement, the reference arm's step accounting and the per-workload step
+defaults."""
 import datetime
 import sys
 import time
@@ -61,12 +62,32 @@ def test_step_defaults(bench, monkeypatch):
         assert bench.parse().steps == steps
 
 
-def test_oracle_sample_fits_fixed_and_per_row_cost(bench):
+def test_oracle_refinement_is_timed_whole(bench):
     from paper_2602_19090_gb300 import synth
     A, X0, D0, _ = synth.refine_workload(96, 1e4, "spd", case=3)
-    r = bench.cpu_oracle_sample(A, X0, D0, 1e-14, 100, 2, rows=(16, 32, 64))
-    assert r["kind"] == "oracle" and r["unit"] == "s" and r["value"] > 0
-    assert "r = 16, 32, 64" in r["sample"] and "2 x plan" in r["sample"]
-    # rows past n are clamped, and the doubling stops at n
-    r = bench.cpu_oracle_sample(A, X0, D0, 1e-14, 100, 2, rows=(32, 64), min_seconds=1e9)
-    assert "r = 32, 64, 96" in r["sample"]
+    rec, X, info = bench.cpu_oracle_refine(A, X0, D0, 1e-14)
+    assert rec["kind"] == "oracle" and rec["unit"] == "s" and rec["value"] > 0
+    assert info["status"] == "converged" and X.shape == (96, 96)
+    assert f"{info['iters']} iterations, {info['products']} slice products" in rec["sample"]
+
+
+def test_reference_arm_reports_the_steps_it_ran(bench, monkeypatch, capsys):
+    # each fake oracle refinement "takes" 70 s of a fake clock: with a 180 s budget the arm
+    # runs two (the third would end past the budget) and says so, whatever --steps asked
+    import json
+    clock = [0.0]
+    monkeypatch.setattr(bench.time, "perf_counter", lambda: clock[0])
+
+    def fake(A, X0, D0, delta):
+        clock[0] += 70.0
+        return {"value": 70.0, "unit": "s", "cores": 1, "kind": "oracle", "sample": "fake"}, None, None
+
+    monkeypatch.setattr(bench, "cpu_oracle_refine", fake)
+    monkeypatch.setattr(bench, "oracle_warmup", lambda *a: None)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--n", "64", "--steps", "20",
+                                      "--warmup", "5", "--ref-budget", "180"])
+    bench.run_reference(bench.parse())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["requested_steps"] == 20
+    assert line["ms_per_step"] == 70000.0 and line["value"] == 70.0
+    assert line["steps"] * line["ms_per_step"] / 1e3 <= 180
