@@ -269,6 +269,11 @@ FRX_API int frx_plane_products(const uint16_t* L, int64_t L_plane_stride, const 
  *   gemm_ops         algorithmic operations of those launches: 2 m n K per slice pair
  *   gemm_bytes       algorithmic bytes: every digit plane read once (2 bytes per
  *                    digit) plus every int64 group word written once
+ *   simt_launches    slice-product launches among gemm_launches that ran on the CUDA cores
+ *                    instead of the tensor cores (about 100 times slower): the driver lacks
+ *                    the tensor-map encoder, an operand of frx_plane_products is not 16-byte
+ *                    aligned or its plane stride or pitch is not a multiple of 8 digits, or
+ *                    FRX_GEMM=simt is set.  The library's own products never take it.
  * frx_profile_enable(1) starts timing every GEMM launch with a pair of CUDA events;
  * frx_profile_read waits for the recorded events, fills `out` (host) and, if `reset`
  * is nonzero, clears the counters.  Thread-safe; the counters are process-wide.
@@ -279,6 +284,7 @@ typedef struct {
   double gemm_ms;
   double gemm_ops;
   double gemm_bytes;
+  long long simt_launches;
 } frx_profile;
 
 FRX_API void frx_profile_enable(int on);

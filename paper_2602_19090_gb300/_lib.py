@@ -30,7 +30,8 @@ class Info(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_longlong), ("gemm_launches", C.c_longlong),
-                ("gemm_ms", C.c_double), ("gemm_ops", C.c_double), ("gemm_bytes", C.c_double)]
+                ("gemm_ms", C.c_double), ("gemm_ops", C.c_double), ("gemm_bytes", C.c_double),
+                ("simt_launches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -169,6 +169,7 @@ int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s) {
     return launch_plane_gemm_tc(g, g.flags, tile, s);
   }
   GemmTimer timer(g, s);
+  count_simt_launch();
   return launch_plane_gemm_simt(g, s);
 }
 

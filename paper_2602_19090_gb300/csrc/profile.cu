@@ -16,7 +16,7 @@ struct Timed {
 
 std::mutex mu;
 bool enabled = false;
-long long launches = 0, gemm_launches = 0;
+long long launches = 0, gemm_launches = 0, simt_launches = 0;
 double gemm_ms = 0.0, gemm_ops = 0.0, gemm_bytes = 0.0;
 std::vector<Timed> pending;
 std::vector<cudaEvent_t> free_events;
@@ -37,6 +37,11 @@ cudaEvent_t get_event() {
 void count_launches(int k) {
   std::lock_guard<std::mutex> g(mu);
   launches += k;
+}
+
+void count_simt_launch() {
+  std::lock_guard<std::mutex> g(mu);
+  simt_launches += 1;
 }
 
 // operations of plan-driven products, known only once the device plan has run
@@ -105,9 +110,10 @@ int frx_profile_read(frx_profile* out, int reset) {
     out->gemm_ms = gemm_ms;
     out->gemm_ops = gemm_ops;
     out->gemm_bytes = gemm_bytes;
+    out->simt_launches = simt_launches;
   }
   if (reset) {
-    launches = gemm_launches = 0;
+    launches = gemm_launches = simt_launches = 0;
     gemm_ms = gemm_ops = gemm_bytes = 0.0;
   }
   return FRX_OK;

@@ -6,6 +6,7 @@
 namespace frx {
 
 void count_launches(int k);
+void count_simt_launch();   // a slice product that ran on the CUDA cores (see frx_profile)
 void profile_add_gemm_work(double ops);
 
 // RAII: counts one GEMM launch and, with profiling on, brackets it with CUDA events

@@ -194,7 +194,11 @@ def test_refine_converges_like_the_oracle(api):
     A, X0, D0 = synth.workload0()
     Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
     At, Xt, Dt = g.to_dev(A), g.to_dev(X0), g.to_dev(D0)
+    api.profile_read(reset=True)
     info = api.refine(At, Xt, Dt, 1e-14)
+    prof = api.profile_read(reset=True)
+    # every slice product of the refinement ran on the tensor cores
+    assert prof["gemm_launches"] > 0 and prof["simt_launches"] == 0
     Xo, lo, oi = orf.refine(A, X0, D0, 1e-14, orf.Options())
     assert info["status"] == 0 and info["iters"] == oi["iters"]
     assert info["products"] == oi["products"]

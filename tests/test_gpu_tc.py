@@ -22,11 +22,15 @@ def _both(api, Lp, Rp, K, kL, kR, T):
     import torch
     old = os.environ.get("FRX_GEMM")
     try:
+        # the profile counts each product that ran on the CUDA cores
+        api.profile_read(reset=True)
         os.environ["FRX_GEMM"] = "simt"
         ref, gs = api.plane_products(Lp, Rp, K, kL, kR, T)
+        assert api.profile_read(reset=True)["simt_launches"] == 1
         os.environ["FRX_GEMM"] = "tc"
         got, gs2 = api.plane_products(Lp, Rp, K, kL, kR, T)
         torch.cuda.synchronize()
+        assert api.profile_read(reset=True)["simt_launches"] == 0
     finally:
         if old is None:
             os.environ.pop("FRX_GEMM", None)
