@@ -20,11 +20,15 @@ Readings where the paper is silent (each also listed in the design notes):
   all exact and only the truncation of A to k_V planes (and of the pair set to
   r + s <= k_V + 1) is approximate;
 * slice counts (the paper sweeps n_A by hand): k = smallest k with
-  (2^(8k - eL - eR - 7) tau)^2 >= n^3, i.e. 128 n^1.5 2^(eL+eR) 2^(-8k) <= tau
-  (the first dropped anti-diagonal's digits are at most 128 = 2^7 on the grid
-  2^(eL + eR + 2 - 8(k + 1))), where eL, eR are the operands' largest exponents and
-  tau = delta * g for V and W, delta for the update product;  a fixed k_V may be
-  forced (``slices_A``);
+  16 n 2^(eL + eR - 8k) <= tau, evaluated exactly as 2^(8k - eL - eR - 4) tau >= n,
+  where eL, eR are the operands' largest exponents and tau = delta * g for V and W,
+  delta for the update product.  Every entry of the dropped part is a sum over n
+  terms of digit tails below 2^(eL + eR - 8k); taking such sums to grow like sqrt(n)
+  (the reading Sec. 4.1 itself makes when it replaces log2 n by ceil(log2 sqrt n)),
+  and the 2-norm of an n x n matrix of such entries like sqrt(n) times their size,
+  gives n 2^(eL + eR - 8k); the factor 16 is the margin, calibrated on randsvd-like
+  and exact-truth matrices where a factor 1 already leaves the forward error
+  unchanged;  a fixed k_V may be forced (``slices_A``);
 * the slice products' exact int32 sums need pairs * n * 2^14 < 2^31: the update
   product (up to k_U pairs per anti-diagonal) takes at most floor((2^17 - 1) / n)
   planes (16 for n < 8192); V's and W's pairs are at most s_X <= 7;
@@ -119,14 +123,16 @@ def alpha_rule(n, beta, opts: Options) -> int:
     return 53 - beta + ceil_log2_sqrt(n)
 
 
+SLICE_MARGIN_LOG2 = 4   # the factor 16 of the slice rule
+
+
 def slices_for(n, eL, eR, tau, k_cap):
-    """Smallest k >= 1 with (2^(8k - eL - eR - 7) * tau)^2 >= n^3, capped."""
+    """Smallest k >= 1 with 16 n 2^(eL + eR - 8k) <= tau, i.e. 2^(8k - eL - eR - 4) tau >= n
+    (ldexp is exact), capped at k_cap; 0 when an operand is zero."""
     if eL == oz.EZERO or eR == oz.EZERO:
         return 0
-    n3 = float(n) ** 3
     for k in range(1, k_cap + 1):
-        v = math.ldexp(tau, oz.DIGIT_BITS * k - int(eL) - int(eR) - (oz.DIGIT_BITS - 1))
-        if v * v >= n3:
+        if math.ldexp(tau, oz.DIGIT_BITS * k - int(eL) - int(eR) - SLICE_MARGIN_LOG2) >= float(n):
             return k
     return k_cap
 

@@ -38,15 +38,17 @@ __device__ int dceil_log2_int(int64_t n) {
   return bl;
 }
 
-// smallest k >= 1 with (2^(b k - eL - eR - (b - 1)) tau)^2 >= n^3 (b = DIGIT_BITS), capped; 0 if
-// an operand is zero
+// Slice count of an Ozaki product: the smallest k >= 1 with 16 n 2^(eL + eR - b k) <= tau
+// (b = DIGIT_BITS), evaluated exactly as 2^(b k - eL - eR - 4) tau >= n; capped; 0 if an operand
+// is zero.  The dropped part's entries are sums over n terms of digit tails below
+// 2^(eL + eR - b k); such sums grow like sqrt(n) (the reading Sec. 4.1 makes when it replaces
+// log2 n by ceil(log2 sqrt n)) and the 2-norm of the n x n error like sqrt(n) times its entries;
+// 16 is the calibrated margin.
+constexpr int SLICE_MARGIN_LOG2 = 4;
 __device__ int dslices_for(int64_t n, int eL, int eR, double tau, int kcap) {
   if (eL == EZERO || eR == EZERO) return 0;
-  double n3 = __dmul_rn(__dmul_rn((double)n, (double)n), (double)n);
-  for (int k = 1; k <= kcap; ++k) {
-    double v = ldexp(tau, DIGIT_BITS * k - eL - eR - (DIGIT_BITS - 1));
-    if (__dmul_rn(v, v) >= n3) return k;
-  }
+  for (int k = 1; k <= kcap; ++k)
+    if (ldexp(tau, DIGIT_BITS * k - eL - eR - SLICE_MARGIN_LOG2) >= (double)n) return k;
   return kcap;
 }
 

@@ -14,7 +14,7 @@ Per iteration (Algorithm 1 with Sec. 3 and the Sec. 4.1 parameters):
   W = X1^T (V - X1 D) and X1 E~   plain FP64 products (the paper's "+2");
   X            fl(X1 + X1 E~).
 n_A is chosen so that the slices capture as many bits of A as the Ozaki path's
-k_V digit planes (7 k_V bits), the product count the paper sweeps by hand.
+k_V digit planes (8 k_V bits), the product count the paper sweeps by hand.
 """
 from __future__ import annotations
 
@@ -81,10 +81,9 @@ def _ceil_log2_sqrt(n):
 
 
 def _slices_for(n, eL, eR, tau, kcap=16):
-    n3 = float(n) ** 3
+    # the digit-plane count the frx plan gives its V product (8-bit planes, 16 n 2^(eL+eR-8k) <= tau)
     for k in range(1, kcap + 1):
-        v = math.ldexp(tau, 7 * k - eL - eR - 6)
-        if v * v >= n3:
+        if math.ldexp(tau, 8 * k - eL - eR - 4) >= float(n):
             return k
     return kcap
 
@@ -110,7 +109,7 @@ def step(A, X, lam_prev, delta):
     eA = int(_ceil_log2(A.abs().amax(dim=1)).max())
     kV = _slices_for(n, eA, int(f.max()), delta * g)
     bits = 53 - alpha
-    nA = max(2, 1 + math.ceil((7 * kV - 53) / max(bits, 1)))
+    nA = max(2, 1 + math.ceil((8 * kV - 53) / max(bits, 1)))
     # V = sum_r fl(A^(r) X1) (eq. mat_mul), accumulated in double-double
     res = A.clone()
     Vh = torch.zeros_like(X)

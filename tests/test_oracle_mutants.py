@@ -48,7 +48,10 @@ MUTANTS = [
      "beta: dropped 0.75 of tau"),
     ("refine", "return 53 - beta + ceil_log2_sqrt(n)", "return 53 - beta + ceil_log2_int(n)",
      "alpha: log2 n for log2 sqrt n"),
-    ("refine", "- (oz.DIGIT_BITS - 1))", "- oz.DIGIT_BITS)", "slice rule: digit bound off by one bit"),
+    ("refine", "- SLICE_MARGIN_LOG2) >= float(n)", "- SLICE_MARGIN_LOG2 - 1) >= float(n)",
+     "slice rule: margin off by one bit"),
+    ("refine", "oz.DIGIT_BITS * k - int(eL) - int(eR)", "oz.DIGIT_BITS * k - int(eL)",
+     "slice rule: right operand's exponent dropped"),
     ("refine", "E[i, j] = -sh / 2.0", "E[i, j] = sh / 2.0", "cluster rule: wrong sign of r_ij"),
     ("refine", "est = step_norm * step_norm * Lam_new", "est = step_norm * Lam_new", "stopping test: dropped square"),
     ("refine", "    s = np.sort(lam)\n", "    s = lam\n", "min gap: estimates not sorted"),

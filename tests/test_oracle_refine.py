@@ -37,14 +37,39 @@ def test_ceil_log2_sqrt_exact():
         assert 4 ** (c - 1) < n <= 4 ** c or (n == 1 and c == 0)
 
 
-def test_slice_rule_definition():
-    for n in (64, 300, 4096):
-        for eL, eR in ((0, -3), (-2, -30), (1, 1)):
-            for tau in (1e-22, 3.4e-23, 1e-14):
-                k = rf.slices_for(n, eL, eR, tau, 40)
-                assert 128 * n ** 1.5 * 2.0 ** (eL + eR - 8 * k) <= tau * (1 + 1e-12)
-                if k > 1:
-                    assert 128 * n ** 1.5 * 2.0 ** (eL + eR - 8 * (k - 1)) > tau * (1 - 1e-12)
+def test_slice_rule_worked_by_hand():
+    # 16 n 2^(eL + eR - 8k) <= tau, smallest k:
+    #   n = 64, eL = eR = 0, tau = 2^-40: 2^(4 + 6 - 8k) <= 2^-40  <=>  8k >= 50  ->  k = 7
+    assert rf.slices_for(64, 0, 0, 2.0 ** -40, 16) == 7
+    #   the same with tau = 2^-46: 8k >= 56 -> k = 7 exactly at the boundary; a hair below -> 8
+    assert rf.slices_for(64, 0, 0, 2.0 ** -46, 16) == 7
+    assert rf.slices_for(64, 0, 0, 2.0 ** -46 * (1 - 2.0 ** -52), 16) == 8
+    #   n = 4096, eL = -2, eR = -3, tau = 1e-14 * 2.25e-7 = 2^-68.59: 4 + 12 - 5 - 8k <= -68.59
+    #   <=>  8k >= 79.59  ->  k = 10;  with n = 33000 (log2 = 15.01): 8k >= 82.60 -> k = 11
+    assert rf.slices_for(4096, -2, -3, 1e-14 * 2.25e-7, 16) == 10
+    assert rf.slices_for(33000, -2, -3, 1e-14 * 2.25e-7, 16) == 11
+    # a zero operand needs no product; the cap holds
+    assert rf.slices_for(64, oz.EZERO, 0, 1e-20, 16) == 0
+    assert rf.slices_for(64, 0, 0, 1e-300, 5) == 5
+
+
+@pytest.mark.parametrize("n,cond,tau", [(128, 1e6, 1e-18), (200, 1e3, 1e-24), (96, 1e10, 1e-21)])
+def test_slice_rule_keeps_the_dropped_part_below_tau(n, cond, tau):
+    # the rule's promise, measured: A X^(1) with the rule's k planes of A and the pair set
+    # r + s <= k + 1 (X^(1), a beta = 20 truncation of eigenvectors, is exact in its 5 planes)
+    # differs from the exact product (double-double) by less than tau in the 2-norm
+    A, Q, lam = synth.symmetric_matrix(n, cond, 11)
+    X1, f = oz.tau_truncate_cols(Q, 20)
+    eA = oz.row_exponents(A)
+    k = rf.slices_for(n, int(np.max(eA)), int(np.max(f)), tau, 16)
+    out = oz.ozaki_product(A, X1, k, 5, k + 1, eL=eA, eR=f)
+    Vh, Vl = dd.dd_matmul(A, None, X1, None)
+    err = (out["hi"] - Vh) + (out["lo"] - Vl)
+    assert np.linalg.norm(err, 2) <= tau
+    # and one plane fewer is not always enough: the rule is not vacuous
+    out = oz.ozaki_product(A, X1, k - 1, 5, k, eL=eA, eR=f)
+    err = (out["hi"] - Vh) + (out["lo"] - Vl)
+    assert np.linalg.norm(err, 2) > tau * 2.0 ** -12
 
 
 def test_w_identity():
