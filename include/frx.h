@@ -65,7 +65,8 @@ typedef enum {
 /* Options of frx_refine.  Fill with frx_default_opts, then override. */
 typedef struct {
   int slices_A;          /* 0: automatic number of A slices k_V; > 0: fixed (e.g. 8)        */
-  double xi;             /* <= 0: xi = n, the Sec. 4.1 "n delta" form; > 0: eq. proposed_beta */
+  double xi;             /* > 0: eq. proposed_beta with this xi (default 1); <= 0: xi = n, the
+                            "n delta" form of the Sec. 4.1 experiments                          */
   int beta_ceil;         /* 0: floor (Sec. 4.1); 1: ceil (eq. proposed_beta)                  */
   int theory_alpha;      /* 0: alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1);
                             1: alpha = 53 - beta + ceil(log2 n) (eq. proposed_beta)           */
@@ -101,7 +102,8 @@ typedef struct {
   int clustered_pairs;   /* cluster pairs treated by the r_ij / 2 rule in the last iteration */
 } frx_info;
 
-/* Default options: automatic slices, Sec. 4.1 rule, k_cap 16, max_iter 10. */
+/* Default options: automatic slices, eq. proposed_beta with xi = 1 and floor rounding (Sec. 4.1),
+ * k_cap 16, max_iter 10. */
 FRX_API void frx_default_opts(frx_opts* opts);
 
 /* Text for a status code (static storage). */

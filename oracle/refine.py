@@ -3,8 +3,9 @@
 ORACLE: test infrastructure only.
 
 One iteration (Algorithm 1 with the Sec. 3 modification, eq. mat_mul):
-  plan   beta from eq. proposed_beta in its Sec. 4.1 form (floor, n*delta, i.e.
-         xi = n), alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1), using the
+  plan   beta from eq. proposed_beta with floor rounding (Sec. 4.1) and the error
+         model's xi = 1 by default (xi = n, the "n delta" of the Sec. 4.1 experiments,
+         is an option), alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1), using the
          previous eigenvalue estimates (the circularity is broken by lagging them);
   X1     = fl((tau_j + x_ij) - tau_j), tau_j = 0.75 2^ceil(log2 w_j) 2^beta (eq. tau, x);
   V      = accurate A X1 from exact 8-bit digit-plane products (line 1, eq. mat_mul);
@@ -58,7 +59,7 @@ U = 2.0 ** -53
 @dataclasses.dataclass
 class Options:
     slices_A: int = 0            # 0: automatic k_V; >0: fixed number of A planes
-    xi: float | None = None      # None: xi = n (Sec. 4.1 "n delta"); else eq. proposed_beta's xi
+    xi: float | None = 1.0       # eq. proposed_beta's xi; None: xi = n (the Sec. 4.1 "n delta")
     beta_rounding: str = "floor"  # Sec. 4.1 floor; "ceil" = eq. proposed_beta
     theory_alpha: bool = False   # alpha = ceil(53 + log2 n - beta) instead of Sec. 4.1
     beta_override: int | None = None

@@ -28,7 +28,7 @@ class FrxError(RuntimeError):
 @dataclasses.dataclass
 class Options:
     slices_A: int = 0
-    xi: float = 0.0
+    xi: float = 1.0              # <= 0: xi = n (the Sec. 4.1 "n delta" form)
     beta_ceil: bool = False
     theory_alpha: bool = False
     beta_override: int = -1

@@ -843,7 +843,7 @@ extern "C" {
 void frx_default_opts(frx_opts* o) {
   if (!o) return;
   o->slices_A = 0;
-  o->xi = 0.0;
+  o->xi = 1.0;
   o->beta_ceil = 0;
   o->theory_alpha = 0;
   o->beta_override = -1;

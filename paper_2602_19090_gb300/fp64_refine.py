@@ -5,7 +5,9 @@ This is the paper's own formulation run on the GPU with library DGEMM, used by
 It is not part of the frx product path and shares no code with it.
 
 Per iteration (Algorithm 1 with Sec. 3 and the Sec. 4.1 parameters):
-  beta, alpha  Sec. 4.1 (floor, n*delta, ceil(log2 sqrt n)), from the previous estimates;
+  beta, alpha  eq. proposed_beta with floor rounding and ceil(log2 sqrt n) (Sec. 4.1), the
+               error model's xi as in the frx plan (1 by default; xi <= 0: n, the
+               "n delta" of the Sec. 4.1 experiments), from the previous estimates;
   X1           fl((tau_j + x) - tau_j) (eq. tau, eq. x);
   A slices     eq. sigma / eq. a with alpha and a rescan of the residual's row maxima,
                n_A - 1 slices plus the remainder (eq. mat_mul);
@@ -96,12 +98,13 @@ def _min_gap(lam):
     return (float(g.min()) if g.numel() else Lam), Lam
 
 
-def step(A, X, lam_prev, delta):
+def step(A, X, lam_prev, delta, xi=1.0):
     n = X.shape[0]
     g, Lam = _min_gap(lam_prev)
     f = _ceil_log2(X.abs().amax(dim=0))
     S2 = float(torch.sum(_pow2(2 * f)))
-    q = math.sqrt((n * delta * g) / (Lam * S2)) / (0.75 * U)
+    xi = xi if xi > 0 else float(n)
+    q = math.sqrt((xi * delta * g) / (Lam * S2)) / (0.75 * U)
     beta = min(max(math.frexp(q)[1] - 1, 3), 47)
     alpha = 53 - beta + _ceil_log2_sqrt(n)
     tau = 0.75 * _pow2(f + beta)
@@ -148,14 +151,14 @@ def step(A, X, lam_prev, delta):
     return Xn, lam, dict(beta=beta, alpha=alpha, nA=nA, products=nA + 2, step=stp, est=est)
 
 
-def refine(A, X, D, delta, max_iter=10):
+def refine(A, X, D, delta, max_iter=10, xi=1.0):
     """Returns (X, lam, info); A, X, D float64 CUDA tensors (X, D are not modified)."""
     lam = D.clone()
     prev = None
     noncontract = 0
     status, it, total, est = "max_iter", 0, 0, math.inf
     for it in range(1, max_iter + 1):
-        X, lam, info = step(A, X, lam, delta)
+        X, lam, info = step(A, X, lam, delta, xi)
         total += info["products"]
         est = info["est"]
         noncontract = noncontract + 1 if (prev is not None and info["step"] > 0.5 * prev) else 0

@@ -20,9 +20,12 @@ def test_beta_alpha_worked_example():
     # log2 = 22.12 -> beta = 22 (floor), 23 (ceil);  alpha = 53 - 22 + ceil(log2 64) = 37
     # (theory: 53 - 22 + log2 4096 = 43);  X^(1) keeps bits 2^f ... 2^(f+22-53):
     # 32 bit positions -> ceil(32 / 8) = 4 planes of 8-bit digits.
-    o = rf.Options()
+    o = rf.Options(xi=None)
     assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, o) == 22
-    assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, rf.Options(beta_rounding="ceil")) == 23
+    assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, rf.Options(xi=None, beta_rounding="ceil")) == 23
+    # the default xi = 1 of eq. proposed_beta: 1e-14 * 2.25e-7 / 64 = 3.516e-23; sqrt = 5.930e-12;
+    # / (0.75 * 2^-53) = 7.121e4; log2 = 16.12 -> beta = 16 (sqrt 4096 = 2^6 below the n delta form)
+    assert rf.beta_rule(4096, 1e-14, 2.25e-7, 1.0, 64.0, rf.Options()) == 16
     assert rf.alpha_rule(4096, 22, o) == 37
     assert rf.alpha_rule(4096, 22, rf.Options(theory_alpha=True)) == 43
     X = np.full((4096, 3), 0.07)
@@ -315,15 +318,19 @@ def test_sparse_rule_is_the_paper_formula():
     beta = min(max(math.floor(math.log2(q)), 3), 47)
     assert p["beta"] == beta
     assert p["alpha"] == 53 - beta + 3
-    # denser than the dense rule: min(k, sqrt n)^2 = 25 < n keeps more bits of X (smaller beta)
-    assert p["beta"] < rf.plan(A, X0, D0, delta, rf.Options())["beta"]
+    # finer than the dense n delta form of Sec. 4.1: min(k, sqrt n)^2 = 25 < n keeps more bits of
+    # X (smaller beta); coarser than xi = 1 (25 > 1)
+    assert p["beta"] < rf.plan(A, X0, D0, delta, rf.Options(xi=None))["beta"]
+    assert p["beta"] > rf.plan(A, X0, D0, delta, rf.Options(xi=1.0))["beta"]
 
 
-def _plan_case(lam_prev, omega_prev=0.0, col_max=0.25):
+def _plan_case(lam_prev, omega_prev=0.0, col_max=0.25, xi=None):
     # n = 4, X = col_max * I: every column maximum is col_max, so f_j = ceil(log2 col_max);
-    # A = I (only its exponents and nonzero counts enter the plan)
+    # A = I (only its exponents and nonzero counts enter the plan); the n delta form of Sec. 4.1
+    # unless xi is given
     X = col_max * np.eye(4)
-    return rf.plan(np.eye(4), X, np.asarray(lam_prev, dtype=np.float64), 2.0 ** -30, rf.Options(), omega_prev)
+    return rf.plan(np.eye(4), X, np.asarray(lam_prev, dtype=np.float64), 2.0 ** -30, rf.Options(xi=xi),
+                   omega_prev)
 
 
 def test_plan_gap_and_beta_worked_by_hand():
@@ -338,6 +345,8 @@ def test_plan_gap_and_beta_worked_by_hand():
     assert p["g"] == 2.0 ** -20 and p["Lam"] == 2.0
     assert p["f"].tolist() == [-2, -2, -2, -2] and p["S2"] == 0.25
     assert p["beta"] == 29
+    # with xi = 1 in place of n = 4 the square root loses a factor 2: 2^28.915 -> beta = 28
+    assert _plan_case([0.5, -1.0, 0.5 + 2.0 ** -20, 2.0], xi=1.0)["beta"] == 28
     # a gap at or below the cluster threshold omega = 2^-19 is not a gap: g = 1.5 - 2^-20;
     #   4 * 2^-30 * (1.5 - 2^-20) / (2 * 2^-2) = 2^-27 (1.5 - 2^-20); log2 of its square root
     #   = (0.58496 - 27) / 2 = -13.2075; + 53 + log2(4/3) = 40.2  ->  beta = 40
