@@ -31,7 +31,7 @@ def test_refine_step_n4096_all_outputs(api):
     from tests.test_gpu_parity import _step_compare
     A, X0, D0, lam = synth.refine_workload(4096, 1e4, "spd", case=0)
     info, oi = _step_compare(api, A, X0, D0, 1e-14, orf.Options(), api.Options())
-    assert info["k_V"] == 10 and info["s_X"] == 5     # the plan of the timed workload
+    assert info["k_V"] == 11 and info["s_X"] == 5     # the plan of the timed workload
 
 
 def _gemm_compare(Ch, Cl, A, B, k, mode):
