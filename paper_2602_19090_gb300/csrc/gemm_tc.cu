@@ -8,8 +8,12 @@
 // terms per lane (|sum| <= 2^24); the accumulator is therefore drained into integer
 // registers every CHUNK_KB k-blocks (and at the end of every anti-diagonal t).  With int32
 // planes each anti-diagonal's exact sum S_t is stored as one plane (while
-// pairs * K * 2^14 < 2^31); otherwise BN = 128 and the int64 sums are combined in Horner
-// form per group: R_g = sum_{t in g} 2^(8 (t_last - t)) S_t.
+// pairs * K * 2^14 < 2^31).  Beyond that the sums are int64 Horner groups
+// R_g = sum_{t in g} 2^(8 (t_last - t)) S_t, formed by split-K: the inner dimension is cut into
+// chunks short enough for every chunk's S_t to be exact in int32 registers, and each unit adds
+// its chunk's 2^(8 (t_last - t)) S_t to the zeroed group word with a 64-bit atomic (integer
+// addition: exact and independent of the order the chunks land in).  A BN = 128 kernel that
+// accumulates the Horner groups in int64 registers remains for FRX_SPLITK=0.
 //
 // Tile configurations (int32 planes): 128 x 128 or 128 x 256 output tiles per CTA.  The
 // configuration changes no result; the autotuner picks it.  Every CTA loads its own operand
@@ -171,6 +175,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 struct TcArgs {
   int64_t M, N;
   int nkb;       // k-blocks of 64
+  int nsplit;    // split-K chunks (1: none); each unit covers k-blocks [c kcb, (c + 1) kcb)
+  int kcb;
   void* out;     // int64 groups, or int32 per-t planes when W32
   int64_t ogs, ldo;
   int* flags;
@@ -193,7 +199,7 @@ struct TcProblem {
 // per-launch scalars read once at kernel entry
 struct TcRun {
   int64_t M, N;
-  int nkb, kL, kR, tmax, gs, groups, ntm, ntn, units;
+  int nkb, kL, kR, tmax, gs, groups, ntm, ntn, units, nsplit, kcb;
   void* out;
   int64_t ogs, ldo;
   int* flags;
@@ -235,13 +241,16 @@ __device__ __forceinline__ int unit_of_round(int r, bool serp) {
 }
 
 // the product description of a launch's problem, resolved from its arguments; the tiling
-// (128 x BN tiles, units = tiles x groups) belongs to the kernel variant, not to the plan
-template <int BN, bool W32>
+// (128 x BN tiles, units = tiles x groups x split-K chunks) belongs to the kernel variant, not
+// to the plan.  W32: int32 accumulation in registers; SPLIT: int64 Horner groups accumulated
+// by atomics over K-chunks (W32 without SPLIT writes one int32 plane per anti-diagonal).
+template <int BN, bool W32, bool SPLIT>
 __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*& gorder) {
   if (a0.done && *a0.done) return false;
   const GemmDesc* D = a0.dyn ? a0.dyn : &a0.d;
   if (!D->active || D->groups <= 0) return false;
-  if (a0.bn != BN || D->word32 != (W32 ? 1 : 0)) {
+  if (a0.bn != BN || D->word32 != ((W32 && !SPLIT) ? 1 : 0) ||
+      (SPLIT && (a0.nsplit < 1 || a0.kcb < 1 || (long long)a0.nsplit * a0.kcb < a0.nkb))) {
     // the tensor map's box or the exact-sum layout does not fit this variant: no product
     if (a0.flags) atomicOr(a0.flags, FLAG_CONFIG);
     return false;
@@ -256,7 +265,9 @@ __device__ __forceinline__ bool tc_run_of(const TcArgs& a0, TcRun& a, const int*
   a.groups = D->groups;
   a.ntm = (int)((a0.M + BM - 1) / BM);
   a.ntn = (int)((a0.N + BN - 1) / BN);
-  a.units = a.ntm * a.ntn * D->groups;
+  a.nsplit = SPLIT ? a0.nsplit : 1;
+  a.kcb = SPLIT ? a0.kcb : a0.nkb;
+  a.units = a.ntm * a.ntn * D->groups * a.nsplit;
   a.out = a0.out;
   a.ogs = a0.ogs;
   a.ldo = a0.ldo;
@@ -326,7 +337,7 @@ struct GroupedSrc {
     }
     if (lo != cur) {
       cur = lo;
-      tc_run_of<BN, W32>(probs[lo].a, run, gorder);
+      tc_run_of<BN, W32, false>(probs[lo].a, run, gorder);
       mapL = &probs[lo].mapL;
       mapR = &probs[lo].mapR;
     }
@@ -336,8 +347,10 @@ struct GroupedSrc {
 };
 
 // BN_ = 128: int64 Horner groups of gs anti-diagonals, 64 columns per epilogue thread.
-// BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread.
-template <int BN_, bool W32, class Src>
+// BN_ = 256 (W32): one exact int32 plane per anti-diagonal t (gs = 1), 128 columns per thread;
+// with SPLIT the unit's K-chunk sum of each t is added to its int64 Horner group by atomics.
+// A unit's slot q = lu / tiles names its group gorder[q / nsplit] and K-chunk q % nsplit.
+template <int BN_, bool W32, bool SPLIT, class Src>
 __device__ __forceinline__ void tc_body(Src& src) {
   constexpr int BN = BN_;
   constexpr int STAGES = BN == 256 ? 4 : 6;
@@ -389,14 +402,15 @@ __device__ __forceinline__ void tc_body(Src& src) {
         const TcRun& a = src.run;
         const int* gorder = src.gorder;
         const int tiles = a.ntm * a.ntn;
-        const int grp = gorder[lu / tiles], tile = lu % tiles;
+        const int q = lu / tiles, tile = lu % tiles;
+        const int grp = gorder[q / a.nsplit], kb0 = (q % a.nsplit) * a.kcb, kb1 = min(a.nkb, kb0 + a.kcb);
         int i0, j0;
         tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           for (int r = pair_lo(t, a.kR); r <= pair_hi(t, a.kL) && ok; ++r) {
             int s = t - r;
-            for (int kb = 0; kb < a.nkb; ++kb) {
+            for (int kb = kb0; kb < kb1; ++kb) {
               if (!mbar_wait(&sm->empty[stage], phase ^ 1, abort, a.flags)) {
                 ok = false;
                 break;
@@ -455,14 +469,15 @@ __device__ __forceinline__ void tc_body(Src& src) {
         const TcRun& a = src.run;
         const int* gorder = src.gorder;
         const int tiles = a.ntm * a.ntn;
-        const int grp = gorder[lu / tiles];
+        const int q = lu / tiles;
+        const int grp = gorder[q / a.nsplit], kb0 = (q % a.nsplit) * a.kcb, kb1 = min(a.nkb, kb0 + a.kcb);
         int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
         for (int t = t0; t <= t1 && ok; ++t) {
           int rlo = pair_lo(t, a.kR), rhi = pair_hi(t, a.kL);
-          int total = (rhi - rlo + 1) * a.nkb;
+          int total = (rhi - rlo + 1) * (kb1 - kb0);
           int cnt = 0, done = 0;
           for (int r = rlo; r <= rhi && ok; ++r) {
-            for (int kb = 0; kb < a.nkb; ++kb) {
+            for (int kb = kb0; kb < kb1; ++kb) {
               if (cnt == 0) {
                 if (!mbar_wait(&sm->acc_empty[buf], acc_phase[buf] ^ 1, abort, a.flags)) {
                   ok = false;
@@ -524,13 +539,14 @@ __device__ __forceinline__ void tc_body(Src& src) {
       const TcRun& a = src.run;
       const int* gorder = src.gorder;
       const int tiles = a.ntm * a.ntn;
-      const int grp = gorder[lu / tiles], tile = lu % tiles;
+      const int q = lu / tiles, tile = lu % tiles;
+      const int grp = gorder[q / a.nsplit], kb0 = (q % a.nsplit) * a.kcb, kb1 = min(a.nkb, kb0 + a.kcb);
       int i0, j0;
       tile_origin(tile, a.ntm, a.ntn, BM, BN, i0, j0);
       const int64_t row = (int64_t)i0 + quad * 32 + lane;
       int t0 = 2 + grp * a.gs, t1 = min(t0 + a.gs - 1, a.tmax);
       for (int t = t0; t <= t1 && ok; ++t) {
-        int total = (pair_hi(t, a.kL) - pair_lo(t, a.kR) + 1) * a.nkb;
+        int total = (pair_hi(t, a.kL) - pair_lo(t, a.kR) + 1) * (kb1 - kb0);
         int chunks = (total + CHUNK_KB - 1) / CHUNK_KB;
         if constexpr (!W32) {
 #pragma unroll
@@ -556,9 +572,23 @@ __device__ __forceinline__ void tc_body(Src& src) {
           acc_phase[buf] ^= 1;
           buf ^= 1;
         }
+        if constexpr (SPLIT) {
+          // this chunk's exact S_t, weighted for its Horner group, added to the group word
+          if (ok && row < a.M) {
+            unsigned long long* o = reinterpret_cast<unsigned long long*>(a.out) + grp * a.ogs + row;
+            const int sh = DIGIT_BITS * (t1 - t);
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) {
+              const int64_t j = (int64_t)j0 + col0 + c;
+              if (j < a.N && R[c] != 0) atomicAdd(o + j * a.ldo, (unsigned long long)((i64)R[c] << sh));
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < NCOL; ++c) R[c] = 0;
+        }
       }
       if (!ok) break;
-      if (row < a.M) {
+      if (!SPLIT && row < a.M) {
         Acc* o = reinterpret_cast<Acc*>(a.out) + grp * a.ogs + row;
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
@@ -577,12 +607,12 @@ __device__ __forceinline__ void tc_body(Src& src) {
 }
 
 
-template <int BN_, bool W32>
+template <int BN_, bool W32, bool SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc(const __grid_constant__ CUtensorMap mapL, const __grid_constant__ CUtensorMap mapR,
                     const __grid_constant__ TcArgs a0) {
   SingleSrc src;
-  if (!tc_run_of<BN_, W32>(a0, src.run, src.gorder)) return;
+  if (!tc_run_of<BN_, W32, SPLIT>(a0, src.run, src.gorder)) return;
   src.mapL = &mapL;
   src.mapR = &mapR;
   src.flags0 = a0.flags;
@@ -590,7 +620,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapL) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapR) : "memory");
   }
-  tc_body<BN_, W32>(src);
+  tc_body<BN_, W32, SPLIT>(src);
 }
 
 // In-place exclusive prefix sum of a[0..count-1] in shared memory, a[count] = the total, by
@@ -635,7 +665,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   for (int m = threadIdx.x; m < count; m += NUM_THREADS) {
     TcRun r;
     const int* g;
-    prefix[m] = tc_run_of<BN_, W32>(probs[m].a, r, g) ? r.units : 0;
+    prefix[m] = tc_run_of<BN_, W32, false>(probs[m].a, r, g) ? r.units : 0;
   }
   __syncthreads();
   block_exclusive_scan(prefix, count, warp_tot);
@@ -649,7 +679,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   src.mapL = src.mapR = nullptr;
   src.flags0 = probs[0].a.flags;
   memset(&src.run, 0, sizeof(src.run));
-  tc_body<BN_, W32>(src);
+  tc_body<BN_, W32, false>(src);
 }
 
 // A wait that nothing completes (no thread ever arrives on the barrier): the bounded wait of
@@ -719,7 +749,7 @@ int sm_count(int& sms) {
   return FRX_OK;
 }
 
-template <int BN, bool W32>
+template <int BN, bool W32, bool SPLIT>
 int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   // tensor maps span the allocated planes (g.d.kL, g.d.kR: the capacity when d comes from the
   // device)
@@ -730,15 +760,24 @@ int launch_variant(const PlaneGemm& g, const TcArgs& a, cudaStream_t s) {
   static PerDevice pd;
   FRX_TRY(once_per_device(pd, [&](int) -> int {
     FRX_CUDA_TRY(
-        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaFuncSetAttribute(k_plane_gemm_tc<BN, W32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
     return FRX_OK;
   }));
   int sms = 0;
   FRX_TRY(sm_count(sms));
-  const int64_t units = a.dyn ? (int64_t)sms : ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups;
+  const int64_t units = a.dyn ? (int64_t)sms
+                              : ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * (int64_t)a.d.groups * a.nsplit;
   const unsigned grid = (unsigned)(units < sms ? units : sms);
   if (grid == 0) return FRX_OK;
-  k_plane_gemm_tc<BN, W32><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
+  if (SPLIT) {
+    // the units add into the group words: start them at zero (groups are ogs apart, each m x n
+    // column-major with leading dimension ldo)
+    for (int q = 0; q < a.d.groups; ++q)
+      FRX_CUDA_TRY(cudaMemset2DAsync(g.out + q * g.ogs, sizeof(i64) * (size_t)g.ldo, 0, sizeof(i64) * (size_t)g.M,
+                                     (size_t)g.N, s));
+  }
+  k_plane_gemm_tc<BN, W32, SPLIT><<<grid, NUM_THREADS, smem, s>>>(mL, mR, a);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
 }
@@ -773,6 +812,8 @@ int tc_problem_fill(const PlaneGemm& g, int* flags, void* host_entry, int tile) 
   e->a.dyn = g.dyn;
   e->a.done = g.done;
   e->a.bn = bn;
+  e->a.nsplit = 1;
+  e->a.kcb = e->a.nkb;
   return FRX_OK;
 }
 
@@ -805,12 +846,43 @@ int launch_plane_gemm_grouped(const void* table, int count, int tile, cudaStream
   return FRX_OK;
 }
 
-// tile: TILE_128x128 or TILE_128x256 for int32 planes (int64 groups always use 128 x 128 tiles)
+// Split-K for int64 Horner groups: every K-chunk's anti-diagonal sums must stay exact in int32
+// (pmax pairs x kcb k-blocks x 64 x 2^14 < 2^31).  The chunk is as long as that allows; when the
+// output leaves SMs idle, more chunks (of at least 8 k-blocks) give them work.
+void split_k_of(const PlaneGemm& g, int nkb, int tiles, int sms, int& nsplit, int& kcb) {
+  int pmax = 1;
+  for (int t = 2; t <= g.d.tmax; ++t) {
+    const int lo = t - g.d.kR > 1 ? t - g.d.kR : 1, hi = g.d.kL < t - 1 ? g.d.kL : t - 1;
+    pmax = hi - lo + 1 > pmax ? hi - lo + 1 : pmax;
+  }
+  const long long kmax = (((1ll << 31) - 1) / ((long long)pmax << PRODUCT_BITS)) / BK;   // k-blocks
+  kcb = (int)(kmax < nkb ? kmax : nkb);
+  nsplit = (nkb + kcb - 1) / kcb;
+  // raise the requested chunk count one at a time (the chunk length only shrinks, so every
+  // chunk stays exact); stop once the units fill the SMs or a chunk would drop below 8 k-blocks
+  const long long base = (long long)tiles * g.d.groups;
+  for (int want = nsplit + 1; base * nsplit < sms; ++want) {
+    const int k2 = (nkb + want - 1) / want;
+    if (k2 < 8) break;
+    kcb = k2;
+    nsplit = (nkb + kcb - 1) / kcb;
+  }
+}
+
+bool split_k_enabled() {
+  const char* env = getenv("FRX_SPLITK");
+  return !(env && env[0] == '0');
+}
+
+// tile: TILE_128x128 or TILE_128x256 for int32 planes.  Int64 groups run split-K on 128 x 256
+// tiles (FRX_SPLITK=0: the int64-register kernel on 128 x 128 tiles).
 int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int tile, cudaStream_t s) {
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
   a.nkb = (int)((g.K + BK - 1) / BK);
+  a.nsplit = 1;
+  a.kcb = a.nkb;
   a.out = (void*)g.out;
   a.ogs = g.ogs;
   a.ldo = g.ldo;
@@ -819,17 +891,26 @@ int launch_plane_gemm_tc(const PlaneGemm& g, int* flags, int tile, cudaStream_t 
   a.dyn = g.dyn;
   a.done = g.done;
   if (!g.d.word32) {
+    if (!g.dyn && split_k_enabled()) {
+      int sms = 0;
+      FRX_TRY(sm_count(sms));
+      const int tiles = (int)(((g.M + BM - 1) / BM) * ((g.N + 255) / 256));
+      split_k_of(g, a.nkb, tiles, sms, a.nsplit, a.kcb);
+      a.bn = 256;
+      last_tile() = TILE_128x256;
+      return launch_variant<256, true, true>(g, a, s);
+    }
     a.bn = 128;
     last_tile() = TILE_128x128;
-    return launch_variant<128, false>(g, a, s);
+    return launch_variant<128, false, false>(g, a, s);
   }
   last_tile() = tile;
   a.bn = tile_bn(tile);
   switch (tile) {
     case TILE_128x128:
-      return launch_variant<128, true>(g, a, s);
+      return launch_variant<128, true, false>(g, a, s);
     case TILE_128x256:
-      return launch_variant<256, true>(g, a, s);
+      return launch_variant<256, true, false>(g, a, s);
     default:
       return FRX_E_UNSUPPORTED;
   }

@@ -94,3 +94,30 @@ def test_ozaki_gemm_tensor_core_equals_cuda_core(api, m, k, n, slices, mode):
         else:
             os.environ["FRX_GEMM"] = old
     assert torch.equal(ch0, ch1) and torch.equal(cl0, cl1)
+
+
+@pytest.mark.parametrize("m,K,n,k,mode", [(300, 65536, 260, 8, "full"),     # 4 exact chunks of 16384
+                                          (200, 30000, 130, 6, "triangular"),   # few tiles: more chunks
+                                          (129, 65536, 257, 16, "full")])       # 16 planes, ragged
+def test_split_k_matches_the_int64_register_kernel(api, m, K, n, k, mode):
+    # long inner dimensions make the anti-diagonal sums exceed int32: split-K (int32 chunks added
+    # to int64 Horner groups by atomics) and the int64-register kernel give the same bits
+    import torch
+    from tests import gpu_util as g
+    A = g.to_dev(synth.gemm_operand(m, K, 1.0, 800 + m))
+    B = g.to_dev(synth.gemm_operand(K, n, 1.0, 801 + n))
+    out = {}
+    old = os.environ.get("FRX_SPLITK")
+    try:
+        for flag in ("1", "0"):
+            os.environ["FRX_SPLITK"] = flag
+            Ch, Cl = api.ozaki_gemm(A, B, k, mode, return_lo=True)
+            torch.cuda.synchronize()
+            out[flag] = (Ch.cpu().numpy(), Cl.cpu().numpy(), api.last_tile())
+    finally:
+        if old is None:
+            os.environ.pop("FRX_SPLITK", None)
+        else:
+            os.environ["FRX_SPLITK"] = old
+    assert out["1"][2] == "128x256" and out["0"][2] == "128x128"
+    assert np.array_equal(out["1"][0], out["0"][0]) and np.array_equal(out["1"][1], out["0"][1])
