@@ -73,12 +73,12 @@ def parse():
                    help="skip the exact-truth companion run that measures the forward error")
     p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64 comparator")
     p.add_argument("--no-gemm", action="store_true", help="skip the stand-alone Ozaki GEMM figures")
-    p.add_argument("--workload", choices=["refine", "batched", "configs", "figures", "previous", "gemm"],
+    p.add_argument("--workload", choices=["refine", "batched", "configs", "figures", "previous", "gemm", "sparse"],
                    default="refine",
                    help="refine: one n=4096 refinement per step; batched: 256 matrices, n in [32, 512]; "
                         "configs: the n=2048 variants and the n=8192 forward-error sweep; figures: the "
                         "paper's convergence-figure settings with measured forward errors ('previous' is "
-                        "an alias); gemm: the ozaki_gemm sweep")
+                        "an alias); gemm: the ozaki_gemm sweep; sparse: the sparse rule with V over A's nonzeros")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--sweep-n", default="1024,4096,8192", help="matrix orders of the ozaki_gemm sweep")
     p.add_argument("--tile", default="auto", choices=["auto", "128x128", "128x256"],
@@ -428,7 +428,7 @@ def run_ours(args):
         # delta = 1e-16 (independent of the frx kernels; checked against the CPU oracle's
         # double-double eigenvectors by a GPU test) ...
         from paper_2602_19090_gb300 import fp64_refine
-        T, _, it = fp64_refine.refine(At, X0t, D0t, 1e-16, max_iter=8)
+        T, _, it = fp64_refine.refine(At, X0t, D0t, 1e-16, max_iter=8, xi=0.0)
         X.copy_(X0t)
         D.copy_(D0t)
         ih = api.refine(At, X, D, delta, opts, work=work)
@@ -436,8 +436,8 @@ def run_ours(args):
         line["forward_error"] = {
             "value": feh["two"], "norm": "2-norm (power iteration), columns sign-aligned", "fro": feh["fro"],
             "delta": delta, "ratio_to_delta": feh["two"] / delta, "status": ih["status_name"],
-            "reference": (f"native-FP64 comparator iterated to delta = 1e-16 ({it['status']}, {it['iters']} "
-                          f"iterations, est {it['err_est']:.2e})"),
+            "reference": (f"native-FP64 comparator (Sec. 4.1 xi = n) iterated to delta = 1e-16 ({it['status']}, "
+                          f"{it['iters']} iterations, est {it['err_est']:.2e})"),
             # ... and an exact-truth matrix of the same order and condition
             "exact_truth_companion": truth_companion(api, synth, dev, n, args.cond, delta, opts)}
         del T
@@ -788,7 +788,8 @@ def run_figures(args):
                    of the earlier method that slices both operands;
       fp64         the native-FP64 comparator (cuBLAS DGEMM, the paper's FP64 slicing), xi = 1.
     Each arm: status, iterations, slice products, time and the measured forward error
-    ||X - X^||_2 against a reference X: the native-FP64 comparator iterated to delta = 1e-16 (an
+    ||X - X^||_2 against a reference X: the native-FP64 comparator in its Sec. 4.1 form (xi = n)
+    iterated to delta = 1e-16 (an
     implementation independent of the frx kernels; its agreement with the CPU oracle's
     double-double eigenvectors is a GPU test).  Then the exact-truth rotated-Hadamard matrix
     (n = 4096, cond 1e10), whose eigenvectors are known exactly."""
@@ -815,7 +816,7 @@ def run_figures(args):
         A, X0, D0, lam = synth.refine_workload(n, 1e10, "spd", case=600 + n % 97)
         At, X0t, D0t = dev_inputs(A, X0, D0)
         del A, X0
-        T, _, it = fp64_refine.refine(At, X0t, D0t, 1e-16, max_iter=8)
+        T, _, it = fp64_refine.refine(At, X0t, D0t, 1e-16, max_iter=8, xi=0.0)
         work = api.workspace(api.refine_workspace_bytes(n), dev)
         for delta in (1e-8, 1e-10, 1e-12):
             rec = {"n": n, "delta": delta, "reference": {"status": it["status"], "iters": it["iters"],
@@ -842,6 +843,45 @@ def run_figures(args):
             rec[name] = arm_record(ms, info, X, Qht, Qlt)
         out["exact_truth_rotated_n4096_cond1e10"].append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
+def run_sparse(args):
+    """The sparse-matrix setting of Sec. 4 (sparse_rule): stand-ins for the paper's ELSES and
+    SuiteSparse matrices (not in the container) - a band matrix (k = 5 nonzeros per row) and a
+    symmetric matrix with about 16 nonzeros per row at random positions, n = 4096, delta = 1e-12.
+    Each is refined with V = A X^(1) over A's nonzeros and with the dense tensor-core V product
+    (FRX_SPARSE_V=0), which must give identical bits; times are CUDA events (best of 3)."""
+    import numpy as np
+    import torch
+
+    from paper_2602_19090_gb300 import api, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    out = {"metric": "sparse_rule", "cases": []}
+    n, delta = args.n, 1e-12
+    work = api.workspace(api.refine_workspace_bytes(n), dev)
+    cases = (("band, k = 5", synth.banded_workload(n, 2, 31)),
+             ("random pattern, ~16 per row", synth.random_sparse_workload(n, 16, 32)))
+    for name, (A, X0, D0, lam) in cases:
+        At = torch.from_numpy(A).to(dev)
+        X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
+        D0t = torch.from_numpy(D0).to(dev)
+        rec = {"case": name, "n": n, "max_row_nonzeros": int(np.max(np.count_nonzero(A, axis=1))), "delta": delta}
+        Xs = {}
+        for flag, key in (("1", "sparse_v"), ("0", "dense_v")):
+            os.environ["FRX_SPARSE_V"] = flag
+            ms, info, X = _timed_refine(api, At, X0t, D0t, delta, api.Options(sparse_rule=True), work, reps=3)
+            Xs[key] = X
+            rec[key] = {"ms": ms, "status": info["status_name"], "iters": info["iters"], "products": info["products"],
+                        "k_V": info["k_V"], "s_X": info["s_X"], "err_est": info["err_est"]}
+        os.environ.pop("FRX_SPARSE_V", None)
+        rec["identical_X"] = bool(torch.equal(Xs["sparse_v"], Xs["dense_v"]))
+        rec["speedup"] = rec["dense_v"]["ms"] / rec["sparse_v"]["ms"]
+        out["cases"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+        del At, X0t, D0t, Xs
     print(json.dumps(out), flush=True)
 
 
@@ -966,6 +1006,8 @@ def main():
         run_figures(args)
     elif args.workload == "gemm":
         run_gemm_sweep(args)
+    elif args.workload == "sparse":
+        run_sparse(args)
     else:
         run_ours(args)
 

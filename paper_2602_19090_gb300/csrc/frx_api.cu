@@ -49,9 +49,11 @@ struct RefineWs {
   double *X1, *Res, *E;
   __nv_bfloat16 *Ap, *Xp, *Rp, *X1rp;
   i64* groups;
+  int32_t* ell;    // nonzero columns of A's rows (sparse V product), ELL_MAX per row
   int64_t pitch, ps;
   size_t bytes;
   int tile;        // tile configuration of the slice products (set by the autotuner)
+  int sparse_v;    // 1: V = A X^(1) over A's nonzeros (sparse_rule and a sparse A)
 };
 
 RefineWs carve_refine(void* work, int64_t n, int kcap) {
@@ -79,8 +81,10 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   w.Rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
   w.X1rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
   w.groups = c.take<i64>((size_t)8 * n * n);   // 64 bytes per entry: 8 int64 groups or 16 int32 planes
+  w.ell = c.take<int32_t>((size_t)ELL_MAX * n);
   w.bytes = c.off + 256;
   w.tile = TILE_128x256;
+  w.sparse_v = 0;
   return w;
 }
 
@@ -163,6 +167,12 @@ struct DebugOut {
   double *X1, *Vh, *Vl, *Res, *W, *E, *r;
 };
 
+// FRX_SPARSE_V=0 keeps the dense V product under the sparse rule (for cross-checks)
+bool sparse_v_enabled() {
+  const char* env = getenv("FRX_SPARSE_V");
+  return !(env && env[0] == '0');
+}
+
 int validate_opts(const frx_opts& o) {
   if (o.k_cap < 1 || o.k_cap > MAX_PLANES || o.max_iter < 1 || o.slices_A < 0 || o.slices_A > o.k_cap)
     return FRX_E_ARG;
@@ -240,7 +250,10 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   FRX_TRY(launch_truncate_slice_x(X, ldx, n, ws.f, 0, 0, ws.X1, n, ws.Xp, ws.ps, ws.pitch, s, dx));
   // S5/S6: V = A X^(1), pairs r + s <= k_V + 1
   PlaneGemm gv = dyn_gemm(ws.Ap, kcap, ws.Xp, 8, ws, n, &P->V);
-  FRX_TRY(launch_plane_gemm(gv, s));
+  if (ws.sparse_v)
+    FRX_TRY(launch_sparse_v(ws.Ap, ws.Xp, ws.ps, ws.pitch, ws.ell, n, &P->V, done, flags, gv.out32(), gv.ogs, s));
+  else
+    FRX_TRY(launch_plane_gemm(gv, s));
   // S7/S8: r, lambda, Res (lines 2-4)
   ResidualArgs ra;
   ra.n = n;
@@ -335,6 +348,7 @@ int ensure_attributes() {
   return once_per_device(pd, [](int) {
     int st = set_refine_kernel_attributes();
     if (st == FRX_OK) st = set_plan_kernel_attributes();
+    if (st == FRX_OK) st = set_sparse_v_attributes();
     if (st == FRX_OK) st = prepare_plane_gemm_grouped();
     return st;
   });
@@ -370,6 +384,17 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
       FRX_TRY(plan_plane_gemm(rep));
       FRX_TRY(tune_tile_refine(rep, s, ws.tile));
       FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s, nullptr, &ws.plan->rownnz));
+      if (o.sparse_rule && sparse_v_enabled()) {
+        // the sparse-matrix setting: V over A's nonzeros when every row holds at most ELL_MAX of
+        // them and they are a sixteenth of the row or fewer (one read of the count)
+        int nz = 0;
+        FRX_CUDA_TRY(cudaMemcpyAsync(&nz, &ws.plan->rownnz, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FRX_CUDA_TRY(cudaStreamSynchronize(s));
+        if (nz >= 1 && nz <= ELL_MAX && (int64_t)nz * 16 <= n) {
+          FRX_TRY(launch_build_ell(A, lda, n, ws.ell, s));
+          ws.sparse_v = 1;
+        }
+      }
       FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));
       for (int it = 1; it <= max_iter; ++it) {
         FRX_TRY(enqueue_iteration(A, lda, X, ldx, n, o, po, ws, dbg, s));

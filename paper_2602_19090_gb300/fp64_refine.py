@@ -112,7 +112,11 @@ def step(A, X, lam_prev, delta, xi=1.0):
     eA = int(_ceil_log2(A.abs().amax(dim=1)).max())
     kV = _slices_for(n, eA, int(f.max()), delta * g)
     bits = 53 - alpha
-    nA = max(2, 1 + math.ceil((8 * kV - 53) / max(bits, 1)))
+    if bits < 1:
+        # alpha >= 53 leaves the FP64 slices of eq. sigma no bits: the slicing cannot represent
+        # this target (happens for tiny delta with xi = 1; the xi = n form keeps alpha lower)
+        raise ValueError(f"fp64 comparator: alpha = {alpha} >= 53 (beta = {beta}); use xi = 0 for this delta")
+    nA = max(2, 1 + math.ceil((8 * kV - 53) / bits))
     # V = sum_r fl(A^(r) X1) (eq. mat_mul), accumulated in double-double
     res = A.clone()
     Vh = torch.zeros_like(X)

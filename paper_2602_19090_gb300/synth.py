@@ -311,3 +311,21 @@ def banded_workload(n: int, bw: int, seed: int, rel: float = 1e-8):
     lam, Q = np.linalg.eigh(A)
     X0, D0 = initial_guess(Q, lam, seed, rel)
     return np.ascontiguousarray(A), X0, D0, lam
+
+
+def random_sparse_workload(n: int, per_row: int, seed: int, rel: float = 1e-8):
+    """Sparse stand-in with an irregular pattern: a symmetric matrix whose row i holds
+    per_row / 2 entries N(0, 1) at seeded random columns, mirrored (about per_row nonzeros per
+    row), and a diagonal N(0, 1) + 4.  The start is its FP64 eigenvector basis (numpy eigh)
+    perturbed by `rel` and re-orthonormalised.  Returns (A, X0, D0, lam)."""
+    g = rng(seed)
+    A = np.zeros((n, n))
+    for i in range(n):
+        cols = g.choice(n, per_row // 2, replace=False)
+        v = g.standard_normal(cols.size)
+        A[i, cols] = v
+        A[cols, i] = v
+    A[np.arange(n), np.arange(n)] = g.standard_normal(n) + 4.0
+    lam, Q = np.linalg.eigh(A)
+    X0, D0 = initial_guess(Q, lam, seed, rel)
+    return np.ascontiguousarray(A), X0, D0, lam

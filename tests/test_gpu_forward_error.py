@@ -3,8 +3,9 @@
 * Exact-truth matrices (rotated Hadamard eigenvectors, not FP64 numbers, geometric spectrum)
   at n = 2048, cond 1e4 and 1e10, delta = 1e-14: ||X - X^||_2 <= delta, with the iteration
   and product counts of the CPU oracle on the same inputs.
-* The reference X that bench.py uses for randsvd-like matrices (the native-FP64 comparator
-  iterated to delta = 1e-16) agrees with the oracle's double-double eigenvectors.
+* The reference X that bench.py uses for randsvd-like matrices (the native-FP64 comparator in
+  its Sec. 4.1 form, iterated to delta = 1e-16) agrees with the oracle's double-double
+  eigenvectors.
 """
 import numpy as np
 import pytest
@@ -57,6 +58,6 @@ def test_fp64_reference_matches_the_oracle_truth(api):
     Xh, Xl, _, _ = tr.eigvecs_dd(A, X0)
     dev = torch.device("cuda", 0)
     T, _, it = fp64_refine.refine(torch.from_numpy(A).to(dev), torch.from_numpy(X0).to(dev),
-                                  torch.from_numpy(D0).to(dev), 1e-16, max_iter=8)
+                                  torch.from_numpy(D0).to(dev), 1e-16, max_iter=8, xi=0.0)
     assert it["status"] == "converged"
     assert tr.forward_error(Xh, Xl, T.cpu().numpy()) <= 1e-15

@@ -328,3 +328,38 @@ def test_refine_batched_more_problems_than_one_grouped_launch(api):
         ref = api.refine(As[b], Xs, Ds, 1e-12)
         assert infos[b]["iters"] == ref["iters"] and infos[b]["products"] == ref["products"]
         assert np.array_equal(Xb[b].cpu().numpy(), Xs.cpu().numpy())
+
+
+@pytest.mark.parametrize("kind", ["banded", "random"])
+def test_sparse_v_product_matches_the_dense_one(api, kind):
+    # under the sparse rule, V = A X^(1) over A's nonzeros gives the tensor-core product's exact
+    # sums bit for bit: the whole refinement returns identical X, D and report
+    import os
+    g = G()
+    if kind == "banded":
+        A, X0, D0, lam = synth.banded_workload(1024, 3, 21)
+    else:
+        A, X0, D0, lam = synth.random_sparse_workload(768, 12, 22)
+    assert int(np.max(np.count_nonzero(A, axis=1))) * 16 <= A.shape[0]
+    res = {}
+    old = os.environ.get("FRX_SPARSE_V")
+    try:
+        for flag in ("1", "0"):
+            os.environ["FRX_SPARSE_V"] = flag
+            X, D = g.to_dev(X0), g.to_dev(D0)
+            info = api.refine(g.to_dev(A), X, D, 1e-12, api.Options(sparse_rule=True))
+            res[flag] = (X.cpu().numpy(), D.cpu().numpy(), info)
+    finally:
+        if old is None:
+            os.environ.pop("FRX_SPARSE_V", None)
+        else:
+            os.environ["FRX_SPARSE_V"] = old
+    assert res["1"][2]["status"] == 0
+    assert np.array_equal(res["1"][0], res["0"][0]) and np.array_equal(res["1"][1], res["0"][1])
+    for key in ("iters", "products", "err_est", "step", "beta", "k_V"):
+        assert res["1"][2][key] == res["0"][2][key]
+
+
+def test_sparse_v_step_matches_the_oracle_on_a_random_pattern(api):
+    A, X0, D0, lam = synth.random_sparse_workload(400, 10, 23)
+    _step_compare(api, A, X0, D0, 1e-12, orf.Options(sparse_rule=True), api.Options(sparse_rule=True))

@@ -88,3 +88,13 @@ def test_generators_are_deterministic_per_seed():
     s2, c2 = synth.batched_sizes(64, case=1)
     assert np.array_equal(s1, s2) and np.array_equal(c1, c2)
     assert s1.min() >= 32 and s1.max() <= 512
+
+
+def test_random_sparse_workload_is_symmetric_sparse_and_seeded():
+    A, X0, D0, lam = synth.random_sparse_workload(200, 8, 5)
+    assert np.array_equal(A, A.T)
+    nnz = np.count_nonzero(A, axis=1)
+    assert nnz.min() >= 5 and nnz.max() <= 20
+    assert np.allclose(X0.T @ X0, np.eye(200), atol=1e-13)
+    B = synth.random_sparse_workload(200, 8, 5)[0]
+    assert np.array_equal(A, B)
