@@ -848,10 +848,11 @@ def run_figures(args):
 
 def run_sparse(args):
     """The sparse-matrix setting of Sec. 4 (sparse_rule): stand-ins for the paper's ELSES and
-    SuiteSparse matrices (not in the container) - a band matrix (k = 5 nonzeros per row) and a
-    symmetric matrix with about 16 nonzeros per row at random positions, n = 4096, delta = 1e-12.
-    Each is refined with V = A X^(1) over A's nonzeros and with the dense tensor-core V product
-    (FRX_SPARSE_V=0), which must give identical bits; times are CUDA events (best of 3)."""
+    SuiteSparse matrices (not in the container) - a band matrix (k = 5 nonzeros per row) and
+    symmetric matrices with about 8 and 16 nonzeros per row at random positions, n = 4096,
+    delta = 1e-12. Each is refined with V = A X^(1) over A's nonzeros (FRX_SPARSE_V=1), with the
+    dense tensor-core V product (FRX_SPARSE_V=0) - identical bits required - and with the
+    library's automatic choice (sparse when nnz * 256 <= n); CUDA-event times, best of 3."""
     import numpy as np
     import torch
 
@@ -862,23 +863,30 @@ def run_sparse(args):
     out = {"metric": "sparse_rule", "cases": []}
     n, delta = args.n, 1e-12
     work = api.workspace(api.refine_workspace_bytes(n), dev)
-    cases = (("band, k = 5", synth.banded_workload(n, 2, 31)),
-             ("random pattern, ~16 per row", synth.random_sparse_workload(n, 16, 32)))
-    for name, (A, X0, D0, lam) in cases:
+    cases = (("band, k = 5", lambda: synth.banded_workload(n, 2, 31)),
+             ("random pattern, ~8 per row", lambda: synth.random_sparse_workload(n, 8, 33)),
+             ("random pattern, ~16 per row", lambda: synth.random_sparse_workload(n, 16, 32)))
+    for name, make in cases:
+        A, X0, D0, lam = make()
         At = torch.from_numpy(A).to(dev)
         X0t = api.colmajor(torch.from_numpy(X0).to(dev))[0]
         D0t = torch.from_numpy(D0).to(dev)
-        rec = {"case": name, "n": n, "max_row_nonzeros": int(np.max(np.count_nonzero(A, axis=1))), "delta": delta}
+        nnz = int(np.max(np.count_nonzero(A, axis=1)))
+        rec = {"case": name, "n": n, "max_row_nonzeros": nnz, "delta": delta,
+               "auto_choice": "sparse" if nnz * 256 <= n else "dense"}
         Xs = {}
-        for flag, key in (("1", "sparse_v"), ("0", "dense_v")):
-            os.environ["FRX_SPARSE_V"] = flag
+        for flag, key in (("1", "sparse_v"), ("0", "dense_v"), (None, "auto")):
+            if flag is None:
+                os.environ.pop("FRX_SPARSE_V", None)
+            else:
+                os.environ["FRX_SPARSE_V"] = flag
             ms, info, X = _timed_refine(api, At, X0t, D0t, delta, api.Options(sparse_rule=True), work, reps=3)
             Xs[key] = X
             rec[key] = {"ms": ms, "status": info["status_name"], "iters": info["iters"], "products": info["products"],
                         "k_V": info["k_V"], "s_X": info["s_X"], "err_est": info["err_est"]}
         os.environ.pop("FRX_SPARSE_V", None)
-        rec["identical_X"] = bool(torch.equal(Xs["sparse_v"], Xs["dense_v"]))
-        rec["speedup"] = rec["dense_v"]["ms"] / rec["sparse_v"]["ms"]
+        rec["identical_X"] = bool(torch.equal(Xs["sparse_v"], Xs["dense_v"]) and torch.equal(Xs["auto"], Xs["dense_v"]))
+        rec["speedup_sparse_over_dense"] = rec["dense_v"]["ms"] / rec["sparse_v"]["ms"]
         out["cases"].append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
         del At, X0t, D0t, Xs

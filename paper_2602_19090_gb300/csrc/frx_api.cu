@@ -167,10 +167,16 @@ struct DebugOut {
   double *X1, *Vh, *Vl, *Res, *W, *E, *r;
 };
 
-// FRX_SPARSE_V=0 keeps the dense V product under the sparse rule (for cross-checks)
-bool sparse_v_enabled() {
+// Choice of the V product under the sparse rule: FRX_SPARSE_V=0 keeps the dense product,
+// FRX_SPARSE_V=1 takes the sparse one whenever the pattern fits the ELL layout (cross-checks and
+// measurements), otherwise the sparse one is taken when its CUDA-core work (nnz per row) stays
+// well below the dense tensor-core work (n per row): nnz * 256 <= n, the measured crossover with
+// a margin.
+int sparse_v_mode() {
   const char* env = getenv("FRX_SPARSE_V");
-  return !(env && env[0] == '0');
+  if (env && env[0] == '0') return 0;
+  if (env && env[0] == '1') return 2;
+  return 1;
 }
 
 int validate_opts(const frx_opts& o) {
@@ -384,13 +390,14 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
       FRX_TRY(plan_plane_gemm(rep));
       FRX_TRY(tune_tile_refine(rep, s, ws.tile));
       FRX_TRY(launch_col_exponents(A, lda, n, n, ws.eA, &ws.plan->flags, s, nullptr, &ws.plan->rownnz));
-      if (o.sparse_rule && sparse_v_enabled()) {
+      const int svm = o.sparse_rule ? sparse_v_mode() : 0;
+      if (svm) {
         // the sparse-matrix setting: V over A's nonzeros when every row holds at most ELL_MAX of
-        // them and they are a sixteenth of the row or fewer (one read of the count)
+        // them and (unless forced) nnz * 256 <= n (one read of the count)
         int nz = 0;
         FRX_CUDA_TRY(cudaMemcpyAsync(&nz, &ws.plan->rownnz, sizeof(int), cudaMemcpyDeviceToHost, s));
         FRX_CUDA_TRY(cudaStreamSynchronize(s));
-        if (nz >= 1 && nz <= ELL_MAX && (int64_t)nz * 16 <= n) {
+        if (nz >= 1 && nz <= ELL_MAX && (svm == 2 || (int64_t)nz * 256 <= n)) {
           FRX_TRY(launch_build_ell(A, lda, n, ws.ell, s));
           ws.sparse_v = 1;
         }

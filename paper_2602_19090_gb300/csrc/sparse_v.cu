@@ -93,16 +93,22 @@ __global__ void __launch_bounds__(SPV_ROWS * SPV_COLS) k_sparse_v(SparseVArgs a)
     const unsigned short* xj = a.Xp + j * a.pitch;
     for (int q = 0; q < nnz; ++q) {
       const int l = sidx[q * SPV_ROWS + tx];
+      // the loops are unrolled (S, xs stay in registers) and left at the plan's k_V, s_X and
+      // pair bound by warp-uniform breaks, so only the pairs of the product are executed
       int xs[SPV_MAXR];
 #pragma unroll
-      for (int s = 0; s < SPV_MAXR; ++s) xs[s] = s < sX ? bf16_digit(xj[s * a.ps + l]) : 0;
+      for (int s = 0; s < SPV_MAXR; ++s) {
+        if (s >= sX) break;
+        xs[s] = bf16_digit(xj[s * a.ps + l]);
+      }
 #pragma unroll
       for (int r = 0; r < SPV_MAXL; ++r) {
-        if (r < kV) {
-          const int ar = sa[(q * SPV_MAXL + r) * SPV_ROWS + tx];
+        if (r >= kV) break;
+        const int ar = sa[(q * SPV_MAXL + r) * SPV_ROWS + tx];
 #pragma unroll
-          for (int s = 0; s < SPV_MAXR; ++s)
-            if (r + s + 2 <= T) S[r + s] += ar * xs[s];   // (r + 1) + (s + 1) = t <= T
+        for (int s = 0; s < SPV_MAXR; ++s) {
+          if (s >= sX || r + s + 2 > T) break;   // (r + 1) + (s + 1) = t <= T
+          S[r + s] += ar * xs[s];
         }
       }
     }
