@@ -858,6 +858,7 @@ void split_k_of(const PlaneGemm& g, int nkb, int tiles, int sms, int& nsplit, in
   const long long kmax = (((1ll << 31) - 1) / ((long long)pmax << PRODUCT_BITS)) / BK;   // k-blocks
   kcb = (int)(kmax < nkb ? kmax : nkb);
   nsplit = (nkb + kcb - 1) / kcb;
+  kcb = (nkb + nsplit - 1) / nsplit;   // the same count of chunks, balanced (kcb only shrinks)
   // raise the requested chunk count one at a time (the chunk length only shrinks, so every
   // chunk stays exact); stop once the units fill the SMs or a chunk would drop below 8 k-blocks
   const long long base = (long long)tiles * g.d.groups;

@@ -7,7 +7,8 @@ It is not part of the frx product path and shares no code with it.
 Per iteration (Algorithm 1 with Sec. 3 and the Sec. 4.1 parameters):
   beta, alpha  eq. proposed_beta with floor rounding and ceil(log2 sqrt n) (Sec. 4.1), the
                error model's xi as in the frx plan (1 by default; xi <= 0: n, the
-               "n delta" of the Sec. 4.1 experiments), from the previous estimates;
+               "n delta" of the Sec. 4.1 experiments), from the previous estimates; beta is
+               raised where needed so that alpha <= 52 (every FP64 slice keeps a bit);
   X1           fl((tau_j + x) - tau_j) (eq. tau, eq. x);
   A slices     eq. sigma / eq. a with alpha and a rescan of the residual's row maxima,
                n_A - 1 slices plus the remainder (eq. mat_mul);
@@ -106,16 +107,15 @@ def step(A, X, lam_prev, delta, xi=1.0):
     xi = xi if xi > 0 else float(n)
     q = math.sqrt((xi * delta * g) / (Lam * S2)) / (0.75 * U)
     beta = min(max(math.frexp(q)[1] - 1, 3), 47)
+    # the FP64 slices of eq. sigma carry 53 - alpha bits: keep at least one (alpha <= 52) by
+    # raising beta where a tight target and small gaps would push alpha to 53 or beyond
+    beta = max(beta, _ceil_log2_sqrt(n) + 1)
     alpha = 53 - beta + _ceil_log2_sqrt(n)
     tau = 0.75 * _pow2(f + beta)
     X1 = (tau[None, :] + X) - tau[None, :]
     eA = int(_ceil_log2(A.abs().amax(dim=1)).max())
     kV = _slices_for(n, eA, int(f.max()), delta * g)
     bits = 53 - alpha
-    if bits < 1:
-        # alpha >= 53 leaves the FP64 slices of eq. sigma no bits: the slicing cannot represent
-        # this target (happens for tiny delta with xi = 1; the xi = n form keeps alpha lower)
-        raise ValueError(f"fp64 comparator: alpha = {alpha} >= 53 (beta = {beta}); use xi = 0 for this delta")
     nA = max(2, 1 + math.ceil((8 * kV - 53) / bits))
     # V = sum_r fl(A^(r) X1) (eq. mat_mul), accumulated in double-double
     res = A.clone()
