@@ -852,7 +852,7 @@ def run_sparse(args):
     symmetric matrices with about 8 and 16 nonzeros per row at random positions, n = 4096,
     delta = 1e-12. Each is refined with V = A X^(1) over A's nonzeros (FRX_SPARSE_V=1), with the
     dense tensor-core V product (FRX_SPARSE_V=0) - identical bits required - and with the
-    library's automatic choice (sparse when nnz * 256 <= n); CUDA-event times, best of 3."""
+    library's automatic choice (sparse when nnz * 160 <= n); CUDA-event times, best of 3."""
     import numpy as np
     import torch
 
@@ -873,7 +873,7 @@ def run_sparse(args):
         D0t = torch.from_numpy(D0).to(dev)
         nnz = int(np.max(np.count_nonzero(A, axis=1)))
         rec = {"case": name, "n": n, "max_row_nonzeros": nnz, "delta": delta,
-               "auto_choice": "sparse" if nnz * 256 <= n else "dense"}
+               "auto_choice": "sparse" if nnz * 160 <= n else "dense"}
         Xs = {}
         for flag, key in (("1", "sparse_v"), ("0", "dense_v"), (None, "auto")):
             if flag is None:

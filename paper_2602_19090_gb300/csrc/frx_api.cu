@@ -53,7 +53,7 @@ struct RefineWs {
   int64_t pitch, ps;
   size_t bytes;
   int tile;        // tile configuration of the slice products (set by the autotuner)
-  int sparse_v;    // 1: V = A X^(1) over A's nonzeros (sparse_rule and a sparse A)
+  int sparse_v;    // > 0: V = A X^(1) over A's nonzeros, at most sparse_v of them per row
 };
 
 RefineWs carve_refine(void* work, int64_t n, int kcap) {
@@ -170,8 +170,8 @@ struct DebugOut {
 // Choice of the V product under the sparse rule: FRX_SPARSE_V=0 keeps the dense product,
 // FRX_SPARSE_V=1 takes the sparse one whenever the pattern fits the ELL layout (cross-checks and
 // measurements), otherwise the sparse one is taken when its CUDA-core work (nnz per row) stays
-// well below the dense tensor-core work (n per row): nnz * 256 <= n, the measured crossover with
-// a margin.
+// below the dense tensor-core work (n per row): nnz * 160 <= n.  Measured on GB300 at n = 2048
+// and 4096, the two take equal time near nnz * 136 = n; the factor 160 keeps a margin.
 int sparse_v_mode() {
   const char* env = getenv("FRX_SPARSE_V");
   if (env && env[0] == '0') return 0;
@@ -257,7 +257,8 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   // S5/S6: V = A X^(1), pairs r + s <= k_V + 1
   PlaneGemm gv = dyn_gemm(ws.Ap, kcap, ws.Xp, 8, ws, n, &P->V);
   if (ws.sparse_v)
-    FRX_TRY(launch_sparse_v(ws.Ap, ws.Xp, ws.ps, ws.pitch, ws.ell, n, &P->V, done, flags, gv.out32(), gv.ogs, s));
+    FRX_TRY(launch_sparse_v(ws.Ap, ws.Xp, ws.ps, ws.pitch, ws.ell, ws.sparse_v, n, &P->V, done, flags, gv.out32(),
+                            gv.ogs, s));
   else
     FRX_TRY(launch_plane_gemm(gv, s));
   // S7/S8: r, lambda, Res (lines 2-4)
@@ -393,13 +394,13 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
       const int svm = o.sparse_rule ? sparse_v_mode() : 0;
       if (svm) {
         // the sparse-matrix setting: V over A's nonzeros when every row holds at most ELL_MAX of
-        // them and (unless forced) nnz * 256 <= n (one read of the count)
+        // them and (unless forced) nnz * 160 <= n (one read of the count)
         int nz = 0;
         FRX_CUDA_TRY(cudaMemcpyAsync(&nz, &ws.plan->rownnz, sizeof(int), cudaMemcpyDeviceToHost, s));
         FRX_CUDA_TRY(cudaStreamSynchronize(s));
-        if (nz >= 1 && nz <= ELL_MAX && (svm == 2 || (int64_t)nz * 256 <= n)) {
+        if (nz >= 1 && nz <= ELL_MAX && (svm == 2 || (int64_t)nz * 160 <= n)) {
           FRX_TRY(launch_build_ell(A, lda, n, ws.ell, s));
-          ws.sparse_v = 1;
+          ws.sparse_v = nz;
         }
       }
       FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));

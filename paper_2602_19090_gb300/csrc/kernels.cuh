@@ -90,8 +90,8 @@ constexpr int ELL_MAX = 64;
 int launch_build_ell(const double* A, int64_t lda, int64_t n, int32_t* ell, cudaStream_t s);
 int set_sparse_v_attributes();
 int launch_sparse_v(const __nv_bfloat16* Ap, const __nv_bfloat16* Xp, int64_t ps, int64_t pitch, const int32_t* ell,
-                    int64_t n, const GemmDesc* dV, const int* done, int* flags, int32_t* out, int64_t ogs,
-                    cudaStream_t s);
+                    int nzcap, int64_t n, const GemmDesc* dV, const int* done, int* flags, int32_t* out,
+                    int64_t ogs, cudaStream_t s);
 
 // gemm_simt.cu / gemm_tc.cu
 int launch_plane_gemm(const PlaneGemm& g, cudaStream_t s);
