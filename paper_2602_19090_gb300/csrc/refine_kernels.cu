@@ -495,10 +495,23 @@ __device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
 }
 
 // Integer fast path of lines 2-4 for int32 planes (at most 16) that combine exactly in 128
-// bits.  Pass 1 forms each V entry N_i 2^(c_i) (kept in shared memory), x^T x exactly and a
-// bound 2^T on the terms of x^T v; pass 2 accumulates x^T v on the fixed grid 2^(T + log2 n
-// - 126) (every term truncated once: relative error below 2^(2 log2 n - 126) of the largest
-// term); pass 3 rounds Res = V - x lambda once from its exact integer value.
+// bits.  One pass over the rows forms each V entry N_i 2^(c_i) (kept in shared memory), x^T x
+// exactly, and x^T v on a fixed grid: each warp keeps an anchor T_w, the largest bound 2^T_w on
+// its terms so far, and accumulates every term truncated once on the grid 2^(T_w + log2 n - 126)
+// (when T_w grows, the partial sums move to the coarser grid, truncated once more).  With T the
+// final largest bound, the sum's error stays below 2^(T + 2 log2 n - 125), and every partial sum
+// fits 128 bits.  A second pass rounds Res = V - x lambda once from its exact integer value.
+__device__ __forceinline__ i128 shift_down(i128 v, int d) { return d >= 127 ? (i128)0 : (v >> d); }
+
+// debug copies of V = N 2^ex as double-doubles
+__device__ __noinline__ void write_v_copies(const ResidualArgs& a, i128 N, int ex, int64_t at) {
+  const double h = i128_to_double_rn(N), l = i128_to_double_rn(N - double_to_i128(h));
+  const dd vd = (ex >= -1022 + 130 && ex <= 1023 - 130) ? dd{__dmul_rn(h, pow2(ex)), __dmul_rn(l, pow2(ex))}
+                                                        : dd{ldexp(h, ex), ldexp(l, ex)};
+  if (a.Vh) a.Vh[at] = vd.h;
+  if (a.Vl) a.Vl[at] = vd.l;
+}
+
 __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsigned) {
   if (a.done && *a.done) return;
   a.V = resolve(a.V);
@@ -520,52 +533,53 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   const int cbase = fj + 2 - DIGIT_BITS * a.V.tmax;   // c_i = eA_i + cbase
   const double* x = a.X1 + j * a.ld1;
   const int nb = a.V.groups;
+  const int lane = threadIdx.x & 31;
+  int lg = 0;
+  while (((int64_t)1 << lg) < n) ++lg;
   u128 nn = 0;
+  i128 acc = 0;                 // x^T v in units of 2^(aw + lg - 126 + gj)
+  int aw = -(1 << 30);          // the warp's anchor (warp-uniform)
   int tb = -(1 << 30);
-  int bmmax = 0, bnmax = 0, emin = 1 << 30, emax = -(1 << 30);   // bounds for pass 3
-  // pass 1
-  for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)FRX_RPT_RESIDUAL * blockDim.x) {
-    double xv[FRX_RPT_RESIDUAL];
-    int ei[FRX_RPT_RESIDUAL];
-    int32_t v[FRX_RPT_RESIDUAL][MP_RESIDUAL];
-#pragma unroll
-    for (int k = 0; k < FRX_RPT_RESIDUAL; ++k) {
-      const int64_t i = i0 + (int64_t)k * blockDim.x;
-      const bool ok = i < n;
-      xv[k] = ok ? x[i] : 0.0;
-      ei[k] = ok ? a.eA[i] : EZERO;
-      load_planes<MP_RESIDUAL>(a.V, i, j, ok && ei[k] != EZERO, v[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < FRX_RPT_RESIDUAL; ++k) {
-      const int64_t i = i0 + (int64_t)k * blockDim.x;
-      if (i >= n) continue;
-      const i128 N = ei[k] == EZERO ? (i128)0 : horner<MP_RESIDUAL>(v[k], nb);
+  int bmmax = 0, bnmax = 0, emin = 1 << 30, emax = -(1 << 30);   // bounds for pass 2
+  // pass 1 (warp-uniform trips: the anchor is a warp maximum)
+  for (int64_t w0 = (int64_t)threadIdx.x - lane; w0 < n; w0 += blockDim.x) {
+    const int64_t i = w0 + lane;
+    const bool ok = i < n;
+    const double xv = ok ? x[i] : 0.0;
+    const int ei = ok ? a.eA[i] : EZERO;
+    int32_t v[MP_RESIDUAL];
+    load_planes<MP_RESIDUAL>(a.V, i, j, ok && ei != EZERO, v);
+    i128 N = 0;
+    i64 m = 0;
+    int t = -(1 << 30);
+    if (ok) {
+      N = ei == EZERO ? (i128)0 : horner<MP_RESIDUAL>(v, nb);
       ncol[i] = N;
-      if (a.Vh || a.Vl) {   // debug copies of V as double-doubles
-        const double h = i128_to_double_rn(N), l = i128_to_double_rn(N - double_to_i128(h));
-        const int ex = ei[k] + cbase;
-        const dd vd = (ex >= -1022 + 130 && ex <= 1023 - 130) ? dd{__dmul_rn(h, pow2(ex)), __dmul_rn(l, pow2(ex))}
-                                                              : dd{ldexp(h, ex), ldexp(l, ex)};
-        if (a.Vh) a.Vh[i + j * n] = vd.h;
-        if (a.Vl) a.Vl[i + j * n] = vd.l;
-      }
-      const i64 m = grid_mantissa(xv[k], gj);
+      if (a.Vh || a.Vl) write_v_copies(a, N, ei + cbase, i + j * n);
+      m = grid_mantissa(xv, gj);
       const u64 am = m < 0 ? (u64)0 - (u64)m : (u64)m;
       nn += (u128)am * am;
       const int bm = am ? bitlen_u64(am) : 0;
       const int bn = N != 0 ? bitlen_bound_i128(N) : 0;
       bmmax = bm > bmmax ? bm : bmmax;
       bnmax = bn > bnmax ? bn : bnmax;
-      if (ei[k] != EZERO) {
-        emin = ei[k] < emin ? ei[k] : emin;
-        emax = ei[k] > emax ? ei[k] : emax;
+      if (ei != EZERO) {
+        emin = ei < emin ? ei : emin;
+        emax = ei > emax ? ei : emax;
       }
       if (N != 0 && m != 0) {
-        const int t = bm + bn + ei[k] + cbase;
+        t = bm + bn + ei + cbase;
         tb = t > tb ? t : tb;
       }
     }
+    int tw = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tw = max(tw, __shfl_xor_sync(0xffffffffu, tw, o));
+    if (tw > aw) {
+      acc = aw > -(1 << 29) ? shift_down(acc, tw - aw) : (i128)0;
+      aw = tw;
+    }
+    if (t > -(1 << 29)) acc += mul_shift(m, N, aw + lg - 126 - (ei + cbase));
   }
   // block reductions: x^T x (exact) and the term bound
   {
@@ -619,20 +633,9 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   emin = redb[0][2];
   emax = redb[0][3];
   __syncthreads();
-  // pass 2: x^T v on the grid 2^(lsb + gj)
-  int lg = 0;
-  while (((int64_t)1 << lg) < n) ++lg;
+  // x^T v: every warp's partial sums moved to the grid of the final bound T
   const int lsb = T + lg - 126;
-  i128 acc = 0;
-  if (T > -(1 << 29)) {
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const i128 N = ncol[i];
-      if (N == 0) continue;
-      const i64 m = grid_mantissa(x[i], gj);
-      if (m == 0) continue;
-      acc += mul_shift(m, N, lsb - (a.eA[i] + cbase));
-    }
-  }
+  acc = aw > -(1 << 29) ? shift_down(acc, T - aw) : (i128)0;
   acc = warp_sum_i128(acc);
   {
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -662,7 +665,7 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   }
   const double lam = __longlong_as_double((long long)redu[0]);
   __syncthreads();
-  // pass 3: Res = N 2^c - (m L) 2^(gj + qL), rounded once.  The aligned difference fits
+  // pass 2: Res = N 2^c - (m L) 2^(gj + qL), rounded once.  The aligned difference fits
   // 128 bits for every row when the block-wide bounds say so; otherwise per row.
   i64 L = 0;
   int qL = 0;
