@@ -205,18 +205,8 @@ __device__ __forceinline__ i128 warp_sum_i128(i128 v) {
   return v;
 }
 
-// Rows handled per thread and loop trip in the element-wise kernels (every load of those
-// rows is issued before the first use) and the minimum resident blocks per SM requested
-// from the register allocator; tuning constants, measured on GB300.
-#ifndef FRX_RPT_RESIDUAL
-#define FRX_RPT_RESIDUAL 1
-#endif
-#ifndef FRX_RPT_CORRECTION
-#define FRX_RPT_CORRECTION 1
-#endif
-#ifndef FRX_RPT_UPDATE
-#define FRX_RPT_UPDATE 1
-#endif
+// Minimum resident blocks per SM requested from the register allocator by the element-wise
+// kernels; tuning constants, measured on GB300.
 #ifndef FRX_MINB_RESIDUAL
 #define FRX_MINB_RESIDUAL 3
 #endif
@@ -241,6 +231,37 @@ __device__ __forceinline__ void load_planes(const GroupArgs& g, int64_t i, int64
   const int32_t* p = reinterpret_cast<const int32_t*>(g.out) + j * g.ldo + i;
 #pragma unroll
   for (int q = 0; q < MP; ++q) v[q] = (valid && q < g.groups) ? __ldg(p + q * g.ogs) : 0;
+}
+
+// Per-thread asynchronous copies into shared memory (cp.async): the element-wise kernels keep
+// the loads of the next PIPE - 1 row trips in flight while they work on the current one.  Each
+// thread reads back only what it copied, so a wait on its own copy groups is all the ordering
+// needed.  A copy with ok = false reads nothing and fills zeros (src must still be a valid
+// address).
+constexpr int PIPE = 3;
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// copies of the int32 planes of entry (i, j) (q < groups) into slots at dst + q * stride
+template <int MP>
+__device__ __forceinline__ void copy_planes_async(const GroupArgs& g, int64_t i, int64_t j, bool ok, int32_t* dst,
+                                                  int stride) {
+  const int32_t* p = reinterpret_cast<const int32_t*>(g.out) + j * g.ldo + (ok ? i : 0);
+#pragma unroll
+  for (int q = 0; q < MP; ++q)
+    if (q < g.groups) cp_async4(dst + q * stride, p + q * g.ogs, ok);
 }
 
 // sum_q v_q 2^(b (groups - 1 - q)) exactly (b = DIGIT_BITS; |result| < 2^127 when the product's
@@ -752,54 +773,68 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
   const int cbase = hj + 2 - DIGIT_BITS * a.W.tmax;   // c_i = f_i + cbase
   if (threadIdx.x == 0) ccount = 0;
   __syncthreads();
+  // copy slots per stage: lambda_i (double), then f_i and the planes (int32), [slot][thread]
+  extern __shared__ __align__(16) unsigned char cpipe[];
+  const int B = blockDim.x, tid = threadIdx.x;
+  double* sl = reinterpret_cast<double*>(cpipe);                          // [PIPE][B]
+  int32_t* si = reinterpret_cast<int32_t*>(sl + PIPE * B);                // [PIPE][1 + MP_CORRECTION][B]
+  auto issue = [&](int64_t i, int st) {
+    const bool ok = i < n;
+    const int64_t ic = ok ? i : 0;
+    cp_async8(sl + st * B + tid, a.lam + ic, ok);
+    int32_t* d = si + st * (1 + MP_CORRECTION) * B + tid;
+    cp_async4(d, a.f + ic, ok);
+    if (have_w && fast) copy_planes_async<MP_CORRECTION>(a.W, i, j, ok, d + B, B);
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int st = 0; st < PIPE - 1; ++st) issue(tid + (int64_t)st * B, st);
   float s2f = 0.f;
   double s2d = 0.0;
   u64 mx = 0;
-  for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)FRX_RPT_CORRECTION * blockDim.x) {
-    double li[FRX_RPT_CORRECTION];
-    int fi[FRX_RPT_CORRECTION];
-    int32_t v[FRX_RPT_CORRECTION][MP_CORRECTION];
+  for (int64_t k = 0; k * B < n; ++k) {   // block-uniform trips
+    const int64_t i = tid + k * B;
+    issue(i + (int64_t)(PIPE - 1) * B, (int)((k + PIPE - 1) % PIPE));
+    cp_async_wait<PIPE - 1>();
+    if (i >= n) continue;
+    const int st = (int)(k % PIPE);
+    const double li = sl[st * B + tid];
+    const int32_t* d = si + st * (1 + MP_CORRECTION) * B + tid;
+    const int fi = d[0];
+    double w = 0.0;
+    if (have_w && fi != EZERO) {
+      bool ok = false;
+      if (fast) {
+        int32_t v[MP_CORRECTION];
 #pragma unroll
-    for (int k = 0; k < FRX_RPT_CORRECTION; ++k) {
-      const int64_t i = i0 + (int64_t)k * blockDim.x;
-      const bool ok = i < n;
-      li[k] = ok ? a.lam[i] : 0.0;
-      fi[k] = ok ? a.f[i] : EZERO;
-      load_planes<MP_CORRECTION>(a.W, i, j, ok && have_w && fast && fi[k] != EZERO, v[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < FRX_RPT_CORRECTION; ++k) {
-      const int64_t i = i0 + (int64_t)k * blockDim.x;
-      if (i >= n) continue;
-      double w = 0.0;
-      if (have_w && fi[k] != EZERO) {
-        bool ok = false;
-        if (fast) ok = rn_scaled(horner<MP_CORRECTION>(v[k], a.W.groups), fi[k] + cbase, w);
-        if (!ok) w = gather_d_general(a.W, i, j, fi[k], hj);
+        for (int q = 0; q < MP_CORRECTION; ++q) v[q] = q < a.W.groups ? d[(1 + q) * B] : 0;
+        ok = rn_scaled(horner<MP_CORRECTION>(v, a.W.groups), fi + cbase, w);
       }
-      if (a.Wout) a.Wout[i + j * n] = w;
-      double e;
-      if (i == j) {
-        e = a.r[j] * 0.5;
+      if (!ok) w = gather_d_general(a.W, i, j, fi, hj);
+    }
+    if (a.Wout) a.Wout[i + j * n] = w;
+    double e;
+    if (i == j) {
+      e = a.r[j] * 0.5;
+    } else {
+      const double diff = __dsub_rn(lj, li);
+      if (fabs(diff) <= a.omega) {
+        const int slot = atomicAdd(&ccount, 1);
+        if (slot < 64) clist[slot] = (int)i;
+        else atomicOr(a.flags, FLAG_RANGE);
+        e = 0.0;
       } else {
-        const double diff = __dsub_rn(lj, li[k]);
-        if (fabs(diff) <= a.omega) {
-          const int slot = atomicAdd(&ccount, 1);
-          if (slot < 64) clist[slot] = (int)i;
-          else atomicOr(a.flags, FLAG_RANGE);
-          e = 0.0;
-        } else {
-          e = __ddiv_rn(w, diff);
-        }
+        e = __ddiv_rn(w, diff);
       }
-      a.E[i + j * a.lde] = e;
-      float f;
-      if (f32_of_double(e, 32, f)) s2f = __fmaf_rn(f, f, s2f);
-      else s2d = __fma_rn(e, e, s2d);
-      const u64 ab = double_to_bits(e) & 0x7fffffffffffffffull;
-      mx = ab > mx ? ab : mx;
     }
+    a.E[i + j * a.lde] = e;
+    float f;
+    if (f32_of_double(e, 32, f)) s2f = __fmaf_rn(f, f, s2f);
+    else s2d = __fma_rn(e, e, s2d);
+    const u64 ab = double_to_bits(e) & 0x7fffffffffffffffull;
+    mx = ab > mx ? ab : mx;
   }
+  cp_async_wait<0>();
   __syncthreads();
   const int nc = ccount < 64 ? ccount : 64;
   const double* xj = a.X1 + j * a.ld1;
@@ -825,6 +860,11 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
     a.norms[j] = s2;
     a.eta[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
   }
+}
+
+// dynamic shared memory of the correction's copy pipeline for blocks of `threads`
+__host__ __device__ inline size_t correction_pipe_smem(int threads) {
+  return (size_t)PIPE * threads * (sizeof(double) + (1 + MP_CORRECTION) * sizeof(int32_t));
 }
 
 // ---- line 6: X <- RN(X1 + X1 E~) (pair arithmetic), ||X_new - X_old||_F^2 ----------------
@@ -928,46 +968,64 @@ __device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned)
   a.U = resolve(a.U);
   if (a.beta_dyn) a.beta = *a.beta_dyn;
   __shared__ double red[32];
+  // copy slots per stage: x1, x_old (doubles), then rho and the planes (int32), [slot][thread]
+  extern __shared__ __align__(16) unsigned char upipe[];
+  const int B = blockDim.x, tid = threadIdx.x;
+  double* sx = reinterpret_cast<double*>(upipe);                          // [PIPE][2][B]
+  int32_t* si = reinterpret_cast<int32_t*>(sx + PIPE * 2 * B);            // [PIPE][1 + MP_UPDATE][B]
   const int64_t j = bx;
   const int ej = a.eta[j];
   const bool none = a.U.groups == 0 || ej == EZERO;
   const bool fast = a.U.word32 && a.U.exact128 && a.U.groups <= MP_UPDATE;
   const double* x1c = a.X1 + j * a.ld1;
   double* xc = a.X + j * a.ldx;
+  const int64_t n = a.n;
+  auto issue = [&](int64_t i, int st) {
+    const bool ok = i < n;
+    const int64_t ic = ok ? i : 0;
+    cp_async8(sx + (st * 2 + 0) * B + tid, x1c + ic, ok);
+    cp_async8(sx + (st * 2 + 1) * B + tid, xc + ic, ok);
+    int32_t* d = si + st * (1 + MP_UPDATE) * B + tid;
+    cp_async4(d, a.rho + ic, ok);
+    if (fast && !none) copy_planes_async<MP_UPDATE>(a.U, i, j, ok, d + B, B);
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int st = 0; st < PIPE - 1; ++st) issue(tid + (int64_t)st * B, st);
   float d2f = 0.f;
   double d2d = 0.0;
-  for (int64_t i0 = threadIdx.x; i0 < a.n; i0 += (int64_t)FRX_RPT_UPDATE * blockDim.x) {
-    double x1[FRX_RPT_UPDATE], xo[FRX_RPT_UPDATE];
-    int ri[FRX_RPT_UPDATE];
-    int32_t v[FRX_RPT_UPDATE][MP_UPDATE];
+  for (int64_t k = 0; k * B < n; ++k) {   // block-uniform trips
+    const int64_t i = tid + k * B;
+    issue(i + (int64_t)(PIPE - 1) * B, (int)((k + PIPE - 1) % PIPE));
+    cp_async_wait<PIPE - 1>();
+    if (i >= n) continue;
+    const int st = (int)(k % PIPE);
+    const double x1 = sx[(st * 2 + 0) * B + tid], xo = sx[(st * 2 + 1) * B + tid];
+    const int32_t* d = si + st * (1 + MP_UPDATE) * B + tid;
+    const int ri = d[0];
+    double xn = x1;
+    if (!none && ri != EZERO) {
+      bool done = false;
+      if (fast) {
+        int32_t v[MP_UPDATE];
 #pragma unroll
-    for (int k = 0; k < FRX_RPT_UPDATE; ++k) {
-      const int64_t i = i0 + (int64_t)k * blockDim.x;
-      const bool ok = i < a.n;
-      x1[k] = ok ? x1c[i] : 0.0;
-      xo[k] = ok ? xc[i] : 0.0;
-      ri[k] = ok ? a.rho[i] : EZERO;
-      load_planes<MP_UPDATE>(a.U, i, j, ok && fast && !none, v[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < FRX_RPT_UPDATE; ++k) {
-      const int64_t i = i0 + (int64_t)k * blockDim.x;
-      if (i >= a.n) continue;
-      double xn = x1[k];
-      if (!none && ri[k] != EZERO) {
-        bool done = false;
-        if (fast) {
-          const int c = ri[k] + ej + 2 - DIGIT_BITS * a.U.tmax;
-          done = add_exact_rn(x1[k], horner<MP_UPDATE>(v[k], a.U.groups), c, xn);
-        }
-        if (!done) xn = update_general(a, x1[k], i, j, ri[k], ej);
+        for (int q = 0; q < MP_UPDATE; ++q) v[q] = q < a.U.groups ? d[(1 + q) * B] : 0;
+        const int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
+        done = add_exact_rn(x1, horner<MP_UPDATE>(v, a.U.groups), c, xn);
       }
-      xc[i] = xn;
-      accumulate_dx2(xn, xo[k], d2f, d2d);
+      if (!done) xn = update_general(a, x1, i, j, ri, ej);
     }
+    xc[i] = xn;
+    accumulate_dx2(xn, xo, d2f, d2d);
   }
+  cp_async_wait<0>();
   const double d2 = block_sum_d(__fma_rn((double)d2f, 0x1p-64, d2d), red);
   if (threadIdx.x == 0) a.norms[2 * a.n + j] = d2;
+}
+
+// dynamic shared memory of the update's copy pipeline for blocks of `threads`
+__host__ __device__ inline size_t update_pipe_smem(int threads) {
+  return (size_t)PIPE * threads * (2 * sizeof(double) + (1 + MP_UPDATE) * sizeof(int32_t));
 }
 
 // ---- single-problem kernels (one block per column) ---------------------------------
@@ -1016,6 +1074,16 @@ int set_refine_kernel_attributes() {
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<ResidualArgs, residual_body, ELEM_THREADS, FRX_MINB_RESIDUAL>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(sizeof(dd) * (size_t)FRX_MAX_N)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_correction, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)correction_pipe_smem(ELEM_THREADS)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<CorrectionArgs, correction_body, ELEM_THREADS, FRX_MINB_CORRECTION>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)correction_pipe_smem(ELEM_THREADS)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)update_pipe_smem(ELEM_THREADS)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<UpdateArgs, update_body, ELEM_THREADS, FRX_MINB_UPDATE>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)update_pipe_smem(ELEM_THREADS)));
   return FRX_OK;
 }
 
@@ -1043,8 +1111,10 @@ int launch_w_offdiag_norm2(const CorrectionArgs& a0, cudaStream_t s) {
 int launch_correction(const CorrectionArgs& a0, cudaStream_t s) {
   CorrectionArgs a = a0;
   a.gx = (unsigned)a.n;
-  if (record_launch(LK_CORRECTION, a, a.n, elem_threads(a.n), 0)) return FRX_OK;
-  k_correction<<<(unsigned)a.n, elem_threads(a.n), 0, s>>>(a);
+  const int threads = elem_threads(a.n);
+  const size_t smem = correction_pipe_smem(threads);
+  if (record_launch(LK_CORRECTION, a, a.n, threads, smem)) return FRX_OK;
+  k_correction<<<(unsigned)a.n, threads, smem, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
@@ -1053,8 +1123,10 @@ int launch_correction(const CorrectionArgs& a0, cudaStream_t s) {
 int launch_update(const UpdateArgs& a0, cudaStream_t s) {
   UpdateArgs a = a0;
   a.gx = (unsigned)a.n;
-  if (record_launch(LK_UPDATE, a, a.n, elem_threads(a.n), 0)) return FRX_OK;
-  k_update<<<(unsigned)a.n, elem_threads(a.n), 0, s>>>(a);
+  const int threads = elem_threads(a.n);
+  const size_t smem = update_pipe_smem(threads);
+  if (record_launch(LK_UPDATE, a, a.n, threads, smem)) return FRX_OK;
+  k_update<<<(unsigned)a.n, threads, smem, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
@@ -1076,11 +1148,11 @@ int launch_grouped_refine(int kind, const void* tab, const long long* start, int
       break;
     case LK_CORRECTION:
       k_grouped<CorrectionArgs, correction_body, ELEM_THREADS, FRX_MINB_CORRECTION>
-          <<<grid, threads, 0, s>>>((const CorrectionArgs*)tab, start, count);
+          <<<grid, threads, correction_pipe_smem(threads), s>>>((const CorrectionArgs*)tab, start, count);
       break;
     case LK_UPDATE:
       k_grouped<UpdateArgs, update_body, ELEM_THREADS, FRX_MINB_UPDATE>
-          <<<grid, threads, 0, s>>>((const UpdateArgs*)tab, start, count);
+          <<<grid, threads, update_pipe_smem(threads), s>>>((const UpdateArgs*)tab, start, count);
       break;
     default:
       return FRX_E_UNSUPPORTED;
