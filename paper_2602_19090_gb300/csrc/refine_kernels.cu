@@ -254,16 +254,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// copies of the int32 planes of entry (i, j) (q < groups) into slots at dst + q * stride
-template <int MP>
-__device__ __forceinline__ void copy_planes_async(const GroupArgs& g, int64_t i, int64_t j, bool ok, int32_t* dst,
-                                                  int stride) {
-  const int32_t* p = reinterpret_cast<const int32_t*>(g.out) + j * g.ldo + (ok ? i : 0);
-#pragma unroll
-  for (int q = 0; q < MP; ++q)
-    if (q < g.groups) cp_async4(dst + q * stride, p + q * g.ogs, ok);
-}
-
 // sum_q v_q 2^(b (groups - 1 - q)) exactly (b = DIGIT_BITS; |result| < 2^127 when the product's
 // exact128 flag holds): Horner in int64 chunks of four planes, merged in 128 bits
 template <int MP>
@@ -778,13 +768,23 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
   const int B = blockDim.x, tid = threadIdx.x;
   double* sl = reinterpret_cast<double*>(cpipe);                          // [PIPE][B]
   int32_t* si = reinterpret_cast<int32_t*>(sl + PIPE * B);                // [PIPE][1 + MP_CORRECTION][B]
+  const int np = have_w && fast ? a.W.groups : 0;                        // planes copied per row
+  const int32_t* pcol = reinterpret_cast<const int32_t*>(a.W.out) + j * a.W.ldo;
+  const int64_t ogs = a.W.ogs;
   auto issue = [&](int64_t i, int st) {
     const bool ok = i < n;
     const int64_t ic = ok ? i : 0;
     cp_async8(sl + st * B + tid, a.lam + ic, ok);
     int32_t* d = si + st * (1 + MP_CORRECTION) * B + tid;
     cp_async4(d, a.f + ic, ok);
-    if (have_w && fast) copy_planes_async<MP_CORRECTION>(a.W, i, j, ok, d + B, B);
+    const int32_t* p = pcol + ic;
+#pragma unroll
+    for (int q = 0; q < MP_CORRECTION; ++q) {
+      if (q >= np) break;
+      d += B;
+      cp_async4(d, p, ok);
+      p += ogs;
+    }
     cp_async_commit();
   };
 #pragma unroll
@@ -792,14 +792,16 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
   float s2f = 0.f;
   double s2d = 0.0;
   u64 mx = 0;
-  for (int64_t k = 0; k * B < n; ++k) {   // block-uniform trips
-    const int64_t i = tid + k * B;
-    issue(i + (int64_t)(PIPE - 1) * B, (int)((k + PIPE - 1) % PIPE));
+  int st = 0, sti = PIPE - 1;   // stage of the current trip, stage the next copies go to
+  for (int64_t i = tid, i0 = 0; i0 < n; i += B, i0 += B) {   // block-uniform trips
+    issue(i + (int64_t)(PIPE - 1) * B, sti);
+    sti = sti == PIPE - 1 ? 0 : sti + 1;
     cp_async_wait<PIPE - 1>();
+    const int cur = st;
+    st = st == PIPE - 1 ? 0 : st + 1;
     if (i >= n) continue;
-    const int st = (int)(k % PIPE);
-    const double li = sl[st * B + tid];
-    const int32_t* d = si + st * (1 + MP_CORRECTION) * B + tid;
+    const double li = sl[cur * B + tid];
+    const int32_t* d = si + cur * (1 + MP_CORRECTION) * B + tid;
     const int fi = d[0];
     double w = 0.0;
     if (have_w && fi != EZERO) {
@@ -807,8 +809,8 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
       if (fast) {
         int32_t v[MP_CORRECTION];
 #pragma unroll
-        for (int q = 0; q < MP_CORRECTION; ++q) v[q] = q < a.W.groups ? d[(1 + q) * B] : 0;
-        ok = rn_scaled(horner<MP_CORRECTION>(v, a.W.groups), fi + cbase, w);
+        for (int q = 0; q < MP_CORRECTION; ++q) v[q] = q < np ? d[(1 + q) * B] : 0;
+        ok = rn_scaled(horner<MP_CORRECTION>(v, np), fi + cbase, w);
       }
       if (!ok) w = gather_d_general(a.W, i, j, fi, hj);
     }
@@ -923,6 +925,31 @@ __device__ __noinline__ double update_general(const UpdateArgs& a, double x1, in
   return __dadd_rn(c2.h, cl);
 }
 
+// RN(x1 + N 2^c) for the usual update, a correction far below x1 whose sum stays in x1's
+// binade: with x1 = P 2^q (P a signed 53-bit integer) and s = q - c >= 1, the sum is
+// (P + floor(N / 2^s) + f) 2^q with 0 <= f < 1; bit s - 1 of N and the bits below it (sticky)
+// decide round-half-even to an integer R, and R 2^q is the correctly rounded sum when
+// 2^52 < |P + floor(N / 2^s)| and |R| < 2^53.  False otherwise (the caller takes the exact
+// 128-bit path): x1 zero, subnormal or not finite, s outside [1, 127], or a sum that may leave
+// the binade.
+__device__ __forceinline__ bool add_on_grid_rn(double x1, i128 N, int c, double& out) {
+  const u64 b = double_to_bits(x1);
+  const int be = (int)((b >> 52) & 0x7ff);
+  const int s = be - 1075 - c;
+  if (be == 0 || be == 0x7ff || s < 1 || s > 127) return false;
+  const i128 T2 = N >> (s - 1);                        // floor(N / 2^(s-1))
+  const i64 t2 = (i64)T2;
+  if ((i128)t2 != T2 || t2 > (1ll << 60) || t2 < -(1ll << 60)) return false;
+  const bool sticky = s > 1 && ((u128)N << (129 - s)) != 0;
+  const i64 m = (i64)((b & ((1ull << 52) - 1)) | (1ull << 52));
+  const i64 F = ((b >> 63) ? -m : m) + (t2 >> 1);        // P + floor(N / 2^s)
+  const i64 R = F + ((t2 & 1) && (sticky || (F & 1)) ? 1 : 0);
+  const u64 aF = F < 0 ? (u64)0 - (u64)F : (u64)F, aR = R < 0 ? (u64)0 - (u64)R : (u64)R;
+  if (aF <= (1ull << 52) || aR >= (1ull << 53)) return false;
+  out = __longlong_as_double((long long)((R < 0 ? (1ull << 63) : 0ull) | ((u64)be << 52) | (aR & ((1ull << 52) - 1))));
+  return true;
+}
+
 // RN(x1 + N 2^c) exactly in 128-bit integers; false when the aligned sum would not fit
 // or the result leaves the normal range
 __device__ __forceinline__ bool add_exact_rn(double x1, i128 N, int c, double& out) {
@@ -977,9 +1004,13 @@ __device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned)
   const int ej = a.eta[j];
   const bool none = a.U.groups == 0 || ej == EZERO;
   const bool fast = a.U.word32 && a.U.exact128 && a.U.groups <= MP_UPDATE;
+  const int np = fast && !none ? a.U.groups : 0;                          // planes copied per row
   const double* x1c = a.X1 + j * a.ld1;
   double* xc = a.X + j * a.ldx;
+  const int32_t* pcol = reinterpret_cast<const int32_t*>(a.U.out) + j * a.U.ldo;
+  const int64_t ogs = a.U.ogs;
   const int64_t n = a.n;
+  const int cshift = ej + 2 - DIGIT_BITS * a.U.tmax;                      // c = rho_i + cshift
   auto issue = [&](int64_t i, int st) {
     const bool ok = i < n;
     const int64_t ic = ok ? i : 0;
@@ -987,21 +1018,30 @@ __device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned)
     cp_async8(sx + (st * 2 + 1) * B + tid, xc + ic, ok);
     int32_t* d = si + st * (1 + MP_UPDATE) * B + tid;
     cp_async4(d, a.rho + ic, ok);
-    if (fast && !none) copy_planes_async<MP_UPDATE>(a.U, i, j, ok, d + B, B);
+    const int32_t* p = pcol + ic;
+#pragma unroll
+    for (int q = 0; q < MP_UPDATE; ++q) {
+      if (q >= np) break;
+      d += B;
+      cp_async4(d, p, ok);
+      p += ogs;
+    }
     cp_async_commit();
   };
 #pragma unroll
   for (int st = 0; st < PIPE - 1; ++st) issue(tid + (int64_t)st * B, st);
   float d2f = 0.f;
   double d2d = 0.0;
-  for (int64_t k = 0; k * B < n; ++k) {   // block-uniform trips
-    const int64_t i = tid + k * B;
-    issue(i + (int64_t)(PIPE - 1) * B, (int)((k + PIPE - 1) % PIPE));
+  int st = 0, sti = PIPE - 1;   // stage of the current trip, stage the next copies go to
+  for (int64_t i = tid, i0 = 0; i0 < n; i += B, i0 += B) {   // block-uniform trips
+    issue(i + (int64_t)(PIPE - 1) * B, sti);
+    sti = sti == PIPE - 1 ? 0 : sti + 1;
     cp_async_wait<PIPE - 1>();
+    const int cur = st;
+    st = st == PIPE - 1 ? 0 : st + 1;
     if (i >= n) continue;
-    const int st = (int)(k % PIPE);
-    const double x1 = sx[(st * 2 + 0) * B + tid], xo = sx[(st * 2 + 1) * B + tid];
-    const int32_t* d = si + st * (1 + MP_UPDATE) * B + tid;
+    const double x1 = sx[(cur * 2 + 0) * B + tid], xo = sx[(cur * 2 + 1) * B + tid];
+    const int32_t* d = si + cur * (1 + MP_UPDATE) * B + tid;
     const int ri = d[0];
     double xn = x1;
     if (!none && ri != EZERO) {
@@ -1009,9 +1049,10 @@ __device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned)
       if (fast) {
         int32_t v[MP_UPDATE];
 #pragma unroll
-        for (int q = 0; q < MP_UPDATE; ++q) v[q] = q < a.U.groups ? d[(1 + q) * B] : 0;
-        const int c = ri + ej + 2 - DIGIT_BITS * a.U.tmax;
-        done = add_exact_rn(x1, horner<MP_UPDATE>(v, a.U.groups), c, xn);
+        for (int q = 0; q < MP_UPDATE; ++q) v[q] = q < np ? d[(1 + q) * B] : 0;
+        const i128 N = horner<MP_UPDATE>(v, np);
+        const int c = ri + cshift;
+        done = add_on_grid_rn(x1, N, c, xn) || add_exact_rn(x1, N, c, xn);
       }
       if (!done) xn = update_general(a, x1, i, j, ri, ej);
     }
