@@ -534,6 +534,11 @@ int build_stages(const std::vector<std::vector<LaunchRecord>>& recs, const std::
       for (int b = 0; b < count; ++b) most = recs[b][k].blocks > most ? recs[b][k].blocks : most;
       if (most <= 1024) st.threads = 128;
       if (most <= 512) st.threads = FRX_BATCH_SMALL_THREADS;
+      // the residual's copy stages follow its V column and grow with the block
+      if (st.kind == LK_RESIDUAL) {
+        if (residual_launch_smem(most, st.threads) > RESIDUAL_SMEM_MAX) st.threads = 128;
+        st.smem = residual_launch_smem(most, st.threads);
+      }
     }
     stages.push_back(st);
   }

@@ -514,6 +514,23 @@ __device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
 // fits 128 bits.  A second pass rounds Res = V - x lambda once from its exact integer value.
 __device__ __forceinline__ i128 shift_down(i128 v, int d) { return d >= 127 ? (i128)0 : (v >> d); }
 
+// The residual's first pass streams x_i, eA_i and the planes through a two-stage copy
+// pipeline placed after the V column in dynamic shared memory; blocks of 256 threads while the
+// column and the stages fit, else 128.
+constexpr int PIPE_R = 2;
+constexpr size_t RES_SMEM_MAX = RESIDUAL_SMEM_MAX;
+
+__host__ __device__ inline size_t residual_pipe_smem(int threads) {
+  return (size_t)PIPE_R * threads * (sizeof(double) + (1 + MP_RESIDUAL) * sizeof(int32_t));
+}
+__host__ __device__ inline int residual_threads(int64_t n) {
+  const int t = elem_threads(n);
+  return sizeof(dd) * (size_t)n + residual_pipe_smem(t) <= RES_SMEM_MAX ? t : 128;
+}
+__host__ __device__ inline size_t residual_smem(int64_t n, int threads) {
+  return sizeof(dd) * (size_t)n + residual_pipe_smem(threads);
+}
+
 // debug copies of V = N 2^ex as double-doubles
 __device__ __noinline__ void write_v_copies(const ResidualArgs& a, i128 N, int ex, int64_t at) {
   const double h = i128_to_double_rn(N), l = i128_to_double_rn(N - double_to_i128(h));
@@ -544,7 +561,6 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   const int cbase = fj + 2 - DIGIT_BITS * a.V.tmax;   // c_i = eA_i + cbase
   const double* x = a.X1 + j * a.ld1;
   const int nb = a.V.groups;
-  const int lane = threadIdx.x & 31;
   int lg = 0;
   while (((int64_t)1 << lg) < n) ++lg;
   u128 nn = 0;
@@ -552,14 +568,44 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   int aw = -(1 << 30);          // the warp's anchor (warp-uniform)
   int tb = -(1 << 30);
   int bmmax = 0, bnmax = 0, emin = 1 << 30, emax = -(1 << 30);   // bounds for pass 2
-  // pass 1 (warp-uniform trips: the anchor is a warp maximum)
-  for (int64_t w0 = (int64_t)threadIdx.x - lane; w0 < n; w0 += blockDim.x) {
-    const int64_t i = w0 + lane;
+  // pass 1 (block-uniform trips: the anchor is a warp maximum)
+  const int B = blockDim.x, tid = threadIdx.x;
+  double* sx = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(vcol) + sizeof(dd) * n);   // [PIPE_R][B]
+  int32_t* si = reinterpret_cast<int32_t*>(sx + PIPE_R * B);              // [PIPE_R][1 + MP_RESIDUAL][B]
+  const int32_t* pcol = reinterpret_cast<const int32_t*>(a.V.out) + j * a.V.ldo;
+  const int64_t ogs = a.V.ogs;
+  auto issue = [&](int64_t i, int st) {
     const bool ok = i < n;
-    const double xv = ok ? x[i] : 0.0;
-    const int ei = ok ? a.eA[i] : EZERO;
+    const int64_t ic = ok ? i : 0;
+    cp_async8(sx + st * B + tid, x + ic, ok);
+    int32_t* d = si + st * (1 + MP_RESIDUAL) * B + tid;
+    cp_async4(d, a.eA + ic, ok);
+    const int32_t* p = pcol + ic;
+#pragma unroll
+    for (int q = 0; q < MP_RESIDUAL; ++q) {
+      if (q >= nb) break;
+      d += B;
+      cp_async4(d, p, ok);
+      p += ogs;
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int st = 0; st < PIPE_R - 1; ++st) issue(tid + (int64_t)st * B, st);
+  int st = 0, sti = PIPE_R - 1;   // stage of the current trip, stage the next copies go to
+  for (int64_t i = tid, i0 = 0; i0 < n; i += B, i0 += B) {
+    issue(i + (int64_t)(PIPE_R - 1) * B, sti);
+    sti = sti == PIPE_R - 1 ? 0 : sti + 1;
+    cp_async_wait<PIPE_R - 1>();
+    const int cur = st;
+    st = st == PIPE_R - 1 ? 0 : st + 1;
+    const bool ok = i < n;
+    const int32_t* d = si + cur * (1 + MP_RESIDUAL) * B + tid;
+    const double xv = ok ? sx[cur * B + tid] : 0.0;
+    const int ei = ok ? d[0] : EZERO;
     int32_t v[MP_RESIDUAL];
-    load_planes<MP_RESIDUAL>(a.V, i, j, ok && ei != EZERO, v);
+#pragma unroll
+    for (int q = 0; q < MP_RESIDUAL; ++q) v[q] = q < nb ? d[(1 + q) * B] : 0;
     i128 N = 0;
     i64 m = 0;
     int t = -(1 << 30);
@@ -592,6 +638,7 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
     }
     if (t > -(1 << 29)) acc += mul_shift(m, N, aw + lg - 126 - (ei + cbase));
   }
+  cp_async_wait<0>();
   // block reductions: x^T x (exact) and the term bound
   {
     u64 lo = (u64)nn, hi = (u64)(nn >> 64);
@@ -757,6 +804,10 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
   const int64_t j = bx;
   const int64_t n = a.n;
   const double lj = a.lam[j];
+  // |diff| <= omega compared on the bit patterns (exact for non-negative doubles; a negative
+  // omega marks no cluster), which keeps the FP64 pipe for the division
+  const bool any_cluster = a.omega >= 0.0;
+  const u64 omega_bits = any_cluster ? double_to_bits(a.omega) : 0ull;
   const int hj = a.h[j];
   const bool have_w = a.W.groups > 0 && hj != EZERO;
   const bool fast = a.W.word32 && a.W.exact128 && a.W.groups <= MP_CORRECTION;
@@ -820,7 +871,7 @@ __device__ __forceinline__ void correction_body(CorrectionArgs a, unsigned bx, u
       e = a.r[j] * 0.5;
     } else {
       const double diff = __dsub_rn(lj, li);
-      if (fabs(diff) <= a.omega) {
+      if (any_cluster && (double_to_bits(diff) & 0x7fffffffffffffffull) <= omega_bits) {
         const int slot = atomicAdd(&ccount, 1);
         if (slot < 64) clist[slot] = (int)i;
         else atomicOr(a.flags, FLAG_RANGE);
@@ -1109,12 +1160,12 @@ int launch_groups_to_dd(const PlaneGemm& g, const int32_t* eL, const int32_t* eR
   return FRX_OK;
 }
 
+size_t residual_launch_smem(int64_t n, int threads) { return residual_smem(n, threads); }
+
 int set_refine_kernel_attributes() {
-  FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(dd) * (size_t)FRX_MAX_N)));
+  FRX_CUDA_TRY(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RES_SMEM_MAX));
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<ResidualArgs, residual_body, ELEM_THREADS, FRX_MINB_RESIDUAL>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(dd) * (size_t)FRX_MAX_N)));
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RES_SMEM_MAX));
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_correction, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)correction_pipe_smem(ELEM_THREADS)));
   FRX_CUDA_TRY(cudaFuncSetAttribute(k_grouped<CorrectionArgs, correction_body, ELEM_THREADS, FRX_MINB_CORRECTION>,
@@ -1131,9 +1182,10 @@ int set_refine_kernel_attributes() {
 int launch_residual(const ResidualArgs& a0, cudaStream_t s) {
   ResidualArgs a = a0;
   a.gx = (unsigned)a.n;
-  size_t smem = sizeof(dd) * (size_t)a.n;
-  if (record_launch(LK_RESIDUAL, a, a.n, elem_threads(a.n), smem)) return FRX_OK;
-  k_residual<<<(unsigned)a.n, elem_threads(a.n), smem, s>>>(a);
+  const int threads = residual_threads(a.n);
+  const size_t smem = residual_smem(a.n, threads);
+  if (record_launch(LK_RESIDUAL, a, a.n, threads, smem)) return FRX_OK;
+  k_residual<<<(unsigned)a.n, threads, smem, s>>>(a);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;

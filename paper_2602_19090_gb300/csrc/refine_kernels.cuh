@@ -75,6 +75,11 @@ struct UpdateArgs {
 
 GroupArgs group_args(const PlaneGemm& g);
 int set_refine_kernel_attributes();
+// dynamic shared memory of a residual launch over columns of order at most n with blocks of
+// `threads` (the V column, then the first pass's copy stages), and its ceiling: 220 KB, which
+// leaves room for the kernel's static shared memory within the 227 KB a block may hold
+size_t residual_launch_smem(int64_t n, int threads);
+constexpr size_t RESIDUAL_SMEM_MAX = 220 * 1024;
 int launch_residual(const ResidualArgs& a, cudaStream_t s);
 int launch_w_offdiag_norm2(const CorrectionArgs& a, cudaStream_t s);
 int launch_correction(const CorrectionArgs& a, cudaStream_t s);
