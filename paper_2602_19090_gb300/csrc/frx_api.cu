@@ -50,6 +50,7 @@ struct RefineWs {
   __nv_bfloat16 *Ap, *Xp, *Rp, *X1rp;
   i64* groups;
   int32_t* ell;    // nonzero columns of A's rows (sparse V product), ELL_MAX per row
+  uint32_t* rank;  // positions of the eigenvalue estimates in ascending order (plan kernels)
   int64_t pitch, ps;
   size_t bytes;
   int tile;        // tile configuration of the slice products (set by the autotuner)
@@ -82,6 +83,7 @@ RefineWs carve_refine(void* work, int64_t n, int kcap) {
   w.X1rp = c.take<__nv_bfloat16>((size_t)kcap * w.ps);
   w.groups = c.take<i64>((size_t)8 * n * n);   // 64 bytes per entry: 8 int64 groups or 16 int32 planes
   w.ell = c.take<int32_t>((size_t)ELL_MAX * n);
+  w.rank = c.take<uint32_t>(n);
   w.bytes = c.off + 256;
   w.tile = TILE_128x256;
   w.sparse_v = 0;
@@ -344,7 +346,7 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   ua.norms = ws.colsq;
   FRX_TRY(launch_update(ua, s));
   // S12: stopping test
-  FRX_TRY(launch_plan_end(P, ws.lam, ws.lam_prev, ws.colsq, po, s));
+  FRX_TRY(launch_plan_end(P, ws.lam, ws.lam_prev, ws.colsq, po, ws.rank, s));
   return FRX_OK;
 }
 
@@ -403,7 +405,7 @@ int refine_common(const double* A, int64_t lda, double* X, int64_t ldx, double* 
           ws.sparse_v = nz;
         }
       }
-      FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, s));
+      FRX_TRY(launch_plan_init(ws.plan, ws.eA, D, ws.lam_prev, po, omega_prev, ws.rank, s));
       for (int it = 1; it <= max_iter; ++it) {
         FRX_TRY(enqueue_iteration(A, lda, X, ldx, n, o, po, ws, dbg, s));
         int done = 0;
@@ -634,7 +636,7 @@ int record_phases(const double* const* A, const int64_t* lda, double* const* X, 
       FRX_TRY(record_bytes(ws[b].rowmax, nullptr, sizeof(u64) * (size_t)n[b]));
       FRX_TRY(launch_col_exponents(A[b], lda[b], n[b], n[b], ws[b].eA, &ws[b].plan->flags, none, nullptr,
                                     &ws[b].plan->rownnz));
-      FRX_TRY(launch_plan_init(ws[b].plan, ws[b].eA, D[b], ws[b].lam_prev, po[b], 0.0, none));
+      FRX_TRY(launch_plan_init(ws[b].plan, ws[b].eA, D[b], ws[b].lam_prev, po[b], 0.0, nullptr, none));
       rec[0][b] = std::move(R.recs);
       R.recs.clear();
       FRX_TRY(enqueue_iteration(A[b], lda[b], X[b], ldx[b], n[b], o, po[b], ws[b], nullptr, none));

@@ -114,23 +114,25 @@ __device__ __forceinline__ double key_value(u64 k) {
 }
 
 // Smallest adjacent gap of the sorted estimates exceeding omega (Lam if none) and max |lam|.
-// s: dynamic smem of next_pow2(n) doubles (bitonic sort of their integer keys).
+// s: dynamic smem of next_pow2(n) doubles.  With `rank` (each estimate's position in ascending
+// order, from k_rank_keys) the keys are placed by rank; without, this block sorts them (bitonic
+// network on their integer keys).
 __device__ void gap_of(const double* lam, int64_t n, double omega, double* s, double* red, double& g,
-                       double& Lam) {
+                       double& Lam, const uint32_t* rank) {
   u64* key = reinterpret_cast<u64*>(s);
   int64_t m = 1;
   while (m < n) m <<= 1;
   u64 amax = 0;
-  for (int64_t i = threadIdx.x; i < m; i += PT) {
+  for (int64_t i = threadIdx.x; i < (rank ? n : m); i += PT) {
     const double v = i < n ? lam[i] : INFINITY;
-    key[i] = order_key(v);
+    key[rank ? (int64_t)rank[i] : i] = order_key(v);
     if (i < n) {
       const u64 ab = double_to_bits(v) & 0x7fffffffffffffffull;
       amax = ab > amax ? ab : amax;
     }
   }
   __syncthreads();
-  for (int64_t k = 2; k <= m; k <<= 1) {
+  for (int64_t k = 2; !rank && k <= m; k <<= 1) {
     for (int64_t jj = k >> 1; jj > 0; jj >>= 1) {
       for (int64_t i = threadIdx.x; i < m; i += PT) {
         const int64_t l = i ^ jj;
@@ -166,7 +168,8 @@ __device__ void raise(DevPlan* p, int st) {
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void plan_init_impl(DevPlan* p, const int32_t* eA, const double* D,
-                                                  double* lam_prev, PlanOpts o, double omega_prev) {
+                                                  double* lam_prev, PlanOpts o, double omega_prev,
+                                                  const uint32_t* rank) {
   extern __shared__ double sbuf[];
   __shared__ int redi[32];
   __shared__ double redd[32];
@@ -181,7 +184,7 @@ __device__ __forceinline__ void plan_init_impl(DevPlan* p, const int32_t* eA, co
   emax = bmax_int(emax, redi);
   int anybad = bmax_int(bad ? 1 : 0, redi);
   double g, Lam;
-  gap_of(D, o.n, omega_prev, sbuf, redd, g, Lam);
+  gap_of(D, o.n, omega_prev, sbuf, redd, g, Lam, rank);
   if (threadIdx.x == 0) {
     p->iter = 0;
     p->done = 0;
@@ -420,13 +423,13 @@ __device__ __forceinline__ void plan_u_impl(DevPlan* p, const int32_t* rho, cons
 
 // stopping test (reading R7): est = step^2 max|lam| / (xi_stop gap) <= delta
 __device__ __forceinline__ void plan_end_impl(DevPlan* p, const double* lam_new, double* lam_prev,
-                                              const double* colsq, PlanOpts o) {
+                                              const double* colsq, PlanOpts o, const uint32_t* rank) {
   extern __shared__ double sbuf[];
   __shared__ double redd[32];
   if (p->done) return;
   const double omega = p->omega;
   double g, Lam;
-  gap_of(lam_new, o.n, omega, sbuf, redd, g, Lam);
+  gap_of(lam_new, o.n, omega, sbuf, redd, g, Lam, rank);
   for (int64_t i = threadIdx.x; i < o.n; i += PT) lam_prev[i] = lam_new[i];
   const double e2 = sum_columns(colsq, o.n, redd);
   __syncthreads();
@@ -490,8 +493,8 @@ struct PlanArgs {
 };
 
 __global__ void __launch_bounds__(PT) k_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev,
-                                                  PlanOpts o, double omega_prev) {
-  plan_init_impl(p, eA, D, lam_prev, o, omega_prev);
+                                                  PlanOpts o, double omega_prev, const uint32_t* rank) {
+  plan_init_impl(p, eA, D, lam_prev, o, omega_prev, rank);
 }
 __global__ void __launch_bounds__(PT) k_plan_v(DevPlan* p, const int32_t* f, PlanOpts o) { plan_v_impl(p, f, o); }
 __global__ void k_plan_mark_sliced(DevPlan* p) { plan_mark_sliced_impl(p); }
@@ -502,13 +505,55 @@ __global__ void __launch_bounds__(PT) k_plan_omega(DevPlan* p, const double* r, 
 __global__ void __launch_bounds__(PT) k_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
   plan_u_impl(p, rho, eta, o);
 }
-__global__ void __launch_bounds__(PT)
-    k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const double* colsq, PlanOpts o) {
-  plan_end_impl(p, lam_new, lam_prev, colsq, o);
+__global__ void __launch_bounds__(PT) k_plan_end(DevPlan* p, const double* lam_new, double* lam_prev,
+                                                 const double* colsq, PlanOpts o, const uint32_t* rank) {
+  plan_end_impl(p, lam_new, lam_prev, colsq, o, rank);
+}
+
+// Position of every estimate in ascending order of its integer key, ties by index:
+// rank_i = #{j : k_j < k_i} + #{j < i : k_j = k_i}, a permutation of 0..n-1 (the order the
+// bitonic network of gap_of produces).  Blocks cover 256 estimates i by a slice of the j; their
+// counts are added to rank (zeroed first).  Skipped, like the plan kernel after it, once the
+// refinement has finished.
+constexpr int RANK_TILE = 1024;
+
+__global__ void __launch_bounds__(256) k_rank_keys(const DevPlan* p, const double* lam, int64_t n, int64_t per,
+                                                   uint32_t* rank) {
+  __shared__ u64 kj[RANK_TILE];
+  if (p && p->done) return;
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const u64 ki = i < n ? order_key(lam[i]) : 0ull;
+  const int64_t j0 = (int64_t)blockIdx.y * per, j1 = min(n, j0 + per);
+  uint32_t cnt = 0;
+  for (int64_t t0 = j0; t0 < j1; t0 += RANK_TILE) {
+    const int m = (int)min((int64_t)RANK_TILE, j1 - t0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += 256) kj[q] = order_key(lam[t0 + q]);
+    __syncthreads();
+    const int64_t below = i - t0;   // kj[q] comes before k_i on ties when q < below
+    for (int q = 0; q < m; ++q) {
+      const u64 k = kj[q];
+      cnt += (k < ki || (k == ki && q < below)) ? 1u : 0u;
+    }
+  }
+  if (i < n && cnt) atomicAdd(&rank[i], cnt);
+}
+
+// ranks of lam[0..n) into `rank` (n words of scratch), on stream s
+static int launch_rank_keys(const DevPlan* p, const double* lam, int64_t n, uint32_t* rank, cudaStream_t s) {
+  FRX_CUDA_TRY(cudaMemsetAsync(rank, 0, sizeof(uint32_t) * (size_t)n, s));
+  const int64_t bx = (n + 255) / 256;
+  int64_t by = (4 * 152 + bx - 1) / bx;                 // about four blocks per SM in all
+  by = by < 1 ? 1 : (by > (n + 255) / 256 ? (n + 255) / 256 : by);
+  const int64_t per = (n + by - 1) / by;
+  k_rank_keys<<<dim3((unsigned)bx, (unsigned)by), 256, 0, s>>>(p, lam, n, per, rank);
+  count_launches(1);
+  FRX_CUDA_TRY(cudaGetLastError());
+  return FRX_OK;
 }
 
 __device__ __forceinline__ void plan_init_body(PlanArgs a, unsigned, unsigned) {
-  plan_init_impl(a.p, a.e0, a.d0, a.d1, a.o, a.omega_prev);
+  plan_init_impl(a.p, a.e0, a.d0, a.d1, a.o, a.omega_prev, nullptr);
 }
 __device__ __forceinline__ void plan_v_body(PlanArgs a, unsigned, unsigned) { plan_v_impl(a.p, a.e0, a.o); }
 __device__ __forceinline__ void plan_mark_sliced_body(PlanArgs a, unsigned, unsigned) { plan_mark_sliced_impl(a.p); }
@@ -518,14 +563,15 @@ __device__ __forceinline__ void plan_omega_body(PlanArgs a, unsigned, unsigned) 
 }
 __device__ __forceinline__ void plan_u_body(PlanArgs a, unsigned, unsigned) { plan_u_impl(a.p, a.e0, a.e1, a.o); }
 __device__ __forceinline__ void plan_end_body(PlanArgs a, unsigned, unsigned) {
-  plan_end_impl(a.p, a.d0, a.d1, a.colsq, a.o);
+  plan_end_impl(a.p, a.d0, a.d1, a.colsq, a.o, nullptr);
 }
 
 int launch_plan_init(DevPlan* p, const int32_t* eA, const double* D, double* lam_prev, const PlanOpts& o,
-                     double omega_prev, cudaStream_t s) {
+                     double omega_prev, uint32_t* rank, cudaStream_t s) {
   size_t sm = sort_smem(o.n);
   if (record_launch(LK_PLAN_INIT, PlanArgs{p, eA, nullptr, D, lam_prev, o, omega_prev, 1u}, 1, PT, sm)) return FRX_OK;
-  k_plan_init<<<1, PT, sm, s>>>(p, eA, D, lam_prev, o, omega_prev);
+  if (rank) FRX_TRY(launch_rank_keys(nullptr, D, o.n, rank, s));   // the plan is reset below: no done test
+  k_plan_init<<<1, PT, sm, s>>>(p, eA, D, lam_prev, o, omega_prev, rank);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;
@@ -575,11 +621,12 @@ int launch_plan_u(DevPlan* p, const int32_t* rho, const int32_t* eta, const Plan
 }
 
 int launch_plan_end(DevPlan* p, const double* lam_new, double* lam_prev, const double* colsq, const PlanOpts& o,
-                    cudaStream_t s) {
+                    uint32_t* rank, cudaStream_t s) {
   size_t sm = sort_smem(o.n);
   if (record_launch(LK_PLAN_END, PlanArgs{p, nullptr, nullptr, lam_new, lam_prev, o, 0.0, 1u, colsq}, 1, PT, sm))
     return FRX_OK;
-  k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, colsq, o);
+  if (rank) FRX_TRY(launch_rank_keys(p, lam_new, o.n, rank, s));
+  k_plan_end<<<1, PT, sm, s>>>(p, lam_new, lam_prev, colsq, o, rank);
   count_launches(1);
   FRX_CUDA_TRY(cudaGetLastError());
   return FRX_OK;

@@ -175,6 +175,19 @@ def test_refine_step_parity_several_tiles(api, n, cond, variant):
     _step_compare(api, A, X0, D0, 1e-12, orf.Options(), api.Options())
 
 
+@pytest.mark.parametrize("n", [300, 1100])
+def test_refine_step_parity_repeated_estimates(api, n):
+    # the smallest gap of the starting estimates (Sec. 4.1, in beta) taken over an order of D
+    # with exactly repeated values: the device ranks the estimates with many blocks and places
+    # them by rank, ties broken by index, and the plan must match the oracle's sorted gaps
+    A, X0, D0, lam = synth.refine_workload(n, 1e4, "indefinite", case=n + 7)
+    D0 = D0.copy()
+    D0[5::11] = D0[4::11][: len(D0[5::11])]            # exact duplicates next to each other
+    D0[n // 2] = D0[3]                                  # and one far from its twin
+    assert len(np.unique(D0)) < n
+    _step_compare(api, A, X0, D0, 1e-12, orf.Options(), api.Options())
+
+
 @pytest.mark.parametrize("xp", [3, 7])
 def test_refine_step_parity_previous_study_form(api, xp):
     # X kept at xp digit planes (no truncation rule): beta = 54 - 8 xp, below 3 for xp = 7
