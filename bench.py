@@ -520,6 +520,18 @@ def run_batched(args):
     stats = {}
     for i in infos:
         stats[i["status_name"]] = stats.get(i["status_name"], 0) + 1
+    # algorithmic work of the batch's slice products: every product of matrix b is an n_b x n_b x
+    # n_b digit-plane GEMM (2 n_b^3 operations); its rate over the whole step is a lower bound on
+    # the grouped tensor-core launches' own rate (which the step shares with everything else)
+    gemm_ops = float(sum(int(i["products"]) * 2.0 * float(p[0].shape[0]) ** 3 for i, p in zip(infos, probs)))
+    pk, src = peaks()
+    peak = pk.get("bf16_tflops")
+    step_rate = gemm_ops / (ms * 1e-3) / 1e12
+    slice_work = {"tflop_per_step": gemm_ops / 1e12, "tflops_over_whole_step": step_rate,
+                  "peak": peak, "peak_source": src,
+                  "fraction_of_peak_over_whole_step": step_rate / peak if peak else None,
+                  "note": "lower bound on the grouped slice-product launches' rate: the step also holds the "
+                          "element-wise, slicing and plan stages"}
 
     # end to end through the public API: every step copies all matrices, starting vectors and
     # estimates in from pinned host memory and the refined X, D back
@@ -585,6 +597,7 @@ def run_batched(args):
                    "l2": (f"inputs larger than L2 (A, X and D of the batch: "
                           f"{(sum(p[0].nbytes + p[1].nbytes + p[2].nbytes for p in probs)) / 1e6:.0f} MB > 129 MB)")},
         "statuses": stats, "gpu_launches": prof["kernel_launches"],
+        "slice_product_work": slice_work,
         "e2e": e2e,
         "tile": {"used": api.last_tile(), "policy": "autotuned" if args.tile == "auto" else "forced",
                  "tuner": api.tune_stats()},

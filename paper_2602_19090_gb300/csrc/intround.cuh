@@ -15,14 +15,23 @@ namespace frx {
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
-__device__ __forceinline__ int bitlen_u64(u64 a) { return 64 - __clzll((long long)a); }
-
-__device__ __forceinline__ int bitlen_u128(u128 a) {
-  u64 hi = (u64)(a >> 64);
-  return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)(u64)a);
+// leading zeros of a nonzero 64-bit word (host and device)
+__host__ __device__ __forceinline__ int clz64(u64 a) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)a);
+#else
+  return a ? __builtin_clzll(a) : 64;
+#endif
 }
 
-__device__ __forceinline__ u128 abs_i128(i128 v) { return v < 0 ? (u128)0 - (u128)v : (u128)v; }
+__host__ __device__ __forceinline__ int bitlen_u64(u64 a) { return 64 - clz64(a); }
+
+__host__ __device__ __forceinline__ int bitlen_u128(u128 a) {
+  u64 hi = (u64)(a >> 64);
+  return hi ? 128 - clz64(hi) : 64 - clz64((u64)a);
+}
+
+__host__ __device__ __forceinline__ u128 abs_i128(i128 v) { return v < 0 ? (u128)0 - (u128)v : (u128)v; }
 
 // an upper bound on the bit length of |v| (exact for v >= 0, at most one more for v < 0):
 // the bit length of v XOR its sign mask, plus one for negatives
@@ -42,7 +51,7 @@ __device__ __forceinline__ i128 mul_i64(i64 a, i64 b) {
 // Bits of RN-even((-1)^neg * a * 2^c) for a > 0.  False when the result is subnormal or
 // overflows (the caller then takes a general path).  Works on the 64-bit halves: the top
 // 64 bits of a and a sticky bit for the rest decide the rounding exactly.
-__device__ __forceinline__ bool rn_bits(u128 a, bool neg, int c, u64& bits) {
+__host__ __device__ __forceinline__ bool rn_bits(u128 a, bool neg, int c, u64& bits) {
   const u64 hi = (u64)(a >> 64), lo = (u64)a;
   int E;
   u64 mant;
@@ -83,15 +92,57 @@ __device__ __forceinline__ bool rn_bits(u128 a, bool neg, int c, u64& bits) {
 }
 
 // out = RN-even(S * 2^c); false (out untouched) for a subnormal or overflowing result.
-__device__ __forceinline__ bool rn_scaled(i128 S, int c, double& out) {
+__host__ __device__ __forceinline__ bool rn_scaled(i128 S, int c, double& out) {
   if (S == 0) {
     out = 0.0;
     return true;
   }
   u64 b;
   if (!rn_bits(abs_i128(S), S < 0, c, b)) return false;
-  out = __longlong_as_double((long long)b);
+  out = bits_to_double(b);
   return true;
+}
+
+// RN(x1 + N 2^c) for the usual update, a correction far below x1 whose sum stays in x1's
+// binade: with x1 = P 2^q (P a signed 53-bit integer) and s = q - c >= 1, the sum is
+// (P + floor(N / 2^s) + f) 2^q with 0 <= f < 1; bit s - 1 of N and the bits below it (sticky)
+// decide round-half-even to an integer R, and R 2^q is the correctly rounded sum when
+// 2^52 < |P + floor(N / 2^s)| and |R| < 2^53.  False otherwise (the caller takes the exact
+// 128-bit path): x1 zero, subnormal or not finite, s outside [1, 127], or a sum that may leave
+// the binade.
+__host__ __device__ __forceinline__ bool add_on_grid_rn(double x1, i128 N, int c, double& out) {
+  const u64 b = double_to_bits(x1);
+  const int be = (int)((b >> 52) & 0x7ff);
+  const int s = be - 1075 - c;
+  if (be == 0 || be == 0x7ff || s < 1 || s > 127) return false;
+  const i128 T2 = N >> (s - 1);                        // floor(N / 2^(s-1))
+  const i64 t2 = (i64)T2;
+  if ((i128)t2 != T2 || t2 > (1ll << 60) || t2 < -(1ll << 60)) return false;
+  const bool sticky = s > 1 && ((u128)N << (129 - s)) != 0;
+  const i64 m = (i64)((b & ((1ull << 52) - 1)) | (1ull << 52));
+  const i64 F = ((b >> 63) ? -m : m) + (t2 >> 1);        // P + floor(N / 2^s)
+  const i64 R = F + ((t2 & 1) && (sticky || (F & 1)) ? 1 : 0);
+  const u64 aF = F < 0 ? (u64)0 - (u64)F : (u64)F, aR = R < 0 ? (u64)0 - (u64)R : (u64)R;
+  if (aF <= (1ull << 52) || aR >= (1ull << 53)) return false;
+  out = bits_to_double((R < 0 ? (1ull << 63) : 0ull) | ((u64)be << 52) | (aR & ((1ull << 52) - 1)));
+  return true;
+}
+
+// RN(x1 + N 2^c) exactly in 128-bit integers; false when the aligned sum would not fit
+// or the result leaves the normal range
+__host__ __device__ __forceinline__ bool add_exact_rn(double x1, i128 N, int c, double& out) {
+  if (is_zero(x1)) return rn_scaled(N, c, out);
+  i64 P;
+  int q;
+  decompose(x1, P, q);
+  const int bn = N == 0 ? 0 : bitlen_u128(abs_i128(N));
+  const int d = q - c;
+  if (d >= 0) {
+    if (d > 72 || bn > 125) return false;
+    return rn_scaled(((i128)P << d) + N, c, out);
+  }
+  if (bn - d > 125) return false;
+  return rn_scaled((i128)P + (N << (-d)), q, out);
 }
 
 // Single-precision value of D * 2^q truncated to 24 bits (for sums of squares that only

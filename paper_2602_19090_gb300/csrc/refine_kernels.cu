@@ -976,48 +976,6 @@ __device__ __noinline__ double update_general(const UpdateArgs& a, double x1, in
   return __dadd_rn(c2.h, cl);
 }
 
-// RN(x1 + N 2^c) for the usual update, a correction far below x1 whose sum stays in x1's
-// binade: with x1 = P 2^q (P a signed 53-bit integer) and s = q - c >= 1, the sum is
-// (P + floor(N / 2^s) + f) 2^q with 0 <= f < 1; bit s - 1 of N and the bits below it (sticky)
-// decide round-half-even to an integer R, and R 2^q is the correctly rounded sum when
-// 2^52 < |P + floor(N / 2^s)| and |R| < 2^53.  False otherwise (the caller takes the exact
-// 128-bit path): x1 zero, subnormal or not finite, s outside [1, 127], or a sum that may leave
-// the binade.
-__device__ __forceinline__ bool add_on_grid_rn(double x1, i128 N, int c, double& out) {
-  const u64 b = double_to_bits(x1);
-  const int be = (int)((b >> 52) & 0x7ff);
-  const int s = be - 1075 - c;
-  if (be == 0 || be == 0x7ff || s < 1 || s > 127) return false;
-  const i128 T2 = N >> (s - 1);                        // floor(N / 2^(s-1))
-  const i64 t2 = (i64)T2;
-  if ((i128)t2 != T2 || t2 > (1ll << 60) || t2 < -(1ll << 60)) return false;
-  const bool sticky = s > 1 && ((u128)N << (129 - s)) != 0;
-  const i64 m = (i64)((b & ((1ull << 52) - 1)) | (1ull << 52));
-  const i64 F = ((b >> 63) ? -m : m) + (t2 >> 1);        // P + floor(N / 2^s)
-  const i64 R = F + ((t2 & 1) && (sticky || (F & 1)) ? 1 : 0);
-  const u64 aF = F < 0 ? (u64)0 - (u64)F : (u64)F, aR = R < 0 ? (u64)0 - (u64)R : (u64)R;
-  if (aF <= (1ull << 52) || aR >= (1ull << 53)) return false;
-  out = __longlong_as_double((long long)((R < 0 ? (1ull << 63) : 0ull) | ((u64)be << 52) | (aR & ((1ull << 52) - 1))));
-  return true;
-}
-
-// RN(x1 + N 2^c) exactly in 128-bit integers; false when the aligned sum would not fit
-// or the result leaves the normal range
-__device__ __forceinline__ bool add_exact_rn(double x1, i128 N, int c, double& out) {
-  if (is_zero(x1)) return rn_scaled(N, c, out);
-  i64 P;
-  int q;
-  decompose(x1, P, q);
-  const int bn = N == 0 ? 0 : bitlen_u128(abs_i128(N));
-  const int d = q - c;
-  if (d >= 0) {
-    if (d > 72 || bn > 125) return false;
-    return rn_scaled(((i128)P << d) + N, c, out);
-  }
-  if (bn - d > 125) return false;
-  return rn_scaled((i128)P + (N << (-d)), q, out);
-}
-
 // (xn - xo)^2 into a single-precision partial (scaled by 2^64) when the two exponents are
 // close, else into an FP64 partial; only the norm estimate of the stopping test reads it
 __device__ __forceinline__ void accumulate_dx2(double xn, double xo, float& d2f, double& d2d) {

@@ -1,0 +1,71 @@
+// Host-side check of the roundings the update kernel uses for X <- RN(X1 + U) (Alg. 1 line 6):
+// add_on_grid_rn (the usual case, on x1's grid) and add_exact_rn (exact 128-bit sum), compiled
+// as host code from the library's own header.  Random, tie and binade-edge inputs; where both
+// succeed their bits must agree, and every case the on-grid form accepts is written out so that
+// the test can check it against exact rational rounding.
+//
+// usage: host_rounding_check CASES SEED DUMPFILE MAXDUMP
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+
+#include "intround.cuh"
+
+using namespace frx;
+
+int main(int argc, char** argv) {
+  if (argc != 5) {
+    std::fprintf(stderr, "usage: %s CASES SEED DUMPFILE MAXDUMP\n", argv[0]);
+    return 2;
+  }
+  const long long cases = std::atoll(argv[1]);
+  std::mt19937_64 g(std::strtoull(argv[2], nullptr, 10));
+  FILE* df = std::fopen(argv[3], "w");
+  const long long maxdump = std::atoll(argv[4]);
+  if (!df) return 2;
+  long long grid = 0, both = 0, mismatches = 0, dumped = 0, ties = 0;
+  for (long long it = 0; it < cases; ++it) {
+    // x1: random sign, binade in [-20, 5]; some exact powers of two and values next to them
+    u64 mant = g() & ((1ull << 52) - 1);
+    const int kind = (int)(g() % 8);
+    if (kind == 0) mant = 0;
+    if (kind == 1) mant = (1ull << 52) - 1 - g() % 4;
+    if (kind == 2) mant = g() % 4;
+    const int e = (int)(g() % 26) - 20;
+    const u64 b = ((u64)(e + 1023) << 52) | mant | ((g() & 1) ? (1ull << 63) : 0ull);
+    const double x1 = bits_to_double(b);
+    // N: up to 118 bits, either sign; s = q - c from -6 to 133 (q = e - 52, x1's ulp exponent)
+    const int w = 1 + (int)(g() % 118);
+    u128 mag = ((u128)g() << 64) | (u128)g();
+    mag &= (((u128)1) << w) - 1;
+    i128 N = (g() & 1) ? -(i128)mag : (i128)mag;
+    const int s = (int)(g() % 140) - 6;
+    if (g() % 4 == 0 && s >= 1 && s < 120) {   // an exact tie: bit s-1 set, nothing below
+      N &= ~((((i128)1) << s) - 1);
+      N |= ((i128)1) << (s - 1);
+      if (g() & 1) N = -N;
+      ++ties;
+    }
+    const int c = (e - 52) - s;
+    double r1 = 0.0, r2 = 0.0;
+    const bool ok1 = add_on_grid_rn(x1, N, c, r1);
+    const bool ok2 = add_exact_rn(x1, N, c, r2);
+    if (ok1) {
+      ++grid;
+      if (dumped < maxdump) {
+        std::fprintf(df, "%016llx %d %016llx %016llx %016llx\n", (unsigned long long)b, c,
+                     (unsigned long long)((u128)N >> 64), (unsigned long long)(u64)N,
+                     (unsigned long long)double_to_bits(r1));
+        ++dumped;
+      }
+      if (ok2) {
+        ++both;
+        if (double_to_bits(r1) != double_to_bits(r2)) ++mismatches;
+      }
+    }
+  }
+  std::fclose(df);
+  std::printf("cases %lld ties %lld grid %lld both %lld mismatches %lld dumped %lld\n", cases, ties, grid, both,
+              mismatches, dumped);
+  return mismatches != 0;
+}

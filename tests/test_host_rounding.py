@@ -1,0 +1,57 @@
+"""The update's roundings of X1 + U (Alg. 1 line 6, one rounding), checked on the host.
+
+`tests/host_rounding_check.cu` compiles the library's rounding helpers as host code (nvcc, no GPU
+needed) and runs them on random, tie and binade-edge inputs.  Where the on-grid form and the
+exact 128-bit form both succeed their bits must agree, and every result the on-grid form
+returns must equal the correctly rounded value of x1 + N 2^c computed with Python's exact
+rationals (float(Fraction) rounds to nearest, ties to even).
+"""
+import os
+import shutil
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bits_to_float(u):
+    import struct
+    return struct.unpack("<d", struct.pack("<Q", u))[0]
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = tmp_path_factory.mktemp("hostround") / "host_rounding_check"
+    cmd = [nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
+           "-I", os.path.join(ROOT, "paper_2602_19090_gb300", "csrc"),
+           os.path.join(ROOT, "tests", "host_rounding_check.cu"), "-o", str(out)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return str(out)
+
+
+def test_on_grid_rounding_matches_exact_path_and_rationals(checker, tmp_path):
+    dump = tmp_path / "grid_cases.txt"
+    r = subprocess.run([checker, "2000000", "20261204", str(dump), "40000"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    fields = dict(zip(r.stdout.split()[0::2], map(int, r.stdout.split()[1::2])))
+    assert fields["mismatches"] == 0
+    assert fields["both"] > 100000 and fields["ties"] > 100000      # both paths and exact ties exercised
+    checked = 0
+    for line in dump.read_text().split("\n"):
+        if not line:
+            continue
+        xb, c, hi, lo, rb = line.split()
+        x1 = _bits_to_float(int(xb, 16))
+        N = (int(hi, 16) << 64) | int(lo, 16)
+        if N >= 1 << 127:
+            N -= 1 << 128
+        exact = Fraction(x1) + Fraction(N) * Fraction(2) ** int(c)
+        assert float(exact) == _bits_to_float(int(rb, 16)), line
+        checked += 1
+    assert checked == fields["dumped"] and checked >= 20000
