@@ -292,6 +292,7 @@ struct SingleSrc {
     serp = run.units <= SERPENTINE_MAX_ROUNDS * P;
     rnd = 0;
   }
+  __device__ void prefetch_next() {}
   // the next unit of this CTA in round order
   __device__ bool next(int& lu) {
     while ((long long)rnd * P < run.units) {
@@ -313,10 +314,64 @@ constexpr int MAX_GROUPED = 2048;   // problems of one grouped launch
 // run of units with an equal share of the slice-pair work was measured slower on a batch of
 // 256 matrices of n in [32, 512]: 37.9 against 26.5 ms, since the small problems' many short
 // units carry a fixed epilogue cost that the work measure leaves out.)
+// The per-unit fields of one problem of a grouped launch, kept in shared memory so that a CTA
+// moving to another problem's unit (most units, for small problems) reads them there instead
+// of following the problem's argument and plan pointers through global memory.
+struct RunRec {
+  int M, N;
+  void* out;
+  int64_t ogs, ldo;
+  int* flags;
+  const int* gorder;
+  int nkb, kL, kR, tmax, gs, groups, ntm, ntn, units;
+};
+constexpr int RUN_CACHE = 256;   // problems whose records fit beside the stages
+
+__device__ __forceinline__ void rec_of(const TcRun& r, const int* g, RunRec& c) {
+  c.M = (int)r.M;
+  c.N = (int)r.N;
+  c.out = r.out;
+  c.ogs = r.ogs;
+  c.ldo = r.ldo;
+  c.flags = r.flags;
+  c.gorder = g;
+  c.nkb = r.nkb;
+  c.kL = r.kL;
+  c.kR = r.kR;
+  c.tmax = r.tmax;
+  c.gs = r.gs;
+  c.groups = r.groups;
+  c.ntm = r.ntm;
+  c.ntn = r.ntn;
+  c.units = r.units;
+}
+
+__device__ __forceinline__ void run_of_rec(const RunRec& c, TcRun& r, const int*& g) {
+  r.M = c.M;
+  r.N = c.N;
+  r.nkb = c.nkb;
+  r.kL = c.kL;
+  r.kR = c.kR;
+  r.tmax = c.tmax;
+  r.gs = c.gs;
+  r.groups = c.groups;
+  r.ntm = c.ntm;
+  r.ntn = c.ntn;
+  r.units = c.units;
+  r.nsplit = 1;
+  r.kcb = c.nkb;
+  r.out = c.out;
+  r.ogs = c.ogs;
+  r.ldo = c.ldo;
+  r.flags = c.flags;
+  g = c.gorder;
+}
+
 template <int BN, bool W32>
 struct GroupedSrc {
   const TcProblem* probs;
   const int* prefix;   // shared: units of problems 0..m-1
+  const RunRec* recs;  // shared records of every problem, or nullptr (more than RUN_CACHE)
   int count;
   int cur;             // problem `run` currently describes
   TcRun run;
@@ -326,18 +381,33 @@ struct GroupedSrc {
   int* flags0;
   int rnd;
   __device__ void begin() { rnd = 0; }
-  __device__ bool next(int& lu) {
-    const int u = (int)blockIdx.x + rnd++ * (int)gridDim.x;
-    if (u >= prefix[count]) return false;
-    int lo = 0, hi = count - 1;   // last m with prefix[m] <= u
+  // problem of global unit u (last m with prefix[m] <= u)
+  __device__ int problem_of(int u) const {
+    int lo = 0, hi = count - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (prefix[mid] <= u) lo = mid;
       else hi = mid - 1;
     }
+    return lo;
+  }
+  // the producer asks for the tensor maps of this CTA's next unit ahead of its loads
+  __device__ void prefetch_next() {
+    const int u = (int)blockIdx.x + rnd * (int)gridDim.x;
+    if (u >= prefix[count]) return;
+    const int m = problem_of(u);
+    if (m == cur) return;
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&probs[m].mapL) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&probs[m].mapR) : "memory");
+  }
+  __device__ bool next(int& lu) {
+    const int u = (int)blockIdx.x + rnd++ * (int)gridDim.x;
+    if (u >= prefix[count]) return false;
+    const int lo = problem_of(u);
     if (lo != cur) {
       cur = lo;
-      tc_run_of<BN, W32, false>(probs[lo].a, run, gorder);
+      if (recs) run_of_rec(recs[lo], run, gorder);
+      else tc_run_of<BN, W32, false>(probs[lo].a, run, gorder);
       mapL = &probs[lo].mapL;
       mapR = &probs[lo].mapR;
     }
@@ -399,6 +469,7 @@ __device__ __forceinline__ void tc_body(Src& src) {
       src.begin();
       int lu;
       while (ok && src.next(lu)) {
+        src.prefetch_next();
         const TcRun& a = src.run;
         const int* gorder = src.gorder;
         const int tiles = a.ntm * a.ntn;
@@ -662,10 +733,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_plane_gemm_tc_grouped(const TcProblem* __restrict__ probs, int count) {
   __shared__ int prefix[MAX_GROUPED + 1];
   __shared__ int warp_tot[NUM_THREADS / 32];
+  __shared__ RunRec recs[RUN_CACHE];
+  const bool cached = count <= RUN_CACHE;
   for (int m = threadIdx.x; m < count; m += NUM_THREADS) {
     TcRun r;
     const int* g;
-    prefix[m] = tc_run_of<BN_, W32, false>(probs[m].a, r, g) ? r.units : 0;
+    const bool live = tc_run_of<BN_, W32, false>(probs[m].a, r, g);
+    prefix[m] = live ? r.units : 0;
+    if (cached && live) rec_of(r, g, recs[m]);
   }
   __syncthreads();
   block_exclusive_scan(prefix, count, warp_tot);
@@ -673,6 +748,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   GroupedSrc<BN_, W32> src;
   src.probs = probs;
   src.prefix = prefix;
+  src.recs = cached ? recs : nullptr;
   src.count = count;
   src.cur = -1;
   src.gorder = nullptr;
