@@ -515,8 +515,8 @@ __device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
 __device__ __forceinline__ i128 shift_down(i128 v, int d) { return d >= 127 ? (i128)0 : (v >> d); }
 
 // The residual's first pass streams x_i, eA_i and the planes through a two-stage copy
-// pipeline placed after the V column in dynamic shared memory; blocks of 256 threads while the
-// column and the stages fit, else 128.
+// pipeline placed after the V column in dynamic shared memory (the second pass streams x_i and
+// eA_i through it again); blocks of 256 threads while the column and the stages fit, else 128.
 constexpr int PIPE_R = 2;
 constexpr size_t RES_SMEM_MAX = RESIDUAL_SMEM_MAX;
 
@@ -734,9 +734,26 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
   const bool safe = dmin >= -60 && dmax <= 60 && bmmax + bL + (dmax > 0 ? dmax : 0) <= 125 &&
                     bnmax + (dmin < 0 ? -dmin : 0) <= 125 && bnmax <= 125 && bmmax + bL <= 125;
   u64 mx = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double xi = x[i];
-    const int ei = a.eA[i];
+  // x_i and eA_i come through the first pass's stages again, one trip ahead
+  auto issue2 = [&](int64_t i, int st2) {
+    const bool ok = i < n;
+    const int64_t ic = ok ? i : 0;
+    cp_async8(sx + st2 * B + tid, x + ic, ok);
+    cp_async4(si + st2 * (1 + MP_RESIDUAL) * B + tid, a.eA + ic, ok);
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int q = 0; q < PIPE_R - 1; ++q) issue2(tid + (int64_t)q * B, q);
+  int sc = 0, sci = PIPE_R - 1;   // stage of the current trip, stage the next copies go to
+  for (int64_t i = tid, i0 = 0; i0 < n; i += B, i0 += B) {
+    issue2(i + (int64_t)(PIPE_R - 1) * B, sci);
+    sci = sci == PIPE_R - 1 ? 0 : sci + 1;
+    cp_async_wait<PIPE_R - 1>();
+    const int cur = sc;
+    sc = sc == PIPE_R - 1 ? 0 : sc + 1;
+    if (i >= n) continue;
+    const double xi = sx[cur * B + tid];
+    const int ei = si[cur * (1 + MP_RESIDUAL) * B + tid];
     const i128 N = ncol[i];
     const i128 ML = mul_i64(grid_mantissa(xi, gj), L);
     const int c = ei == EZERO ? gq : ei + cbase;
@@ -757,6 +774,7 @@ __device__ __forceinline__ void residual_body(ResidualArgs a, unsigned bx, unsig
     const u64 ab = double_to_bits(res) & 0x7fffffffffffffffull;
     mx = ab > mx ? ab : mx;
   }
+  cp_async_wait<0>();
   mx = block_max_u64(mx, redu);
   if (threadIdx.x == 0) a.h[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
 }
