@@ -62,3 +62,17 @@ def test_dd_div():
     for i in range(200):
         ex = F(a[i]) / (F(b[i]) + F(bl[i]))
         assert abs(F(q[0][i]) + F(q[1][i]) - ex) <= abs(ex) * F(2) ** -100
+
+
+def test_dd_sum_against_fractions():
+    # the column sums of the residual step (x^T x, x^T v, r_ij) are double-double sums of
+    # double-double terms; the chain of dd additions stays within about 2^-100 of the exact
+    # sum, relative to the sum of the terms' magnitudes
+    g = np.random.default_rng(6)
+    h = g.standard_normal((64, 9))
+    l = h * 2.0 ** -58 * g.standard_normal((64, 9))
+    sh, sl = dd.dd_sum(h, l, axis=0)
+    for j in range(9):
+        ex = sum((F(h[k, j]) + F(l[k, j]) for k in range(64)), F(0))
+        mag = sum((abs(F(h[k, j])) for k in range(64)), F(0))
+        assert abs(F(sh[j]) + F(sl[j]) - ex) <= mag * F(2) ** -100

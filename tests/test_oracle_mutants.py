@@ -69,6 +69,23 @@ MUTANTS = [
      "subspace error: columns of X^ not orthonormalised"),
     ("truth", "return float(np.linalg.norm(P, 2))", "return float(np.linalg.norm(P))",
      "subspace error: Frobenius norm for the 2-norm"),
+    ("ddarith", "    q2 = rh / bh\n", "    q2 = 0.0 * rh / bh\n", "dd division: Newton correction dropped"),
+    ("ddarith", "sh, sl = dd_add(sh, sl, h[k], l[k])", "sh, sl = dd_add(sh, sl, h[k], 0.0 * l[k])",
+     "dd sum: low words dropped"),
+    ("refine", "b = floor_log2(q) if opts.beta_rounding == \"floor\" else ceil_log2f(q)",
+     "b = ceil_log2f(q) if opts.beta_rounding == \"floor\" else floor_log2(q)", "beta: ceiling for the floor"),
+    ("refine", "return (2 ** 31 - 1) // (n * oz.DIGIT_MAX * oz.DIGIT_MAX)",
+     "return (2 ** 32 - 1) // (n * oz.DIGIT_MAX * oz.DIGIT_MAX)", "int32 plane bound: 2^32 for 2^31"),
+    ("refine", "xi=float(min(kmax * kmax, n))", "xi=float(min(kmax, n))", "sparse rule: k for k^2"),
+    ("refine", "53 - beta + ceil_log2_int(kmax)", "53 - beta + ceil_log2_int(kmax + 1)",
+     "sparse rule: alpha from k + 1"),
+    ("refine", "beta = 54 - oz.DIGIT_BITS * opts.x_planes", "beta = 53 - oz.DIGIT_BITS * opts.x_planes",
+     "previous-study form: beta off by one"),
+    ("refine", "        X1 = X - resid\n", "        X1 = X\n", "previous-study form: X not cut to its planes"),
+    ("refine", "sX = -(-(54 - beta) // oz.DIGIT_BITS)", "sX = (54 - beta) // oz.DIGIT_BITS",
+     "s_X: floor for the ceiling"),
+    ("ozaki", "for s in range(1, kR + 1) if r + s <= T]", "for s in range(1, kR) if r + s <= T]",
+     "pair set: last plane of the right operand dropped"),
 ]
 
 

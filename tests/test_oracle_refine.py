@@ -324,6 +324,44 @@ def test_sparse_rule_is_the_paper_formula():
     assert p["beta"] > rf.plan(A, X0, D0, delta, rf.Options(xi=1.0))["beta"]
 
 
+def test_previous_study_step_works_on_x_at_its_planes():
+    # the iteration itself (not only its plan) works on X kept at x_planes digit planes: with
+    # three planes X^(1) is X rounded to the tau grid of beta = 30, exactly representable by
+    # its three planes
+    A, X0, D0 = synth.workload0()
+    _, _, info = rf.step(A, X0, D0, 1e-14, rf.Options(x_planes=3))
+    f = info["plan"]["f"]
+    T, _ = oz.tau_truncate_cols(X0, 30, f)
+    assert np.array_equal(info["X1"], T)
+    assert not np.any(oz.slice_cols(info["X1"], 3, f)[2])
+
+
+def test_sparse_rule_reduces_to_the_dense_form_when_k_is_sqrt_n():
+    # Sec. 4 replaces sqrt n by min(k, sqrt n) in beta and ceil(log2 sqrt n) by ceil(log2 k) in
+    # alpha.  A 64 x 64 matrix with exactly k = 8 = sqrt 64 nonzeros in every row (eight dense
+    # symmetric 8 x 8 blocks) must get the beta and alpha of the dense n delta form of Sec. 4.1.
+    g = np.random.default_rng(11)
+    A = np.zeros((64, 64))
+    for b in range(8):
+        M = g.standard_normal((8, 8))
+        A[8 * b:8 * b + 8, 8 * b:8 * b + 8] = M + M.T + 20.0 * np.eye(8) * (b + 1)
+    assert np.all(np.count_nonzero(A, axis=1) == 8)
+    lam, Q = np.linalg.eigh(A)
+    X0 = Q + 1e-9 * g.standard_normal(Q.shape)
+    for delta in (1e-10, 1e-13):
+        ps = rf.plan(A, X0, lam, delta, rf.Options(sparse_rule=True))
+        pd = rf.plan(A, X0, lam, delta, rf.Options(xi=None))
+        assert ps["beta"] == pd["beta"] and ps["alpha"] == pd["alpha"]
+
+
+def test_int32_plane_bound_is_the_largest_exact_count():
+    # k anti-diagonal pairs of digit products (|d| <= 128, so |product| <= 2^14) summed over n
+    # terms fit int32 exactly while k n 2^14 <= 2^31 - 1; int32_planes(n) is the largest such k
+    for n in (1, 7, 64, 1000, 4096, 8192, 12288):
+        k = rf.int32_planes(n)
+        assert k * n * 128 * 128 <= 2 ** 31 - 1 < (k + 1) * n * 128 * 128
+
+
 def _plan_case(lam_prev, omega_prev=0.0, col_max=0.25, xi=None):
     # n = 4, X = col_max * I: every column maximum is col_max, so f_j = ceil(log2 col_max);
     # A = I (only its exponents and nonzero counts enter the plan); the n delta form of Sec. 4.1
