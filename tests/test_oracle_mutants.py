@@ -86,6 +86,20 @@ MUTANTS = [
      "s_X: floor for the ceiling"),
     ("ozaki", "for s in range(1, kR + 1) if r + s <= T]", "for s in range(1, kR) if r + s <= T]",
      "pair set: last plane of the right operand dropped"),
+    ("ddarith", "    y = b - (x - a)\n", "    y = b + (x - a)\n", "fast TwoSum: wrong sign"),
+    ("ddarith", "    pe = pe + al * b\n", "    pe = pe\n", "dd * d: low word dropped"),
+    ("ddarith", "            e = e + Ll[:, k:k + 1] * b\n", "            e = e\n", "dd matmul: low words of L dropped"),
+    ("ddarith", "    hi = c - (c - a)\n", "    hi = c - (c + a)\n", "Veltkamp split: wrong sign"),
+    ("ozaki", "e = np.where(fr == 0.5, ex - 1, ex).astype(np.int64)", "e = ex.astype(np.int64)",
+     "exponent: powers of two one too high"),
+    ("ozaki", "return ceil_log2(np.max(np.abs(M), axis=1))", "return ceil_log2(np.max(M, axis=1))",
+     "exponent: absolute value dropped"),
+    ("ozaki", "0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + 54 - DIGIT_BITS * r))",
+     "np.ldexp(1.0, np.where(e == EZERO, 0, e + 54 - DIGIT_BITS * r))", "sigma trick: 0.75 dropped"),
+    ("ozaki", "            lo[i, j] = math.fsum(terms + [-h])\n", "            lo[i, j] = 0.0\n",
+     "exact recombination: low word dropped"),
+    ("ozaki", "T = 2 * k if mode == \"full\" else k + 1", "T = 2 * k if mode == \"full\" else k",
+     "triangular set: last anti-diagonal dropped"),
 ]
 
 
