@@ -100,6 +100,12 @@ MUTANTS = [
      "exact recombination: low word dropped"),
     ("ozaki", "T = 2 * k if mode == \"full\" else k + 1", "T = 2 * k if mode == \"full\" else k",
      "triangular set: last anti-diagonal dropped"),
+    ("ozaki", "        v = np.max(np.abs(res), axis=1) if M.shape[1] else np.zeros(M.shape[0])\n",
+     "        v = np.max(np.abs(M), axis=1) if M.shape[1] else np.zeros(M.shape[0])\n",
+     "adaptive slicing: no rescan of the residual"),
+    ("ozaki", "0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + alpha)))",
+     "0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + alpha + 1)))", "adaptive slicing: sigma off by one"),
+    ("ozaki", "        res = res - sl\n", "        res = res + sl\n", "adaptive slicing: residual wrong sign"),
 ]
 
 
