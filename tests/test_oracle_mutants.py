@@ -106,6 +106,25 @@ MUTANTS = [
     ("ozaki", "0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + alpha)))",
      "0.75 * np.ldexp(1.0, np.where(e == EZERO, 0, e + alpha + 1)))", "adaptive slicing: sigma off by one"),
     ("ozaki", "        res = res - sl\n", "        res = res + sl\n", "adaptive slicing: residual wrong sign"),
+    ("refine", "omega = 2.0 * (math.sqrt", "omega = (math.sqrt", "cluster threshold: factor 2 dropped"),
+    ("refine", " + p[\"Lam\"] * float(np.linalg.norm(r)))", ")", "cluster threshold: max|lam| ||r|| term dropped"),
+    ("refine", "int(np.max(h)), delta * g, opts.k_cap)", "int(np.max(h)), delta, opts.k_cap)",
+     "k_W: gap factor dropped"),
+    ("refine", "info[\"step\"] > 0.5 * prev_step", "info[\"step\"] > prev_step", "stagnation: growth for failure to halve"),
+    ("refine", "if noncontract >= 2:", "if noncontract >= 1:", "stagnation: one failing step stops"),
+    ("refine", "/ (xs * g_new) if", "/ (xs) if", "stopping test: gap dropped"),
+    ("refine", "g_new, Lam_new = min_gap(lam, omega)", "g_new, Lam_new = min_gap(lam, 0.0)",
+     "stopping test: cluster gaps kept"),
+    ("refine", "    ql = ql + X1 * Vl\n", "    ql = ql\n", "estimates: low word of V dropped"),
+    ("refine", "Res = dd.dd_add(Vh, Vl, -mh, -ml)[0]", "Res = dd.dd_add(Vh, Vl, -mh, 0.0 * ml)[0]",
+     "Res: low word of X1 diag(lam) dropped"),
+    ("refine", "lam = dd.dd_div_dd(dh, dl, nh, nl)[0]", "lam = dh / nh", "estimates: FP64 division"),
+    ("refine", "Up = oz.ozaki_product(X1, E, kU, kU, kU + 1,", "Up = oz.ozaki_product(X1, E, kU, kU, kU,",
+     "U: last anti-diagonal dropped"),
+    ("refine", "Wp = oz.ozaki_product(X1.T, Res, min(sX, kW), kW, kW + 1,",
+     "Wp = oz.ozaki_product(X1.T, Res, min(sX, kW), kW, kW,", "W: last anti-diagonal dropped"),
+    ("refine", "V = oz.ozaki_product(A, X1, kV, sX, kV + 1,", "V = oz.ozaki_product(A, X1, kV, sX, kV,",
+     "V: last anti-diagonal dropped"),
 ]
 
 

@@ -473,3 +473,77 @@ def test_subspace_error_closed_form():
     Xhat[:, 0] = 3.0 * (c * I[:, 0] + s * I[:, 1])
     Xhat[:, 1] = -s * I[:, 0] + c * I[:, 1]
     assert tr.subspace_error(I, np.zeros((n, n)), Xhat, [0, 1]) <= 1e-15
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_estimates_are_the_correctly_rounded_rayleigh_quotients(seed):
+    # Alg. 1 line 3: lam_i = x_i^T v_i / (1 - r_i) with v_i = A x_i and 1 - r_i = x_i^T x_i,
+    # the Rayleigh quotient of x_i = X^(1)[:, i].  With A's entries small integers, A lies
+    # wholly in its first digit plane, so V holds A X^(1) to double-double accuracy, and the
+    # estimate must be the quotient computed in exact rationals, rounded once.  beta = 2 keeps
+    # X^(1) at 51 bits, so A X^(1) needs more than 53 and V's low words are nonzero.  An
+    # indefinite A and columns unrelated to its eigenvectors make x^T A x cancel (up to several
+    # hundred times smaller than |A x| |x|), which exposes a dropped low word of V or an FP64
+    # division.
+    from fractions import Fraction
+    n = 40
+    rng = np.random.default_rng(seed)
+    B = rng.integers(-50, 51, size=(n, n)).astype(np.float64)
+    A = np.triu(B) + np.triu(B, 1).T
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Xn, lam, info = rf.step(A, Q, np.linalg.eigvalsh(A), 1e-14, rf.Options(beta_override=2))
+    assert info["sX"] <= info["kV"]                    # every pair with A's first plane is kept
+    assert np.count_nonzero(info["Vl"]) > n * n // 2
+    X1 = info["X1"]
+    Af = [[Fraction(int(a)) for a in row] for row in A]
+    for i in range(n):
+        x = [Fraction(float(v)) for v in X1[:, i]]
+        Ax = [sum(Af[r][c] * x[c] for c in range(n)) for r in range(n)]
+        q = sum(x[r] * Ax[r] for r in range(n)) / sum(v * v for v in x)
+        assert lam[i] == float(q), (i, lam[i], float(q))
+
+
+@pytest.mark.parametrize("eps,clustered", [(2.0 ** -10, True), (2.0 ** -8, False)])
+def test_auto_cluster_threshold_worked_by_hand(eps, clustered):
+    # The automatic threshold omega = 2 (||W offdiag||_F + max|lam| ||r||_2) worked by hand on
+    # A = diag(1, 1 + eps, 4) with X mixing the first two axes, x0 = (p, q, 0), x1 = (-q, p, 0),
+    # x2 = e3, p = 1 - 2^-14, q = 2^-8 (beta = 2 keeps X^(1) = X).  With m = p^2 + q^2:
+    #   lam0 = 1 + eps q^2 / m,  lam1 = 1 + eps p^2 / m,  lam2 = 4;  r0 = r1 = 1 - m, r2 = 0;
+    #   w01 = w10 = eps p q (x0^T x1 = 0), every other off-diagonal w is 0;
+    #   omega = 2 (sqrt 2 eps p q + 4 sqrt 2 (1 - m)) = 1.2192e-3 (eps = 2^-10), 1.2515e-3 (2^-8).
+    # lam1 - lam0 = eps (p^2 - q^2) / m = 9.765e-4 lies below omega for eps = 2^-10 (a cluster
+    # pair: e~01 = r01 / 2 = 0) but above omega / 2 and above 2 sqrt 2 (eps p q + 1 - m), and
+    # 3.906e-3 lies above omega for eps = 2^-8 (e~01 = w01 / (lam1 - lam0) = p q m / (p^2 - q^2)).
+    p, q = 1.0 - 2.0 ** -14, 2.0 ** -8
+    m = p * p + q * q
+    A = np.diag([1.0, 1.0 + eps, 4.0])
+    X = np.array([[p, -q, 0.0], [q, p, 0.0], [0.0, 0.0, 1.0]])
+    Xn, lam, info = rf.step(A, X, np.diag(A).copy(), 1e-14, rf.Options(cluster="auto", beta_override=2))
+    assert np.array_equal(info["X1"], X)
+    omega = 2.0 * math.sqrt(2.0) * (eps * p * q + 4.0 * (1.0 - m))
+    assert info["omega"] == pytest.approx(omega, rel=1e-12)
+    assert lam[1] - lam[0] == pytest.approx(eps * (p * p - q * q) / m, rel=1e-12)
+    if clustered:
+        assert info["E"][0, 1] == 0.0 and info["E"][1, 0] == 0.0
+    else:
+        e01 = p * q * m / (p * p - q * q)
+        assert info["E"][0, 1] == pytest.approx(e01, rel=1e-12)
+        assert info["E"][1, 0] == pytest.approx(-e01, rel=1e-12)
+
+
+@pytest.mark.parametrize("k_cap,case", [(5, 0), (5, 1), (5, 2), (4, 0)])
+def test_capped_products_stop_as_stagnated_at_their_floor(k_cap, case):
+    # With every product capped at k_cap digit planes the iteration can only reach an error
+    # floor far above delta (step norms about 4e-8 for 5 planes, 1e-5 for 4).  The stopping
+    # rule for such a run (two consecutive steps that fail to halve) must end it as stagnated
+    # within two iterations of the first step that fails to halve, with no step before that
+    # one failing, rather than run on at the floor until max_iter.
+    A, X0, D0, _ = synth.refine_workload(48, 1e4, case=case, rel=1e-6)
+    hist = []
+    X, lam, info = rf.refine(A, X0, D0, 1e-14, rf.Options(k_cap=k_cap, max_iter=12), history=hist)
+    steps = [h["step"] for h in hist]
+    first = next(i for i in range(1, len(steps)) if steps[i] > 0.5 * steps[i - 1])
+    assert info["status"] == "stagnated"
+    assert info["iters"] <= first + 2
+    assert info["err_est"] > 50 * 1e-14                     # the floor lies far above delta
+    assert min(steps[first:]) > 0.1 * steps[first]         # the run hovers at its floor
