@@ -225,10 +225,9 @@ FRX_API int frx_ozaki_gemm(const double* A, int64_t lda, const double* B, int64_
  *   CUDA_MODULE_LOADING=EAGER when the library is loaded), and it is held until the process
  *   exits.  A caller whose framework later takes all free device memory must therefore make
  *   one call on each device first.  The call allocates nothing.  Every call looks up the
- *   array's device address on the current device (a host-side query); make the first call on
- *   a device before any stream capture begins.  Call with the device that owns `stream`
- *   current.  Like frx_ozaki_gemm, every call synchronises `stream` to read back its status
- *   word.
+ *   array's device address on the current device (a host-side query).  Call with the device
+ *   that owns `stream` current.  Like frx_ozaki_gemm, every call synchronises `stream` to
+ *   read back its status word, so no call may be made while `stream` is being captured.
  *   Sharing: every call uses the same array and leaves its contents behind (each call
  *   clears what it needs).  Calls whose GPU work overlaps (different streams or host
  *   threads without ordering) race on the array: order them, e.g. on one stream.
