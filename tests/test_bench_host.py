@@ -1,6 +1,6 @@
 """Host-side logic of bench.py that needs no GPU: the clock record kept from the timed region,
-the timed oracle refinement, the reference arm's step accounting and the per-workload step
-defaults."""
+the timed oracle refinement, the reference arm's step accounting, the per-workload step
+defaults, the ncu traffic figure's tie to the profiled kernel source and the whole-job rate."""
 import datetime
 import sys
 import time
@@ -91,3 +91,31 @@ def test_reference_arm_reports_the_steps_it_ran(bench, monkeypatch, capsys):
     assert line["impl"] == "reference" and line["steps"] == 2 and line["requested_steps"] == 20
     assert line["ms_per_step"] == 70000.0 and line["value"] == 70.0
     assert line["steps"] * line["ms_per_step"] / 1e3 <= 180
+
+
+def test_gemm_traffic_only_while_the_kernel_source_matches(bench, tmp_path, monkeypatch):
+    # the committed ncu traffic figure is reported only for the kernel it was taken on: a
+    # source whose hash differs from the one in the summary gives null
+    import hashlib
+    import os
+    csrc = tmp_path / "paper_2602_19090_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = b"// kernel source as profiled\n"
+    (csrc / "gemm_tc.cu").write_bytes(src)
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    (tmp_path / "profiles" / "plane_gemm_tc256_n4096_traffic.md").write_text(
+        f"Average per launch (read + write): traffic_bytes_per_launch: 123456\n"
+        f"kernel_source_sha256_16: {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.gemm_traffic() == 123456
+    (csrc / "gemm_tc.cu").write_bytes(src + b"// changed\n")
+    assert bench.gemm_traffic() is None
+    os.remove(csrc / "gemm_tc.cu")
+    assert bench.gemm_traffic() is None
+
+
+def test_job_throughput_is_all_ranks_units_over_the_slowest(bench):
+    # 4 ranks, 10 units each, the slowest rank took 2 s: 40 units / 2 s
+    assert bench.job_throughput(4, 10, 2000.0) == pytest.approx(20.0)
+    assert bench.job_throughput(1, 1, 16.5) == pytest.approx(1e3 / 16.5)
