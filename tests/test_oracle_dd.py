@@ -76,3 +76,25 @@ def test_dd_sum_against_fractions():
         ex = sum((F(h[k, j]) + F(l[k, j]) for k in range(64)), F(0))
         mag = sum((abs(F(h[k, j])) for k in range(64)), F(0))
         assert abs(F(sh[j]) + F(sl[j]) - ex) <= mag * F(2) ** -100
+
+
+def test_dd_add_relative_bound_under_cancellation():
+    # The accurate double-double sum (two TwoSums, a renormalisation, the low error term and a
+    # second renormalisation) has relative error at most 3u^2 + 13u^3, u = 2^-53 (Joldes,
+    # Muller and Popescu, ACM TOMS 2017), even when the high words cancel.  Exact cancellation
+    # leaves the sum of the two low words, which a double-double holds exactly.
+    g = np.random.default_rng(7)
+    u = F(2) ** -53
+    n = 400
+    ah = g.standard_normal(n)
+    al = ah * 2.0 ** -54 * g.uniform(-1, 1, n)
+    bh = -ah * (1.0 + 2.0 ** -40 * g.standard_normal(n))
+    bh[: n // 2] = -ah[: n // 2]                        # exact cancellation of the high words
+    bl = bh * 2.0 ** -54 * g.uniform(-1, 1, n) * 2.0 ** -int(g.integers(0, 40))
+    rh, rl = dd.dd_add(ah, al, bh, bl)
+    for i in range(n):
+        ex = F(ah[i]) + F(al[i]) + F(bh[i]) + F(bl[i])
+        got = F(rh[i]) + F(rl[i])
+        assert abs(got - ex) <= abs(ex) * (3 * u * u + 13 * u ** 3), i
+        if i < n // 2:
+            assert got == F(al[i]) + F(bl[i]), i

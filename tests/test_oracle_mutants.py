@@ -125,6 +125,23 @@ MUTANTS = [
      "Wp = oz.ozaki_product(X1.T, Res, min(sX, kW), kW, kW,", "W: last anti-diagonal dropped"),
     ("refine", "V = oz.ozaki_product(A, X1, kV, sX, kV + 1,", "V = oz.ozaki_product(A, X1, kV, sX, kV,",
      "V: last anti-diagonal dropped"),
+    ("ozaki", "    return row_exponents(M.T)\n", "    return row_exponents(M)\n", "column exponents: row maxima taken"),
+    ("ozaki", "0.75 * np.ldexp(1.0, np.where(f == EZERO, 0, f + beta)))",
+     "np.ldexp(1.0, np.where(f == EZERO, 0, f + beta)))", "tau: 0.75 dropped"),
+    ("ozaki", "P = (fL[r - 1] @ fR[s - 1]).astype(np.int64)", "P = (fL[s - 1] @ fR[r - 1]).astype(np.int64)",
+     "slice products: plane indices swapped"),
+    ("ozaki", "T = 2 * k if mode == \"full\" else k + 1", "T = 2 * k - 1 if mode == \"full\" else k + 1",
+     "full pair set: last pair dropped"),
+    ("ozaki", "ceil_log2(np.max(np.abs(M), axis=1)) if", "ceil_log2(np.max(np.abs(M), axis=0)) if",
+     "row exponents: column maxima taken"),
+    ("ddarith", "_SPLITTER = 134217729.0", "_SPLITTER = 67108865.0", "Veltkamp split: 2^26 + 1"),
+    ("ddarith", "    se = se + te\n", "    se = se\n", "dd add: low words' rounding error dropped"),
+    ("ddarith", "    se = se + th\n", "    se = se\n", "dd add: low words' sum dropped"),
+    ("ddarith", "            e = e + a * Rl[k:k + 1, :]\n", "            e = e\n", "dd matmul: low words of R dropped"),
+    ("ddarith", "sl = sl + (t + e)", "sl = sl + t", "dd matmul: product error dropped"),
+    ("ddarith", "ph, pl = dd_mul_d(bh, bl, q1)", "ph, pl = dd_mul_d(bh, 0.0 * bl, q1)",
+     "dd division: low word of the divisor dropped"),
+    ("ddarith", "    lo = a - hi\n", "    lo = a + hi\n", "split: low part wrong sign"),
 ]
 
 

@@ -142,6 +142,24 @@ def test_ozaki_gemm_enough_slices_is_correctly_rounded():
             assert F(out["hi"][i, j]) + F(out["lo"][i, j]) - ex[i][j] <= abs(ex[i][j]) * F(2) ** -104
 
 
+def test_full_pair_set_is_exact_for_integer_operands():
+    # Sec. 2.3: with every operand held exactly by its k planes, the product over all k^2
+    # slice pairs is the exact product.  Integers below 2^23 need three 8-bit planes, and the
+    # last pair (3, 3) carries the units digits, so the exact integer product tells whether
+    # every pair was taken.
+    g = np.random.default_rng(23)
+    A = g.integers(-(1 << 23) + 1, 1 << 23, size=(6, 9)).astype(np.float64)
+    B = g.integers(-(1 << 23) + 1, 1 << 23, size=(9, 5)).astype(np.float64)
+    assert np.all(oz.slice_rows(A, 3)[2] == 0) and np.all(oz.slice_cols(B, 3)[2] == 0)
+    C, out = oz.ozaki_gemm(A, B, 3, "full")
+    assert len(out["pairs"]) == 9
+    for i in range(6):
+        for j in range(5):
+            ex = sum(int(A[i, q]) * int(B[q, j]) for q in range(9))
+            assert F(out["hi"][i, j]) + F(out["lo"][i, j]) == ex
+            assert C[i, j] == float(ex)
+
+
 @pytest.mark.parametrize("k", [2, 3, 4, 6])
 def test_triangular_truncation_bound(k):
     A = synth.gemm_operand(7, 11, 2.0, 31)
