@@ -142,6 +142,14 @@ MUTANTS = [
     ("ddarith", "ph, pl = dd_mul_d(bh, bl, q1)", "ph, pl = dd_mul_d(bh, 0.0 * bl, q1)",
      "dd division: low word of the divisor dropped"),
     ("ddarith", "    lo = a - hi\n", "    lo = a + hi\n", "split: low part wrong sign"),
+    ("refine", "return int(min(max(b, 3), 47))", "return int(min(max(b, 3), 53))", "beta: clamp at 53"),
+    ("refine", "    return ex - 1\n\n\ndef ceil_log2f", "    return ex\n\n\ndef ceil_log2f", "floor log2: off by one"),
+    ("refine", "            return k\n    return k_cap\n", "            return k\n    return k_cap - 1\n",
+     "slice rule: one plane below the cap"),
+    ("refine", "eAmax = int(np.max(eA))", "eAmax = int(np.min(eA))", "k_V: smallest row exponent of A"),
+    ("refine", "fmax = int(np.max(f))", "fmax = int(np.min(f))", "k_V: smallest column exponent of X"),
+    ("refine", "kW = slices_for(n, int(np.max(f)), int(np.max(h))", "kW = slices_for(n, int(np.max(f)), int(np.min(h))",
+     "k_W: smallest column exponent of Res"),
 ]
 
 

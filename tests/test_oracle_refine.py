@@ -547,3 +547,39 @@ def test_capped_products_stop_as_stagnated_at_their_floor(k_cap, case):
     assert info["iters"] <= first + 2
     assert info["err_est"] > 50 * 1e-14                     # the floor lies far above delta
     assert min(steps[first:]) > 0.1 * steps[first]         # the run hovers at its floor
+
+
+def test_beta_clamped_so_x1_keeps_its_leading_bits():
+    # A loose target asks for a coarse truncation: on this 2 x 2 problem at delta = 0.01 the
+    # Sec. 4.1 rule gives floor(log2 q) = 49.  beta is clamped to 47, so X^(1) lies on the grid
+    # ulp(tau_j) = 2^(f_j + beta - 53) = 2^(f_j - 6) and keeps its leading 7 bits (one digit
+    # plane); near beta = 53 that grid reaches 2^f_j and X^(1) would keep no bits at all.
+    A = np.array([[2.0, 0.5], [0.5, 1.0]])
+    w, Q = np.linalg.eigh(A)
+    X = Q + 1e-3 * np.array([[0.3, -0.2], [0.1, 0.4]])
+    p = rf.plan(A, X, w, 0.01, rf.Options())
+    assert p["f"].tolist() == [0, 0] and p["beta"] == 47 and p["sX"] == 1
+    g, Lam = rf.min_gap(w)
+    q = math.sqrt(0.01 * g / (Lam * rf.sum_pow4(p["f"]))) / (0.75 * U)
+    assert math.floor(math.log2(q)) == 49
+    Xn, lam, info = rf.step(A, X, w, 0.01, rf.Options())
+    grid = 2.0 ** -6
+    assert np.array_equal(info["X1"], np.round(X / grid) * grid)   # np.round: ties to even
+    assert np.all(info["X1"] != 0.0)
+
+
+def test_v_slices_cover_the_largest_column():
+    # The slice count of V = A X^(1) bounds the dropped part by tau = delta gap for every
+    # column at once, so it is set by the largest column exponent.  With one column scaled
+    # down by 2^-24 the exponents span 24 bits (three planes), and the dropped part measured
+    # against A X^(1) formed in double-double must still stay below tau in the 2-norm.
+    A, X0, D0, _ = synth.refine_workload(48, 1e4, case=0, rel=1e-6)
+    X = X0.copy()
+    X[:, 0] *= 2.0 ** -24
+    delta = 1e-12
+    Xn, lam, info = rf.step(A, X, D0, delta, rf.Options())
+    f = info["plan"]["f"]
+    assert int(np.max(f)) - int(np.min(f)) >= 24
+    Vh, Vl = dd.dd_matmul(A, None, info["X1"], None)
+    err = np.linalg.norm((info["Vh"] - Vh) + (info["Vl"] - Vl), 2)
+    assert err <= delta * info["plan"]["g"]
