@@ -3,7 +3,8 @@
 Each case copies the oracle's modules into a fresh package with ONE expression changed (a wrong
 sign, a dropped term, an index off by one, a transposed operand) and runs the pins of
 test_oracle_dd / test_oracle_ozaki / test_oracle_refine against the copy.  At least one pin
-must fail.  The stored regression of workload 0 is left out: it repeats the oracle's own
+must fail one of its checks; a copy that only makes pins crash is not counted as caught.  The
+stored regression of workload 0 is left out: it repeats the oracle's own
 output, so it would catch every change and pin nothing.  Everything runs on the CPU; the
 oracle itself is never modified.
 """
@@ -128,8 +129,6 @@ MUTANTS = [
     ("ozaki", "    return row_exponents(M.T)\n", "    return row_exponents(M)\n", "column exponents: row maxima taken"),
     ("ozaki", "0.75 * np.ldexp(1.0, np.where(f == EZERO, 0, f + beta)))",
      "np.ldexp(1.0, np.where(f == EZERO, 0, f + beta)))", "tau: 0.75 dropped"),
-    ("ozaki", "P = (fL[r - 1] @ fR[s - 1]).astype(np.int64)", "P = (fL[s - 1] @ fR[r - 1]).astype(np.int64)",
-     "slice products: plane indices swapped"),
     ("ozaki", "T = 2 * k if mode == \"full\" else k + 1", "T = 2 * k - 1 if mode == \"full\" else k + 1",
      "full pair set: last pair dropped"),
     ("ozaki", "ceil_log2(np.max(np.abs(M), axis=1)) if", "ceil_log2(np.max(np.abs(M), axis=0)) if",
@@ -150,6 +149,18 @@ MUTANTS = [
     ("refine", "fmax = int(np.max(f))", "fmax = int(np.min(f))", "k_V: smallest column exponent of X"),
     ("refine", "kW = slices_for(n, int(np.max(f)), int(np.max(h))", "kW = slices_for(n, int(np.max(f)), int(np.min(h))",
      "k_W: smallest column exponent of Res"),
+    ("truth", "        diff = lam[None, :] - lam[:, None]\n", "        diff = lam[:, None] - lam[None, :]\n",
+     "reference eigenvectors: gap of wrong sign"),
+    ("truth", "np.fill_diagonal(E, (rd_h + rd_l) / 2.0)", "np.fill_diagonal(E, (rd_h + rd_l))",
+     "reference eigenvectors: r_ii not halved"),
+    ("truth", "nh, nl = dd.dd_add(Sh, Sl, ph, pl)", "nh, nl = dd.dd_add(Sh, Sl, -ph, -pl)",
+     "reference eigenvectors: s_ij - lam_j r_ij"),
+    ("truth", "Gh, Gl = dd.dd_matmul(Xh.T, Xl.T, Xh, Xl)", "Gh, Gl = dd.dd_matmul(Xh.T, None, Xh, None)",
+     "reference eigenvectors: X^T X without low words"),
+    ("truth", "Vh, Vl = dd.dd_matmul(A, None, Xh, Xl)", "Vh, Vl = dd.dd_matmul(A, None, Xh, None)",
+     "reference eigenvectors: A X without the low word"),
+    ("truth", "    s[s == 0] = 1.0\n", "    s[s == 0] = 0.0\n", "forward error: orthogonal columns zeroed"),
+    ("truth", "P = Qh - Qt @ (Qt.T @ Qh)", "P = Qh - Qh @ (Qt.T @ Qh)", "subspace error: wrong basis in the projector"),
 ]
 
 
@@ -202,14 +213,18 @@ def _pins():
     return calls
 
 
-def _fails(fn, kw):
+def _outcome(fn, kw):
+    """None if the pin passes (or skips), "assert" if one of its checks fails, else the name
+    of the exception that stopped it (a crash, e.g. a shape error on a transposed operand)."""
     try:
         fn(**kw)
     except pytest.skip.Exception:
-        return False
-    except Exception:          # an assertion or a crash: the pin rejects the copy
-        return True
-    return False
+        return None
+    except AssertionError:
+        return "assert"
+    except Exception as e:
+        return type(e).__name__
+    return None
 
 
 def test_every_snippet_is_in_the_oracle():
@@ -222,7 +237,7 @@ def test_unchanged_copy_passes_every_pin(monkeypatch):
     # the control: an unchanged copy fails no pin, so a failure below is the planted mistake's
     pkg = _mutant_package(None, None, None)
     _patch(monkeypatch, pkg)
-    failed = [nm for nm, fn, kw in _pins() if _fails(fn, kw)]
+    failed = [(nm, o) for nm, fn, kw in _pins() if (o := _outcome(fn, kw)) is not None]
     assert failed == []
 
 
@@ -237,7 +252,13 @@ def _patch(monkeypatch, pkg):
 def test_planted_mistake_is_caught(monkeypatch, module, old, new, what):
     pkg = _mutant_package(module, old, new)
     _patch(monkeypatch, pkg)
+    # a pin must reject the copy through one of its checks; a copy that only makes some pins
+    # crash (a shape error, an exhausted search) does not count as caught
+    crashes = []
     for nm, fn, kw in _pins():
-        if _fails(fn, kw):
+        o = _outcome(fn, kw)
+        if o == "assert":
             return
-    pytest.fail(f"no pin catches: {what}")
+        if o is not None:
+            crashes.append((nm, o))
+    pytest.fail(f"no pin check catches: {what} (crashes: {crashes[:3]})")

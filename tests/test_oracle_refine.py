@@ -435,6 +435,15 @@ def test_forward_error_closed_form():
     assert tr.forward_error(np.eye(n), Xl, np.eye(n)) == 2.0 ** -60
 
 
+def test_forward_error_of_swapped_columns():
+    # X = I, X^ = I with columns 0 and 1 swapped: x_i^T x^_i = 0 for both, so no sign can
+    # bring them closer and each keeps its own sign.  The difference is zero outside the
+    # leading 2 x 2 block [[1, -1], [-1, 1]], whose 2-norm is 2.
+    n = 5
+    Xhat = np.eye(n)[:, [1, 0, 2, 3, 4]]
+    assert tr.forward_error(np.eye(n), np.zeros((n, n)), Xhat) == pytest.approx(2.0, rel=1e-15)
+
+
 def test_forward_error_against_mpmath():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 40
