@@ -124,7 +124,7 @@ FRX_API size_t frx_refine_workspace_bytes(int64_t n, const frx_opts* opts);
  *   D     (in/out)  n: eigenvalue estimates; on entry they set the first iteration's
  *                   beta and slice counts (the estimates of iteration k-1 are used in
  *                   iteration k); on exit the estimates lam_i = x_i^T v_i / (1 - r_i)
- *                   of the last iteration (Alg. 1 line 3).
+ *                   of the last iteration (the estimates of Alg. 1).
  *   delta (in)      target forward error, delta > 2^-53.
  *   opts  (in,host) options, or NULL for the defaults.
  *   info  (out,host) may be NULL.
@@ -146,11 +146,11 @@ FRX_API int frx_refine(const double* A, int64_t lda, double* X, int64_t ldx, dou
  * is the cluster threshold of the previous iteration (0 on the first).  Each
  * optional output (NULL to skip) is an n x n column-major FP64 matrix with ld = n:
  *   X1  the truncated slice X^(1) (eq. tau, eq. x)
- *   Vh, Vl  V = A X^(1) as a double-double (Alg. 1 line 1, eq. mat_mul)
- *   Res     V - X^(1) diag(lam), rounded to FP64 (inside line 4)
- *   W       X^(1)^T Res (line 4)
- *   E       the correction E~ (line 5)
- * `r_out` (n, device, optional) receives r_i = 1 - x_i^T x_i (line 2).
+ *   Vh, Vl  V = A X^(1) as a double-double (Alg. 1, eq. mat_mul)
+ *   Res     V - X^(1) diag(lam), rounded to FP64 (inside W, Alg. 1)
+ *   W       X^(1)^T Res (Alg. 1)
+ *   E       the correction E~ (Alg. 1)
+ * `r_out` (n, device, optional) receives r_i = 1 - x_i^T x_i (Alg. 1).
  * info->err_est/step refer to this single step.
  */
 FRX_API int frx_refine_step(const double* A, int64_t lda, double* X, int64_t ldx, double* D, int64_t n,

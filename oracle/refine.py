@@ -8,12 +8,12 @@ One iteration (Algorithm 1 with the Sec. 3 modification, eq. mat_mul):
          is an option), alpha = 53 - beta + ceil(log2 sqrt n) (Sec. 4.1), using the
          previous eigenvalue estimates (the circularity is broken by lagging them);
   X1     = fl((tau_j + x_ij) - tau_j), tau_j = 0.75 2^ceil(log2 w_j) 2^beta (eq. tau, x);
-  V      = accurate A X1 from exact 8-bit digit-plane products (line 1, eq. mat_mul);
-  r_i    = 1 - x1_i^T x1_i                                            (line 2);
-  lam_i  = x1_i^T v_i / (1 - r_i)                                     (line 3);
-  W      = X1^T (V - X1 diag(lam))                                    (line 4);
-  E~_ij  = w_ij / (lam_j - lam_i) (i != j), r_i / 2 (i = j)           (line 5);
-  X      <- RN(X1 + X1 E~) by pair arithmetic                         (line 6, Sec. 2.2).
+  V      = accurate A X1 from exact 8-bit digit-plane products (eq. mat_mul);
+  r_i    = 1 - x1_i^T x1_i                                            (Alg. 1);
+  lam_i  = x1_i^T v_i / (1 - r_i)                                     (Alg. 1);
+  W      = X1^T (V - X1 diag(lam))                                    (Alg. 1);
+  E~_ij  = w_ij / (lam_j - lam_i) (i != j), r_i / 2 (i = j)           (Alg. 1);
+  X      <- RN(X1 + X1 E~) by pair arithmetic                         (Alg. 1, Sec. 2.2).
 
 Readings where the paper is silent (each also listed in the design notes):
 * digit planes: 8-bit digits on a fixed grid (see ``ozaki``); X1 is exactly the
@@ -187,7 +187,7 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
     p = plan(A, X, lam_prev, delta, opts, omega_prev)
     beta, sX, kV, f, eA = p["beta"], p["sX"], p["kV"], p["f"], p["eA"]
 
-    # X^(1) (eq. tau, eq. x) and V = A X^(1) (line 1, eq. mat_mul)
+    # X^(1) (eq. tau, eq. x) and V = A X^(1) (eq. mat_mul)
     if opts.x_planes > 0:
         # the sum of the x_planes digit planes of X (exact: X minus the slicing residual)
         _, _, resid = oz.slice_cols(X, opts.x_planes, f)
@@ -197,7 +197,7 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
     V = oz.ozaki_product(A, X1, kV, sX, kV + 1, eL=eA, eR=f, exact=exact)
     Vh, Vl = V["hi"], V["lo"]
 
-    # line 2: r_i = 1 - x_i^T x_i ; line 3: lam_i = x_i^T v_i / (1 - r_i)
+    # r_i = 1 - x_i^T x_i ; lam_i = x_i^T v_i / (1 - r_i)
     ph, pl = dd.two_prod(X1, X1)
     nh, nl = dd.dd_sum(ph, pl, axis=0)            # x_i^T x_i (double-double)
     r = dd.dd_add_d(-nh, -nl, 1.0)[0]
@@ -206,7 +206,7 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
     dh, dl = dd.dd_sum(qh, ql, axis=0)            # x_i^T v_i
     lam = dd.dd_div_dd(dh, dl, nh, nl)[0]
 
-    # line 4: Res = V - X1 diag(lam) (double-double, then FP64); W = X1^T Res
+    # Res = V - X1 diag(lam) (double-double, then FP64); W = X1^T Res
     mh, ml = dd.two_prod(X1, lam[None, :])
     Res = dd.dd_add(Vh, Vl, -mh, -ml)[0]
     h = oz.col_exponents(Res)
@@ -219,7 +219,7 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
         Wp = None
         W = np.zeros((n, n))
 
-    # line 5: E~ with the optional cluster rule
+    # E~ with the optional cluster rule
     if opts.cluster == "auto":
         offd = W - np.diag(np.diag(W))
         omega = 2.0 * (math.sqrt(float(np.sum(offd * offd))) + p["Lam"] * float(np.linalg.norm(r)))
@@ -238,7 +238,7 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
             E[i, j] = -sh / 2.0                       # r_ij / 2
     np.fill_diagonal(E, r / 2.0)
 
-    # line 6: X <- accsum(X1, X1 E~): U = X1 E~ (rows of X1, columns of E~)
+    # the update X <- accsum(X1, X1 E~): U = X1 E~ (rows of X1, columns of E~)
     rho = oz.row_exponents(X1)
     eta = oz.col_exponents(E)
     kU = min(slices_for(n, int(np.max(rho)), int(np.max(eta)), delta, opts.k_cap), int32_planes(n))

@@ -263,7 +263,7 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
                             gv.ogs, s));
   else
     FRX_TRY(launch_plane_gemm(gv, s));
-  // S7/S8: r, lambda, Res (lines 2-4)
+  // S7/S8: r, lambda, Res (Alg. 1)
   ResidualArgs ra;
   ra.n = n;
   ra.V = group_args(gv);
@@ -290,7 +290,7 @@ int enqueue_iteration(const double* A, int64_t lda, double* X, int64_t ldx, int6
   FRX_TRY(launch_slice_cols(ws.Res, n, n, n, ws.h, 0, ws.Rp, ws.ps, ws.pitch, s, dr));
   PlaneGemm gw = dyn_gemm(ws.Xp, 8, ws.Rp, kcap, ws, n, &P->W);
   FRX_TRY(launch_plane_gemm(gw, s));
-  // S10: E~ (line 5) with the cluster threshold
+  // S10: E~ (Alg. 1) with the cluster threshold
   CorrectionArgs ca;
   ca.n = n;
   ca.W = group_args(gw);

@@ -209,7 +209,7 @@ __device__ __forceinline__ void plan_init_impl(DevPlan* p, const int32_t* eA, co
   if (anybad) raise(p, FRX_E_NONFINITE);
 }
 
-// beta, alpha, s_X, k_V and the V product (Alg. 1 line 1 with Sec. 3 and Sec. 4.1)
+// beta, alpha, s_X, k_V and the V product (Alg. 1 with Sec. 3 and Sec. 4.1)
 __device__ __forceinline__ void plan_v_impl(DevPlan* p, const int32_t* f, PlanOpts o) {
   __shared__ int redi[32];
   __shared__ double redd[32];
@@ -324,7 +324,7 @@ __device__ __forceinline__ void plan_mark_sliced_impl(DevPlan* p) {
   if (threadIdx.x == 0 && !p->done && p->kV > p->sliced_kA) p->sliced_kA = p->kV;
 }
 
-// k_W and the W product (Alg. 1 line 4)
+// k_W and the W product (Alg. 1)
 __device__ __forceinline__ void plan_w_impl(DevPlan* p, const int32_t* h, PlanOpts o) {
   __shared__ int redi[32];
   if (p->done) return;
@@ -383,7 +383,7 @@ __device__ __forceinline__ void plan_omega_impl(DevPlan* p, const double* r, con
   }
 }
 
-// k_U and the update product (Alg. 1 line 6)
+// k_U and the update product (Alg. 1)
 __device__ __forceinline__ void plan_u_impl(DevPlan* p, const int32_t* rho, const int32_t* eta, PlanOpts o) {
   __shared__ int redi[32];
   if (p->done) return;

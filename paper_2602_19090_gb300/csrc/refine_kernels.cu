@@ -1,8 +1,8 @@
 // Element-wise and per-column kernels of one refinement iteration (Alg. 1, Sec. 3):
 // recombination of the exact slice-product groups into double-double, r and lambda
-// (lines 2-3), the residual V - X^(1) diag(lambda) (line 4), the correction E~
-// (line 5, with the Ogita-Aishima cluster rule) and the update by pair arithmetic
-// (line 6, Sec. 2.2).
+// (Alg. 1), the residual V - X^(1) diag(lambda) (inside W), the correction E~
+// (with the Ogita-Aishima cluster rule) and the update by pair arithmetic
+// (Sec. 2.2).
 #include "frx_internal.cuh"
 #include "grouped.cuh"
 #include "intround.cuh"
@@ -375,7 +375,7 @@ __device__ u64 block_max_u64(u64 v, u64* red) {
   return r;
 }
 
-// ---- lines 2-4 (inner part): one block per column j --------------------------------
+// ---- r, lambda, Res (inner part): one block per column j --------------------------------
 // smem: n double-doubles (V column).  x^T x is exact in integers (X1 lies on the grid
 // 2^(f_j + beta - 53)); x^T v is accumulated with TwoProduct/TwoSum (Dot2 form).
 __device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
@@ -505,7 +505,7 @@ __device__ __noinline__ void residual_general(ResidualArgs a, int64_t jcol) {
   if (threadIdx.x == 0) a.h[j] = mx == 0 ? EZERO : ceil_log2_absbits(mx);
 }
 
-// Integer fast path of lines 2-4 for int32 planes (at most 16) that combine exactly in 128
+// Integer fast path of r, lambda, Res for int32 planes (at most 16) that combine exactly in 128
 // bits.  One pass over the rows forms each V entry N_i 2^(c_i) (kept in shared memory), x^T x
 // exactly, and x^T v on a fixed grid: each warp keeps an anchor T_w, the largest bound 2^T_w on
 // its terms so far, and accumulates every term truncated once on the grid 2^(T_w + log2 n - 126)
@@ -799,7 +799,7 @@ __device__ __forceinline__ void w_offdiag_body(CorrectionArgs a, unsigned bx, un
   if (threadIdx.x == 0) a.norms[a.n + j] = s;
 }
 
-// ---- line 5: E~ column j, its exponent, ||E~||_F^2 -----------------------------------
+// ---- the correction: E~ column j, its exponent, ||E~||_F^2 -----------------------------------
 // e_ij = w_ij / (lambda_j - lambda_i) (one IEEE division), e_jj = r_j / 2, and the
 // Ogita-Aishima rule e_ij = r_ij / 2 inside clusters (|lambda_j - lambda_i| <= omega, with
 // r_ij = -x_i^T x_j in double-double).  w_ij is the exact W entry rounded once on the
@@ -938,7 +938,7 @@ __host__ __device__ inline size_t correction_pipe_smem(int threads) {
   return (size_t)PIPE * threads * (sizeof(double) + (1 + MP_CORRECTION) * sizeof(int32_t));
 }
 
-// ---- line 6: X <- RN(X1 + X1 E~) (pair arithmetic), ||X_new - X_old||_F^2 ----------------
+// ---- the update: X <- RN(X1 + X1 E~) (pair arithmetic), ||X_new - X_old||_F^2 ----------------
 // RN(x1 + N 2^c) for int64 N with |N 2^c| well below |x1|: x1 = P 2^q (53-bit P) and the
 // sum is rounded on x1's grid with round-half-even on the combined integer.  Returns false
 // when the result leaves x1's binade (then the caller takes the general path).
@@ -1014,7 +1014,7 @@ __device__ __forceinline__ void accumulate_dx2(double xn, double xo, float& d2f,
   d2d = __fma_rn(dx, dx, d2d);
 }
 
-// X(:, j) <- RN(X1(:, j) + U(:, j)) (Alg. 1 line 6, one rounding); ||X_new - X_old||_F^2
+// X(:, j) <- RN(X1(:, j) + U(:, j)) (Alg. 1's update, one rounding); ||X_new - X_old||_F^2
 // partial per column.  One block per column; exact sums and their rounding run on the
 // integer pipes.
 __device__ __forceinline__ void update_body(UpdateArgs a, unsigned bx, unsigned) {

@@ -21,8 +21,8 @@ struct ResidualArgs {
   const int32_t* f;
   const double* X1;
   int64_t ld1;
-  double* lam;           // out: lambda_j (Alg. 1 line 3)
-  double* r;             // out: r_j (line 2)
+  double* lam;           // out: lambda_j (Alg. 1)
+  double* r;             // out: r_j (Alg. 1)
   double* Res;           // out: V - X1 diag(lambda) rounded to FP64
   int64_t ldr;
   int32_t* h;            // out: column exponents of Res

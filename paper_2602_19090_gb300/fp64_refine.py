@@ -132,7 +132,7 @@ def step(A, X, lam_prev, delta, xi=1.0):
         P = Ar @ X1
         Vh, e = _two_sum(Vh, P)
         Vl = Vl + e
-    # lines 2-4
+    # r, lambda, Res and W (Alg. 1)
     ph, pl = _two_prod(X1, X1)
     nh, nl = _dd_colsum(ph, pl)
     qh, ql = _two_prod(X1, Vh)

@@ -1,4 +1,4 @@
-// Host-side check of the roundings the update kernel uses for X <- RN(X1 + U) (Alg. 1 line 6):
+// Host-side check of the roundings the update kernel uses for X <- RN(X1 + U) (Alg. 1's update):
 // add_on_grid_rn (the usual case, on x1's grid) and add_exact_rn (exact 128-bit sum), compiled
 // as host code from the library's own header.  Random, tie and binade-edge inputs; where both
 // succeed their bits must agree, and every case the on-grid form accepts is written out so that

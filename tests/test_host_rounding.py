@@ -1,4 +1,4 @@
-"""The update's roundings of X1 + U (Alg. 1 line 6, one rounding), checked on the host.
+"""The update's roundings of X1 + U (Alg. 1's update, one rounding), checked on the host.
 
 `tests/host_rounding_check.cu` compiles the library's rounding helpers as host code (nvcc, no GPU
 needed) and runs them on random, tie and binade-edge inputs.  Where the on-grid form and the

@@ -486,7 +486,7 @@ def test_subspace_error_closed_form():
 
 @pytest.mark.parametrize("seed", [1, 3])
 def test_estimates_are_the_correctly_rounded_rayleigh_quotients(seed):
-    # Alg. 1 line 3: lam_i = x_i^T v_i / (1 - r_i) with v_i = A x_i and 1 - r_i = x_i^T x_i,
+    # Alg. 1: lam_i = x_i^T v_i / (1 - r_i) with v_i = A x_i and 1 - r_i = x_i^T x_i,
     # the Rayleigh quotient of x_i = X^(1)[:, i].  With A's entries small integers, A lies
     # wholly in its first digit plane, so V holds A X^(1) to double-double accuracy, and the
     # estimate must be the quotient computed in exact rationals, rounded once.  beta = 2 keeps
