@@ -259,7 +259,8 @@ def step(A, X, lam_prev, delta, opts: Options | None = None, omega_prev=0.0, exa
     info = dict(plan=p, beta=beta, alpha=p["alpha"], sX=sX, kV=kV, kW=kW, kU=kU,
                 products=len(V["pairs"]) + (len(Wp["pairs"]) if Wp else 0) + (len(Up["pairs"]) if Up else 0),
                 normE=normE, step=step_norm, est=est, omega=omega, r=r, W=W, E=E, X1=X1, Vh=Vh, Vl=Vl,
-                Res=Res, h=h, S_V=V["S"], clustered=int(np.sum(clus)) // 2)
+                Res=Res, h=h, S_V=V["S"], clustered=int(np.sum(clus)) // 2,
+                Uh=Up["hi"] if Up else np.zeros((n, n)), Ul=Up["lo"] if Up else np.zeros((n, n)))
     return Xn, lam, info
 
 

@@ -592,3 +592,36 @@ def test_v_slices_cover_the_largest_column():
     Vh, Vl = dd.dd_matmul(A, None, info["X1"], None)
     err = np.linalg.norm((info["Vh"] - Vh) + (info["Vl"] - Vl), 2)
     assert err <= delta * info["plan"]["g"]
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_each_product_within_its_tau(case):
+    # The slice rule sets each product's planes so that what it drops stays below its own tau
+    # in the 2-norm: delta * gap for V = A X^(1) and W = X^(1)^T Res, delta for the update
+    # product U = X^(1) E~.  Each is measured here against the same product formed in
+    # double-double from the step's own operands.
+    A, X0, D0, _ = synth.refine_workload(64, 1e8, case=case, rel=1e-8)
+    delta = 1e-14
+    Xn, lam, info = rf.step(A, X0, D0, delta, rf.Options())
+    X1, g = info["X1"], info["plan"]["g"]
+    Vh, Vl = dd.dd_matmul(A, None, X1, None)
+    assert np.linalg.norm((info["Vh"] - Vh) + (info["Vl"] - Vl), 2) <= delta * g
+    Wh, Wl = dd.dd_matmul(X1.T, None, info["Res"], None)
+    assert np.linalg.norm((info["W"] - Wh) - Wl, 2) <= delta * g
+    Uh, Ul = dd.dd_matmul(X1, None, info["E"], None)
+    assert np.linalg.norm((info["Uh"] - Uh) + (info["Ul"] - Ul), 2) <= delta
+
+
+def test_residual_is_the_correctly_rounded_difference():
+    # Res = V - X^(1) diag(lam) formed in double-double and rounded once (Alg. 1's residual):
+    # on sampled entries it equals the exact rational value of Vh + Vl - x1_ij lam_j rounded to
+    # nearest.  The entries cancel by about eight digits here (V ~ X^(1) diag(lam)), so a low
+    # word dropped on either side shows.
+    from fractions import Fraction as Fr
+    A, X0, D0 = synth.workload0()
+    Xn, lam, info = rf.step(A, X0, D0, 1e-14, rf.Options())
+    X1, Vh, Vl, Res = info["X1"], info["Vh"], info["Vl"], info["Res"]
+    g = np.random.default_rng(11)
+    for i, j in zip(g.integers(0, 64, 400), g.integers(0, 64, 400)):
+        ex = Fr(Vh[i, j]) + Fr(Vl[i, j]) - Fr(X1[i, j]) * Fr(lam[j])
+        assert Res[i, j] == float(ex), (i, j)
