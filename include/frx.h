@@ -128,8 +128,9 @@ FRX_API size_t frx_refine_workspace_bytes(int64_t n, const frx_opts* opts);
  *   delta (in)      target forward error, delta > 2^-53.
  *   opts  (in,host) options, or NULL for the defaults.
  *   info  (out,host) may be NULL.
- * Errors: FRX_E_ARG, FRX_E_DELTA, FRX_E_NONFINITE, FRX_E_WORKSPACE, FRX_E_UNSUPPORTED
- * (n > FRX_MAX_N), FRX_E_RANGE, FRX_E_TIMEOUT, FRX_E_CUDA.  The plan of each iteration
+ * Errors: FRX_E_ARG (also for n < 1: an empty problem is refused, not refined), FRX_E_DELTA,
+ * FRX_E_NONFINITE, FRX_E_WORKSPACE, FRX_E_UNSUPPORTED (n > FRX_MAX_N), FRX_E_RANGE,
+ * FRX_E_TIMEOUT, FRX_E_CUDA.  The plan of each iteration
  * (beta, alpha, plane counts, the stopping test) is computed on the device; the host
  * synchronises `stream` once per iteration to read the finish flag, and once more at the end
  * to read the report.  The first call for a new n may time the tile configurations of the

@@ -91,6 +91,21 @@ def test_argument_errors_before_any_device_work(lib):
     assert st == -1
 
 
+def test_empty_sizes_are_refused_before_any_device_work(lib):
+    # n = 0 (or m, n, k = 0 for a product) is an argument error, with no device work and no
+    # scratch requirement
+    p = ctypes.c_void_p(256)
+    assert lib.frx_refine(p, 4, p, 4, p, 0, 1e-10, None, p, 1 << 20, None, None) == -1
+    assert lib.frx_refine(p, 4, p, 4, p, -1, 1e-10, None, p, 1 << 20, None, None) == -1
+    N = None
+    assert lib.frx_refine_step(p, 4, p, 4, p, 0, 1e-10, None, 0.0, p, 1 << 20, None,
+                               N, N, N, N, N, N, N, None) == -1
+    for m, n, k in ((0, 8, 8), (8, 0, 8), (8, 8, 0)):
+        assert lib.frx_ozaki_gemm(p, 8, p, 8, p, 8, None, m, n, k, 4, 0, p, 1 << 30, None) == -1
+    assert lib.frx_refine_workspace_bytes(0, None) == 0
+    assert lib.frx_ozaki_gemm_workspace_bytes(0, 8, 8, 4) == 0
+
+
 def test_group_size_keeps_sums_exact(lib):
     # groups of gs anti-diagonals: max|S_t| * 2^(8 (gs - 1)) * 256/255 < 2^62, where
     # max|S_t| = pairs * K * 128^2 (8-bit digits)
